@@ -1,0 +1,250 @@
+"""Seeded synthetic inputs for the coupled two-fluid system.
+
+This module only builds initial states and problem descriptions. It holds
+none of the scheme's arithmetic. Tests and benchmarks hand its output to both
+the CUDA library and the CPU oracle, so both sides see the same input.
+
+Geometry. x lies in (-5, 5) and is periodic, with dx = 10/nx. Rows are stacked
+bottom to top as slow (S) | buffer (B) | fast (F). S and B are fluid 1 (the
+ocean, below the interface at z = 0). F is fluid 2 (the atmosphere, above it).
+Cell centres are z = -(n1 - k - 1/2) dz1 for fluid-1 row k, where
+n1 = nS + nB, and z = (k - n1 + 1/2) dz2 for fluid-2 rows.
+
+Rest state. This is the neutrally stratified state of the paper's thermal
+convection setup (Sec. 5.2) with delta theta = 0: Psi = 1 + g z / c_p with
+c_p = 1/(gamma-1) and g = -0.008140864714, T = Psi,
+p = Psi^(gamma/(gamma-1)) / gamma and rho = Psi^(1/(gamma-1)).
+
+Perturbations. These are the synthetic stand-ins for the paper's workloads,
+whose initial conditions are not given in the paper.
+* gaussian_bumps: K bumps with seeded centres and width sigma (in cells).
+  They perturb rho by amp*rho0*env, and (u, w) by amp*env along a seeded
+  direction. Pressure stays at rest.
+* fourier_modes: 10 modes with seeded integer wave numbers kx, kz in [1, 8]
+  and seeded phases. Each mode has amplitude amp/10. Independent draws
+  perturb rho/rho0, u and w. Pressure stays at rest.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GAMMA = 1.4
+PR = 0.72
+MU1 = 1.0 / 20000.0
+MU2 = 1.0 / 5000.0
+G_SIGNED = -0.008140864714  # the g of Sec. 5.2 (points down)
+SEED0 = 0xC0FFEE
+
+
+@dataclass
+class Grid:
+    nx: int
+    nS: int
+    nB: int
+    nF: int
+    dx: float = 0.0
+    dz1: float = 0.0
+    dz2: float = 0.0
+
+    def __post_init__(self):
+        if self.dx <= 0.0:
+            self.dx = 10.0 / self.nx
+        if self.dz1 <= 0.0:
+            self.dz1 = self.dx
+        if self.dz2 <= 0.0:
+            self.dz2 = self.dx
+
+    @property
+    def nz(self) -> int:
+        return self.nS + self.nB + self.nF
+
+    @property
+    def n1(self) -> int:
+        return self.nS + self.nB
+
+    def x_centres(self) -> np.ndarray:
+        return -5.0 + (np.arange(self.nx) + 0.5) * self.dx
+
+    def z_centres(self) -> np.ndarray:
+        k = np.arange(self.nz)
+        z1 = -(self.n1 - k - 0.5) * self.dz1
+        z2 = (k - self.n1 + 0.5) * self.dz2
+        return np.where(k < self.n1, z1, z2)
+
+
+def conserved(rho, u, w, p, gamma=GAMMA) -> np.ndarray:
+    """Stack (rho, rho u, rho w, rho E) from primitive fields of shape [nz][nx]."""
+    q = np.empty((4,) + rho.shape)
+    q[0] = rho
+    q[1] = rho * u
+    q[2] = rho * w
+    q[3] = p / (gamma - 1.0) + 0.5 * rho * (u * u + w * w)
+    return q
+
+
+def rest_primitives(grid: Grid, gamma=GAMMA, g=G_SIGNED):
+    z = grid.z_centres()[:, None] * np.ones((1, grid.nx))
+    cp = 1.0 / (gamma - 1.0)
+    psi = 1.0 + g * z / cp
+    rho = psi ** (1.0 / (gamma - 1.0))
+    p = psi ** (gamma / (gamma - 1.0)) / gamma
+    return rho, p
+
+
+def rest_state(grid: Grid, gamma=GAMMA, g=G_SIGNED) -> np.ndarray:
+    rho, p = rest_primitives(grid, gamma, g)
+    zero = np.zeros_like(rho)
+    return conserved(rho, zero, zero, p, gamma)
+
+
+def gaussian_bumps(grid: Grid, seed: int, k_bumps: int = 4, sigma_cells: float = 4.0,
+                   amp: float = 1e-2, gamma=GAMMA, g=G_SIGNED) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    rho0, p0 = rest_primitives(grid, gamma, g)
+    x = grid.x_centres()[None, :]
+    z = grid.z_centres()[:, None]
+    zlo = -grid.n1 * grid.dz1
+    zhi = (grid.nz - grid.n1) * grid.dz2
+    sig = sigma_cells * grid.dx
+    drho = np.zeros_like(rho0)
+    u = np.zeros_like(rho0)
+    w = np.zeros_like(rho0)
+    for _ in range(k_bumps):
+        xc = rng.uniform(-5.0, 5.0)
+        zc = rng.uniform(zlo, zhi)
+        phi = rng.uniform(0.0, 2.0 * np.pi)
+        ddx = (x - xc + 5.0) % 10.0 - 5.0  # periodic distance in x
+        env = np.exp(-(ddx ** 2 + (z - zc) ** 2) / (2.0 * sig * sig))
+        drho += amp * env
+        u += amp * env * np.cos(phi)
+        w += amp * env * np.sin(phi)
+    return conserved(rho0 * (1.0 + drho), u, w, p0, gamma)
+
+
+def _modes(rng, xi, zeta, n_modes, amp):
+    f = np.zeros((zeta.shape[0], xi.shape[1]))
+    for _ in range(n_modes):
+        kx = int(rng.integers(1, 9))
+        kz = int(rng.integers(1, 9))
+        ph = rng.uniform(0.0, 2.0 * np.pi)
+        ps = rng.uniform(0.0, 2.0 * np.pi)
+        f += (amp / n_modes) * np.cos(2.0 * np.pi * kx * xi + ph) * np.cos(np.pi * kz * zeta + ps)
+    return f
+
+
+def fourier_modes(grid: Grid, seed: int, n_modes: int = 10, amp: float = 1e-2,
+                  gamma=GAMMA, g=G_SIGNED) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    rho0, p0 = rest_primitives(grid, gamma, g)
+    xi = ((grid.x_centres() + 5.0) / 10.0)[None, :]
+    z = grid.z_centres()
+    zlo = -grid.n1 * grid.dz1
+    zhi = (grid.nz - grid.n1) * grid.dz2
+    zeta = ((z - zlo) / (zhi - zlo))[:, None]
+    drho = _modes(rng, xi, zeta, n_modes, amp)
+    u = _modes(rng, xi, zeta, n_modes, amp)
+    w = _modes(rng, xi, zeta, n_modes, amp)
+    return conserved(rho0 * (1.0 + drho), u, w, p0, gamma)
+
+
+def thermal_bubble(grid: Grid, gamma=GAMMA, g=G_SIGNED, theta0=300.0,
+                   centre=(0.0, -2.5), radius=2.5, amp=0.25) -> np.ndarray:
+    """Warm bubble in fluid 1 of Sec. 5.2: delta theta = amp(1 + cos(pi r)) for
+    r <= radius around centre, 0 elsewhere and in fluid 2."""
+    x = grid.x_centres()[None, :] * np.ones((grid.nz, 1))
+    z = grid.z_centres()[:, None] * np.ones((1, grid.nx))
+    r = np.sqrt((x - centre[0]) ** 2 + (z - centre[1]) ** 2)
+    k = np.arange(grid.nz)[:, None] * np.ones((1, grid.nx))
+    dth = np.where((r <= radius) & (k < grid.n1), amp * (1.0 + np.cos(np.pi * r)), 0.0)
+    cp = 1.0 / (gamma - 1.0)
+    fac = 1.0 + dth / theta0
+    psi = 1.0 + g * z / (cp * fac)
+    p = psi ** (gamma / (gamma - 1.0)) / gamma
+    rho = theta0 / (theta0 + dth) * psi ** (1.0 / (gamma - 1.0))
+    zero = np.zeros_like(rho)
+    return conserved(rho, zero, zero, p, gamma)
+
+
+@dataclass
+class Workload:
+    """One solve: grid, rate ratio, slow steps, precision and initial state recipe."""
+    name: str
+    grid: Grid
+    m: int
+    steps: int
+    precision: str  # "fp64" or "fp32flux"
+    perturbation: str  # "bumps" or "fourier"
+    seed: int
+    extra: dict = field(default_factory=dict)
+
+    def initial_state(self) -> np.ndarray:
+        if self.perturbation == "bumps":
+            return gaussian_bumps(self.grid, self.seed)
+        if self.perturbation == "fourier":
+            return fourier_modes(self.grid, self.seed)
+        if self.perturbation == "rest":
+            return rest_state(self.grid)
+        raise ValueError(self.perturbation)
+
+    def cell_stages_per_step(self) -> int:
+        """Cell RHS evaluations per slow step: nx (s nS + m s (nB + nF)), s = 2."""
+        g = self.grid
+        return g.nx * (2 * g.nS + 2 * self.m * (g.nB + g.nF))
+
+
+def plain_64():
+    """64x64 grid, S rows 0-29, B 30-33, F 34-63, m = 4, 100 slow steps, FP64."""
+    return Workload("plain_64x64_m4_fp64", Grid(64, 30, 4, 30), 4, 100, "fp64", "bumps", SEED0 + 0)
+
+
+def large_2048():
+    """2048x1024 grid, S 480 / B 64 / F 480 rows, m = 8, 200 slow steps, FP64."""
+    return Workload("large_2048x1024_m8_fp64", Grid(2048, 480, 64, 480), 8, 200, "fp64", "fourier",
+                    SEED0 + 1)
+
+
+def mixed_4096():
+    """4096x2048 grid, S 960 / B 128 / F 960 rows, m = 8, 500 slow steps, FP32 flux."""
+    return Workload("mixed_4096x2048_m8_fp32flux", Grid(4096, 960, 128, 960), 8, 500, "fp32flux",
+                    "fourier", SEED0 + 2)
+
+
+def batched_256(count: int = 256, seed: int = SEED0 + 3, steps: int = 100):
+    """Independent instances: sides log-uniform in [64, 512], m in {2,4,8},
+    buffer 4-16 rows, S = (nz-B)//2, F = nz-B-S; Gaussian-bump initial states."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(count):
+        nx = int(round(np.exp(rng.uniform(np.log(64), np.log(512)))))
+        nz = int(round(np.exp(rng.uniform(np.log(64), np.log(512)))))
+        m = int(rng.choice([2, 4, 8]))
+        nB = int(rng.integers(4, 17))
+        nS = (nz - nB) // 2
+        nF = nz - nB - nS
+        out.append(Workload(f"batch_{j}", Grid(nx, nS, nB, nF), m, steps, "fp64", "bumps",
+                            seed * 1000 + j))
+    return out
+
+
+def served_stream(count: int, seed: int = SEED0 + 4, rate_hz: float = 200.0,
+                  side_lo: int = 32, side_hi: int = 1024, steps_lo: int = 10, steps_hi: int = 1000):
+    """Poisson arrivals (mean rate_hz) of solves with sides log-uniform in
+    [side_lo, side_hi], m in {2,4,8}, buffer 4-16 rows, slow steps log-uniform
+    in [steps_lo, steps_hi], FP32 flux. Returns (arrival times, workloads)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, size=count))
+    out = []
+    for j in range(count):
+        nx = int(round(np.exp(rng.uniform(np.log(side_lo), np.log(side_hi)))))
+        nz = int(round(np.exp(rng.uniform(np.log(max(side_lo, 24)), np.log(side_hi)))))
+        nx = max(nx, 8)
+        m = int(rng.choice([2, 4, 8]))
+        nB = int(rng.integers(4, 17))
+        nS = max((nz - nB) // 2, 2)
+        nF = max(nz - nB - nS, 2)
+        steps = int(round(np.exp(rng.uniform(np.log(steps_lo), np.log(steps_hi)))))
+        out.append(Workload(f"req_{j}", Grid(nx, nS, nB, nF), m, steps, "fp32flux", "bumps",
+                            seed * 1000 + j))
+    return t, out
