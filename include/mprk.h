@@ -1,0 +1,162 @@
+/*
+ * mprk.h — C ABI of the GB300 (sm_103a) library for one slow step of the
+ * multirate partitioned Runge–Kutta method MPRK2 applied to two coupled
+ * compressible Navier–Stokes fluids (Kang, Dener, Hamilton, Zhang,
+ * Constantinescu, Jacob, arXiv 2202.11890).
+ *
+ * The problem (Sec. 3, Eq. semi-discretized-coupled-model): a structured x–z
+ * grid, periodic in x, split in z, bottom to top, into a slow band S, a slow
+ * buffer band B and a fast band F. S and B hold fluid 1 (the ocean), F holds
+ * fluid 2 (the atmosphere), and the rigid-lid interface Gamma separates them
+ * (App. B). One slow step of size dt advances S and B with the base RK2 and F
+ * with m RK2 substeps of dt/m, coupled as in Eq. MRK2, Table 1 (generalised
+ * to any m) and Algorithm 1. The right-hand side is the cell-centred
+ * finite-volume scheme of Sec. 2.1 and App. B (Lax–Friedrichs inviscid flux,
+ * linear reconstruction, common-gradient viscous flux, bulk interface fluxes).
+ *
+ * State layout on every host or device buffer that crosses this ABI:
+ * structure of arrays [4][nz][nx] of double, contiguous, nz = nz_S + nz_B +
+ * nz_F, components (rho, rho*u, rho*w, rho*E), rows bottom to top.
+ *
+ * Conventions. Every call returns 0 (MPRK_OK) or a negative MPRK_E* code, and
+ * on error mprk_last_error() returns a message for the calling thread.
+ * Nothing runs on the CPU: without a usable CUDA device every compute call
+ * fails with MPRK_ECUDA. Pointers passed in stay owned by the caller; the
+ * library copies what it needs. All instance work runs asynchronously on the
+ * instance's CUDA stream unless a call says it synchronises.
+ */
+#ifndef MPRK_H
+#define MPRK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define MPRK_OK 0
+#define MPRK_EINVAL (-1)     /* invalid argument or configuration          */
+#define MPRK_ENOMEM (-2)     /* device or host allocation failed           */
+#define MPRK_EBUDGET (-3)    /* the request can never fit the HBM budget   */
+#define MPRK_ECUDA (-4)      /* a CUDA call failed (message has details)   */
+#define MPRK_ENONFINITE (-5) /* the state holds NaN or Inf                 */
+#define MPRK_ECFL (-6)       /* a Courant number exceeded the limit        */
+#define MPRK_ETIMEOUT (-7)   /* a bounded device wait gave up              */
+#define MPRK_EBUSY (-8)      /* resource busy (e.g. server queue full)     */
+#define MPRK_ENOTFOUND (-9)  /* unknown ticket                             */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define MPRK_FP64 0     /* every operation in double precision                 */
+#define MPRK_FP32FLUX 1 /* fluxes and RHS in float; stage values, the buffer
+                           accumulation and all stage combinations in double  */
+
+#define MPRK_SCHEME_MPRK2 0  /* Eq. MRK2 with the Table 1 tableaus (s = 2)     */
+#define MPRK_SCHEME_SR_RK2 1 /* single rate: m RK2 steps of dt/m everywhere    */
+
+#define MPRK_WALL_NOSLIP 0 /* outer z walls: no-slip, adiabatic               */
+#define MPRK_WALL_SLIP 1   /* outer z walls: free slip, adiabatic             */
+
+#define MPRK_HOST 0   /* pointer is host memory   */
+#define MPRK_DEVICE 1 /* pointer is device memory */
+
+/* ---- configuration ----------------------------------------------------- */
+typedef struct {
+  int nx;         /* columns (periodic), >= 4                                 */
+  int nz_S;       /* rows of the slow band, >= 2                              */
+  int nz_B;       /* rows of the buffer band, >= 4 (buffer condition, Sec. 3) */
+  int nz_F;       /* rows of the fast band, >= 2                              */
+  int m;          /* rate ratio, 1..64: dt_fast = dt / m                      */
+  int precision;  /* MPRK_FP64 or MPRK_FP32FLUX                               */
+  int scheme;     /* MPRK_SCHEME_MPRK2 or MPRK_SCHEME_SR_RK2                  */
+  int wall;       /* MPRK_WALL_NOSLIP or MPRK_WALL_SLIP                       */
+  int diag_every; /* monitor the state every this many slow steps (0 = never) */
+  int reserved;   /* must be 0                                                */
+  double dt;      /* slow step; 0 = from the initial state at Courant cfl     */
+  double cfl;     /* used when dt == 0; 0 means 0.4                           */
+  double dx;      /* cell width                                              */
+  double dz1;     /* cell height in fluid 1 (S and B rows)                    */
+  double dz2;     /* cell height in fluid 2 (F rows)                          */
+  double gamma;   /* ratio of specific heats (both fluids)                    */
+  double Pr;      /* Prandtl number (both fluids)                             */
+  double mu1;     /* nondimensional viscosity of fluid 1 (App. A)             */
+  double mu2;     /* nondimensional viscosity of fluid 2                      */
+  double G;       /* gravity magnitude: source (0, 0, -rho G, -rho w G)       */
+} mprk_config;
+
+typedef struct mprk_instance mprk_instance;
+
+/* Fill cfg with the paper's constants (Sec. 5.2: gamma 1.4, Pr 0.72,
+ * mu1 1/20000, mu2 1/5000, G 0.008140864714), dx = 10/nx, dz1 = dz2 = dx,
+ * MPRK2, FP64, no-slip walls, dt = 0 (automatic, cfl 0.4), no monitoring. */
+int mprk_config_default(mprk_config* cfg, int nx, int nz_S, int nz_B, int nz_F, int m);
+
+/* Create an instance: allocate its device buffers (about 3 to 4 states of
+ * nz*nx*32 bytes), copy q0 from q0_location (MPRK_HOST or MPRK_DEVICE), pick
+ * dt if cfg->dt == 0, and capture the slow step in a CUDA graph.
+ * cuda_stream: a cudaStream_t to run on, or NULL for a new non-blocking
+ * stream owned by the instance. Synchronises. Errors: MPRK_EINVAL,
+ * MPRK_ENOMEM, MPRK_ECUDA, MPRK_ENONFINITE (q0 not finite or not positive). */
+int mprk_create(const mprk_config* cfg, const double* q0, int q0_location, void* cuda_stream,
+                mprk_instance** out);
+
+/* Free every resource of the instance (synchronises its stream first). */
+int mprk_destroy(mprk_instance* inst);
+
+/* Advance n_slow_steps slow steps (Algorithm 1 per step). Asynchronous on the
+ * instance stream; monitoring (if diag_every > 0) sets the status word that
+ * mprk_status reads. */
+int mprk_step(mprk_instance* inst, int n_slow_steps);
+
+/* Copy the current state q_n to q_out ([4][nz][nx], location MPRK_HOST or
+ * MPRK_DEVICE). Synchronises the instance stream. */
+int mprk_get_state(mprk_instance* inst, double* q_out, int location);
+
+/* Replace the state (checkpoint restore; the step counter is kept by the
+ * caller). Synchronises. */
+int mprk_set_state(mprk_instance* inst, const double* q, int location);
+
+/* Monitoring quantities of the current state (Sec. 5.1), computed on the
+ * device in a fixed order: out[0..3] sums of rho, rho u, rho w, rho E times
+ * the cell area over fluid 1, out[4..7] over fluid 2, out[8..10] Courant
+ * numbers of S, B and F ((max(|u|,|w|)+a) dt_region / min(dx, dz)),
+ * out[11] count of non-finite entries, out[12] minimum density, out[13]
+ * minimum pressure, out[14] slow steps taken, out[15] dt. Synchronises. */
+int mprk_diagnostics(mprk_instance* inst, double out[16]);
+
+/* Wait for the instance's queued work. */
+int mprk_sync(mprk_instance* inst);
+
+/* Status word of the instance: 0, or MPRK_ENONFINITE / MPRK_ECFL /
+ * MPRK_ETIMEOUT if monitoring or a batched launch flagged it. Synchronises. */
+int mprk_status(mprk_instance* inst);
+
+/* Read-only facts: dt, the number of cell right-hand-side evaluations per
+ * slow step (nx (2 nz_S + 2 m (nz_B + nz_F)) for MPRK2, Sec. 4), device bytes
+ * held, and the CUDA stream. Any out pointer may be NULL. */
+int mprk_info(const mprk_instance* inst, double* dt, long long* cell_stages_per_step,
+              long long* device_bytes, void** cuda_stream);
+
+/* Test hook: the semi-discrete right-hand side R(W) (Sec. 2.1, App. B) for
+ * rows [k_lo, k_hi) of a full state W, computed by the same kernel and
+ * precision as the step. W_dev and R_dev are device buffers [4][nz][nx];
+ * rows of R outside [k_lo, k_hi) are left untouched. Asynchronous. */
+int mprk_rhs(mprk_instance* inst, const double* W_dev, double* R_dev, int k_lo, int k_hi);
+
+/* Timing hook: run one slow step (it advances the state) with every launch
+ * enqueued on its own, bracketed by CUDA events on the instance stream.
+ * launch_ms[j] receives the duration of launch j and launch_cells[j] the
+ * cell right-hand-side evaluations it made (0 for the step completion); the
+ * launches are the 2m stages in order, then the completion. Returns the
+ * number of launches (at most cap are written) or a negative error code.
+ * Synchronises. */
+int mprk_profile_step(mprk_instance* inst, double* launch_ms, long long* launch_cells, int cap);
+
+/* ---- errors ------------------------------------------------------------ */
+/* Message for the last failing call on this thread ("" if none). */
+const char* mprk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

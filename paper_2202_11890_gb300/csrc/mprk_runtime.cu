@@ -1,0 +1,510 @@
+// mprk_runtime.cu — host runtime behind the C ABI of include/mprk.h: instance
+// buffers, the slow step captured as a CUDA graph, state I/O, monitoring and
+// the right-hand-side test hook. No code path computes on the CPU.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "mprk.h"
+#include "mprk_internal.h"
+
+using namespace mprk;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CU(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(MPRK_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                 \
+  } while (0)
+
+std::mutex g_prep_mu;
+bool g_prepared[64] = {false};
+
+int prepare_device(int dev) {
+  std::lock_guard<std::mutex> lk(g_prep_mu);
+  if (dev < 0 || dev >= 64) return fail(MPRK_ECUDA, "device ordinal %d out of range", dev);
+  if (!g_prepared[dev]) {
+    CU(prepare_kernels());
+    g_prepared[dev] = true;
+  }
+  return MPRK_OK;
+}
+
+}  // namespace
+
+struct mprk_instance {
+  mprk_config cfg;
+  Geom g;
+  Bufs b;
+  int precision;
+  int device;
+  cudaStream_t stream;
+  bool own_stream;
+  double* partials;
+  double* diag_dev;
+  unsigned* status_dev;
+  int diag_nblocks;
+  double* rhs_in;   // lazily allocated padded buffers for mprk_rhs
+  double* rhs_out;
+  cudaGraphExec_t exec;       // one slow step
+  cudaGraphExec_t exec_diag;  // one slow step followed by monitoring
+  long long steps_done;
+  long long bytes;
+};
+
+namespace {
+
+int validate(const mprk_config* c) {
+  if (!c) return fail(MPRK_EINVAL, "config is NULL");
+  if (c->nx < 4) return fail(MPRK_EINVAL, "nx = %d: need at least 4 columns", c->nx);
+  if (c->nz_S < 2) return fail(MPRK_EINVAL, "nz_S = %d: need at least 2 slow rows", c->nz_S);
+  if (c->nz_B < 4)
+    return fail(MPRK_EINVAL,
+                "nz_B = %d: the buffer needs at least 4 rows for the buffer condition", c->nz_B);
+  if (c->nz_F < 2) return fail(MPRK_EINVAL, "nz_F = %d: need at least 2 fast rows", c->nz_F);
+  if (c->m < 1 || c->m > 64) return fail(MPRK_EINVAL, "m = %d: need 1 <= m <= 64", c->m);
+  if (c->precision != MPRK_FP64 && c->precision != MPRK_FP32FLUX)
+    return fail(MPRK_EINVAL, "unknown precision %d", c->precision);
+  if (c->scheme != MPRK_SCHEME_MPRK2 && c->scheme != MPRK_SCHEME_SR_RK2)
+    return fail(MPRK_EINVAL, "unknown scheme %d", c->scheme);
+  if (c->wall != MPRK_WALL_NOSLIP && c->wall != MPRK_WALL_SLIP)
+    return fail(MPRK_EINVAL, "unknown wall type %d", c->wall);
+  if (c->diag_every < 0) return fail(MPRK_EINVAL, "diag_every must be >= 0");
+  if (c->reserved != 0) return fail(MPRK_EINVAL, "reserved must be 0");
+  if (!(c->dt >= 0.0) || !std::isfinite(c->dt)) return fail(MPRK_EINVAL, "dt must be >= 0");
+  if (!(c->cfl >= 0.0) || c->cfl > 10.0) return fail(MPRK_EINVAL, "cfl out of range");
+  if (!(c->dx > 0) || !(c->dz1 > 0) || !(c->dz2 > 0))
+    return fail(MPRK_EINVAL, "cell sizes must be positive");
+  if (!(c->gamma > 1.0) || !(c->Pr > 0.0)) return fail(MPRK_EINVAL, "need gamma > 1 and Pr > 0");
+  if (!(c->mu1 > 0.0) || !(c->mu2 > 0.0)) return fail(MPRK_EINVAL, "viscosities must be positive");
+  if (!(c->G >= 0.0)) return fail(MPRK_EINVAL, "G must be >= 0");
+  long long cells = (long long)c->nx * (c->nz_S + c->nz_B + c->nz_F);
+  if (cells > (1LL << 31)) return fail(MPRK_EINVAL, "grid too large");
+  return MPRK_OK;
+}
+
+void fill_geom(mprk_instance* I) {
+  const mprk_config& c = I->cfg;
+  Geom& g = I->g;
+  g.nx = c.nx;
+  g.pitch = (c.nx + 31) / 32 * 32;
+  g.nz = c.nz_S + c.nz_B + c.nz_F;
+  g.n1 = c.nz_S + c.nz_B;
+  if (c.scheme == MPRK_SCHEME_MPRK2) {
+    g.nS_r = c.nz_S;
+    g.n1_r = g.n1;
+  } else {
+    g.nS_r = 0;
+    g.n1_r = 0;
+  }
+  g.nS_g = c.nz_S;
+  g.m = c.m;
+  g.wall = c.wall;
+  g.dt = c.dt;
+  g.inv_dx = 1.0 / c.dx;
+  g.inv_dz1 = 1.0 / c.dz1;
+  g.inv_dz2 = 1.0 / c.dz2;
+  g.gamma = c.gamma;
+  g.gm1 = c.gamma - 1.0;
+  g.mu1 = c.mu1;
+  g.mu2 = c.mu2;
+  const double cp = 1.0 / (c.gamma - 1.0);  // c~_p of App. A
+  g.kap1 = cp * c.mu1 / c.Pr;
+  g.kap2 = cp * c.mu2 / c.Pr;
+  g.G = c.G;
+  // bulk coefficients of App. B: 2 k1 k2 / (dz2 k1 + dz1 k2)
+  g.bu = 2.0 * c.mu1 * c.mu2 / (c.dz2 * c.mu1 + c.dz1 * c.mu2);
+  g.bT = 2.0 * g.kap1 * g.kap2 / (c.dz2 * g.kap1 + c.dz1 * g.kap2);
+  g.cu1 = c.dz1 / (2.0 * c.mu1);
+  g.cT1 = c.dz1 / (2.0 * g.kap1);
+}
+
+void free_instance(mprk_instance* I) {
+  if (!I) return;
+  if (I->stream) cudaStreamSynchronize(I->stream);
+  if (I->exec) cudaGraphExecDestroy(I->exec);
+  if (I->exec_diag) cudaGraphExecDestroy(I->exec_diag);
+  cudaFree(I->b.qA);
+  cudaFree(I->b.qB);
+  cudaFree(I->b.Ra);
+  cudaFree(I->b.accB);
+  cudaFree(I->b.accS);
+  cudaFree(I->partials);
+  cudaFree(I->diag_dev);
+  cudaFree(I->status_dev);
+  cudaFree(I->rhs_in);
+  cudaFree(I->rhs_out);
+  if (I->own_stream && I->stream) cudaStreamDestroy(I->stream);
+  delete I;
+}
+
+// Enqueue the stage launches and the completion of one slow step.
+int enqueue_step(mprk_instance* I, cudaStream_t s) {
+  const Geom& g = I->g;
+  const int tiles_x = (g.nx + TX - 1) / TX;
+  for (int st = 0; st < 2 * g.m; st++) {
+    StageArgs a;
+    memset(&a, 0, sizeof a);
+    a.g = g;
+    a.b = I->b;
+    const bool even_sub = ((st / 2) % 2) == 0;
+    a.qF = even_sub ? I->b.qA : I->b.qB;
+    a.qF_next = even_sub ? I->b.qB : I->b.qA;
+    a.stage = st;
+    a.row0 = st < 2 ? 0 : g.nS_r;
+    a.tiles_x = tiles_x;
+    const int tiles_z = (g.nz - a.row0 + TZ - 1) / TZ;
+    CU(launch_stage(a, I->precision, tiles_x * tiles_z, s));
+  }
+  CU(launch_finalize(g, I->b, g.m & 1, s));
+  return MPRK_OK;
+}
+
+int capture(mprk_instance* I, bool with_diag, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  CU(cudaStreamBeginCapture(I->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_step(I, I->stream);
+  if (rc == MPRK_OK && with_diag) {
+    cudaError_t e = launch_diag(I->g, I->b.qA, I->partials, I->diag_nblocks, I->diag_dev,
+                                I->status_dev, 0.0, I->stream);
+    if (e != cudaSuccess) rc = fail(MPRK_ECUDA, "monitoring launch: %s", cudaGetErrorString(e));
+  }
+  cudaError_t e = cudaStreamEndCapture(I->stream, &graph);
+  if (rc != MPRK_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(MPRK_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(MPRK_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return MPRK_OK;
+}
+
+int copy_state_in(mprk_instance* I, const double* q, int loc) {
+  const Geom& g = I->g;
+  cudaMemcpyKind kind = loc == MPRK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CU(cudaMemcpy2DAsync(I->b.qA, (size_t)g.pitch * 8, q, (size_t)g.nx * 8, (size_t)g.nx * 8,
+                       (size_t)4 * g.nz, kind, I->stream));
+  return MPRK_OK;
+}
+
+// Run the monitoring kernels now and read the 16 results (synchronises).
+int run_diag(mprk_instance* I, double out[16]) {
+  CU(launch_diag(I->g, I->b.qA, I->partials, I->diag_nblocks, I->diag_dev, I->status_dev, 0.0,
+                 I->stream));
+  CU(cudaMemcpyAsync(out, I->diag_dev, 16 * sizeof(double), cudaMemcpyDeviceToHost, I->stream));
+  CU(cudaStreamSynchronize(I->stream));
+  out[14] = (double)I->steps_done;
+  return MPRK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mprk_config_default(mprk_config* cfg, int nx, int nz_S, int nz_B, int nz_F, int m) {
+  if (!cfg) return fail(MPRK_EINVAL, "config is NULL");
+  if (nx <= 0) return fail(MPRK_EINVAL, "nx must be positive");
+  memset(cfg, 0, sizeof *cfg);
+  cfg->nx = nx;
+  cfg->nz_S = nz_S;
+  cfg->nz_B = nz_B;
+  cfg->nz_F = nz_F;
+  cfg->m = m;
+  cfg->precision = MPRK_FP64;
+  cfg->scheme = MPRK_SCHEME_MPRK2;
+  cfg->wall = MPRK_WALL_NOSLIP;
+  cfg->diag_every = 0;
+  cfg->dt = 0.0;
+  cfg->cfl = 0.4;
+  cfg->dx = 10.0 / nx;
+  cfg->dz1 = cfg->dx;
+  cfg->dz2 = cfg->dx;
+  cfg->gamma = 1.4;
+  cfg->Pr = 0.72;
+  cfg->mu1 = 1.0 / 20000.0;
+  cfg->mu2 = 1.0 / 5000.0;
+  cfg->G = 0.008140864714;
+  return MPRK_OK;
+}
+
+int mprk_create(const mprk_config* cfg, const double* q0, int q0_location, void* cuda_stream,
+                mprk_instance** out) {
+  if (!out) return fail(MPRK_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc) return rc;
+  if (!q0) return fail(MPRK_EINVAL, "q0 is NULL");
+  if (q0_location != MPRK_HOST && q0_location != MPRK_DEVICE)
+    return fail(MPRK_EINVAL, "q0_location must be MPRK_HOST or MPRK_DEVICE");
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if ((rc = prepare_device(dev))) return rc;
+
+  mprk_instance* I = new (std::nothrow) mprk_instance();
+  if (!I) return fail(MPRK_ENOMEM, "host allocation failed");
+  memset(I, 0, sizeof *I);
+  I->cfg = *cfg;
+  if (I->cfg.cfl == 0.0) I->cfg.cfl = 0.4;
+  I->precision = cfg->precision;
+  I->device = dev;
+  fill_geom(I);
+  const Geom& g = I->g;
+
+  auto alloc = [&](void** p, size_t bytes) -> int {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MPRK_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    I->bytes += (long long)bytes;
+    return MPRK_OK;
+  };
+  const size_t plane = (size_t)g.nz * g.pitch;
+  const size_t rsz = I->precision == MPRK_FP64 ? sizeof(double) : sizeof(float);
+  I->diag_nblocks = diag_blocks(g);
+  if ((rc = alloc((void**)&I->b.qA, 4 * plane * 8)) || (rc = alloc((void**)&I->b.qB, 4 * plane * 8)) ||
+      (rc = alloc(&I->b.Ra, 4 * plane * rsz)) ||
+      (rc = alloc((void**)&I->b.accB, 4 * (size_t)(g.n1_r - g.nS_r) * g.pitch * 8)) ||
+      (rc = alloc((void**)&I->b.accS, 4 * (size_t)g.nS_r * g.pitch * 8)) ||
+      (rc = alloc((void**)&I->partials, (size_t)I->diag_nblocks * 16 * 8)) ||
+      (rc = alloc((void**)&I->diag_dev, 16 * 8)) || (rc = alloc((void**)&I->status_dev, 16))) {
+    free_instance(I);
+    return rc;
+  }
+  if (cuda_stream) {
+    I->stream = (cudaStream_t)cuda_stream;
+    I->own_stream = false;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&I->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      free_instance(I);
+      return fail(MPRK_ECUDA, "stream create: %s", cudaGetErrorString(e));
+    }
+    I->own_stream = true;
+  }
+  auto fin = [&](int code) {
+    free_instance(I);
+    return code;
+  };
+  if (cudaMemsetAsync(I->b.qA, 0, 4 * plane * 8, I->stream) != cudaSuccess ||
+      cudaMemsetAsync(I->b.qB, 0, 4 * plane * 8, I->stream) != cudaSuccess ||
+      cudaMemsetAsync(I->b.Ra, 0, 4 * plane * rsz, I->stream) != cudaSuccess ||
+      cudaMemsetAsync(I->status_dev, 0, 16, I->stream) != cudaSuccess)
+    return fin(fail(MPRK_ECUDA, "memset failed"));
+  if ((rc = copy_state_in(I, q0, q0_location))) return fin(rc);
+
+  // check the initial state and pick dt
+  double d[16];
+  I->g.dt = 1.0;  // placeholder for the Courant numbers of the check
+  if ((rc = run_diag(I, d))) return fin(rc);
+  if (d[11] > 0.0 || !(d[12] > 0.0) || !(d[13] > 0.0))
+    return fin(fail(MPRK_ENONFINITE, "q0 has %g non-finite entries, min rho %g, min p %g", d[11],
+                    d[12], d[13]));
+  if (cudaMemsetAsync(I->status_dev, 0, 16, I->stream) != cudaSuccess)
+    return fin(fail(MPRK_ECUDA, "memset failed"));
+  double dt = cfg->dt;
+  if (dt == 0.0) {
+    // wave speeds: d[8..10] hold max(|u|,|w|)+a per band times dt/min(dx,dz)
+    // with dt = 1 (S, B at dt, F at dt/m)
+    const double sr = cfg->scheme == MPRK_SCHEME_MPRK2 ? 1.0 : (double)cfg->m;
+    const double c1 = fmax(d[8], d[9]) * sr * fmin(cfg->dx, cfg->dz1);
+    const double c2 = d[10] * cfg->m * fmin(cfg->dx, cfg->dz2);
+    const double cfl = I->cfg.cfl;
+    const double d1 = cfl * fmin(cfg->dx, cfg->dz1) / c1;
+    const double d2 = cfg->m * cfl * fmin(cfg->dx, cfg->dz2) / c2;
+    dt = cfg->scheme == MPRK_SCHEME_MPRK2 ? fmin(d1, d2) : cfg->m * fmin(d1, d2 / cfg->m);
+  }
+  I->cfg.dt = dt;
+  I->g.dt = dt;
+  if ((rc = capture(I, false, &I->exec))) return fin(rc);
+  if (I->cfg.diag_every > 0 && (rc = capture(I, true, &I->exec_diag))) return fin(rc);
+  cudaError_t e = cudaStreamSynchronize(I->stream);
+  if (e != cudaSuccess) return fin(fail(MPRK_ECUDA, "create: %s", cudaGetErrorString(e)));
+  *out = I;
+  return MPRK_OK;
+}
+
+int mprk_destroy(mprk_instance* inst) {
+  if (!inst) return fail(MPRK_EINVAL, "instance is NULL");
+  free_instance(inst);
+  return MPRK_OK;
+}
+
+int mprk_step(mprk_instance* I, int n) {
+  if (!I) return fail(MPRK_EINVAL, "instance is NULL");
+  if (n < 0) return fail(MPRK_EINVAL, "negative step count");
+  for (int s = 0; s < n; s++) {
+    const bool diag = I->cfg.diag_every > 0 && ((I->steps_done + 1) % I->cfg.diag_every) == 0;
+    CU(cudaGraphLaunch(diag ? I->exec_diag : I->exec, I->stream));
+    I->steps_done++;
+  }
+  return MPRK_OK;
+}
+
+int mprk_get_state(mprk_instance* I, double* q_out, int location) {
+  if (!I || !q_out) return fail(MPRK_EINVAL, "NULL argument");
+  if (location != MPRK_HOST && location != MPRK_DEVICE) return fail(MPRK_EINVAL, "bad location");
+  const Geom& g = I->g;
+  cudaMemcpyKind kind = location == MPRK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CU(cudaMemcpy2DAsync(q_out, (size_t)g.nx * 8, I->b.qA, (size_t)g.pitch * 8, (size_t)g.nx * 8,
+                       (size_t)4 * g.nz, kind, I->stream));
+  CU(cudaStreamSynchronize(I->stream));
+  return MPRK_OK;
+}
+
+int mprk_set_state(mprk_instance* I, const double* q, int location) {
+  if (!I || !q) return fail(MPRK_EINVAL, "NULL argument");
+  if (location != MPRK_HOST && location != MPRK_DEVICE) return fail(MPRK_EINVAL, "bad location");
+  int rc = copy_state_in(I, q, location);
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(I->stream));
+  return MPRK_OK;
+}
+
+int mprk_diagnostics(mprk_instance* I, double out[16]) {
+  if (!I || !out) return fail(MPRK_EINVAL, "NULL argument");
+  return run_diag(I, out);
+}
+
+int mprk_sync(mprk_instance* I) {
+  if (!I) return fail(MPRK_EINVAL, "instance is NULL");
+  CU(cudaStreamSynchronize(I->stream));
+  return MPRK_OK;
+}
+
+int mprk_status(mprk_instance* I) {
+  if (!I) return fail(MPRK_EINVAL, "instance is NULL");
+  unsigned st = 0;
+  CU(cudaMemcpyAsync(&st, I->status_dev, sizeof st, cudaMemcpyDeviceToHost, I->stream));
+  CU(cudaStreamSynchronize(I->stream));
+  if (st & ST_NONFINITE) return MPRK_ENONFINITE;
+  if (st & ST_TIMEOUT) return MPRK_ETIMEOUT;
+  if (st & ST_CFL) return MPRK_ECFL;
+  return MPRK_OK;
+}
+
+int mprk_info(const mprk_instance* I, double* dt, long long* cell_stages, long long* bytes,
+              void** stream) {
+  if (!I) return fail(MPRK_EINVAL, "instance is NULL");
+  const mprk_config& c = I->cfg;
+  if (dt) *dt = I->g.dt;
+  if (cell_stages) {
+    const long long nz = c.nz_S + c.nz_B + c.nz_F;
+    *cell_stages = c.scheme == MPRK_SCHEME_MPRK2
+                       ? (long long)c.nx * (2LL * c.nz_S + 2LL * c.m * (c.nz_B + c.nz_F))
+                       : (long long)c.nx * 2LL * c.m * nz;
+  }
+  if (bytes) *bytes = I->bytes;
+  if (stream) *stream = (void*)I->stream;
+  return MPRK_OK;
+}
+
+int mprk_rhs(mprk_instance* I, const double* W_dev, double* R_dev, int k_lo, int k_hi) {
+  if (!I || !W_dev || !R_dev) return fail(MPRK_EINVAL, "NULL argument");
+  const Geom& g = I->g;
+  if (k_lo < 0 || k_hi > g.nz || k_lo >= k_hi) return fail(MPRK_EINVAL, "bad row range");
+  const size_t plane = (size_t)g.nz * g.pitch;
+  if (!I->rhs_in) {
+    CU(cudaMalloc((void**)&I->rhs_in, 4 * plane * 8));
+    CU(cudaMalloc((void**)&I->rhs_out, 4 * plane * 8));
+    CU(cudaMemsetAsync(I->rhs_in, 0, 4 * plane * 8, I->stream));
+  }
+  CU(cudaMemcpy2DAsync(I->rhs_in, (size_t)g.pitch * 8, W_dev, (size_t)g.nx * 8, (size_t)g.nx * 8,
+                       (size_t)4 * g.nz, cudaMemcpyDeviceToDevice, I->stream));
+  StageArgs a;
+  memset(&a, 0, sizeof a);
+  a.g = g;
+  a.b = I->b;
+  a.qF = I->b.qA;
+  a.qF_next = I->b.qB;
+  a.stage = 0;
+  a.row0 = k_lo;
+  a.tiles_x = (g.nx + TX - 1) / TX;
+  a.rhs_only = 1;
+  a.rhs_out = I->rhs_out;
+  a.rhs_hi = k_hi;
+  a.rhs_in = I->rhs_in;
+  const int tiles_z = (k_hi - k_lo + TZ - 1) / TZ;
+  CU(launch_stage(a, I->precision, a.tiles_x * tiles_z, I->stream));
+  for (int c = 0; c < 4; c++) {
+    CU(cudaMemcpy2DAsync(R_dev + ((size_t)c * g.nz + k_lo) * g.nx, (size_t)g.nx * 8,
+                         I->rhs_out + (size_t)c * plane + (size_t)k_lo * g.pitch,
+                         (size_t)g.pitch * 8, (size_t)g.nx * 8, (size_t)(k_hi - k_lo),
+                         cudaMemcpyDeviceToDevice, I->stream));
+  }
+  return MPRK_OK;
+}
+
+int mprk_profile_step(mprk_instance* I, double* launch_ms, long long* launch_cells, int cap) {
+  if (!I) return fail(MPRK_EINVAL, "instance is NULL");
+  const Geom& g = I->g;
+  const int n = 2 * g.m + 1;
+  cudaEvent_t ev[2 * 64 + 2];
+  for (int j = 0; j <= n; j++) CU(cudaEventCreate(&ev[j]));
+  const int tiles_x = (g.nx + TX - 1) / TX;
+  int rc = MPRK_OK;
+  CU(cudaEventRecord(ev[0], I->stream));
+  for (int st = 0; st < 2 * g.m && rc == MPRK_OK; st++) {
+    StageArgs a;
+    memset(&a, 0, sizeof a);
+    a.g = g;
+    a.b = I->b;
+    const bool even_sub = ((st / 2) % 2) == 0;
+    a.qF = even_sub ? I->b.qA : I->b.qB;
+    a.qF_next = even_sub ? I->b.qB : I->b.qA;
+    a.stage = st;
+    a.row0 = st < 2 ? 0 : g.nS_r;
+    a.tiles_x = tiles_x;
+    const int tiles_z = (g.nz - a.row0 + TZ - 1) / TZ;
+    cudaError_t e = launch_stage(a, I->precision, tiles_x * tiles_z, I->stream);
+    if (e != cudaSuccess) rc = fail(MPRK_ECUDA, "stage launch: %s", cudaGetErrorString(e));
+    cudaEventRecord(ev[st + 1], I->stream);
+    if (st < cap && launch_cells) launch_cells[st] = (long long)(g.nz - a.row0) * g.nx;
+  }
+  if (rc == MPRK_OK) {
+    cudaError_t e = launch_finalize(g, I->b, g.m & 1, I->stream);
+    if (e != cudaSuccess) rc = fail(MPRK_ECUDA, "completion launch: %s", cudaGetErrorString(e));
+    cudaEventRecord(ev[n], I->stream);
+    if (n - 1 < cap && launch_cells) launch_cells[n - 1] = 0;
+  }
+  cudaError_t e = cudaStreamSynchronize(I->stream);
+  if (rc == MPRK_OK && e != cudaSuccess) rc = fail(MPRK_ECUDA, "profile: %s", cudaGetErrorString(e));
+  if (rc == MPRK_OK) {
+    for (int j = 0; j < n && j < cap; j++) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[j], ev[j + 1]);
+      if (launch_ms) launch_ms[j] = ms;
+    }
+    I->steps_done++;
+  }
+  for (int j = 0; j <= n; j++) cudaEventDestroy(ev[j]);
+  return rc == MPRK_OK ? n : rc;
+}
+
+const char* mprk_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,429 @@
+// stage_tile.cuh — the fused right-hand-side + stage-combination tile of one
+// MPRK2 stage (device code; included by the kernel translation units).
+//
+// One CTA of TX x TZ threads owns a TX x TZ tile of cells. It
+//   1. stages the stage state of the tile plus a two-cell halo in shared
+//      memory (x periodic; stage values q + h R_a rebuilt on the fly),
+//   2. computes u, w, T on the tile plus a one-cell ring, and the interface
+//      state (bulk fluxes and wall states of App. B) when the tile touches it,
+//   3. computes the cell slopes: central differences of the conserved
+//      variables (reconstruction) and of u, w (tangential viscous gradients),
+//      with mirror or wall-state ghosts beyond walls and the interface,
+//   4. computes every x and z face flux of the tile once (Lax–Friedrichs
+//      inviscid flux of Sec. 2.1 minus the common-value viscous flux of
+//      App. B), in one direction-generic routine written in the face frame,
+//   5. forms R = -div F* + s per cell and applies the partition's stage
+//      combination (Eq. MRK2 in low-storage form) in double precision.
+//
+// Real is the arithmetic type of steps 1-5 up to R (double, or float in the
+// FP32-flux mode); Store is the type of the saved stage-one right-hand side.
+#pragma once
+
+#include "mprk_internal.h"
+
+namespace mprk {
+
+template <typename Real>
+struct TileSmem {
+  Real q[4][TZ + 4][TX + 4];   // stage state, rows k0-2.., cols i0-2..
+  Real v[3][TZ + 2][TX + 2];   // u, w, T, rows k0-1.., cols i0-1..
+  Real hx[4][TZ][TX + 2];      // quarter x differences of q, cols i0-1..
+  Real hz[4][TZ + 2][TX];      // quarter z differences of q, rows k0-1..
+  Real tz[2][TZ][TX + 2];      // d/dz of u, w (tangential at x faces)
+  Real tx[2][TZ + 2][TX];      // d/dx of u, w (tangential at z faces)
+  Real fx[4][TZ][TX + 1];      // x face fluxes, face f between cols f-1, f
+  Real fz[4][TZ + 1][TX];      // z face fluxes seen from above
+  Real fg[4][TX];              // interface flux seen from fluid 1 (below)
+  double gam[4][TX + 2];       // sigma_xz, Pi_z, u_w, T_w per column i0-1..
+};
+
+template <typename Real>
+__device__ __forceinline__ Real rsq(Real x);
+template <>
+__device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
+template <>
+__device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+
+// Lax–Friedrichs flux in the face frame. A state is (rho, m_n, m_t, rho E):
+// m_n is the momentum along the face normal, m_t along the face. Output is
+// (F_rho, F_mn, F_mt, F_E). lambda is the largest |u_n| + a over the left,
+// right and Roe-averaged states (Sec. 2.1).
+template <typename Real>
+__device__ __forceinline__ void lf_face(Real lr, Real lmn, Real lmt, Real lE, Real rr, Real rmn,
+                                        Real rmt, Real rE, Real gamma, Real gm1, Real out[4]) {
+  const Real half = Real(0.5);
+  const Real rsL = rsq(lr), rsR = rsq(rr);
+  const Real invL = rsL * rsL, invR = rsR * rsR;
+  const Real sL = lr * rsL, sR = rr * rsR;  // sqrt(rho)
+  const Real unL = lmn * invL, utL = lmt * invL;
+  const Real unR = rmn * invR, utR = rmt * invR;
+  const Real pL = gm1 * (lE - half * (lmn * unL + lmt * utL));
+  const Real pR = gm1 * (rE - half * (rmn * unR + rmt * utR));
+  const Real XL = gamma * pL * invL, XR = gamma * pR * invR;
+  const Real cL = XL * rsq(XL), cR = XR * rsq(XR);
+  const Real HL = (lE + pL) * invL, HR = (rE + pR) * invR;
+  const Real den = Real(1) / (sL + sR);
+  const Real un = (sL * unL + sR * unR) * den;
+  const Real ut = (sL * utL + sR * utR) * den;
+  const Real H = (sL * HL + sR * HR) * den;
+  const Real X = gm1 * (H - half * (un * un + ut * ut));
+  const Real c = X * rsq(X);
+  const Real lam = fmax(fmax(fabs(unL) + cL, fabs(unR) + cR), fabs(un) + c);
+  const Real hl = half * lam;
+  out[0] = half * (lmn + rmn) + hl * (lr - rr);
+  out[1] = half * ((lmn * unL + pL) + (rmn * unR + pR)) + hl * (lmn - rmn);
+  out[2] = half * (lmt * unL + rmt * unR) + hl * (lmt - rmt);
+  out[3] = half * (unL * (lE + pL) + unR * (rE + pR)) + hl * (lE - rE);
+}
+
+// Viscous flux in the face frame from the common values of App. B: face
+// velocity = mean of the two cells, normal derivatives = two-point
+// differences, tangential derivatives = mean of the two cells' central
+// differences. Output (0, sigma_nn, sigma_nt, u.sigma_n + kappa dT/dn).
+template <typename Real>
+__device__ __forceinline__ void visc_face(Real unL, Real utL, Real TL, Real gnL, Real gtL,
+                                          Real unR, Real utR, Real TR, Real gnR, Real gtR,
+                                          Real inv_dn, Real mu, Real kap, Real out[4]) {
+  const Real half = Real(0.5);
+  const Real un = half * (unL + unR), ut = half * (utL + utR);
+  const Real dn_un = (unR - unL) * inv_dn;
+  const Real dn_ut = (utR - utL) * inv_dn;
+  const Real dn_T = (TR - TL) * inv_dn;
+  const Real dt_un = half * (gnL + gnR);  // tangential derivative of u_n
+  const Real dt_ut = half * (gtL + gtR);  // tangential derivative of u_t
+  const Real snn = mu * (Real(2) * dn_un - Real(2.0 / 3.0) * (dn_un + dt_ut));
+  const Real snt = mu * (dn_ut + dt_un);
+  out[0] = Real(0);
+  out[1] = snn;
+  out[2] = snt;
+  out[3] = un * snn + ut * snt + kap * dn_T;
+}
+
+__device__ __forceinline__ int wrap_col(int i, int nx) {
+  if (i < 0) i += nx;
+  if (i >= nx) i %= nx;
+  return i;
+}
+
+// The tile body. tile = linear tile index within the launch's row range.
+template <typename Real, typename Store>
+__device__ __forceinline__ void stage_tile(const StageArgs& a, int tile, TileSmem<Real>& S) {
+  const Geom& g = a.g;
+  const int tid = threadIdx.x;
+  const int tzi = tile / a.tiles_x;
+  const int txi = tile - tzi * a.tiles_x;
+  const int k0 = a.row0 + tzi * TZ;
+  const int i0 = txi * TX;
+  const int nz = g.nz, nx = g.nx, n1 = g.n1;
+  const int row_hi = a.rhs_only ? a.rhs_hi : nz;
+  const size_t plane = (size_t)nz * g.pitch;
+  const bool odd_stage = !a.rhs_only && (a.stage & 1);  // stages 2, 4, ... (1-based)
+  const Store* Ra = reinterpret_cast<const Store*>(a.b.Ra);
+  const double hF = g.dt / g.m;
+
+  // ---- 1. stage state of the tile and its halo --------------------------
+  for (int e = tid; e < 4 * (TZ + 4) * (TX + 4); e += NTHREADS) {
+    const int c = e / ((TZ + 4) * (TX + 4));
+    const int rem = e - c * ((TZ + 4) * (TX + 4));
+    const int rr = rem / (TX + 4), cc = rem - rr * (TX + 4);
+    const int k = k0 - 2 + rr;
+    Real val = Real(0);
+    if (k >= 0 && k < nz) {
+      const int i = wrap_col(i0 - 2 + cc, nx);
+      const size_t off = (size_t)c * plane + (size_t)k * g.pitch + i;
+      if (a.rhs_only) {
+        val = (Real)a.rhs_in[off];
+      } else {
+        const double* base = k < g.n1_r ? a.b.qA : a.qF;
+        if (odd_stage) {
+          const Real h = (Real)(k < g.n1_r ? g.dt : hF);
+          val = (Real)base[off] + h * (Real)Ra[off];
+        } else {
+          val = (Real)base[off];
+        }
+      }
+    }
+    S.q[c][rr][cc] = val;
+  }
+  const bool has_gamma = (n1 >= k0 && n1 <= k0 + TZ);
+  __syncthreads();
+
+  // ---- 2. u, w, T on the one-cell ring; interface state -----------------
+  const Real gamma = (Real)g.gamma, gm1 = (Real)g.gm1;
+  for (int e = tid; e < (TZ + 2) * (TX + 2); e += NTHREADS) {
+    const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
+    const int k = k0 - 1 + rr;
+    if (k < 0 || k >= nz) continue;
+    const Real r = S.q[0][rr + 1][cc + 1], mu_ = S.q[1][rr + 1][cc + 1];
+    const Real mw = S.q[2][rr + 1][cc + 1], E = S.q[3][rr + 1][cc + 1];
+    const Real inv = Real(1) / r;
+    const Real u = mu_ * inv, w = mw * inv;
+    const Real p = gm1 * (E - Real(0.5) * (mu_ * u + mw * w));
+    S.v[0][rr][cc] = u;
+    S.v[1][rr][cc] = w;
+    S.v[2][rr][cc] = gamma * p * inv;
+  }
+  if (has_gamma && tid < TX + 2) {
+    // Interface state of column i0-1+tid in double precision from the two
+    // cells touching Gamma (App. B, Eq. bulk-flux and the wall states).
+    const int i = wrap_col(i0 - 1 + tid, nx);
+    double u[2], T[2];
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      const int k = n1 - 1 + s;
+      double qq[4];
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const size_t off = (size_t)c * plane + (size_t)k * g.pitch + i;
+        if (a.rhs_only) {
+          qq[c] = a.rhs_in[off];
+        } else {
+          const double* base = k < g.n1_r ? a.b.qA : a.qF;
+          if (odd_stage) {
+            qq[c] = base[off] + (k < g.n1_r ? g.dt : hF) * (double)Ra[off];
+          } else {
+            qq[c] = base[off];
+          }
+        }
+      }
+      const double inv = 1.0 / qq[0];
+      u[s] = qq[1] * inv;
+      const double w = qq[2] * inv;
+      const double p = g.gm1 * (qq[3] - 0.5 * (qq[1] * u[s] + qq[2] * w));
+      T[s] = g.gamma * p * inv;
+    }
+    const double sig = g.bu * (u[1] - u[0]);
+    const double Pi = -g.bT * (T[1] - T[0]);
+    S.gam[0][tid] = sig;
+    S.gam[1][tid] = Pi;
+    S.gam[2][tid] = u[0] + sig * g.cu1;
+    S.gam[3][tid] = T[0] - Pi * g.cT1;
+  }
+  __syncthreads();
+
+  // ---- 3. slopes ---------------------------------------------------------
+  const Real quarter = Real(0.25);
+  const Real hinv_dx = Real(0.5) * (Real)g.inv_dx;
+  // (a) quarter x differences of q on tile rows, cols i0-1 .. i0+TX
+  for (int e = tid; e < TZ * (TX + 2); e += NTHREADS) {
+    const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
+    if (k0 + rr >= row_hi) continue;
+#pragma unroll
+    for (int c = 0; c < 4; c++) S.hx[c][rr][cc] = quarter * (S.q[c][rr + 2][cc + 2] - S.q[c][rr + 2][cc]);
+    // d/dz of u, w at the same cells (tangential at x faces)
+    const int k = k0 + rr;
+    const Real u = S.v[0][rr + 1][cc], w = S.v[1][rr + 1][cc];
+    Real uu, wu, ud, wd;  // values above and below, or their ghosts
+    const bool top_wall = (k + 1 == nz), bot_wall = (k == 0);
+    const bool top_gam = (k + 1 == n1), bot_gam = (k == n1);
+    if (top_wall) { uu = g.wall ? u : -u; wu = -w; }
+    else if (top_gam) { uu = Real(2) * (Real)S.gam[2][cc] - u; wu = -w; }
+    else { uu = S.v[0][rr + 2][cc]; wu = S.v[1][rr + 2][cc]; }
+    if (bot_wall) { ud = g.wall ? u : -u; wd = -w; }
+    else if (bot_gam) { ud = Real(2) * (Real)S.gam[2][cc] - u; wd = -w; }
+    else { ud = S.v[0][rr][cc]; wd = S.v[1][rr][cc]; }
+    const Real hinv_dz = Real(0.5) * (Real)(k < n1 ? g.inv_dz1 : g.inv_dz2);
+    S.tz[0][rr][cc] = (uu - ud) * hinv_dz;
+    S.tz[1][rr][cc] = (wu - wd) * hinv_dz;
+  }
+  // (b) quarter z differences of q on ring rows k0-1 .. k0+TZ, tile cols
+  for (int e = tid; e < (TZ + 2) * TX; e += NTHREADS) {
+    const int rr = e / TX, cc = e - rr * TX;
+    const int k = k0 - 1 + rr;
+    if (k < 0 || k >= nz) continue;
+    const bool up_in = (k + 1 < nz) && ((k + 1 < n1) == (k < n1));
+    const bool dn_in = (k - 1 >= 0) && ((k - 1 < n1) == (k < n1));
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const Real own = S.q[c][rr + 1][cc + 2];
+      const Real mir = (c == 2) ? -own : own;  // mirror ghost: rho w odd
+      const Real up = up_in ? S.q[c][rr + 2][cc + 2] : mir;
+      const Real dn = dn_in ? S.q[c][rr][cc + 2] : mir;
+      S.hz[c][rr][cc] = quarter * (up - dn);
+    }
+    S.tx[0][rr][cc] = (S.v[0][rr][cc + 2] - S.v[0][rr][cc]) * hinv_dx;
+    S.tx[1][rr][cc] = (S.v[1][rr][cc + 2] - S.v[1][rr][cc]) * hinv_dx;
+  }
+  __syncthreads();
+
+  // ---- 4. face fluxes ----------------------------------------------------
+  // z faces first: (TZ+1) rows of TX faces, one warp per face row; then x
+  // faces. Every warp sees one face kind.
+  const Real mu1 = (Real)g.mu1, mu2 = (Real)g.mu2, kap1 = (Real)g.kap1, kap2 = (Real)g.kap2;
+  constexpr int NZF = (TZ + 1) * TX, NXF = TZ * (TX + 1);
+  for (int e = tid; e < NZF + NXF; e += NTHREADS) {
+    Real F[4];
+    if (e < NZF) {
+      const int f = e / TX, cc = e - f * TX;
+      const int ku = k0 + f;  // row above the face
+      const int kd = ku - 1;  // row below the face
+      // needed by a cell of the tile: the cell below (f >= 1) or above (f == 0)
+      if (kd >= row_hi) continue;
+      // reconstructed state of the cell at tile row rq (halo rows) / ring row
+      // rh in the face frame (normal = z): q + sgn * (quarter z difference)
+      auto load_side = [&](int rq, int rh, Real& r, Real& mn, Real& mt, Real& E, Real sgn) {
+        r = S.q[0][rq][cc + 2] + sgn * S.hz[0][rh][cc];
+        mt = S.q[1][rq][cc + 2] + sgn * S.hz[1][rh][cc];
+        mn = S.q[2][rq][cc + 2] + sgn * S.hz[2][rh][cc];
+        E = S.q[3][rq][cc + 2] + sgn * S.hz[3][rh][cc];
+      };
+      if (ku == 0 || ku == nz) {
+        // outer wall: the boundary cell against its mirror (inviscid) and its
+        // ghost 2*wall - interior (viscous); no-slip or slip, adiabatic
+        const bool below = (ku == 0);  // wall under row 0
+        const int rq = below ? f + 2 : f + 1;
+        const int rh = below ? f + 1 : f;
+        const int rv = below ? f + 1 : f;
+        Real r, mn, mt, E;
+        load_side(rq, rh, r, mn, mt, E, below ? Real(-1) : Real(1));
+        Real FI[4], FV[4];
+        if (below) lf_face(r, -mn, mt, E, r, mn, mt, E, gamma, gm1, FI);
+        else lf_face(r, mn, mt, E, r, -mn, mt, E, gamma, gm1, FI);
+        const Real un = S.v[1][rv][cc + 1], ut = S.v[0][rv][cc + 1], T = S.v[2][rv][cc + 1];
+        const Real gn = S.tx[1][rv][cc], gt = S.tx[0][rv][cc];
+        const Real utg = g.wall ? ut : -ut, gtg = g.wall ? gt : -gt;
+        const int k = below ? ku : kd;
+        const Real mu = k < n1 ? mu1 : mu2, kap = k < n1 ? kap1 : kap2;
+        const Real inv_dn = (Real)(k < n1 ? g.inv_dz1 : g.inv_dz2);
+        if (below) visc_face(-un, utg, T, -gn, gtg, un, ut, T, gn, gt, inv_dn, mu, kap, FV);
+        else visc_face(un, ut, T, gn, gt, -un, utg, T, -gn, gtg, inv_dn, mu, kap, FV);
+        S.fz[0][f][cc] = FI[0] - FV[0];
+        S.fz[1][f][cc] = FI[2] - FV[2];
+        S.fz[2][f][cc] = FI[1] - FV[1];
+        S.fz[3][f][cc] = FI[3] - FV[3];
+      } else if (ku == n1) {
+        // the interface: a rigid lid seen from each fluid (inviscid), the bulk
+        // fluxes of App. B (viscous, shared by both fluids)
+        const double sig = S.gam[0][cc + 1], Pi = S.gam[1][cc + 1], uw = S.gam[2][cc + 1];
+        const Real Vt = (Real)sig, VE = (Real)(uw * sig - Pi);
+        Real r, mn, mt, E, FI[4];
+        load_side(f + 2, f + 1, r, mn, mt, E, Real(-1));  // fluid 2, above
+        lf_face(r, -mn, mt, E, r, mn, mt, E, gamma, gm1, FI);
+        S.fz[0][f][cc] = FI[0];
+        S.fz[1][f][cc] = FI[2] - Vt;
+        S.fz[2][f][cc] = FI[1];
+        S.fz[3][f][cc] = FI[3] - VE;
+        load_side(f + 1, f, r, mn, mt, E, Real(1));  // fluid 1, below
+        lf_face(r, mn, mt, E, r, -mn, mt, E, gamma, gm1, FI);
+        S.fg[0][cc] = FI[0];
+        S.fg[1][cc] = FI[2] - Vt;
+        S.fg[2][cc] = FI[1];
+        S.fg[3][cc] = FI[3] - VE;
+      } else {
+        Real lr, lmn, lmt, lE, rr_, rmn, rmt, rE, FI[4], FV[4];
+        load_side(f + 1, f, lr, lmn, lmt, lE, Real(1));
+        load_side(f + 2, f + 1, rr_, rmn, rmt, rE, Real(-1));
+        lf_face(lr, lmn, lmt, lE, rr_, rmn, rmt, rE, gamma, gm1, FI);
+        const int k = kd;
+        const Real mu = k < n1 ? mu1 : mu2, kap = k < n1 ? kap1 : kap2;
+        const Real inv_dn = (Real)(k < n1 ? g.inv_dz1 : g.inv_dz2);
+        visc_face(S.v[1][f][cc + 1], S.v[0][f][cc + 1], S.v[2][f][cc + 1], S.tx[1][f][cc], S.tx[0][f][cc],
+                  S.v[1][f + 1][cc + 1], S.v[0][f + 1][cc + 1], S.v[2][f + 1][cc + 1], S.tx[1][f + 1][cc],
+                  S.tx[0][f + 1][cc], inv_dn, mu, kap, FV);
+        S.fz[0][f][cc] = FI[0] - FV[0];
+        S.fz[1][f][cc] = FI[2] - FV[2];
+        S.fz[2][f][cc] = FI[1] - FV[1];
+        S.fz[3][f][cc] = FI[3] - FV[3];
+      }
+    } else {
+      const int x = e - NZF;
+      const int rr = x / (TX + 1), f = x - rr * (TX + 1);
+      const int k = k0 + rr;
+      if (k >= row_hi) continue;
+      // face between columns i0+f-1 (L, ring col f) and i0+f (R, ring col f+1)
+      const Real lr = S.q[0][rr + 2][f + 1] + S.hx[0][rr][f];
+      const Real lmn = S.q[1][rr + 2][f + 1] + S.hx[1][rr][f];
+      const Real lmt = S.q[2][rr + 2][f + 1] + S.hx[2][rr][f];
+      const Real lE = S.q[3][rr + 2][f + 1] + S.hx[3][rr][f];
+      const Real rr_ = S.q[0][rr + 2][f + 2] - S.hx[0][rr][f + 1];
+      const Real rmn = S.q[1][rr + 2][f + 2] - S.hx[1][rr][f + 1];
+      const Real rmt = S.q[2][rr + 2][f + 2] - S.hx[2][rr][f + 1];
+      const Real rE = S.q[3][rr + 2][f + 2] - S.hx[3][rr][f + 1];
+      Real FI[4], FV[4];
+      lf_face(lr, lmn, lmt, lE, rr_, rmn, rmt, rE, gamma, gm1, FI);
+      const Real mu = k < n1 ? mu1 : mu2, kap = k < n1 ? kap1 : kap2;
+      visc_face(S.v[0][rr + 1][f], S.v[1][rr + 1][f], S.v[2][rr + 1][f], S.tz[0][rr][f], S.tz[1][rr][f],
+                S.v[0][rr + 1][f + 1], S.v[1][rr + 1][f + 1], S.v[2][rr + 1][f + 1], S.tz[0][rr][f + 1],
+                S.tz[1][rr][f + 1], (Real)g.inv_dx, mu, kap, FV);
+      S.fx[0][rr][f] = FI[0] - FV[0];
+      S.fx[1][rr][f] = FI[1] - FV[1];
+      S.fx[2][rr][f] = FI[2] - FV[2];
+      S.fx[3][rr][f] = FI[3] - FV[3];
+    }
+  }
+  __syncthreads();
+
+  // ---- 5. R = -div F* + s and the stage combination ----------------------
+  {
+    const int rr = tid / TX, cc = tid - rr * TX;
+    const int k = k0 + rr, i = i0 + cc;
+    if (k >= row_hi || i >= nx) return;
+    const Real inv_dx = (Real)g.inv_dx;
+    const Real inv_dz = (Real)(k < n1 ? g.inv_dz1 : g.inv_dz2);
+    const bool under_gamma = (k == n1 - 1);
+    Real R[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const Real up = under_gamma ? S.fg[c][cc] : S.fz[c][rr + 1][cc];
+      R[c] = (S.fx[c][rr][cc] - S.fx[c][rr][cc + 1]) * inv_dx + (S.fz[c][rr][cc] - up) * inv_dz;
+    }
+    const Real Gr = (Real)g.G;
+    R[2] -= S.q[0][rr + 2][cc + 2] * Gr;
+    R[3] -= S.q[2][rr + 2][cc + 2] * Gr;
+
+    const size_t row_off = (size_t)k * g.pitch + i;
+    if (a.rhs_only) {
+#pragma unroll
+      for (int c = 0; c < 4; c++) a.rhs_out[(size_t)c * plane + row_off] = (double)R[c];
+      return;
+    }
+    Store* Ra_w = reinterpret_cast<Store*>(a.b.Ra);
+    const int st = a.stage;
+    const double h2 = g.dt / (2.0 * g.m);
+    if (k >= g.n1_r) {
+      // fast region: m Heun substeps of dt/m
+      if (!(st & 1)) {
+#pragma unroll
+        for (int c = 0; c < 4; c++) Ra_w[(size_t)c * plane + row_off] = (Store)R[c];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          const size_t o = (size_t)c * plane + row_off;
+          a.qF_next[o] = a.qF[o] + h2 * ((double)Ra[o] + (double)R[c]);
+        }
+      }
+    } else if (k >= g.nS_r) {
+      // buffer: RK2 restarted from q_n each substep, weights 1/(2m)
+      const size_t pb = (size_t)(g.n1_r - g.nS_r) * g.pitch;
+      const size_t ob = (size_t)(k - g.nS_r) * g.pitch + i;
+      const bool last = (st == 2 * g.m - 1);
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const size_t o = (size_t)c * plane + row_off;
+        double* acc = a.b.accB + (size_t)c * pb + ob;
+        if (!(st & 1)) Ra_w[o] = (Store)R[c];
+        if (st == 0) {
+          *acc = (double)R[c];
+        } else if (last) {
+          *acc = a.b.qA[o] + h2 * (*acc + (double)R[c]);
+        } else {
+          *acc = *acc + (double)R[c];
+        }
+      }
+    } else {
+      // slow region: evaluated at stages 1 and 2 only (Algorithm 1)
+      const size_t ps = (size_t)g.nS_r * g.pitch;
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const size_t o = (size_t)c * plane + row_off;
+        if (st == 0) {
+          Ra_w[o] = (Store)R[c];
+        } else {
+          a.b.accS[(size_t)c * ps + row_off] = a.b.qA[o] + (0.5 * g.dt) * ((double)Ra[o] + (double)R[c]);
+        }
+      }
+    }
+  }
+}
+
+}  // namespace mprk

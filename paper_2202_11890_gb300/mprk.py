@@ -1,0 +1,256 @@
+"""Thin ctypes binding of libmprk.so (C ABI declared in include/mprk.h).
+
+The functions keep the C names and only marshal arguments; every step of the
+computation runs in the library's CUDA kernels. Arrays are numpy float64
+(host) or torch CUDA float64 tensors (device), in the layout [4][nz][nx].
+
+The library must be built first (``paper_2202_11890_gb300.build.build()``).
+There is no CPU fallback: without the library, or without a GPU, these calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MPRK_OK = 0
+MPRK_EINVAL = -1
+MPRK_ENOMEM = -2
+MPRK_EBUDGET = -3
+MPRK_ECUDA = -4
+MPRK_ENONFINITE = -5
+MPRK_ECFL = -6
+MPRK_ETIMEOUT = -7
+MPRK_EBUSY = -8
+MPRK_ENOTFOUND = -9
+
+MPRK_FP64 = 0
+MPRK_FP32FLUX = 1
+MPRK_SCHEME_MPRK2 = 0
+MPRK_SCHEME_SR_RK2 = 1
+MPRK_WALL_NOSLIP = 0
+MPRK_WALL_SLIP = 1
+MPRK_HOST = 0
+MPRK_DEVICE = 1
+
+MPRK_REQ_PENDING = 1
+MPRK_REQ_RUNNING = 2
+MPRK_REQ_DONE = 3
+
+
+class mprk_config(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("nz_S", C.c_int), ("nz_B", C.c_int), ("nz_F", C.c_int),
+        ("m", C.c_int), ("precision", C.c_int), ("scheme", C.c_int), ("wall", C.c_int),
+        ("diag_every", C.c_int), ("reserved", C.c_int),
+        ("dt", C.c_double), ("cfl", C.c_double), ("dx", C.c_double), ("dz1", C.c_double),
+        ("dz2", C.c_double), ("gamma", C.c_double), ("Pr", C.c_double), ("mu1", C.c_double),
+        ("mu2", C.c_double), ("G", C.c_double),
+    ]
+
+    @property
+    def nz(self) -> int:
+        return self.nz_S + self.nz_B + self.nz_F
+
+    @property
+    def shape(self):
+        return (4, self.nz, self.nx)
+
+
+class MprkError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mprk error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libmprk.so (built in-tree). Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(paper_2202_11890_gb300.build.build())")
+    L = C.CDLL(path)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+    cfgp = C.POINTER(mprk_config)
+    sig = {
+        "mprk_config_default": (ip, [cfgp, ip, ip, ip, ip, ip]),
+        "mprk_create": (ip, [cfgp, vp, ip, vp, C.POINTER(vp)]),
+        "mprk_destroy": (ip, [vp]),
+        "mprk_step": (ip, [vp, ip]),
+        "mprk_get_state": (ip, [vp, vp, ip]),
+        "mprk_set_state": (ip, [vp, vp, ip]),
+        "mprk_diagnostics": (ip, [vp, dp]),
+        "mprk_sync": (ip, [vp]),
+        "mprk_status": (ip, [vp]),
+        "mprk_info": (ip, [vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                           C.POINTER(vp)]),
+        "mprk_rhs": (ip, [vp, vp, vp, ip, ip]),
+        "mprk_profile_step": (ip, [vp, dp, C.POINTER(C.c_longlong), ip]),
+        "mprk_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def mprk_last_error() -> str:
+    return lib().mprk_last_error().decode()
+
+
+def _check(rc: int) -> int:
+    if rc != MPRK_OK:
+        raise MprkError(rc, mprk_last_error())
+    return rc
+
+
+def _ptr(a):
+    """(address, location) of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+        return a.ctypes.data, MPRK_HOST
+    import torch  # device memory comes from torch
+    assert isinstance(a, torch.Tensor) and a.dtype == torch.float64 and a.is_contiguous()
+    return a.data_ptr(), (MPRK_DEVICE if a.is_cuda else MPRK_HOST)
+
+
+def mprk_config_default(nx: int, nz_S: int, nz_B: int, nz_F: int, m: int, **overrides) -> mprk_config:
+    cfg = mprk_config()
+    _check(lib().mprk_config_default(C.byref(cfg), nx, nz_S, nz_B, nz_F, m))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def mprk_create(cfg: mprk_config, q0, stream=None) -> int:
+    addr, loc = _ptr(q0)
+    h = C.c_void_p()
+    s = None if stream is None else C.c_void_p(int(stream))
+    _check(lib().mprk_create(C.byref(cfg), C.c_void_p(addr), loc, s, C.byref(h)))
+    return h.value
+
+
+def mprk_destroy(h: int) -> None:
+    _check(lib().mprk_destroy(C.c_void_p(h)))
+
+
+def mprk_step(h: int, n: int) -> None:
+    _check(lib().mprk_step(C.c_void_p(h), int(n)))
+
+
+def mprk_get_state(h: int, out) -> None:
+    addr, loc = _ptr(out)
+    _check(lib().mprk_get_state(C.c_void_p(h), C.c_void_p(addr), loc))
+
+
+def mprk_set_state(h: int, q) -> None:
+    addr, loc = _ptr(q)
+    _check(lib().mprk_set_state(C.c_void_p(h), C.c_void_p(addr), loc))
+
+
+def mprk_diagnostics(h: int) -> np.ndarray:
+    out = np.zeros(16)
+    _check(lib().mprk_diagnostics(C.c_void_p(h), out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def mprk_sync(h: int) -> None:
+    _check(lib().mprk_sync(C.c_void_p(h)))
+
+
+def mprk_status(h: int) -> int:
+    return int(lib().mprk_status(C.c_void_p(h)))
+
+
+def mprk_info(h: int) -> dict:
+    dt = C.c_double()
+    cs = C.c_longlong()
+    nb = C.c_longlong()
+    st = C.c_void_p()
+    _check(lib().mprk_info(C.c_void_p(h), C.byref(dt), C.byref(cs), C.byref(nb), C.byref(st)))
+    return {"dt": dt.value, "cell_stages_per_step": cs.value, "device_bytes": nb.value,
+            "stream": st.value or 0}
+
+
+def mprk_rhs(h: int, W, R, k_lo: int, k_hi: int) -> None:
+    wa, wl = _ptr(W)
+    ra, rl = _ptr(R)
+    if wl != MPRK_DEVICE or rl != MPRK_DEVICE:
+        raise ValueError("mprk_rhs takes device tensors")
+    _check(lib().mprk_rhs(C.c_void_p(h), C.c_void_p(wa), C.c_void_p(ra), k_lo, k_hi))
+
+
+def mprk_profile_step(h: int):
+    """Per-launch durations (ms) and cell-stages of one un-captured slow step."""
+    cap = 2 * 64 + 1
+    ms = np.zeros(cap)
+    cells = np.zeros(cap, dtype=np.int64)
+    n = lib().mprk_profile_step(C.c_void_p(h), ms.ctypes.data_as(C.POINTER(C.c_double)),
+                                cells.ctypes.data_as(C.POINTER(C.c_longlong)), cap)
+    if n < 0:
+        raise MprkError(n, mprk_last_error())
+    return ms[:n].copy(), cells[:n].copy()
+
+
+class Instance:
+    """Owning handle: ``Instance(cfg, q0)``; ``step(n)``; ``state()``."""
+
+    def __init__(self, cfg: mprk_config, q0, stream=None):
+        self.cfg = cfg
+        self.h = mprk_create(cfg, q0, stream)
+
+    def step(self, n: int = 1) -> None:
+        mprk_step(self.h, n)
+
+    def state(self) -> np.ndarray:
+        out = np.empty(self.cfg.shape)
+        mprk_get_state(self.h, out)
+        return out
+
+    def set_state(self, q) -> None:
+        mprk_set_state(self.h, q)
+
+    def diagnostics(self) -> np.ndarray:
+        return mprk_diagnostics(self.h)
+
+    def info(self) -> dict:
+        return mprk_info(self.h)
+
+    def sync(self) -> None:
+        mprk_sync(self.h)
+
+    def status(self) -> int:
+        return mprk_status(self.h)
+
+    def close(self) -> None:
+        if self.h:
+            mprk_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

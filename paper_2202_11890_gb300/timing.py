@@ -1,0 +1,33 @@
+"""CUDA-event timing on an instance's own stream (torch supplies the events)."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import mprk as M
+
+
+def time_steps(h: int, stream_ptr: int, steps: int) -> float:
+    """Milliseconds for `steps` slow steps, events recorded on the stream the
+    step graph is launched on."""
+    import torch
+    ext = torch.cuda.ExternalStream(stream_ptr)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(ext):
+        e0.record(ext)
+        M.mprk_step(h, steps)
+        e1.record(ext)
+    e1.synchronize()
+    return float(e0.elapsed_time(e1))
+
+
+def stage_kernel_times(h: int, stream_ptr: int, reps: int = 3):
+    """Summed duration (ms) of the stage-kernel launches of one slow step and
+    the cell-stages they computed, median over `reps` profiled steps."""
+    tot, cells = [], None
+    for _ in range(reps):
+        ms, c = M.mprk_profile_step(h)
+        stage = c > 0
+        tot.append(float(ms[stage].sum()))
+        cells = int(c[stage].sum())
+    return float(np.median(tot)), cells

@@ -1,0 +1,67 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, exports every function include/mprk.h declares, and rejects
+invalid configurations before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from paper_2202_11890_gb300 import build as B
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(mprk_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = B.build()
+    return C.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["mprk_create", "mprk_step", "mprk_destroy", "mprk_get_state",
+                     "mprk_set_state", "mprk_diagnostics", "mprk_last_error", "mprk_rhs"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_invalid_configs_are_rejected_without_a_device(lib):
+    from paper_2202_11890_gb300 import mprk as M
+    q = np.ones((4, 12, 8))
+    cases = [dict(nz_B=3), dict(nz_B=2), dict(m=0), dict(nx=3), dict(precision=7),
+             dict(scheme=9), dict(wall=5), dict(dt=-1.0), dict(mu1=0.0), dict(reserved=1)]
+    for over in cases:
+        base = dict(nx=8, nz_S=4, nz_B=4, nz_F=4, m=2)
+        geo = {k: over.pop(k) for k in list(over) if k in base}
+        base.update(geo)
+        cfg = M.mprk_config_default(**base)
+        for k, v in over.items():
+            setattr(cfg, k, v)
+        h = C.c_void_p()
+        rc = M.lib().mprk_create(C.byref(cfg), q.ctypes.data_as(C.c_void_p), M.MPRK_HOST, None,
+                                 C.byref(h))
+        assert rc == M.MPRK_EINVAL, (base, over, rc)
+        assert M.mprk_last_error()
+
+
+def test_config_default_matches_the_paper_constants(lib):
+    from paper_2202_11890_gb300 import mprk as M
+    cfg = M.mprk_config_default(64, 30, 4, 30, 4)
+    assert cfg.gamma == 1.4 and cfg.Pr == 0.72
+    assert cfg.mu1 == 1.0 / 20000 and cfg.mu2 == 1.0 / 5000
+    assert cfg.G == 0.008140864714 and cfg.dx == 10.0 / 64

@@ -1,0 +1,268 @@
+"""Parity of the CUDA library with the FP64 CPU oracle, through the C ABI.
+
+Bars: the FP64 path matches the oracle to 1e-12 relative (per component,
+max norm scaled by the component's max) per slow step and for the
+right-hand side alone; the FP32-flux mode to 1e-5 relative after a run.
+
+Why 1e-12 for R as well: R is a difference of face fluxes of order one
+(pressure) divided by dx, and cancels to values of order 1e-2, so rounding
+differences of a few ulp in the fluxes show up as 1e-14..1e-13 relative to
+max |R|. A real mistake in any term shows up at 1e-3 or above."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2202_11890_gb300 import workloads as W
+from pairs import oracle_threads, pair, rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_11890_gb300 import build
+    build.build()
+    oracle_threads()
+
+
+def M():
+    from paper_2202_11890_gb300 import mprk
+    return mprk
+
+
+def gpu_rhs(cfg, W_np, k_lo=0, k_hi=None):
+    mp = M()
+    k_hi = cfg.nz if k_hi is None else k_hi
+    with mp.Instance(cfg, W_np) as inst:
+        Wd = torch.from_numpy(W_np).cuda()
+        Rd = torch.zeros_like(Wd)
+        mp.mprk_rhs(inst.h, Wd, Rd, k_lo, k_hi)
+        inst.sync()
+        return Rd.cpu().numpy()
+
+
+RHS_CASES = [
+    # grid (nx, nS, nB, nF), kwargs
+    ((64, 30, 4, 30), {}),
+    ((37, 9, 5, 11), {}),                       # ragged in x and z
+    ((5, 2, 4, 2), {}),                         # tiny
+    ((40, 7, 6, 9), dict(wall=1)),              # slip walls
+    ((33, 6, 4, 7), dict(mu1=0.02, mu2=0.05)),  # strong viscosity
+    ((48, 10, 4, 12), dict(dz2=0.07)),          # refined fluid 2
+]
+
+
+@pytest.mark.parametrize("dims,kw", RHS_CASES)
+def test_rhs_matches_oracle(dims, kw):
+    kw = dict(kw)
+    g = W.Grid(*dims)
+    if "dz2" in kw:
+        g.dz2 = kw.pop("dz2")
+    q = W.gaussian_bumps(g, 17, sigma_cells=2.5, amp=0.05)
+    cfg, P, _ = pair(g, 2, dt=0.01, **kw)
+    R_or = O.rhs(P, q)
+    R_gpu = gpu_rhs(cfg, q)
+    assert np.all(rel_err(R_gpu, R_or) < 1e-12), rel_err(R_gpu, R_or)
+
+
+def test_rhs_row_ranges():
+    g = W.Grid(45, 10, 6, 13)
+    q = W.gaussian_bumps(g, 3, sigma_cells=2.0, amp=0.05)
+    cfg, P, _ = pair(g, 2, dt=0.01)
+    for lo, hi in [(0, g.nS), (g.nS, g.nz), (g.n1 - 1, g.n1 + 1), (3, 4), (0, g.nz)]:
+        R_or = np.zeros_like(q)
+        O.rhs(P, q, lo, hi, out=R_or)
+        R_gpu = gpu_rhs(cfg, q, lo, hi)
+        assert np.all(rel_err(R_gpu[:, lo:hi], R_or[:, lo:hi]) < 1e-12)
+        outside = np.ones(g.nz, bool)
+        outside[lo:hi] = False
+        assert np.all(R_gpu[:, outside] == 0.0)
+
+
+STEP_CASES = [
+    ((64, 30, 4, 30), 4, {}),      # the 64x64 plain workload's grid and rate
+    ((37, 9, 5, 11), 1, {}),
+    ((37, 9, 5, 11), 2, {}),
+    ((50, 12, 16, 14), 8, {}),
+    ((29, 6, 4, 9), 3, dict(wall=1)),
+    ((40, 8, 4, 8), 4, dict(mu1=0.01, mu2=0.02)),
+    ((5, 2, 4, 2), 2, {}),
+]
+
+
+@pytest.mark.parametrize("dims,m,kw", STEP_CASES)
+def test_step_matches_oracle_every_step(dims, m, kw):
+    """Per slow step from the same q_n: GPU step vs oracle step."""
+    mp = M()
+    g = W.Grid(*dims)
+    q = W.gaussian_bumps(g, 29, sigma_cells=3.0)
+    cfg, P, dt = pair(g, m, q0=q, **kw)
+    with mp.Instance(cfg, q) as inst:
+        for _ in range(3):
+            q_or, _ = O.mprk_step(P, q)
+            inst.set_state(q)
+            inst.step(1)
+            q_gpu = inst.state()
+            err = rel_err(q_gpu, q_or)
+            assert np.all(err < 1e-12), err
+            q = q_or
+
+
+def test_plain_64_whole_run_drift():
+    """The 64x64, m = 4 workload for 100 slow steps: the GPU run alone against
+    the oracle run alone (drift over the whole run is reported, bar 1e-10)."""
+    mp = M()
+    wl = W.plain_64()
+    q0 = wl.initial_state()
+    cfg, P, dt = pair(wl.grid, wl.m, q0=q0)
+    q_or, _ = O.mprk_step(P, q0, wl.steps)
+    with mp.Instance(cfg, q0) as inst:
+        inst.step(wl.steps)
+        q_gpu = inst.state()
+        d_gpu = inst.diagnostics()
+    err = rel_err(q_gpu, q_or)
+    print("whole-run drift per component:", err)
+    assert np.all(err < 1e-10), err
+    d_or = O.diagnostics(P, q_or)
+    assert np.allclose(d_gpu[:8], d_or[:8], rtol=1e-13, atol=1e-15)
+    assert np.allclose(d_gpu[8:11], d_or[8:11], rtol=1e-12)
+    assert d_gpu[11] == 0 and d_gpu[14] == wl.steps
+    d0 = O.diagnostics(P, q0)
+    assert abs(d_gpu[0] - d0[0]) / d0[0] < 1e-13 and abs(d_gpu[4] - d0[4]) / d0[4] < 1e-13
+
+
+def test_single_rate_matches_oracle_rk2():
+    """The single-rate baseline: m Heun steps of dt/m over the whole grid."""
+    mp = M()
+    g = W.Grid(41, 10, 4, 12)
+    q = W.gaussian_bumps(g, 5, sigma_cells=3.0)
+    m = 4
+    cfg, P, dt = pair(g, m, q0=q, scheme=mp.MPRK_SCHEME_SR_RK2)
+    q_or = O.rk2_step(P, q, dt / m, m)
+    with mp.Instance(cfg, q) as inst:
+        inst.step(1)
+        q_gpu = inst.state()
+    assert np.all(rel_err(q_gpu, q_or) < 1e-12)
+
+
+def test_fp32_flux_mode_error_after_run():
+    """FP32 fluxes with FP64 stage values and combinations: <= 1e-5 relative
+    after 100 slow steps of the 64x64 workload; mass drift reported."""
+    mp = M()
+    wl = W.plain_64()
+    q0 = wl.initial_state()
+    cfg, P, dt = pair(wl.grid, wl.m, q0=q0, precision=mp.MPRK_FP32FLUX)
+    q_or, _ = O.mprk_step(P, q0, wl.steps)
+    with mp.Instance(cfg, q0) as inst:
+        inst.step(wl.steps)
+        q_gpu = inst.state()
+        d = inst.diagnostics()
+    err = rel_err(q_gpu, q_or)
+    d0 = O.diagnostics(P, q0)
+    print("fp32flux error per component:", err, "mass drift", (d[0] - d0[0]) / d0[0],
+          (d[4] - d0[4]) / d0[4])
+    assert np.all(err < 1e-5), err
+
+
+def test_auto_dt_matches_oracle():
+    mp = M()
+    wl = W.plain_64()
+    q0 = wl.initial_state()
+    cfg, P, dt = pair(wl.grid, wl.m, q0=q0)
+    cfg.dt = 0.0
+    with mp.Instance(cfg, q0) as inst:
+        assert abs(inst.info()["dt"] - dt) / dt < 1e-14
+
+
+def test_checkpoint_resume_is_bitwise():
+    mp = M()
+    g = W.Grid(36, 8, 4, 10)
+    q = W.gaussian_bumps(g, 8)
+    cfg, P, dt = pair(g, 2, q0=q)
+    with mp.Instance(cfg, q) as a:
+        a.step(3)
+        ck = a.state()
+        a.step(2)
+        qa = a.state()
+    with mp.Instance(cfg, ck) as b:
+        b.step(2)
+        qb = b.state()
+    assert np.array_equal(qa, qb)
+
+
+def test_runs_are_deterministic():
+    mp = M()
+    g = W.Grid(70, 12, 6, 15)
+    q = W.fourier_modes(g, 4)
+    cfg, P, dt = pair(g, 4, q0=q)
+    outs = []
+    for _ in range(2):
+        with mp.Instance(cfg, q) as inst:
+            inst.step(5)
+            outs.append((inst.state(), inst.diagnostics()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_bad_initial_state_is_rejected():
+    mp = M()
+    g = W.Grid(16, 4, 4, 4)
+    q = W.rest_state(g)
+    cfg, P, dt = pair(g, 2, dt=0.01)
+    bad = q.copy()
+    bad[2, 3, 5] = np.nan
+    with pytest.raises(mp.MprkError) as ei:
+        mp.Instance(cfg, bad)
+    assert ei.value.code == mp.MPRK_ENONFINITE
+    bad = q.copy()
+    bad[0, 1, 1] = -1.0
+    with pytest.raises(mp.MprkError) as ei:
+        mp.Instance(cfg, bad)
+    assert ei.value.code == mp.MPRK_ENONFINITE
+
+
+def test_monitoring_flags_a_blow_up():
+    """A step far beyond the stability limit makes the state non-finite; the
+    in-graph monitoring sets the status word (no device trap)."""
+    mp = M()
+    g = W.Grid(32, 8, 4, 8)
+    q = W.gaussian_bumps(g, 2, amp=0.05)
+    cfg, P, dt = pair(g, 2, q0=q, diag_every=1)
+    cfg.dt = dt * 40
+    with mp.Instance(cfg, q) as inst:
+        inst.step(60)
+        assert inst.status() in (mp.MPRK_ENONFINITE, mp.MPRK_ECFL)
+
+
+def test_device_resident_input():
+    mp = M()
+    g = W.Grid(40, 9, 4, 9)
+    q = W.gaussian_bumps(g, 12)
+    cfg, P, dt = pair(g, 2, q0=q)
+    qd = torch.from_numpy(q).cuda()
+    with mp.Instance(cfg, qd) as inst:
+        inst.step(1)
+        out = torch.empty_like(qd)
+        mp.mprk_get_state(inst.h, out)
+        q_or, _ = O.mprk_step(P, q)
+        assert np.all(rel_err(out.cpu().numpy(), q_or) < 1e-12)
+
+
+@pytest.mark.slow
+def test_large_2048_one_step_full_size():
+    """The 2048x1024, m = 8 workload at full size, in the launch configuration
+    the benchmark times: one slow step against the oracle over every cell."""
+    mp = M()
+    wl = W.large_2048()
+    q0 = wl.initial_state()
+    cfg, P, dt = pair(wl.grid, wl.m, q0=q0)
+    q_or, _ = O.mprk_step(P, q0)
+    with mp.Instance(cfg, q0) as inst:
+        inst.step(1)
+        q_gpu = inst.state()
+    err = rel_err(q_gpu, q_or)
+    assert np.all(err < 1e-12), err
