@@ -152,6 +152,39 @@ int mprk_rhs(mprk_instance* inst, const double* W_dev, double* R_dev, int k_lo, 
  * Synchronises. */
 int mprk_profile_step(mprk_instance* inst, double* launch_ms, long long* launch_cells, int cap);
 
+/* ---- allocation-free stepping ------------------------------------------ */
+/* Largest scratch mprk_step_static may use: 32 MiB. In FP64 a grid needs
+ * 8 bytes x 4 components x (2 nx nz + nx (nz_S + nz_B)), each part rounded
+ * up to 256 bytes; that is about 350,000 cells, e.g. 512 x 512. */
+#define MPRK_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* Advance a state the caller already holds on the device by n_slow_steps
+ * slow steps, in place, without allocating any memory. The paper has no
+ * counterpart; this exists for callers that cannot call cudaMalloc. Examples
+ * are code inside another framework's memory pool or allocator, processes
+ * that reserve all device memory up front, and real-time loops where an
+ * allocation could block or fail mid-run.
+ *
+ * q_dev: device buffer [4][nz][nx] of double (the layout above), read and
+ * overwritten; the caller owns it. cfg: as for mprk_create, but dt must be
+ * given (> 0); diag_every is ignored. cuda_stream: the cudaStream_t to run
+ * on (NULL = the default stream). Asynchronous: the result is in q_dev once
+ * the stream reaches this work. It matches mprk_step on the same input.
+ *
+ * Scratch comes from one fixed array of MPRK_STATIC_SCRATCH_BYTES that every
+ * GPU loading the library holds until the process exits. A configuration
+ * needing more is rejected with MPRK_EINVAL and a message giving both sizes.
+ * The function never calls cudaMalloc, cudaFree or any allocating routine.
+ * Its first call on a device (with that device current) looks up the
+ * array's device address and sets the kernels' shared-memory limits; make
+ * that first call before any stream capture on the device. All calls on a
+ * device share the array, which keeps the last call's contents, so calls
+ * whose work overlaps on the GPU race and give undefined results: serialise
+ * them (one stream, or events). No scratch entry is read before the call
+ * writes it, so nothing is cleared between calls. Errors: MPRK_EINVAL,
+ * MPRK_ECUDA; the message is in mprk_last_error(). */
+int mprk_step_static(const mprk_config* cfg, double* q_dev, int n_slow_steps, void* cuda_stream);
+
 /* ---- errors ------------------------------------------------------------ */
 /* Message for the last failing call on this thread ("" if none). */
 const char* mprk_last_error(void);

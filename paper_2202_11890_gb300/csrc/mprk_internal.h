@@ -14,6 +14,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <string>
 
 namespace mprk {
 
@@ -77,5 +78,8 @@ cudaError_t launch_diag(const Geom& g, const double* q, double* partials, int nb
 int diag_blocks(const Geom& g);
 cudaError_t prepare_kernels();  // one-time attribute setup (dynamic shared memory)
 size_t stage_smem_bytes(int precision);
+
+// Sets the calling thread's message for mprk_last_error (mprk_runtime.cu).
+void set_last_error(const std::string& msg);
 
 }  // namespace mprk

@@ -17,8 +17,12 @@
 using namespace mprk;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+void mprk::set_last_error(const std::string& msg) { g_err = msg; }
+
+namespace {
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];

@@ -1,0 +1,178 @@
+// mprk_static.cu — the allocation-free entry point mprk_step_static.
+//
+// Some callers cannot call cudaMalloc. Examples are code running inside
+// another framework's memory pool or a custom allocator, a process whose
+// device memory is already reserved up front, and real-time loops where an
+// allocation could block or fail at the wrong moment. For them this file
+// advances a state that the caller already holds on the device. It keeps
+// its scratch (the odd-substep fast state, the stage-one right-hand side and
+// the buffer and slow accumulators) in one file-scope __device__ array of
+// fixed size. Every GPU that loads the library holds that array until the
+// process exits.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "mprk.h"
+#include "mprk_internal.h"
+
+using namespace mprk;
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = MPRK_STATIC_SCRATCH_BYTES;
+
+// Scratch shared by every call on a device. In host code this name is only a
+// host-side stand-in for the symbol, not a device address: device pointers
+// come from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
+
+std::mutex g_mu;
+void* g_scratch_ptr[64] = {nullptr};  // device address of g_scratch, per device
+
+int sfail(int code, const std::string& msg) {
+  set_last_error(msg);
+  return code;
+}
+
+// Once per device, with that device current: look up the array's device
+// address and set the kernels' shared-memory limits.
+int setup_device(int dev, void** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (dev < 0 || dev >= 64) return sfail(MPRK_ECUDA, "device ordinal out of range");
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p)
+      return sfail(MPRK_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    e = prepare_kernels();
+    if (e != cudaSuccess)
+      return sfail(MPRK_ECUDA, std::string("kernel setup: ") + cudaGetErrorString(e));
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return MPRK_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Scratch bytes a configuration needs: qB | Ra | accB | accS, pitch = nx.
+size_t scratch_bytes(const mprk_config* c) {
+  if (!c || c->nx <= 0 || c->nz_S < 0 || c->nz_B < 0 || c->nz_F < 0) return 0;
+  const size_t nz = (size_t)c->nz_S + c->nz_B + c->nz_F;
+  const size_t plane = nz * (size_t)c->nx;
+  const size_t rsz = c->precision == MPRK_FP64 ? 8 : 4;
+  const bool mprk2 = c->scheme == MPRK_SCHEME_MPRK2;
+  const size_t nB = mprk2 ? (size_t)c->nz_B : 0, nS = mprk2 ? (size_t)c->nz_S : 0;
+  return align256(4 * plane * 8) + align256(4 * plane * rsz) + align256(4 * nB * c->nx * 8) +
+         align256(4 * nS * c->nx * 8);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mprk_step_static(const mprk_config* cfg, double* q_dev, int n_slow_steps, void* cuda_stream) {
+  if (!cfg || !q_dev) return sfail(MPRK_EINVAL, "NULL argument");
+  if (n_slow_steps < 0) return sfail(MPRK_EINVAL, "negative step count");
+  if (cfg->nx < 4 || cfg->nz_S < 2 || cfg->nz_B < 4 || cfg->nz_F < 2 || cfg->m < 1 ||
+      cfg->m > 64 || cfg->reserved != 0)
+    return sfail(MPRK_EINVAL, "invalid grid, buffer width (>= 4), rate ratio or reserved field");
+  if (cfg->precision != MPRK_FP64 && cfg->precision != MPRK_FP32FLUX)
+    return sfail(MPRK_EINVAL, "unknown precision");
+  if (cfg->scheme != MPRK_SCHEME_MPRK2 && cfg->scheme != MPRK_SCHEME_SR_RK2)
+    return sfail(MPRK_EINVAL, "unknown scheme");
+  if (cfg->wall != MPRK_WALL_NOSLIP && cfg->wall != MPRK_WALL_SLIP)
+    return sfail(MPRK_EINVAL, "unknown wall type");
+  if (!(cfg->dt > 0.0))
+    return sfail(MPRK_EINVAL, "mprk_step_static needs an explicit dt > 0");
+  if (!(cfg->dx > 0) || !(cfg->dz1 > 0) || !(cfg->dz2 > 0) || !(cfg->gamma > 1.0) ||
+      !(cfg->Pr > 0.0) || !(cfg->mu1 > 0.0) || !(cfg->mu2 > 0.0) || !(cfg->G >= 0.0))
+    return sfail(MPRK_EINVAL, "invalid physical parameters");
+  const size_t need = scratch_bytes(cfg);
+  if (need > kStaticScratchBytes)
+    return sfail(MPRK_EINVAL, "grid needs " + std::to_string(need) +
+                                  " bytes of scratch, more than the static maximum of " +
+                                  std::to_string(kStaticScratchBytes) + " bytes");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return sfail(MPRK_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  void* base = nullptr;
+  int rc = setup_device(dev, &base);
+  if (rc) return rc;
+
+  // geometry: the caller's state is the home buffer, unpadded (pitch = nx)
+  Geom g;
+  memset(&g, 0, sizeof g);
+  g.nx = cfg->nx;
+  g.pitch = cfg->nx;
+  g.nz = cfg->nz_S + cfg->nz_B + cfg->nz_F;
+  g.n1 = cfg->nz_S + cfg->nz_B;
+  const bool mprk2 = cfg->scheme == MPRK_SCHEME_MPRK2;
+  g.nS_r = mprk2 ? cfg->nz_S : 0;
+  g.n1_r = mprk2 ? g.n1 : 0;
+  g.nS_g = cfg->nz_S;
+  g.m = cfg->m;
+  g.wall = cfg->wall;
+  g.dt = cfg->dt;
+  g.inv_dx = 1.0 / cfg->dx;
+  g.inv_dz1 = 1.0 / cfg->dz1;
+  g.inv_dz2 = 1.0 / cfg->dz2;
+  g.gamma = cfg->gamma;
+  g.gm1 = cfg->gamma - 1.0;
+  g.mu1 = cfg->mu1;
+  g.mu2 = cfg->mu2;
+  const double cp = 1.0 / (cfg->gamma - 1.0);
+  g.kap1 = cp * cfg->mu1 / cfg->Pr;
+  g.kap2 = cp * cfg->mu2 / cfg->Pr;
+  g.G = cfg->G;
+  g.bu = 2.0 * cfg->mu1 * cfg->mu2 / (cfg->dz2 * cfg->mu1 + cfg->dz1 * cfg->mu2);
+  g.bT = 2.0 * g.kap1 * g.kap2 / (cfg->dz2 * g.kap1 + cfg->dz1 * g.kap2);
+  g.cu1 = cfg->dz1 / (2.0 * cfg->mu1);
+  g.cT1 = cfg->dz1 / (2.0 * g.kap1);
+
+  // carve the scratch: qB | Ra | accB | accS (each 256-byte aligned)
+  const size_t plane = (size_t)g.nz * g.pitch;
+  const size_t rsz = cfg->precision == MPRK_FP64 ? 8 : 4;
+  unsigned char* p = static_cast<unsigned char*>(base);
+  Bufs b;
+  b.qA = q_dev;
+  b.qB = reinterpret_cast<double*>(p);
+  p += align256(4 * plane * 8);
+  b.Ra = p;
+  p += align256(4 * plane * rsz);
+  b.accB = reinterpret_cast<double*>(p);
+  p += align256(4 * (size_t)(g.n1_r - g.nS_r) * g.nx * 8);
+  b.accS = reinterpret_cast<double*>(p);
+
+  // Nothing in the scratch needs clearing: every entry a step reads was
+  // written earlier in the same step (stage 1 writes R_a and the buffer sum
+  // on every row, stage 2 writes the fast state of substep 1 and the slow
+  // result, and padding does not exist because the pitch is nx).
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int tiles_x = (g.nx + TX - 1) / TX;
+  for (int step = 0; step < n_slow_steps; step++) {
+    for (int st = 0; st < 2 * g.m; st++) {
+      StageArgs a;
+      memset(&a, 0, sizeof a);
+      a.g = g;
+      a.b = b;
+      const bool even_sub = ((st / 2) % 2) == 0;
+      a.qF = even_sub ? b.qA : b.qB;
+      a.qF_next = even_sub ? b.qB : b.qA;
+      a.stage = st;
+      a.row0 = st < 2 ? 0 : g.nS_r;
+      a.tiles_x = tiles_x;
+      const int tiles_z = (g.nz - a.row0 + TZ - 1) / TZ;
+      e = launch_stage(a, cfg->precision, tiles_x * tiles_z, s);
+      if (e != cudaSuccess) return sfail(MPRK_ECUDA, std::string("stage launch: ") + cudaGetErrorString(e));
+    }
+    e = launch_finalize(g, b, g.m & 1, s);
+    if (e != cudaSuccess) return sfail(MPRK_ECUDA, std::string("completion launch: ") + cudaGetErrorString(e));
+  }
+  return MPRK_OK;
+}
+
+}  // extern "C"

@@ -100,6 +100,7 @@ def lib():
                            C.POINTER(vp)]),
         "mprk_rhs": (ip, [vp, vp, vp, ip, ip]),
         "mprk_profile_step": (ip, [vp, dp, C.POINTER(C.c_longlong), ip]),
+        "mprk_step_static": (ip, [cfgp, vp, ip, vp]),
         "mprk_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -206,6 +207,19 @@ def mprk_profile_step(h: int):
     if n < 0:
         raise MprkError(n, mprk_last_error())
     return ms[:n].copy(), cells[:n].copy()
+
+
+MPRK_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
+
+
+def mprk_step_static(cfg: mprk_config, q_dev, n: int, stream=None) -> None:
+    """Advance a device tensor in place by n slow steps without allocating
+    (scratch lives in the library's fixed device array)."""
+    addr, loc = _ptr(q_dev)
+    if loc != MPRK_DEVICE:
+        raise ValueError("mprk_step_static takes a device tensor")
+    s = None if stream is None else C.c_void_p(int(stream))
+    _check(lib().mprk_step_static(C.byref(cfg), C.c_void_p(addr), int(n), s))
 
 
 class Instance:
