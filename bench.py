@@ -32,14 +32,46 @@ sys.path.insert(0, ROOT)
 from paper_2202_11890_gb300 import workloads as W  # noqa: E402
 
 METRIC = "cell-stage updates/s"
-# stage launches dominate; algorithmic work per cell-stage
-FP64_FLOPS_PER_CELL_STAGE = 418.0
-FP32_FLOPS_PER_CELL_STAGE = 418.0
-HBM_BYTES_PER_CELL_STAGE_FP64 = 80.0
-HBM_BYTES_PER_CELL_STAGE_FP32 = 64.0
+# algorithmic floating-point work per cell-stage of the stage kernel (see
+# the design doc, counted from the formulas: 2.16 faces and 1.33 ring cells per
+# tile cell)
+FLOPS_PER_CELL_STAGE = 418.0
 # FP64 unit count x clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
+
+
+def algorithmic_bytes(g: W.Grid, m: int, fp64: bool):
+    """HBM bytes one slow step must move, each array element read or written
+    once per launch that needs it (stencil halos are L2 hits). Returns
+    (bytes of the stage launches, bytes of the step completion)."""
+    nx, nS, nB, nF = g.nx, g.nS, g.nB, g.nF
+    if fp64:
+        d, r, q, a = 32, 32, 32, 32  # stage state read, R_a, q (double), accumulator
+    else:
+        d, r, q, a = 16, 16, 32, 32  # float shadow, float R_a, double q and accumulator
+    tot = 0
+    for st in range(2 * m):
+        odd = st % 2 == 1
+        last = st == 2 * m - 1
+        # buffer rows: read the stage state (and R_a on odd stages), write R_a
+        # on even stages, read and write the accumulator (write only at stage
+        # 1), and at the last stage read q (the mixed mode reads it apart from
+        # its float shadow)
+        B = d + r + (a if st == 0 else 2 * a) + (q if (last and not fp64) else 0)
+        # slow rows: stage 1 reads the state and writes R_a; stage 2 reads both
+        # and writes q_{n+1} to the accumulator
+        S = (d + r) if st == 0 else ((d + r + a + (0 if fp64 else q)) if st == 1 else 0)
+        if fp64:
+            F = (d + r + q) if odd else (d + r)       # odd: read q, R_a; write q_next
+        else:
+            F = (d + r + q + q + d) if odd else (d + r)  # odd: read d, R_a, q; write q, d
+        tot += nx * (nS * S + nB * B + nF * F)
+    if fp64:
+        fin = nx * (nS + nB) * 64 + (nx * nF * 64 if m % 2 else 0)
+    else:
+        fin = nx * (nS + nB) * 80 + nx * nF * (80 if m % 2 else 48)
+    return tot, fin
 
 
 def workload(name: str) -> W.Workload:
@@ -169,13 +201,12 @@ def run_ours(args):
     # instance stream around each launch of one un-captured slow step)
     stage_ms, stage_cells = T.stage_kernel_times(inst.h, stream, reps=3)
     fp64 = cfg.precision == M.MPRK_FP64
-    flops = FP64_FLOPS_PER_CELL_STAGE if fp64 else FP32_FLOPS_PER_CELL_STAGE
-    peak = FP64_PEAK_GFLOPS if fp64 else FP32_PEAK_GFLOPS
+    peak_alu = FP64_PEAK_GFLOPS if fp64 else FP32_PEAK_GFLOPS
     # achieved over all stage launches of a step: algorithmic work / kernel time
-    ach_gflops = stage_cells * flops / (stage_ms * 1e-3) / 1e9
+    ach_gflops = stage_cells * FLOPS_PER_CELL_STAGE / (stage_ms * 1e-3) / 1e9
     peaks, src = measured_peaks()
-    hbm_bytes = HBM_BYTES_PER_CELL_STAGE_FP64 if fp64 else HBM_BYTES_PER_CELL_STAGE_FP32
-    ach_gbs = stage_cells * hbm_bytes / (stage_ms * 1e-3) / 1e9
+    stage_bytes, fin_bytes = algorithmic_bytes(g, wl.m, fp64)
+    ach_gbs = stage_bytes / (stage_ms * 1e-3) / 1e9
 
     # end to end through the C ABI with host buffers: pinned host state in,
     # one slow step, state out, every step
@@ -202,12 +233,20 @@ def run_ours(args):
             "config": {"workload": wl.name, "nx": g.nx, "nz": g.nz, "rows_S_B_F": [g.nS, g.nB, g.nF],
                        "m": wl.m, "cell_stages_per_step": cs, "parallelism": f"replicas x{ws}",
                        "l2": "working set > L2 (about 4 states of 67 MB); no flush"},
-            "roofline": {"bound": "alu", "achieved": ach_gflops, "peak": peak,
-                         "unit": "GFLOP/s", "frac": ach_gflops / peak, "traffic": None,
-                         "peak_source": "FP64 unit count x max clock (152 SMs x 2 DFMA/clk)"
-                         if fp64 else "FP32 unit count x max clock",
-                         "hbm_achieved_gbs": ach_gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
-                         "hbm_frac": ach_gbs / peaks["hbm_gbs"], "hbm_peak_source": src},
+            "roofline": (
+                {"bound": "alu", "achieved": ach_gflops, "peak": peak_alu, "unit": "GFLOP/s",
+                 "frac": ach_gflops / peak_alu, "traffic": None,
+                 "peak_source": "FP64 unit count x max clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                 "hbm_achieved_gbs": ach_gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
+                 "hbm_frac": ach_gbs / peaks["hbm_gbs"], "hbm_peak_source": src}
+                if fp64 else
+                {"bound": "hbm", "achieved": ach_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": ach_gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                 "alu_achieved_gflops": ach_gflops, "alu_peak_gflops": peak_alu}),
+            "kernel": {"name": "stage_kernel" if fp64 else "stage_kernel_mixed",
+                       "ms_per_step": stage_ms, "cell_stages_per_step": stage_cells,
+                       "algorithmic_bytes_per_step": stage_bytes,
+                       "completion_bytes_per_step": fin_bytes},
             "e2e": {"value": e2e_value, "unit": "cell-stages/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
             "gpu_launches": launches_per_step * args.steps,
@@ -218,6 +257,148 @@ def run_ours(args):
         print(json.dumps(out))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_batched(args):
+    """256 uneven instances (sides log-uniform in [64, 512], m in {2, 4, 8},
+    buffer 4-16 rows, FP64): one persistent launch per slow step
+    (mprk_step_batch) against the same instances stepped one after another
+    with mprk_step on the same stream."""
+    import torch
+    from paper_2202_11890_gb300 import build as B
+    from paper_2202_11890_gb300 import mprk as M
+    from paper_2202_11890_gb300 import timing as T
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    wls = W.batched_256(count=args.batch_count)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    insts, q0s = [], []
+    for wl in wls:
+        g = wl.grid
+        cfg = M.mprk_config_default(g.nx, g.nS, g.nB, g.nF, wl.m)
+        q0 = wl.initial_state()
+        q0s.append(q0)
+        insts.append(M.Instance(cfg, q0, stream=sp))
+    hs = [i.h for i in insts]
+    cs = sum(i.info()["cell_stages_per_step"] for i in insts)
+    cells = sum(wl.grid.nx * wl.grid.nz for wl in wls)
+
+    def plain(n):
+        for _ in range(n):
+            for h in hs:
+                M.mprk_step(h, 1)
+
+    def batched(n):
+        M.mprk_step_batch(hs, n)
+
+    # warm-up both paths (graphs, plan)
+    plain(args.warmup)
+    batched(args.warmup)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    with sampler:
+        t_batch = T.time_region(sp, lambda: batched(args.steps))
+    t_plain = T.time_region(sp, lambda: plain(args.steps))
+    # equal accuracy: same start, same steps, both paths, bitwise
+    same = True
+    for i, q0 in zip(insts[:8], q0s[:8]):
+        i.set_state(q0)
+    M.mprk_step_batch(hs[:8], 2)
+    out_b = [i.state() for i in insts[:8]]
+    for i, q0 in zip(insts[:8], q0s[:8]):
+        i.set_state(q0)
+        i.step(2)
+    for i, ob in zip(insts[:8], out_b):
+        same = same and bool(np.array_equal(i.state(), ob))
+    value = cs * args.steps / (t_batch * 1e-3)
+    plain_value = cs * args.steps / (t_plain * 1e-3)
+    for i in insts:
+        i.close()
+    out = {
+        "metric": METRIC, "value": value, "unit": "cell-stages/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"batched_{len(wls)}_uneven_fp64", "instances": len(wls), "cells": cells,
+                   "cell_stages_per_step": cs, "parallelism": "replicas x1"},
+        "batched_vs_plain": {"batched": value, "plain_sequential": plain_value,
+                             "speedup": value / plain_value, "bitwise_equal": same,
+                             "plain_ms_per_step": t_plain / args.steps},
+        "gpu_launches": args.steps,
+        "clocks": sampler.summary(),
+    }
+    print(json.dumps(out))
+
+
+def run_served(args):
+    """Poisson arrivals (mean 200 requests/s) of FP32-flux solves with sides
+    log-uniform in [32, 1024], m in {2, 4, 8}, buffer 4-16 rows and slow steps
+    log-uniform in [10, 1000], admitted under a 150 GB HBM budget. Reports the
+    aggregate cell-stage rate and p50/p99 latency (finish - submit on the
+    server's clock) of the requests after the warm-up ones."""
+    import torch
+    from paper_2202_11890_gb300 import build as B
+    from paper_2202_11890_gb300 import mprk as M
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    n_warm, n_meas = args.served_warmup, args.served_requests
+    arrivals, wls = W.served_stream(n_warm + n_meas, rate_hz=args.rate)
+    reqs = []
+    for wl in wls:
+        g = wl.grid
+        cfg = M.mprk_config_default(g.nx, g.nS, g.nB, g.nF, wl.m)
+        cfg.precision = M.MPRK_FP32FLUX
+        reqs.append((cfg, wl.initial_state(), wl.steps, wl.cell_stages_per_step() * wl.steps))
+    srv = M.mprk_server_create(hbm_budget_bytes=int(args.budget_gb * 1e9), max_slots=args.slots)
+    sampler = ClockSampler(torch.cuda.current_device())
+    tickets = {}
+    done = {}
+    t0 = time.perf_counter()
+    nxt = 0
+    with sampler:
+        while len(done) < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and arrivals[nxt] <= now:
+                cfg, q, n, _ = reqs[nxt]
+                tickets[M.mprk_submit(srv, cfg, q, n)] = nxt
+                nxt += 1
+            for t, j in list(tickets.items()):
+                st, err, stats = M.mprk_poll(srv, t)
+                if st == M.MPRK_REQ_DONE:
+                    M.mprk_poll(srv, t, np.empty(reqs[j][1].shape))  # read and release
+                    done[j] = (err, stats)
+                    del tickets[t]
+            time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    sstats = M.mprk_server_stats(srv)
+    M.mprk_server_destroy(srv)
+    meas = [done[j] for j in range(n_warm, len(reqs))]
+    lat = np.array([s["t_finish"] - s["t_submit"] for _, s in meas])
+    errors = sum(1 for e, _ in meas if e)
+    t_first = min(s["t_submit"] for _, s in meas)
+    t_last = max(s["t_finish"] for _, s in meas)
+    cells = sum(reqs[j][3] for j in range(n_warm, len(reqs)))
+    value = cells / (t_last - t_first)
+    offered = sum(r[3] for r in reqs) / arrivals[-1]
+    out = {
+        "metric": METRIC, "value": value, "unit": "cell-stages/s", "n_gpus": ws,
+        "steps": n_meas, "warmup": n_warm, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 flux / f64 accumulate",
+        "data": "synthetic",
+        "config": {"workload": "served_poisson_fp32flux", "rate_hz": args.rate, "requests": n_meas,
+                   "budget_gb": args.budget_gb, "max_slots": args.slots, "parallelism": "replicas x1"},
+        "served": {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                   "mean_latency_s": float(lat.mean()), "errors": errors, "offered_cell_stages_per_s": offered,
+                   "batched_steps": sstats[2], "wall_s": wall},
+        "gpu_launches": int(sstats[2]),
+        "clocks": sampler.summary(),
+    }
+    print(json.dumps(out))
 
 
 def oracle_sample(wl: W.Workload, cols: int):
@@ -298,7 +479,14 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large_2048", choices=["large_2048", "plain_64", "mixed_4096"])
+    ap.add_argument("--workload", default="large_2048",
+                    choices=["large_2048", "plain_64", "mixed_4096", "batched_256", "served"])
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--served-warmup", type=int, default=200)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--slots", type=int, default=4096)
+    ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--precision", default="", choices=["", "fp64", "fp32flux"])
     ap.add_argument("--ref-cols", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -307,6 +495,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched_256":
+        run_batched(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_ours(args)
 

@@ -108,6 +108,27 @@ int mprk_destroy(mprk_instance* inst);
  * mprk_status reads. */
 int mprk_step(mprk_instance* inst, int n_slow_steps);
 
+/* Advance `count` instances by n_slow_steps each with one persistent,
+ * graph-captured launch per slow step that covers every instance's stage
+ * tiles and step completions. Items run in stage order; a tile of stage s of
+ * an instance waits (bounded, about one second) for all stage s-1 tiles of
+ * that instance. Instances may differ in size, m, buffer width and dt, but
+ * must share the device and the precision. The batch runs on the first
+ * instance's stream, ordered after and before the other instances' streams
+ * with events. Each instance's result equals what mprk_step gives it alone
+ * (same tile code, same arithmetic). Asynchronous. A wait that gives up sets
+ * MPRK_ETIMEOUT in the affected instances' status words (mprk_status); their
+ * states are then undefined. In-graph monitoring (diag_every) does not run
+ * in batched steps. Errors: MPRK_EINVAL, MPRK_ENOMEM, MPRK_ECUDA. */
+int mprk_step_batch(mprk_instance* const* insts, int count, int n_slow_steps);
+
+/* Test hook for the bounded waits of mprk_step_batch: one batched slow step
+ * in which the tiles of stage `stage` of instance inst_index never report
+ * completion, and each wait gives up after wait_cycles clock cycles. The
+ * waiting tiles give up, set the timeout bit and drain; nothing hangs. */
+int mprk_batch_test_withhold(mprk_instance* const* insts, int count, int inst_index, int stage,
+                             long long wait_cycles);
+
 /* Copy the current state q_n to q_out ([4][nz][nx], location MPRK_HOST or
  * MPRK_DEVICE). Synchronises the instance stream. */
 int mprk_get_state(mprk_instance* inst, double* q_out, int location);
@@ -152,6 +173,16 @@ int mprk_rhs(mprk_instance* inst, const double* W_dev, double* R_dev, int k_lo, 
  * Synchronises. */
 int mprk_profile_step(mprk_instance* inst, double* launch_ms, long long* launch_cells, int cap);
 
+/* Test hook for the FP32-flux mode's conversions, which use integer bit
+ * operations because this GPU converts between float and double at the FP64
+ * rate. For n device doubles in_dev[j] it writes the bit-operation
+ * round-to-nearest narrowing and the hardware cast (float), and the
+ * bit-operation and hardware widening of (float)in_dev[j] (double). All
+ * buffers are device memory of n entries. Runs on the default stream and
+ * synchronises. */
+int mprk_selftest_convert(const double* in_dev, int n, float* narrow_dev, float* narrow_hw_dev,
+                          double* widen_dev, double* widen_hw_dev);
+
 /* ---- allocation-free stepping ------------------------------------------ */
 /* Largest scratch mprk_step_static may use: 32 MiB. In FP64 a grid needs
  * 8 bytes x 4 components x (2 nx nz + nx (nz_S + nz_B)), each part rounded
@@ -184,6 +215,67 @@ int mprk_profile_step(mprk_instance* inst, double* launch_ms, long long* launch_
  * writes it, so nothing is cleared between calls. Errors: MPRK_EINVAL,
  * MPRK_ECUDA; the message is in mprk_last_error(). */
 int mprk_step_static(const mprk_config* cfg, double* q_dev, int n_slow_steps, void* cuda_stream);
+
+/* ---- serving ----------------------------------------------------------- */
+typedef struct mprk_server mprk_server;
+
+typedef struct {
+  long long hbm_budget_bytes; /* device bytes the resident instances may hold */
+  int max_slots;              /* most instances resident at once              */
+  int device;                 /* CUDA device ordinal                         */
+  int max_queue;              /* queued requests beyond which submit is EBUSY */
+  int reserved;               /* must be 0                                   */
+} mprk_server_config;
+
+#define MPRK_REQ_PENDING 1 /* queued, not admitted          */
+#define MPRK_REQ_RUNNING 2 /* resident on the device         */
+#define MPRK_REQ_DONE 3    /* finished; result ready to read */
+
+typedef struct {
+  double t_submit;        /* seconds on the server's clock (starts at create) */
+  double t_admit;
+  double t_finish;
+  long long cell_stages;  /* cell right-hand-side evaluations done            */
+  long long device_bytes; /* bytes the request held while resident           */
+  int steps_done;
+  int error;              /* 0 or an MPRK_E* code for this request           */
+} mprk_stats;
+
+/* Start a server thread on a device. It admits queued requests in arrival
+ * order while a slot is free and the HBM ledger has room, advances all
+ * resident instances together by one batched slow step at a time (the
+ * persistent kernel of mprk_step_batch, one launch per precision), and
+ * retires each request when it reaches its step count. Requests join and
+ * leave between slow steps while the others keep running (continuous
+ * batching). Uploads and downloads run on a copy stream that overlaps the
+ * compute stream, and instance memory is stream-ordered (cudaMallocAsync and
+ * cudaFreeAsync). Errors: MPRK_EINVAL, MPRK_ECUDA. */
+int mprk_server_create(const mprk_server_config* cfg, mprk_server** out);
+
+/* Queue a solve of n_slow_steps from q0_host ([4][nz][nx], copied before
+ * return); cfg->dt == 0 picks dt at admission as mprk_create does.
+ * Non-blocking. Returns MPRK_EBUDGET if
+ * the instance can never fit the budget, MPRK_EBUSY if the queue is full,
+ * MPRK_EINVAL for a bad configuration. A non-finite or non-positive q0 is
+ * reported later as that request's MPRK_ENONFINITE. */
+int mprk_submit(mprk_server* srv, const mprk_config* cfg, const double* q0_host, int n_slow_steps,
+                uint64_t* ticket);
+
+/* Non-blocking status of a ticket: *status is MPRK_REQ_PENDING, _RUNNING or
+ * _DONE. When DONE and q_out_host is non-null, the final state is copied
+ * there ([4][nz][nx]) and the ticket is released. stats may be NULL. Returns
+ * the request's error code (0 if none) or MPRK_ENOTFOUND. */
+int mprk_poll(mprk_server* srv, uint64_t ticket, int* status, double* q_out_host,
+              mprk_stats* stats);
+
+/* Server-wide counters: out[0] requests done, out[1] cell stages done,
+ * out[2] batched slow steps launched, out[3] resident now, out[4] queued now,
+ * out[5] ledger bytes now, out[6] seconds since start, out[7] failed requests. */
+int mprk_server_stats(mprk_server* srv, double out[8]);
+
+/* Stop the server thread (queued and resident requests are dropped) and free
+ * its resources. */
+int mprk_server_destroy(mprk_server* srv);
 
 /* ---- errors ------------------------------------------------------------ */
 /* Message for the last failing call on this thread ("" if none). */

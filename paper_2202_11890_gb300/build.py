@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmprk.so")
-SOURCES = ["mprk_kernels.cu", "mprk_runtime.cu", "mprk_static.cu"]
+SOURCES = ["mprk_kernels.cu", "mprk_runtime.cu", "mprk_static.cu", "mprk_batch.cu", "mprk_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

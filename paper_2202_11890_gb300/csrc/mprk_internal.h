@@ -10,11 +10,16 @@
 //   accB [4][nB][pitch] double   running sum of the buffer right-hand sides,
 //                                then q_{n+1} on B rows
 //   accS [4][nS][pitch] double   q_{n+1} on S rows until the step ends
+// FP32-flux mode only:
+//   dA, dB [4][nz][pitch] float  deviations q - q_ref of qA, qB (float shadows)
+//   rowc [16][nz] float          per-row reference constants (stage_tile_mixed.cuh)
 #pragma once
 
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
+
+#include "mprk.h"
 
 namespace mprk {
 
@@ -44,7 +49,16 @@ struct Geom {
   double G;
   double bu, bT;       // interface bulk coefficients (App. B)
   double cu1, cT1;     // dz1/(2 mu1), dz1/(2 kappa1): wall states from fluid 1
+  double hF;           // dt / m
+  double h2;           // dt / (2 m)
+  double hdt;          // dt / 2
+  // the same constants rounded to float once on the host, so that float
+  // kernels never convert (conversions run at the FP64 rate on this GPU)
+  float gammaf, gm1f, mu1f, mu2f, kap1f, kap2f, Gf;
+  float inv_dxf, inv_dz1f, inv_dz2f;
+  float dtf, hFf, h2f;
 };
+
 
 // Buffers of one instance.
 struct Bufs {
@@ -53,6 +67,9 @@ struct Bufs {
   void* Ra;
   double* accB;
   double* accS;
+  float* dA;    // FP32-flux mode only (else null)
+  float* dB;
+  float* rowc;
 };
 
 // One launch of the stage kernel over rows [row0, nz) of one instance.
@@ -61,6 +78,8 @@ struct StageArgs {
   Bufs b;
   const double* qF;   // base state of F rows this substep (qA or qB)
   double* qF_next;    // F rows of the next substep (the other one)
+  const float* dF;    // FP32-flux mode: shadows matching qF and qF_next
+  float* dF_next;
   int stage;          // 0-based stage index i in [0, 2m)
   int row0;           // first row of the launch (0 at stages 0, 1; nS_r later)
   int tiles_x;        // tiles across x
@@ -70,16 +89,84 @@ struct StageArgs {
   const double* rhs_in;  // full stage state when rhs_only
 };
 
+// Arguments of stage st of one slow step: F rows ping-pong between the A and
+// B buffers at every fast substep.
+__host__ __device__ inline StageArgs stage_args(const Geom& g, const Bufs& b, int st) {
+  StageArgs a{};
+  a.g = g;
+  a.b = b;
+  const bool even_sub = ((st / 2) % 2) == 0;
+  a.qF = even_sub ? b.qA : b.qB;
+  a.qF_next = even_sub ? b.qB : b.qA;
+  a.dF = even_sub ? b.dA : b.dB;
+  a.dF_next = even_sub ? b.dB : b.dA;
+  a.stage = st;
+  a.row0 = st < 2 ? 0 : g.nS_r;
+  a.tiles_x = (g.nx + TX - 1) / TX;
+  return a;
+}
+__host__ __device__ inline int stage_tiles(const StageArgs& a) {
+  const int hi = a.rhs_only ? a.rhs_hi : a.g.nz;
+  return a.tiles_x * ((hi - a.row0 + TZ - 1) / TZ);
+}
+
 // Launchers (mprk_kernels.cu). All enqueue on `stream` and return the launch error.
 cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStream_t stream);
 cudaError_t launch_finalize(const Geom& g, const Bufs& b, int m_odd, cudaStream_t stream);
+// FP32-flux mode: per-row reference of q (row means, refd [4][nz] scratch)
+// and the float shadow dA = q - q_ref of qA.
+cudaError_t launch_reference(const Geom& g, const double* q, double* refd, float* rowc,
+                             cudaStream_t stream);
+cudaError_t launch_shadow(const Geom& g, const double* q, const float* rowc, float* d,
+                          cudaStream_t stream);
 cudaError_t launch_diag(const Geom& g, const double* q, double* partials, int nblocks,
                         double* out, unsigned* status, double cfl_limit, cudaStream_t stream);
 int diag_blocks(const Geom& g);
+cudaError_t launch_convert_check(const double* in, int n, float* nar, float* nar_hw, double* wid,
+                                 double* wid_hw, cudaStream_t stream);
 cudaError_t prepare_kernels();  // one-time attribute setup (dynamic shared memory)
 size_t stage_smem_bytes(int precision);
 
+// Fills g from a configuration; pitch is the row pitch of the buffers
+// (mprk_runtime.cu).
+void geom_from_config(const mprk_config& c, int pitch, Geom* g);
+
 // Sets the calling thread's message for mprk_last_error (mprk_runtime.cu).
 void set_last_error(const std::string& msg);
+
+}  // namespace mprk
+
+struct mprk_instance;
+
+namespace mprk {
+// Instance internals the batch path uses (mprk_runtime.cu).
+int instance_view(const mprk_instance* inst, Geom* g, Bufs* b, int* precision, cudaStream_t* stream,
+                  unsigned** status);
+cudaStream_t instance_stream(const mprk_instance* inst);
+void instance_count_steps(mprk_instance* inst, int n);
+// Drops cached batch plans that mention inst (mprk_batch.cu).
+void batch_forget(const void* inst);
+// One batched launch per slow step on an explicit stream (mprk_batch.cu).
+int batch_step_on(mprk_instance* const* insts, int count, int n, cudaStream_t stream, long long* cell_stages);
+// A persistent batch launcher for a resident set that changes between slow
+// steps (mprk_batch.cu); one launch per call, no graph.
+struct BatchRunner;
+BatchRunner* runner_create(int precision, cudaStream_t stream);
+void runner_destroy(BatchRunner* r);
+int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long long* cell_stages);
+// Forget the cached work list (the resident set changed; an address may be reused).
+void runner_invalidate(BatchRunner* r);
+// Device bytes mprk_create allocates for a configuration (mprk_runtime.cu).
+long long instance_bytes(const mprk_config& c);
+// Configuration check of mprk_create (sets the error message).
+int validate_config(const mprk_config* c);
+// mprk_create with an option: stream_ordered instances allocate with
+// cudaMallocAsync on cuda_stream, free with cudaFreeAsync, capture no graph
+// and advance only through batches (the server's instances).
+int create_instance(const mprk_config* cfg, const double* q0, int q0_location, void* cuda_stream,
+                    bool stream_ordered, mprk_instance** out);
+long long instance_steps(const mprk_instance* inst);
+long long instance_device_bytes(const mprk_instance* inst);
+void destroy_instance(mprk_instance* inst);
 
 }  // namespace mprk

@@ -6,19 +6,26 @@
 //                   energy; Courant numbers; non-finite count)
 #include "mprk_internal.h"
 #include "stage_tile.cuh"
+#include "stage_tile_mixed.cuh"
 
 namespace mprk {
 
 template <typename Real, typename Store>
-__global__ void __launch_bounds__(NTHREADS, (sizeof(Real) == 8 ? 2 : 3))
+__global__ void __launch_bounds__(NTHREADS, 2)
     stage_kernel(const StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TileSmem<Real>& S = *reinterpret_cast<TileSmem<Real>*>(smem_raw);
   stage_tile<Real, Store>(a, blockIdx.x, S);
 }
 
+__global__ void __launch_bounds__(NTHREADS, 3) stage_kernel_mixed(const StageArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MixedSmem& S = *reinterpret_cast<MixedSmem*>(smem_raw);
+  stage_tile_mixed(a, blockIdx.x, S);
+}
+
 size_t stage_smem_bytes(int precision) {
-  return precision == 0 ? sizeof(TileSmem<double>) : sizeof(TileSmem<float>);
+  return precision == 0 ? sizeof(TileSmem<double>) : sizeof(MixedSmem);
 }
 
 cudaError_t prepare_kernels() {
@@ -26,8 +33,8 @@ cudaError_t prepare_kernels() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(TileSmem<double>));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(stage_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(TileSmem<float>));
+  return cudaFuncSetAttribute(stage_kernel_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(MixedSmem));
 }
 
 cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStream_t stream) {
@@ -35,17 +42,105 @@ cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStr
   if (precision == 0) {
     stage_kernel<double, double><<<n_tiles, NTHREADS, sizeof(TileSmem<double>), stream>>>(a);
   } else {
-    stage_kernel<float, float><<<n_tiles, NTHREADS, sizeof(TileSmem<float>), stream>>>(a);
+    stage_kernel_mixed<<<n_tiles, NTHREADS, sizeof(MixedSmem), stream>>>(a);
   }
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
+// FP32-flux mode set-up. Row means of q give the reference q_ref(k), rounded
+// to float; its derived constants are formed in double from the rounded
+// values and stored as float (layout in stage_tile_mixed.cuh).
+// ---------------------------------------------------------------------------
+__global__ void row_mean_kernel(const Geom g, const double* __restrict__ q, double* refd) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= g.nz) return;
+  const size_t plane = (size_t)g.nz * g.pitch;
+  for (int c = 0; c < 4; c++) {
+    double s = 0.0;
+    const double* row = q + (size_t)c * plane + (size_t)k * g.pitch;
+    for (int i = 0; i < g.nx; i++) s += row[i];
+    refd[c * g.nz + k] = (double)(float)(s / g.nx);
+  }
+}
+
+__device__ __forceinline__ double ref_pressure(const Geom& g, const double* refd, int k, double* ke) {
+  const double r = refd[k], mu = refd[g.nz + k], mw = refd[2 * g.nz + k], E = refd[3 * g.nz + k];
+  const double kk = 0.5 * (mu * mu + mw * mw) / r;
+  if (ke) *ke = kk;
+  return g.gm1 * (E - kk);
+}
+
+__global__ void row_const_kernel(const Geom g, const double* __restrict__ refd, float* rowc) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= g.nz) return;
+  const int nz = g.nz, n1 = g.n1;
+  const bool up_in = (k + 1 < nz) && ((k + 1 < n1) == (k < n1));
+  const bool dn_in = (k - 1 >= 0) && ((k - 1 < n1) == (k < n1));
+  for (int c = 0; c < 4; c++) {
+    const double own = refd[c * nz + k];
+    const double mir = (c == 2) ? -own : own;
+    const double up = up_in ? refd[c * nz + k + 1] : mir;
+    const double dn = dn_in ? refd[c * nz + k - 1] : mir;
+    rowc[c * nz + k] = (float)own;
+    rowc[(4 + c) * nz + k] = (float)(0.25 * (up - dn));
+    rowc[(8 + c) * nz + k] = (k + 1 < nz) ? (float)(own - refd[c * nz + k + 1]) : 0.f;
+  }
+  double ke;
+  const double p = ref_pressure(g, refd, k, &ke);
+  // reference pressure carried by the faces below and above row k: a wall
+  // or the interface carries the row's own p_ref, an interior face the mean
+  const bool wall_dn = (k == 0) || (k == n1), wall_up = (k == nz - 1) || (k == n1 - 1);
+  const double p_dn = wall_dn ? p : 0.5 * (p + ref_pressure(g, refd, k - 1, nullptr));
+  const double p_up = wall_up ? p : 0.5 * (p + ref_pressure(g, refd, k + 1, nullptr));
+  const double inv_dz = k < n1 ? g.inv_dz1 : g.inv_dz2;
+  rowc[12 * nz + k] = (float)ke;
+  rowc[13 * nz + k] = (float)((p_dn - p_up) * inv_dz - refd[k] * g.G);
+  rowc[14 * nz + k] = (float)p;
+  rowc[15 * nz + k] = 0.f;
+}
+
+cudaError_t launch_reference(const Geom& g, const double* q, double* refd, float* rowc,
+                             cudaStream_t stream) {
+  const int b = (g.nz + 127) / 128;
+  row_mean_kernel<<<b, 128, 0, stream>>>(g, q, refd);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  row_const_kernel<<<b, 128, 0, stream>>>(g, refd, rowc);
+  return cudaGetLastError();
+}
+
+__global__ void shadow_kernel(const Geom g, const double* __restrict__ q, const float* __restrict__ rowc,
+                              float* d) {
+  const long long total = 4LL * g.nz * g.nx;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e / ((long long)g.nz * g.nx));
+    const int rem = (int)(e - (long long)c * g.nz * g.nx);
+    const int k = rem / g.nx, i = rem - k * g.nx;
+    const size_t o = ((size_t)c * g.nz + k) * g.pitch + i;
+    d[o] = narrow(q[o] - (double)rowc[c * g.nz + k]);
+  }
+}
+
+cudaError_t launch_shadow(const Geom& g, const double* q, const float* rowc, float* d,
+                          cudaStream_t stream) {
+  const long long total = 4LL * g.nz * g.nx;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  shadow_kernel<<<blocks, 256, 0, stream>>>(g, q, rowc, d);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Step completion: S and B rows from accS / accB; F rows from qB when the
-// fast state ended in qB (odd m). One thread per (component, row, column).
+// fast state ended in qB (odd m). In the FP32-flux mode every row's float
+// shadow is also resynchronised to the new double state. One thread per
+// (component, row, column).
 // ---------------------------------------------------------------------------
 __global__ void finalize_kernel(const Geom g, const Bufs b, int m_odd) {
-  const int rows = m_odd ? g.nz : g.n1_r;
+  const bool mixed = b.dA != nullptr;
+  const int rows = (m_odd || mixed) ? g.nz : g.n1_r;
   const long long total = 4LL * rows * g.nx;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -56,18 +151,42 @@ __global__ void finalize_kernel(const Geom g, const Bufs b, int m_odd) {
     double v;
     if (k < g.nS_r) v = b.accS[((size_t)c * g.nS_r + k) * g.pitch + i];
     else if (k < g.n1_r) v = b.accB[((size_t)c * (g.n1_r - g.nS_r) + (k - g.nS_r)) * g.pitch + i];
-    else v = b.qB[o];
+    else v = m_odd ? b.qB[o] : b.qA[o];
     b.qA[o] = v;
+    if (mixed) b.dA[o] = narrow(v - (double)b.rowc[c * g.nz + k]);
   }
 }
 
 cudaError_t launch_finalize(const Geom& g, const Bufs& b, int m_odd, cudaStream_t stream) {
-  const int rows = m_odd ? g.nz : g.n1_r;
+  const int rows = (m_odd || b.dA != nullptr) ? g.nz : g.n1_r;
   if (rows == 0) return cudaSuccess;
   const long long total = 4LL * rows * g.nx;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   finalize_kernel<<<blocks, 256, 0, stream>>>(g, b, m_odd);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Test hook: the bit-operation conversions of the FP32-flux mode next to the
+// hardware conversions, for the same inputs.
+// ---------------------------------------------------------------------------
+__global__ void convert_check_kernel(const double* in, int n, float* nar, float* nar_hw, double* wid,
+                                     double* wid_hw) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double x = in[j];
+  nar[j] = narrow(x);
+  nar_hw[j] = (float)x;
+  const float f = (float)x;
+  wid[j] = widen(f);
+  wid_hw[j] = (double)f;
+}
+
+cudaError_t launch_convert_check(const double* in, int n, float* nar, float* nar_hw, double* wid,
+                                 double* wid_hw, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  convert_check_kernel<<<(n + 255) / 256, 256, 0, stream>>>(in, n, nar, nar_hw, wid, wid_hw);
   return cudaGetLastError();
 }
 

@@ -16,6 +16,9 @@
 
 using namespace mprk;
 
+// per-row float constants of the FP32-flux mode (stage_tile_mixed.cuh)
+constexpr int NROWC_HOST = 16;
+
 namespace {
 thread_local std::string g_err;
 }  // namespace
@@ -71,15 +74,19 @@ struct mprk_instance {
   int diag_nblocks;
   double* rhs_in;   // lazily allocated padded buffers for mprk_rhs
   double* rhs_out;
+  double* refd;     // FP32-flux mode: row means scratch [4][nz]
   cudaGraphExec_t exec;       // one slow step
   cudaGraphExec_t exec_diag;  // one slow step followed by monitoring
   long long steps_done;
   long long bytes;
+  bool stream_ordered;  // buffers from cudaMallocAsync on `stream` (server instances)
 };
 
 namespace {
 
-int validate(const mprk_config* c) {
+}  // namespace
+
+int mprk::validate_config(const mprk_config* c) {
   if (!c) return fail(MPRK_EINVAL, "config is NULL");
   if (c->nx < 4) return fail(MPRK_EINVAL, "nx = %d: need at least 4 columns", c->nx);
   if (c->nz_S < 2) return fail(MPRK_EINVAL, "nz_S = %d: need at least 2 slow rows", c->nz_S);
@@ -108,57 +115,23 @@ int validate(const mprk_config* c) {
   return MPRK_OK;
 }
 
-void fill_geom(mprk_instance* I) {
-  const mprk_config& c = I->cfg;
-  Geom& g = I->g;
-  g.nx = c.nx;
-  g.pitch = (c.nx + 31) / 32 * 32;
-  g.nz = c.nz_S + c.nz_B + c.nz_F;
-  g.n1 = c.nz_S + c.nz_B;
-  if (c.scheme == MPRK_SCHEME_MPRK2) {
-    g.nS_r = c.nz_S;
-    g.n1_r = g.n1;
-  } else {
-    g.nS_r = 0;
-    g.n1_r = 0;
-  }
-  g.nS_g = c.nz_S;
-  g.m = c.m;
-  g.wall = c.wall;
-  g.dt = c.dt;
-  g.inv_dx = 1.0 / c.dx;
-  g.inv_dz1 = 1.0 / c.dz1;
-  g.inv_dz2 = 1.0 / c.dz2;
-  g.gamma = c.gamma;
-  g.gm1 = c.gamma - 1.0;
-  g.mu1 = c.mu1;
-  g.mu2 = c.mu2;
-  const double cp = 1.0 / (c.gamma - 1.0);  // c~_p of App. A
-  g.kap1 = cp * c.mu1 / c.Pr;
-  g.kap2 = cp * c.mu2 / c.Pr;
-  g.G = c.G;
-  // bulk coefficients of App. B: 2 k1 k2 / (dz2 k1 + dz1 k2)
-  g.bu = 2.0 * c.mu1 * c.mu2 / (c.dz2 * c.mu1 + c.dz1 * c.mu2);
-  g.bT = 2.0 * g.kap1 * g.kap2 / (c.dz2 * g.kap1 + c.dz1 * g.kap2);
-  g.cu1 = c.dz1 / (2.0 * c.mu1);
-  g.cT1 = c.dz1 / (2.0 * g.kap1);
-}
+namespace {
+
+void fill_geom(mprk_instance* I) { geom_from_config(I->cfg, (I->cfg.nx + 31) / 32 * 32, &I->g); }
 
 void free_instance(mprk_instance* I) {
   if (!I) return;
-  if (I->stream) cudaStreamSynchronize(I->stream);
+  if (I->stream && !I->stream_ordered) cudaStreamSynchronize(I->stream);
   if (I->exec) cudaGraphExecDestroy(I->exec);
   if (I->exec_diag) cudaGraphExecDestroy(I->exec_diag);
-  cudaFree(I->b.qA);
-  cudaFree(I->b.qB);
-  cudaFree(I->b.Ra);
-  cudaFree(I->b.accB);
-  cudaFree(I->b.accS);
-  cudaFree(I->partials);
-  cudaFree(I->diag_dev);
-  cudaFree(I->status_dev);
-  cudaFree(I->rhs_in);
-  cudaFree(I->rhs_out);
+  void* bufs[] = {I->b.qA,     I->b.qB,     I->b.Ra,     I->b.accB, I->b.accS, I->partials, I->diag_dev,
+                  I->status_dev, I->rhs_in, I->rhs_out, I->b.dA,   I->b.dB,   I->b.rowc,   I->refd};
+  for (void* p : bufs) {
+    if (!p) continue;
+    // stream-ordered buffers go back to the pool after the stream's queued work
+    if (I->stream_ordered) cudaFreeAsync(p, I->stream);
+    else cudaFree(p);
+  }
   if (I->own_stream && I->stream) cudaStreamDestroy(I->stream);
   delete I;
 }
@@ -166,20 +139,9 @@ void free_instance(mprk_instance* I) {
 // Enqueue the stage launches and the completion of one slow step.
 int enqueue_step(mprk_instance* I, cudaStream_t s) {
   const Geom& g = I->g;
-  const int tiles_x = (g.nx + TX - 1) / TX;
   for (int st = 0; st < 2 * g.m; st++) {
-    StageArgs a;
-    memset(&a, 0, sizeof a);
-    a.g = g;
-    a.b = I->b;
-    const bool even_sub = ((st / 2) % 2) == 0;
-    a.qF = even_sub ? I->b.qA : I->b.qB;
-    a.qF_next = even_sub ? I->b.qB : I->b.qA;
-    a.stage = st;
-    a.row0 = st < 2 ? 0 : g.nS_r;
-    a.tiles_x = tiles_x;
-    const int tiles_z = (g.nz - a.row0 + TZ - 1) / TZ;
-    CU(launch_stage(a, I->precision, tiles_x * tiles_z, s));
+    const StageArgs a = stage_args(g, I->b, st);
+    CU(launch_stage(a, I->precision, stage_tiles(a), s));
   }
   CU(launch_finalize(g, I->b, g.m & 1, s));
   return MPRK_OK;
@@ -211,6 +173,7 @@ int copy_state_in(mprk_instance* I, const double* q, int loc) {
   cudaMemcpyKind kind = loc == MPRK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CU(cudaMemcpy2DAsync(I->b.qA, (size_t)g.pitch * 8, q, (size_t)g.nx * 8, (size_t)g.nx * 8,
                        (size_t)4 * g.nz, kind, I->stream));
+  if (I->b.dA && I->b.rowc) CU(launch_shadow(g, I->b.qA, I->b.rowc, I->b.dA, I->stream));
   return MPRK_OK;
 }
 
@@ -225,6 +188,96 @@ int run_diag(mprk_instance* I, double out[16]) {
 }
 
 }  // namespace
+
+int mprk::instance_view(const mprk_instance* I, Geom* g, Bufs* b, int* precision, cudaStream_t* stream,
+                        unsigned** status) {
+  if (!I) return fail(MPRK_EINVAL, "NULL instance");
+  *g = I->g;
+  *b = I->b;
+  *precision = I->precision;
+  *stream = I->stream;
+  *status = I->status_dev;
+  return MPRK_OK;
+}
+
+cudaStream_t mprk::instance_stream(const mprk_instance* I) { return I->stream; }
+
+long long mprk::instance_steps(const mprk_instance* I) { return I->steps_done; }
+
+long long mprk::instance_device_bytes(const mprk_instance* I) { return I->bytes; }
+
+void mprk::destroy_instance(mprk_instance* I) {
+  batch_forget(I);
+  free_instance(I);
+}
+
+void mprk::geom_from_config(const mprk_config& c, int pitch, Geom* gp) {
+  Geom& g = *gp;
+  memset(&g, 0, sizeof g);
+  g.nx = c.nx;
+  g.pitch = pitch;
+  g.nz = c.nz_S + c.nz_B + c.nz_F;
+  g.n1 = c.nz_S + c.nz_B;
+  if (c.scheme == MPRK_SCHEME_MPRK2) {
+    g.nS_r = c.nz_S;
+    g.n1_r = g.n1;
+  } else {
+    g.nS_r = 0;
+    g.n1_r = 0;
+  }
+  g.nS_g = c.nz_S;
+  g.m = c.m;
+  g.wall = c.wall;
+  g.dt = c.dt;
+  g.inv_dx = 1.0 / c.dx;
+  g.inv_dz1 = 1.0 / c.dz1;
+  g.inv_dz2 = 1.0 / c.dz2;
+  g.gamma = c.gamma;
+  g.gm1 = c.gamma - 1.0;
+  g.mu1 = c.mu1;
+  g.mu2 = c.mu2;
+  const double cp = 1.0 / (c.gamma - 1.0);  // c~_p of App. A
+  g.kap1 = cp * c.mu1 / c.Pr;
+  g.kap2 = cp * c.mu2 / c.Pr;
+  g.G = c.G;
+  // bulk coefficients of App. B: 2 k1 k2 / (dz2 k1 + dz1 k2)
+  g.bu = 2.0 * c.mu1 * c.mu2 / (c.dz2 * c.mu1 + c.dz1 * c.mu2);
+  g.bT = 2.0 * g.kap1 * g.kap2 / (c.dz2 * g.kap1 + c.dz1 * g.kap2);
+  g.cu1 = c.dz1 / (2.0 * c.mu1);
+  g.cT1 = c.dz1 / (2.0 * g.kap1);
+  g.hF = c.dt / c.m;
+  g.h2 = c.dt / (2.0 * c.m);
+  g.hdt = 0.5 * c.dt;
+  g.gammaf = (float)g.gamma;
+  g.gm1f = (float)g.gm1;
+  g.mu1f = (float)g.mu1;
+  g.mu2f = (float)g.mu2;
+  g.kap1f = (float)g.kap1;
+  g.kap2f = (float)g.kap2;
+  g.Gf = (float)g.G;
+  g.inv_dxf = (float)g.inv_dx;
+  g.inv_dz1f = (float)g.inv_dz1;
+  g.inv_dz2f = (float)g.inv_dz2;
+  g.dtf = (float)g.dt;
+  g.hFf = (float)g.hF;
+  g.h2f = (float)g.h2;
+}
+
+void mprk::instance_count_steps(mprk_instance* I, int n) { I->steps_done += n; }
+
+long long mprk::instance_bytes(const mprk_config& c) {
+  auto r16 = [](long long b) { return b == 0 ? 16LL : b; };
+  const long long pitch = (c.nx + 31) / 32 * 32;
+  const long long nz = (long long)c.nz_S + c.nz_B + c.nz_F;
+  const long long plane = nz * pitch;
+  const bool mprk2 = c.scheme == MPRK_SCHEME_MPRK2;
+  const long long nB = mprk2 ? c.nz_B : 0, nS = mprk2 ? c.nz_S : 0;
+  const long long rsz = c.precision == MPRK_FP64 ? 8 : 4;
+  long long b = 2 * 4 * plane * 8 + 4 * plane * rsz + r16(4 * nB * pitch * 8) + r16(4 * nS * pitch * 8);
+  b += 1024 * 16 * 8 + 16 * 8 + 16;  // monitoring partials (upper bound), results, status
+  if (c.precision != MPRK_FP64) b += 2 * 4 * plane * 4 + 16 * nz * 4 + 4 * nz * 8;
+  return b;
+}
 
 extern "C" {
 
@@ -254,11 +307,14 @@ int mprk_config_default(mprk_config* cfg, int nx, int nz_S, int nz_B, int nz_F, 
   return MPRK_OK;
 }
 
-int mprk_create(const mprk_config* cfg, const double* q0, int q0_location, void* cuda_stream,
-                mprk_instance** out) {
+}  // extern "C"
+
+int mprk::create_instance(const mprk_config* cfg, const double* q0, int q0_location, void* cuda_stream,
+                          bool stream_ordered, mprk_instance** out) {
   if (!out) return fail(MPRK_EINVAL, "out is NULL");
+  if (stream_ordered && !cuda_stream) return fail(MPRK_EINVAL, "stream-ordered instances need a stream");
   *out = nullptr;
-  int rc = validate(cfg);
+  int rc = validate_config(cfg);
   if (rc) return rc;
   if (!q0) return fail(MPRK_EINVAL, "q0 is NULL");
   if (q0_location != MPRK_HOST && q0_location != MPRK_DEVICE)
@@ -277,9 +333,21 @@ int mprk_create(const mprk_config* cfg, const double* q0, int q0_location, void*
   fill_geom(I);
   const Geom& g = I->g;
 
+  I->stream_ordered = stream_ordered;
+  if (cuda_stream) {
+    I->stream = (cudaStream_t)cuda_stream;
+    I->own_stream = false;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&I->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      free_instance(I);
+      return fail(MPRK_ECUDA, "stream create: %s", cudaGetErrorString(e));
+    }
+    I->own_stream = true;
+  }
   auto alloc = [&](void** p, size_t bytes) -> int {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = stream_ordered ? cudaMallocAsync(p, bytes, I->stream) : cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(MPRK_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
@@ -299,16 +367,12 @@ int mprk_create(const mprk_config* cfg, const double* q0, int q0_location, void*
     free_instance(I);
     return rc;
   }
-  if (cuda_stream) {
-    I->stream = (cudaStream_t)cuda_stream;
-    I->own_stream = false;
-  } else {
-    cudaError_t e = cudaStreamCreateWithFlags(&I->stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
-      free_instance(I);
-      return fail(MPRK_ECUDA, "stream create: %s", cudaGetErrorString(e));
-    }
-    I->own_stream = true;
+  if (I->precision == MPRK_FP32FLUX &&
+      ((rc = alloc((void**)&I->b.dA, 4 * plane * 4)) || (rc = alloc((void**)&I->b.dB, 4 * plane * 4)) ||
+       (rc = alloc((void**)&I->b.rowc, (size_t)NROWC_HOST * g.nz * 4)) ||
+       (rc = alloc((void**)&I->refd, (size_t)4 * g.nz * 8)))) {
+    free_instance(I);
+    return rc;
   }
   auto fin = [&](int code) {
     free_instance(I);
@@ -319,7 +383,17 @@ int mprk_create(const mprk_config* cfg, const double* q0, int q0_location, void*
       cudaMemsetAsync(I->b.Ra, 0, 4 * plane * rsz, I->stream) != cudaSuccess ||
       cudaMemsetAsync(I->status_dev, 0, 16, I->stream) != cudaSuccess)
     return fin(fail(MPRK_ECUDA, "memset failed"));
+  if (I->b.dA &&
+      (cudaMemsetAsync(I->b.dA, 0, 4 * plane * 4, I->stream) != cudaSuccess ||
+       cudaMemsetAsync(I->b.dB, 0, 4 * plane * 4, I->stream) != cudaSuccess))
+    return fin(fail(MPRK_ECUDA, "memset failed"));
   if ((rc = copy_state_in(I, q0, q0_location))) return fin(rc);
+  if (I->b.dA) {
+    // reference rows from the initial state, then the shadow of qA
+    cudaError_t e = launch_reference(g, I->b.qA, I->refd, I->b.rowc, I->stream);
+    if (e == cudaSuccess) e = launch_shadow(g, I->b.qA, I->b.rowc, I->b.dA, I->stream);
+    if (e != cudaSuccess) return fin(fail(MPRK_ECUDA, "reference set-up: %s", cudaGetErrorString(e)));
+  }
 
   // check the initial state and pick dt
   double d[16];
@@ -343,17 +417,27 @@ int mprk_create(const mprk_config* cfg, const double* q0, int q0_location, void*
     dt = cfg->scheme == MPRK_SCHEME_MPRK2 ? fmin(d1, d2) : cfg->m * fmin(d1, d2 / cfg->m);
   }
   I->cfg.dt = dt;
-  I->g.dt = dt;
-  if ((rc = capture(I, false, &I->exec))) return fin(rc);
-  if (I->cfg.diag_every > 0 && (rc = capture(I, true, &I->exec_diag))) return fin(rc);
+  geom_from_config(I->cfg, I->g.pitch, &I->g);
+  if (!stream_ordered) {  // stream-ordered (server) instances advance only in batches
+    if ((rc = capture(I, false, &I->exec))) return fin(rc);
+    if (I->cfg.diag_every > 0 && (rc = capture(I, true, &I->exec_diag))) return fin(rc);
+  }
   cudaError_t e = cudaStreamSynchronize(I->stream);
   if (e != cudaSuccess) return fin(fail(MPRK_ECUDA, "create: %s", cudaGetErrorString(e)));
   *out = I;
   return MPRK_OK;
 }
 
+extern "C" {
+
+int mprk_create(const mprk_config* cfg, const double* q0, int q0_location, void* cuda_stream,
+                mprk_instance** out) {
+  return create_instance(cfg, q0, q0_location, cuda_stream, false, out);
+}
+
 int mprk_destroy(mprk_instance* inst) {
   if (!inst) return fail(MPRK_EINVAL, "instance is NULL");
+  batch_forget(inst);
   free_instance(inst);
   return MPRK_OK;
 }
@@ -361,6 +445,7 @@ int mprk_destroy(mprk_instance* inst) {
 int mprk_step(mprk_instance* I, int n) {
   if (!I) return fail(MPRK_EINVAL, "instance is NULL");
   if (n < 0) return fail(MPRK_EINVAL, "negative step count");
+  if (!I->exec) return fail(MPRK_EINVAL, "this instance advances only in batches");
   for (int s = 0; s < n; s++) {
     const bool diag = I->cfg.diag_every > 0 && ((I->steps_done + 1) % I->cfg.diag_every) == 0;
     CU(cudaGraphLaunch(diag ? I->exec_diag : I->exec, I->stream));
@@ -439,21 +524,13 @@ int mprk_rhs(mprk_instance* I, const double* W_dev, double* R_dev, int k_lo, int
   }
   CU(cudaMemcpy2DAsync(I->rhs_in, (size_t)g.pitch * 8, W_dev, (size_t)g.nx * 8, (size_t)g.nx * 8,
                        (size_t)4 * g.nz, cudaMemcpyDeviceToDevice, I->stream));
-  StageArgs a;
-  memset(&a, 0, sizeof a);
-  a.g = g;
-  a.b = I->b;
-  a.qF = I->b.qA;
-  a.qF_next = I->b.qB;
-  a.stage = 0;
+  StageArgs a = stage_args(g, I->b, 0);
   a.row0 = k_lo;
-  a.tiles_x = (g.nx + TX - 1) / TX;
   a.rhs_only = 1;
   a.rhs_out = I->rhs_out;
   a.rhs_hi = k_hi;
   a.rhs_in = I->rhs_in;
-  const int tiles_z = (k_hi - k_lo + TZ - 1) / TZ;
-  CU(launch_stage(a, I->precision, a.tiles_x * tiles_z, I->stream));
+  CU(launch_stage(a, I->precision, stage_tiles(a), I->stream));
   for (int c = 0; c < 4; c++) {
     CU(cudaMemcpy2DAsync(R_dev + ((size_t)c * g.nz + k_lo) * g.nx, (size_t)g.nx * 8,
                          I->rhs_out + (size_t)c * plane + (size_t)k_lo * g.pitch,
@@ -469,22 +546,11 @@ int mprk_profile_step(mprk_instance* I, double* launch_ms, long long* launch_cel
   const int n = 2 * g.m + 1;
   cudaEvent_t ev[2 * 64 + 2];
   for (int j = 0; j <= n; j++) CU(cudaEventCreate(&ev[j]));
-  const int tiles_x = (g.nx + TX - 1) / TX;
   int rc = MPRK_OK;
   CU(cudaEventRecord(ev[0], I->stream));
   for (int st = 0; st < 2 * g.m && rc == MPRK_OK; st++) {
-    StageArgs a;
-    memset(&a, 0, sizeof a);
-    a.g = g;
-    a.b = I->b;
-    const bool even_sub = ((st / 2) % 2) == 0;
-    a.qF = even_sub ? I->b.qA : I->b.qB;
-    a.qF_next = even_sub ? I->b.qB : I->b.qA;
-    a.stage = st;
-    a.row0 = st < 2 ? 0 : g.nS_r;
-    a.tiles_x = tiles_x;
-    const int tiles_z = (g.nz - a.row0 + TZ - 1) / TZ;
-    cudaError_t e = launch_stage(a, I->precision, tiles_x * tiles_z, I->stream);
+    const StageArgs a = stage_args(g, I->b, st);
+    cudaError_t e = launch_stage(a, I->precision, stage_tiles(a), I->stream);
     if (e != cudaSuccess) rc = fail(MPRK_ECUDA, "stage launch: %s", cudaGetErrorString(e));
     cudaEventRecord(ev[st + 1], I->stream);
     if (st < cap && launch_cells) launch_cells[st] = (long long)(g.nz - a.row0) * g.nx;
@@ -507,6 +573,15 @@ int mprk_profile_step(mprk_instance* I, double* launch_ms, long long* launch_cel
   }
   for (int j = 0; j <= n; j++) cudaEventDestroy(ev[j]);
   return rc == MPRK_OK ? n : rc;
+}
+
+int mprk_selftest_convert(const double* in_dev, int n, float* narrow_dev, float* narrow_hw_dev,
+                          double* widen_dev, double* widen_hw_dev) {
+  if (!in_dev || !narrow_dev || !narrow_hw_dev || !widen_dev || !widen_hw_dev || n < 0)
+    return fail(MPRK_EINVAL, "bad argument");
+  CU(launch_convert_check(in_dev, n, narrow_dev, narrow_hw_dev, widen_dev, widen_hw_dev, 0));
+  CU(cudaStreamSynchronize(0));
+  return MPRK_OK;
 }
 
 const char* mprk_last_error(void) { return g_err.c_str(); }

@@ -58,16 +58,22 @@ int setup_device(int dev, void** out) {
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
-// Scratch bytes a configuration needs: qB | Ra | accB | accS, pitch = nx.
+constexpr int kRowConsts = 16;  // per-row float constants of the FP32-flux mode
+
+// Scratch bytes a configuration needs: qB | Ra | accB | accS, and in the
+// FP32-flux mode also dA | dB | rowc | refd; pitch = nx.
 size_t scratch_bytes(const mprk_config* c) {
   if (!c || c->nx <= 0 || c->nz_S < 0 || c->nz_B < 0 || c->nz_F < 0) return 0;
   const size_t nz = (size_t)c->nz_S + c->nz_B + c->nz_F;
   const size_t plane = nz * (size_t)c->nx;
-  const size_t rsz = c->precision == MPRK_FP64 ? 8 : 4;
+  const bool fp64 = c->precision == MPRK_FP64;
+  const size_t rsz = fp64 ? 8 : 4;
   const bool mprk2 = c->scheme == MPRK_SCHEME_MPRK2;
   const size_t nB = mprk2 ? (size_t)c->nz_B : 0, nS = mprk2 ? (size_t)c->nz_S : 0;
-  return align256(4 * plane * 8) + align256(4 * plane * rsz) + align256(4 * nB * c->nx * 8) +
-         align256(4 * nS * c->nx * 8);
+  size_t b = align256(4 * plane * 8) + align256(4 * plane * rsz) + align256(4 * nB * c->nx * 8) +
+             align256(4 * nS * c->nx * 8);
+  if (!fp64) b += 2 * align256(4 * plane * 4) + align256(kRowConsts * nz * 4) + align256(4 * nz * 8);
+  return b;
 }
 
 }  // namespace
@@ -105,33 +111,7 @@ int mprk_step_static(const mprk_config* cfg, double* q_dev, int n_slow_steps, vo
 
   // geometry: the caller's state is the home buffer, unpadded (pitch = nx)
   Geom g;
-  memset(&g, 0, sizeof g);
-  g.nx = cfg->nx;
-  g.pitch = cfg->nx;
-  g.nz = cfg->nz_S + cfg->nz_B + cfg->nz_F;
-  g.n1 = cfg->nz_S + cfg->nz_B;
-  const bool mprk2 = cfg->scheme == MPRK_SCHEME_MPRK2;
-  g.nS_r = mprk2 ? cfg->nz_S : 0;
-  g.n1_r = mprk2 ? g.n1 : 0;
-  g.nS_g = cfg->nz_S;
-  g.m = cfg->m;
-  g.wall = cfg->wall;
-  g.dt = cfg->dt;
-  g.inv_dx = 1.0 / cfg->dx;
-  g.inv_dz1 = 1.0 / cfg->dz1;
-  g.inv_dz2 = 1.0 / cfg->dz2;
-  g.gamma = cfg->gamma;
-  g.gm1 = cfg->gamma - 1.0;
-  g.mu1 = cfg->mu1;
-  g.mu2 = cfg->mu2;
-  const double cp = 1.0 / (cfg->gamma - 1.0);
-  g.kap1 = cp * cfg->mu1 / cfg->Pr;
-  g.kap2 = cp * cfg->mu2 / cfg->Pr;
-  g.G = cfg->G;
-  g.bu = 2.0 * cfg->mu1 * cfg->mu2 / (cfg->dz2 * cfg->mu1 + cfg->dz1 * cfg->mu2);
-  g.bT = 2.0 * g.kap1 * g.kap2 / (cfg->dz2 * g.kap1 + cfg->dz1 * g.kap2);
-  g.cu1 = cfg->dz1 / (2.0 * cfg->mu1);
-  g.cT1 = cfg->dz1 / (2.0 * g.kap1);
+  geom_from_config(*cfg, cfg->nx, &g);
 
   // carve the scratch: qB | Ra | accB | accS (each 256-byte aligned)
   const size_t plane = (size_t)g.nz * g.pitch;
@@ -146,27 +126,36 @@ int mprk_step_static(const mprk_config* cfg, double* q_dev, int n_slow_steps, vo
   b.accB = reinterpret_cast<double*>(p);
   p += align256(4 * (size_t)(g.n1_r - g.nS_r) * g.nx * 8);
   b.accS = reinterpret_cast<double*>(p);
+  p += align256(4 * (size_t)g.nS_r * g.nx * 8);
+  b.dA = nullptr;
+  b.dB = nullptr;
+  b.rowc = nullptr;
+  double* refd = nullptr;
+  if (cfg->precision != MPRK_FP64) {
+    b.dA = reinterpret_cast<float*>(p);
+    p += align256(4 * plane * 4);
+    b.dB = reinterpret_cast<float*>(p);
+    p += align256(4 * plane * 4);
+    b.rowc = reinterpret_cast<float*>(p);
+    p += align256((size_t)kRowConsts * g.nz * 4);
+    refd = reinterpret_cast<double*>(p);
+  }
 
   // Nothing in the scratch needs clearing: every entry a step reads was
-  // written earlier in the same step (stage 1 writes R_a and the buffer sum
+  // written earlier in the same call (stage 1 writes R_a and the buffer sum
   // on every row, stage 2 writes the fast state of substep 1 and the slow
-  // result, and padding does not exist because the pitch is nx).
+  // result, the FP32-flux reference rows and shadow are rebuilt from q_dev
+  // below, and padding does not exist because the pitch is nx).
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  const int tiles_x = (g.nx + TX - 1) / TX;
+  if (b.dA) {
+    e = launch_reference(g, q_dev, refd, b.rowc, s);
+    if (e == cudaSuccess) e = launch_shadow(g, q_dev, b.rowc, b.dA, s);
+    if (e != cudaSuccess) return sfail(MPRK_ECUDA, std::string("reference set-up: ") + cudaGetErrorString(e));
+  }
   for (int step = 0; step < n_slow_steps; step++) {
     for (int st = 0; st < 2 * g.m; st++) {
-      StageArgs a;
-      memset(&a, 0, sizeof a);
-      a.g = g;
-      a.b = b;
-      const bool even_sub = ((st / 2) % 2) == 0;
-      a.qF = even_sub ? b.qA : b.qB;
-      a.qF_next = even_sub ? b.qB : b.qA;
-      a.stage = st;
-      a.row0 = st < 2 ? 0 : g.nS_r;
-      a.tiles_x = tiles_x;
-      const int tiles_z = (g.nz - a.row0 + TZ - 1) / TZ;
-      e = launch_stage(a, cfg->precision, tiles_x * tiles_z, s);
+      const StageArgs a = stage_args(g, b, st);
+      e = launch_stage(a, cfg->precision, stage_tiles(a), s);
       if (e != cudaSuccess) return sfail(MPRK_ECUDA, std::string("stage launch: ") + cudaGetErrorString(e));
     }
     e = launch_finalize(g, b, g.m & 1, s);

@@ -106,8 +106,11 @@ __device__ __forceinline__ int wrap_col(int i, int nx) {
 }
 
 // The tile body. tile = linear tile index within the launch's row range.
+// Not inlined: the single-instance kernel and the persistent batch kernel
+// then run the very same compiled body, so an instance's results are bitwise
+// the same alone and in a batch.
 template <typename Real, typename Store>
-__device__ __forceinline__ void stage_tile(const StageArgs& a, int tile, TileSmem<Real>& S) {
+__device__ __noinline__ void stage_tile(const StageArgs& a, int tile, TileSmem<Real>& S) {
   const Geom& g = a.g;
   const int tid = threadIdx.x;
   const int tzi = tile / a.tiles_x;
@@ -119,7 +122,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile, TileSme
   const size_t plane = (size_t)nz * g.pitch;
   const bool odd_stage = !a.rhs_only && (a.stage & 1);  // stages 2, 4, ... (1-based)
   const Store* Ra = reinterpret_cast<const Store*>(a.b.Ra);
-  const double hF = g.dt / g.m;
+  const double hF = g.hF;
 
   // ---- 1. stage state of the tile and its halo --------------------------
   for (int e = tid; e < 4 * (TZ + 4) * (TX + 4); e += NTHREADS) {
@@ -379,7 +382,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile, TileSme
     }
     Store* Ra_w = reinterpret_cast<Store*>(a.b.Ra);
     const int st = a.stage;
-    const double h2 = g.dt / (2.0 * g.m);
+    const double h2 = g.h2;
     if (k >= g.n1_r) {
       // fast region: m Heun substeps of dt/m
       if (!(st & 1)) {
@@ -419,7 +422,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int tile, TileSme
         if (st == 0) {
           Ra_w[o] = (Store)R[c];
         } else {
-          a.b.accS[(size_t)c * ps + row_off] = a.b.qA[o] + (0.5 * g.dt) * ((double)Ra[o] + (double)R[c]);
+          a.b.accS[(size_t)c * ps + row_off] = a.b.qA[o] + g.hdt * ((double)Ra[o] + (double)R[c]);
         }
       }
     }

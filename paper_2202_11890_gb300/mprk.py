@@ -61,6 +61,17 @@ class mprk_config(C.Structure):
         return (4, self.nz, self.nx)
 
 
+class mprk_server_config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_longlong), ("max_slots", C.c_int), ("device", C.c_int),
+                ("max_queue", C.c_int), ("reserved", C.c_int)]
+
+
+class mprk_stats(C.Structure):
+    _fields_ = [("t_submit", C.c_double), ("t_admit", C.c_double), ("t_finish", C.c_double),
+                ("cell_stages", C.c_longlong), ("device_bytes", C.c_longlong),
+                ("steps_done", C.c_int), ("error", C.c_int)]
+
+
 class MprkError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"mprk error {code}: {msg}")
@@ -101,6 +112,14 @@ def lib():
         "mprk_rhs": (ip, [vp, vp, vp, ip, ip]),
         "mprk_profile_step": (ip, [vp, dp, C.POINTER(C.c_longlong), ip]),
         "mprk_step_static": (ip, [cfgp, vp, ip, vp]),
+        "mprk_step_batch": (ip, [C.POINTER(vp), ip, ip]),
+        "mprk_batch_test_withhold": (ip, [C.POINTER(vp), ip, ip, ip, C.c_longlong]),
+        "mprk_selftest_convert": (ip, [vp, ip, vp, vp, vp, vp]),
+        "mprk_server_create": (ip, [C.POINTER(mprk_server_config), C.POINTER(vp)]),
+        "mprk_submit": (ip, [vp, cfgp, vp, ip, C.POINTER(C.c_uint64)]),
+        "mprk_poll": (ip, [vp, C.c_uint64, C.POINTER(C.c_int), vp, C.POINTER(mprk_stats)]),
+        "mprk_server_stats": (ip, [vp, dp]),
+        "mprk_server_destroy": (ip, [vp]),
         "mprk_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -209,6 +228,28 @@ def mprk_profile_step(h: int):
     return ms[:n].copy(), cells[:n].copy()
 
 
+def _handles(hs):
+    arr = (C.c_void_p * len(hs))(*[int(h) for h in hs])
+    return arr
+
+
+def mprk_step_batch(handles, n: int) -> None:
+    """One persistent launch per slow step over all the instances."""
+    _check(lib().mprk_step_batch(_handles(handles), len(handles), int(n)))
+
+
+def mprk_batch_test_withhold(handles, inst_index: int, stage: int, wait_cycles: int) -> int:
+    return int(lib().mprk_batch_test_withhold(_handles(handles), len(handles), inst_index, stage,
+                                              int(wait_cycles)))
+
+
+def mprk_selftest_convert(x_dev, narrow, narrow_hw, widen, widen_hw) -> None:
+    """Bit-operation vs hardware float/double conversions (device tensors)."""
+    _check(lib().mprk_selftest_convert(C.c_void_p(x_dev.data_ptr()), int(x_dev.numel()),
+                                       C.c_void_p(narrow.data_ptr()), C.c_void_p(narrow_hw.data_ptr()),
+                                       C.c_void_p(widen.data_ptr()), C.c_void_p(widen_hw.data_ptr())))
+
+
 MPRK_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
@@ -220,6 +261,46 @@ def mprk_step_static(cfg: mprk_config, q_dev, n: int, stream=None) -> None:
         raise ValueError("mprk_step_static takes a device tensor")
     s = None if stream is None else C.c_void_p(int(stream))
     _check(lib().mprk_step_static(C.byref(cfg), C.c_void_p(addr), int(n), s))
+
+
+def mprk_server_create(hbm_budget_bytes: int, max_slots: int = 1024, device: int = 0,
+                       max_queue: int = 1 << 20) -> int:
+    cfg = mprk_server_config(hbm_budget_bytes=int(hbm_budget_bytes), max_slots=max_slots, device=device,
+                             max_queue=max_queue, reserved=0)
+    h = C.c_void_p()
+    _check(lib().mprk_server_create(C.byref(cfg), C.byref(h)))
+    return h.value
+
+
+def mprk_submit(srv: int, cfg: mprk_config, q0: np.ndarray, n_steps: int) -> int:
+    """Queue a solve; returns the ticket. Raises MprkError (EBUDGET, EBUSY, EINVAL)."""
+    q0 = np.ascontiguousarray(q0, dtype=np.float64)
+    t = C.c_uint64()
+    _check(lib().mprk_submit(C.c_void_p(srv), C.byref(cfg), q0.ctypes.data_as(C.c_void_p), int(n_steps),
+                             C.byref(t)))
+    return t.value
+
+
+def mprk_poll(srv: int, ticket: int, out: np.ndarray | None = None):
+    """(status, error, stats dict). With out given and status DONE, the result
+    is copied into out and the ticket is released."""
+    st = C.c_int()
+    stats = mprk_stats()
+    ptr = out.ctypes.data_as(C.c_void_p) if out is not None else None
+    rc = lib().mprk_poll(C.c_void_p(srv), C.c_uint64(ticket), C.byref(st), ptr, C.byref(stats))
+    if rc == MPRK_ENOTFOUND:
+        raise MprkError(rc, mprk_last_error())
+    return st.value, rc, {f: getattr(stats, f) for f, _ in mprk_stats._fields_}
+
+
+def mprk_server_stats(srv: int) -> np.ndarray:
+    out = np.zeros(8)
+    _check(lib().mprk_server_stats(C.c_void_p(srv), out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def mprk_server_destroy(srv: int) -> None:
+    _check(lib().mprk_server_destroy(C.c_void_p(srv)))
 
 
 class Instance:

@@ -21,6 +21,21 @@ def time_steps(h: int, stream_ptr: int, steps: int) -> float:
     return float(e0.elapsed_time(e1))
 
 
+def time_region(stream_ptr: int, fn) -> float:
+    """Milliseconds of the work fn() enqueues on the stream (CUDA events)."""
+    import torch
+    ext = torch.cuda.ExternalStream(stream_ptr)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(ext):
+        e0.record(ext)
+        fn()
+        e1.record(ext)
+    e1.synchronize()
+    return float(e0.elapsed_time(e1))
+
+
 def stage_kernel_times(h: int, stream_ptr: int, reps: int = 3):
     """Summed duration (ms) of the stage-kernel launches of one slow step and
     the cell-stages they computed, median over `reps` profiled steps."""

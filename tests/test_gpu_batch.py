@@ -1,0 +1,113 @@
+"""The persistent batched step (mprk_step_batch): each instance of an uneven
+batch ends bitwise equal to the same instance stepped alone with mprk_step,
+and the bounded stage waits give up with a timeout status instead of
+hanging when a stage never completes."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2202_11890_gb300 import workloads as W
+from pairs import oracle_threads, pair, rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_11890_gb300 import build
+    build.build()
+    oracle_threads()
+
+
+def uneven(count, seed, precision=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(count):
+        nx = int(rng.integers(8, 140))
+        nB = int(rng.integers(4, 17))
+        nS = int(rng.integers(2, 40))
+        nF = int(rng.integers(2, 40))
+        m = int(rng.choice([1, 2, 3, 4, 8]))
+        g = W.Grid(nx, nS, nB, nF)
+        q = W.gaussian_bumps(g, seed * 100 + j, sigma_cells=2.5)
+        cfg, P, dt = pair(g, m, q0=q, precision=precision)
+        out.append((cfg, P, q))
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_equals_each_instance_alone(precision):
+    from paper_2202_11890_gb300 import mprk as M
+    cases = uneven(14, 3 + precision, precision)
+    steps = 3
+    alone = []
+    for cfg, P, q in cases:
+        with M.Instance(cfg, q) as inst:
+            inst.step(steps)
+            alone.append(inst.state())
+    insts = [M.Instance(cfg, q) for cfg, P, q in cases]
+    try:
+        M.mprk_step_batch([i.h for i in insts], steps)
+        for i, ref in zip(insts, alone):
+            out = i.state()
+            assert np.array_equal(out, ref)
+            assert i.status() == 0
+            assert i.diagnostics()[14] == steps
+    finally:
+        for i in insts:
+            i.close()
+
+
+def test_batch_matches_oracle():
+    from paper_2202_11890_gb300 import mprk as M
+    cases = uneven(5, 9)
+    insts = [M.Instance(cfg, q) for cfg, P, q in cases]
+    try:
+        M.mprk_step_batch([i.h for i in insts], 1)
+        for (cfg, P, q), i in zip(cases, insts):
+            q_or, _ = O.mprk_step(P, q)
+            assert np.all(rel_err(i.state(), q_or) < 1e-12)
+    finally:
+        for i in insts:
+            i.close()
+
+
+def test_batch_wait_times_out_without_hanging():
+    """A stage whose tiles never report completion: the waiting tiles give up
+    after the cycle limit, the status word reads MPRK_ETIMEOUT, and the
+    device stays usable."""
+    from paper_2202_11890_gb300 import mprk as M
+    cases = uneven(3, 21)
+    insts = [M.Instance(cfg, q) for cfg, P, q in cases]
+    try:
+        rc = M.mprk_batch_test_withhold([i.h for i in insts], 0, 1, 200_000_000)
+        assert rc == 0
+        torch.cuda.synchronize()
+        assert insts[0].status() == M.MPRK_ETIMEOUT
+    finally:
+        for i in insts:
+            i.close()
+    # the context still works: a fresh instance steps and matches the oracle
+    cfg, P, q = uneven(1, 22)[0]
+    with M.Instance(cfg, q) as inst:
+        inst.step(1)
+        q_or, _ = O.mprk_step(P, q)
+        assert np.all(rel_err(inst.state(), q_or) < 1e-12)
+
+
+def test_batch_rejects_mixed_precisions():
+    from paper_2202_11890_gb300 import mprk as M
+    a = uneven(1, 30, 0)[0]
+    b = uneven(1, 31, 1)[0]
+    ia, ib = M.Instance(a[0], a[2]), M.Instance(b[0], b[2])
+    try:
+        with pytest.raises(M.MprkError) as ei:
+            M.mprk_step_batch([ia.h, ib.h], 1)
+        assert ei.value.code == M.MPRK_EINVAL
+    finally:
+        ia.close()
+        ib.close()

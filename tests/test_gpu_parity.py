@@ -266,3 +266,45 @@ def test_large_2048_one_step_full_size():
         q_gpu = inst.state()
     err = rel_err(q_gpu, q_or)
     assert np.all(err < 1e-12), err
+
+
+def test_bit_operation_conversions_match_hardware():
+    """The FP32-flux mode narrows double -> float (round to nearest, ties to
+    even) and widens float -> double with integer bit operations. They must
+    agree bit for bit with the hardware conversions, including ties, values
+    near the float range limits, zeros, subnormals, Inf and NaN."""
+    mp = M()
+    rng = np.random.default_rng(5)
+    vals = [rng.normal(size=20000), rng.uniform(-1e-30, 1e-30, 2000),
+            np.exp(rng.uniform(-80, 80, 4000)) * rng.choice([-1, 1], 4000)]
+    # exact ties between two floats: 24-bit mantissa + one half-ulp bit
+    m = rng.integers(1 << 23, 1 << 24, 2000).astype(np.float64)
+    e = rng.integers(-30, 30, 2000)
+    ties = (m + 0.5) * np.exp2(e.astype(np.float64) - 23)
+    specials = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1e-40, -1e-45, 3.4028235677973366e38,
+                         3.4028235677973366e38 * 1.0000001, 1.1754943508222875e-38, 2.0 ** -149])
+    x = np.concatenate(vals + [ties, -ties, specials])
+    xd = torch.from_numpy(x).cuda()
+    n = xd.numel()
+    nar = torch.empty(n, dtype=torch.float32, device="cuda")
+    nar_hw = torch.empty_like(nar)
+    wid = torch.empty(n, dtype=torch.float64, device="cuda")
+    wid_hw = torch.empty_like(wid)
+    mp.mprk_selftest_convert(xd, nar, nar_hw, wid, wid_hw)
+    a, b = nar.cpu().numpy().view(np.uint32), nar_hw.cpu().numpy().view(np.uint32)
+    assert np.array_equal(a, b), np.count_nonzero(a != b)
+    a, b = wid.cpu().numpy().view(np.uint64), wid_hw.cpu().numpy().view(np.uint64)
+    assert np.array_equal(a, b)
+
+
+def test_fp32_flux_rhs_close_to_oracle():
+    """The FP32-flux right-hand side (deviation form) against the FP64
+    oracle's."""
+    g = W.Grid(64, 30, 4, 30)
+    q = W.gaussian_bumps(g, 17, sigma_cells=3.0)
+    cfg, P, _ = pair(g, 2, dt=0.01, precision=1)
+    R_or = O.rhs(P, q)
+    R_gpu = gpu_rhs(cfg, q)
+    err = rel_err(R_gpu, R_or)
+    print("fp32flux RHS error per component:", err)
+    assert np.all(err < 1e-4), err

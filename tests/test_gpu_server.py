@@ -1,0 +1,153 @@
+"""The request server (mprk_submit / mprk_poll): continuous batching under
+an HBM budget. Each result equals the same solve alone (mprk_step), in any
+admission order, and the error paths report codes instead of failing."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2202_11890_gb300 import workloads as W
+from pairs import pair
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_11890_gb300 import build
+    build.build()
+
+
+def requests(count, seed, precision=1):
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(count):
+        nx = int(rng.integers(8, 120))
+        nB = int(rng.integers(4, 17))
+        g = W.Grid(nx, int(rng.integers(2, 30)), nB, int(rng.integers(2, 30)))
+        m = int(rng.choice([2, 4, 8]))
+        q = W.gaussian_bumps(g, seed * 100 + j, sigma_cells=2.5)
+        cfg, P, dt = pair(g, m, q0=q, precision=precision)
+        out.append((cfg, q, int(rng.integers(1, 12))))
+    return out
+
+
+def alone(cfg, q, n):
+    from paper_2202_11890_gb300 import mprk as M
+    with M.Instance(cfg, q) as inst:
+        inst.step(n)
+        return inst.state()
+
+
+def drain(M, srv, tickets, timeout=120.0):
+    outs = {}
+    t0 = time.time()
+    while len(outs) < len(tickets):
+        assert time.time() - t0 < timeout, "server did not finish"
+        for t, shape in tickets.items():
+            if t in outs:
+                continue
+            buf = np.empty(shape)
+            st, err, stats = M.mprk_poll(srv, t, buf)
+            if st == M.MPRK_REQ_DONE:
+                outs[t] = (buf, err, stats)
+        time.sleep(0.002)
+    return outs
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_served_results_equal_solo_results(precision):
+    from paper_2202_11890_gb300 import mprk as M
+    reqs = requests(24, 5 + precision, precision)
+    refs = [alone(cfg, q, n) for cfg, q, n in reqs]
+    srv = M.mprk_server_create(hbm_budget_bytes=1 << 30, max_slots=7)
+    try:
+        tickets = {}
+        order = {}
+        for j, (cfg, q, n) in enumerate(reqs):
+            t = M.mprk_submit(srv, cfg, q, n)
+            tickets[t] = q.shape
+            order[t] = j
+            if j % 5 == 4:
+                time.sleep(0.003)  # arrivals while others run
+        outs = drain(M, srv, tickets)
+        for t, (buf, err, stats) in outs.items():
+            j = order[t]
+            assert err == 0
+            assert stats["steps_done"] == reqs[j][2]
+            assert np.array_equal(buf, refs[j]), j
+        s = M.mprk_server_stats(srv)
+        assert s[0] == len(reqs) and s[7] == 0 and s[5] == 0
+    finally:
+        M.mprk_server_destroy(srv)
+
+
+def test_admission_order_does_not_change_results():
+    from paper_2202_11890_gb300 import mprk as M
+    reqs = requests(10, 11)
+    results = []
+    for perm in (np.arange(10), np.random.default_rng(2).permutation(10)):
+        srv = M.mprk_server_create(hbm_budget_bytes=1 << 30, max_slots=3)
+        try:
+            tickets, order = {}, {}
+            for j in perm:
+                cfg, q, n = reqs[j]
+                t = M.mprk_submit(srv, cfg, q, n)
+                tickets[t] = q.shape
+                order[t] = int(j)
+            outs = drain(M, srv, tickets)
+            results.append({order[t]: o[0] for t, o in outs.items()})
+        finally:
+            M.mprk_server_destroy(srv)
+    for j in range(10):
+        assert np.array_equal(results[0][j], results[1][j])
+
+
+def test_budget_queue_and_bad_state_errors():
+    from paper_2202_11890_gb300 import mprk as M
+    cfg, q, n = requests(1, 3)[0]
+    srv = M.mprk_server_create(hbm_budget_bytes=1 << 20, max_slots=2, max_queue=2)
+    try:
+        big = W.Grid(512, 200, 8, 200)
+        cbig, _, _ = pair(big, 2, dt=1e-3, precision=1)
+        with pytest.raises(M.MprkError) as ei:
+            M.mprk_submit(srv, cbig, np.ones((4, big.nz, big.nx)), 1)
+        assert ei.value.code == M.MPRK_EBUDGET
+        bad = q.copy()
+        bad[0, 0, 0] = np.nan
+        t_bad = M.mprk_submit(srv, cfg, bad, 2)
+        outs = drain(M, srv, {t_bad: q.shape})
+        assert outs[t_bad][1] == M.MPRK_ENONFINITE
+        with pytest.raises(M.MprkError) as ei:
+            M.mprk_poll(srv, 987654321)
+        assert ei.value.code == M.MPRK_ENOTFOUND
+    finally:
+        M.mprk_server_destroy(srv)
+    # a full queue answers EBUSY (the server admits nothing: no slot fits)
+    srv = M.mprk_server_create(hbm_budget_bytes=1 << 30, max_slots=1, max_queue=1)
+    try:
+        cfg2, q2, _ = requests(1, 4)[0]
+        M.mprk_submit(srv, cfg2, q2, 200)   # occupies the slot
+        time.sleep(0.05)
+        M.mprk_submit(srv, cfg2, q2, 1)     # queued
+        with pytest.raises(M.MprkError) as ei:
+            for _ in range(50):
+                M.mprk_submit(srv, cfg2, q2, 1)
+        assert ei.value.code == M.MPRK_EBUSY
+    finally:
+        M.mprk_server_destroy(srv)
+
+
+def test_shutdown_with_requests_in_flight():
+    from paper_2202_11890_gb300 import mprk as M
+    srv = M.mprk_server_create(hbm_budget_bytes=1 << 30, max_slots=4)
+    for cfg, q, n in requests(8, 7):
+        M.mprk_submit(srv, cfg, q, 500)
+    time.sleep(0.05)
+    M.mprk_server_destroy(srv)   # returns; nothing hangs
+    cfg, q, n = requests(1, 8)[0]
+    assert alone(cfg, q, 1).shape == q.shape  # the device is still usable

@@ -37,7 +37,10 @@ def test_static_entry_point_matches_mprk_step(dims, m, precision):
     g = W.Grid(*dims)
     q = W.gaussian_bumps(g, 41, sigma_cells=3.0)
     cfg, P, dt = pair(g, m, q0=q, precision=precision)
-    tol = 1e-12
+    # the parity tolerances of the other tests: 1e-12 in FP64; in the
+    # FP32-flux mode 1e-5, because each call rebuilds that mode's reference
+    # rows from the state it is given (the instance keeps those of q0)
+    tol = 1e-12 if precision == 0 else 1e-5
     with M.Instance(cfg, q) as inst:
         inst.step(1)
         ref1 = inst.state()
