@@ -32,10 +32,13 @@ sys.path.insert(0, ROOT)
 from paper_2202_11890_gb300 import workloads as W  # noqa: E402
 
 METRIC = "cell-stage updates/s"
-# algorithmic floating-point work per cell-stage of the stage kernel (see
-# the design doc, counted from the formulas: 2.16 faces and 1.33 ring cells per
-# tile cell)
-FLOPS_PER_CELL_STAGE = 418.0
+# Algorithmic floating-point operations per cell-stage of the stage kernel,
+# counted from its formulas (+ - * / sqrt each 1, a*b+c 2): 130 per face
+# (LF flux 92, viscous flux 26, reconstruction 8, F* assembly 4) times 2.156
+# faces per cell of a 32x8 tile, plus ring primitives 14.6, slopes 28.8,
+# divergence and source 24, stage combination 8. The FP32-flux form adds
+# the reference/deviation sums: 12 per face.
+FLOPS_PER_CELL_STAGE = {True: 355.7, False: 381.6}
 # FP64 unit count x clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
@@ -203,7 +206,7 @@ def run_ours(args):
     fp64 = cfg.precision == M.MPRK_FP64
     peak_alu = FP64_PEAK_GFLOPS if fp64 else FP32_PEAK_GFLOPS
     # achieved over all stage launches of a step: algorithmic work / kernel time
-    ach_gflops = stage_cells * FLOPS_PER_CELL_STAGE / (stage_ms * 1e-3) / 1e9
+    ach_gflops = stage_cells * FLOPS_PER_CELL_STAGE[fp64] / (stage_ms * 1e-3) / 1e9
     peaks, src = measured_peaks()
     stage_bytes, fin_bytes = algorithmic_bytes(g, wl.m, fp64)
     ach_gbs = stage_bytes / (stage_ms * 1e-3) / 1e9

@@ -59,6 +59,9 @@ struct BatchArgs {
 
 constexpr int FIN_CHUNK = NTHREADS * 8;  // cells per completion item
 
+// block size of the batch kernel per precision (the tile's own block size)
+constexpr int batch_threads(int prec) { return prec == 0 ? NTHREADS : MIXED_THREADS; }
+
 __device__ __forceinline__ bool wait_for(const BatchArgs& A, int ctr, int need) {
   // one thread waits with acquire semantics; returns false after an abort or timeout
   cuda::atomic_ref<int, cuda::thread_scope_device> c(A.counters[ctr]);
@@ -82,7 +85,7 @@ __device__ __forceinline__ void finalize_chunk(const Geom& g, const Bufs& b, int
   const int rows = (m_odd || mixed) ? g.nz : g.n1_r;
   const long long total = 4LL * rows * g.nx;
   for (long long e = (long long)chunk * FIN_CHUNK + threadIdx.x; e < total && e < (long long)(chunk + 1) * FIN_CHUNK;
-       e += NTHREADS) {
+       e += blockDim.x) {
     const int c = (int)(e / ((long long)rows * g.nx));
     const int rem = (int)(e - (long long)c * rows * g.nx);
     const int k = rem / g.nx, i = rem - k * g.nx;
@@ -97,7 +100,7 @@ __device__ __forceinline__ void finalize_chunk(const Geom& g, const Bufs& b, int
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(NTHREADS, PREC == 0 ? 2 : 3) batch_kernel(const BatchArgs A) {
+__global__ void __launch_bounds__(batch_threads(PREC), PREC == 0 ? 2 : 3) batch_kernel(const BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
   __shared__ int s_ok;
@@ -249,11 +252,11 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
   if (p->precision == 0) {
     e = cudaFuncSetAttribute(batch_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<0>, NTHREADS, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<0>, batch_threads(0), smem);
   } else {
     e = cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<1>, NTHREADS, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<1>, batch_threads(1), smem);
   }
   if (e != cudaSuccess || per_sm < 1) {
     free_plan(p);
@@ -277,8 +280,8 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
   e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaMemsetAsync(p->d_ctr, 0, sizeof(int) * (2 + p->n_counters), p->stream);
-    if (p->precision == 0) batch_kernel<0><<<p->grid, NTHREADS, smem, p->stream>>>(A);
-    else batch_kernel<1><<<p->grid, NTHREADS, smem, p->stream>>>(A);
+    if (p->precision == 0) batch_kernel<0><<<p->grid, batch_threads(0), smem, p->stream>>>(A);
+    else batch_kernel<1><<<p->grid, batch_threads(1), smem, p->stream>>>(A);
     cudaError_t el = cudaGetLastError();
     e = cudaStreamEndCapture(p->stream, &graph);
     if (el != cudaSuccess) e = el;
@@ -469,10 +472,10 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (r->precision == 0) {
         e = cudaFuncSetAttribute(batch_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r->per_sm, batch_kernel<0>, NTHREADS, smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r->per_sm, batch_kernel<0>, batch_threads(0), smem);
       } else {
         e = cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r->per_sm, batch_kernel<1>, NTHREADS, smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r->per_sm, batch_kernel<1>, batch_threads(1), smem);
       }
       if (e != cudaSuccess || r->per_sm < 1) return bfail(MPRK_ECUDA, "batch runner: occupancy query failed");
       r->grid = r->per_sm * sms;
@@ -493,8 +496,8 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
   if (e != cudaSuccess) return bfail(MPRK_ECUDA, std::string("batch runner: ") + cudaGetErrorString(e));
   const size_t smem = stage_smem_bytes(r->precision);
   const int grid = std::min(r->grid, r->n_items);
-  if (r->precision == 0) batch_kernel<0><<<grid, NTHREADS, smem, r->stream>>>(A);
-  else batch_kernel<1><<<grid, NTHREADS, smem, r->stream>>>(A);
+  if (r->precision == 0) batch_kernel<0><<<grid, batch_threads(0), smem, r->stream>>>(A);
+  else batch_kernel<1><<<grid, batch_threads(1), smem, r->stream>>>(A);
   e = cudaGetLastError();
   if (e != cudaSuccess) return bfail(MPRK_ECUDA, std::string("batch runner launch: ") + cudaGetErrorString(e));
   for (int j = 0; j < count; j++) instance_count_steps(insts[j], 1);

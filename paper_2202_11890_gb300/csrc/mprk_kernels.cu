@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   stage_tile<Real, Store>(a, blockIdx.x, S);
 }
 
-__global__ void __launch_bounds__(NTHREADS, 3) stage_kernel_mixed(const StageArgs a) {
+__global__ void __launch_bounds__(MIXED_THREADS, 4) stage_kernel_mixed(const StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   MixedSmem& S = *reinterpret_cast<MixedSmem*>(smem_raw);
   stage_tile_mixed(a, blockIdx.x, S);
@@ -42,7 +42,7 @@ cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStr
   if (precision == 0) {
     stage_kernel<double, double><<<n_tiles, NTHREADS, sizeof(TileSmem<double>), stream>>>(a);
   } else {
-    stage_kernel_mixed<<<n_tiles, NTHREADS, sizeof(MixedSmem), stream>>>(a);
+    stage_kernel_mixed<<<n_tiles, MIXED_THREADS, sizeof(MixedSmem), stream>>>(a);
   }
   return cudaGetLastError();
 }

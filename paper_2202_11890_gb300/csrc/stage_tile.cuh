@@ -110,7 +110,10 @@ __device__ __forceinline__ int wrap_col(int i, int nx) {
 // then run the very same compiled body, so an instance's results are bitwise
 // the same alone and in a batch.
 template <typename Real, typename Store>
-__device__ __noinline__ void stage_tile(const StageArgs& a, int tile, TileSmem<Real>& S) {
+__device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int tile,
+                                       TileSmem<Real>& __restrict__ S) {
+  // __restrict__: the argument block and shared memory never alias, so its
+  // fields need not be reloaded after shared-memory stores
   const Geom& g = a.g;
   const int tid = threadIdx.x;
   const int tzi = tile / a.tiles_x;

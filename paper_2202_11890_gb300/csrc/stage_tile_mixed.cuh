@@ -20,10 +20,10 @@
 //
 // Layout for few instructions per cell: one thread owns one cell of the
 // TX x TZ tile and computes the x face on its left and the z face below it;
-// the faces on the tile's right and top edges are extra work for warps 0
-// and 1. Per-cell quantities sit in shared memory as float4 (one 16-byte
-// load each). The right x face of a cell comes from the neighbouring lane by
-// a warp shuffle.
+// a ninth warp computes the faces on the tile's right and top edges.
+// Per-cell quantities sit in shared memory as float4 (one 16-byte load
+// each). The right x face of a cell comes from the neighbouring lane by a
+// warp shuffle.
 #pragma once
 
 #include "mprk_internal.h"
@@ -67,6 +67,11 @@ __device__ __forceinline__ float narrow(double x) {
 //   13    reference pressure divergence and gravity for R(rho w)
 //   14    p_ref
 constexpr int NROWC = 16;
+
+// Nine warps: warps 0-7 own the TX x TZ cells, warp 8 computes the faces on
+// the tile's top edge (one pass) and right edge (one pass), so every warp
+// makes two face passes.
+constexpr int MIXED_THREADS = NTHREADS + 32;
 
 struct MixedSmem {
   float4 q[TZ + 4][TX + 4];   // deviation d of the stage state (rho, mu, mw, E)
@@ -234,9 +239,11 @@ __device__ __forceinline__ float4 x_face_visc(const StageArgs& a, const MixedSme
   return make_float4(FV[0], FV[1], FV[2], FV[3]);
 }
 
-// Not inlined, so the single-instance and the batch kernels share one
-// compiled body (bitwise equal results alone and in a batch).
-static __device__ __noinline__ void stage_tile_mixed(const StageArgs& a, int tile, MixedSmem& S) {
+// Inlined into each kernel: launch constants then stay constant-bank
+// operands. The single-instance and batch kernels may contract floating-point
+// operations differently, so their results agree to float rounding (the
+// FP32-flux tolerance), not bit for bit.
+__device__ __forceinline__ void stage_tile_mixed(const StageArgs& a, int tile, MixedSmem& S) {
   const Geom& g = a.g;
   const int tid = threadIdx.x;
   const int ty = tid / TX, tx = tid - ty * TX;  // owned cell
@@ -252,7 +259,7 @@ static __device__ __noinline__ void stage_tile_mixed(const StageArgs& a, int til
   const float* rowc = a.b.rowc;
 
   // ---- 1. deviations of the stage state (tile + halo) and row constants --
-  for (int e = tid; e < (TZ + 4) * (TX + 4); e += NTHREADS) {
+  for (int e = tid; e < (TZ + 4) * (TX + 4); e += MIXED_THREADS) {
     const int rr = e / (TX + 4), cc = e - rr * (TX + 4);
     const int k = k0 - 2 + rr;
     float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -292,7 +299,7 @@ static __device__ __noinline__ void stage_tile_mixed(const StageArgs& a, int til
 
   // ---- 2. u, w, T (full states) on the ring; interface state in double --
   const float gamma = g.gammaf, gm1 = g.gm1f;
-  for (int e = tid; e < (TZ + 2) * (TX + 2); e += NTHREADS) {
+  for (int e = tid; e < (TZ + 2) * (TX + 2); e += MIXED_THREADS) {
     const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
     const int k = k0 - 1 + rr;
     if (k < 0 || k >= nz) continue;
@@ -340,7 +347,7 @@ static __device__ __noinline__ void stage_tile_mixed(const StageArgs& a, int til
 
   // ---- 3. slopes ---------------------------------------------------------
   const float hinv_dx = 0.5f * g.inv_dxf;
-  for (int e = tid; e < TZ * (TX + 2); e += NTHREADS) {
+  for (int e = tid; e < TZ * (TX + 2); e += MIXED_THREADS) {
     const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
     const int k = k0 + rr;
     if (k >= row_hi) continue;
@@ -358,7 +365,7 @@ static __device__ __noinline__ void stage_tile_mixed(const StageArgs& a, int til
     const float hinv_dz = 0.5f * (k < n1 ? g.inv_dz1f : g.inv_dz2f);
     S.tz[rr][cc] = make_float2((uu - ud) * hinv_dz, (wu - wd) * hinv_dz);
   }
-  for (int e = tid; e < (TZ + 2) * TX; e += NTHREADS) {
+  for (int e = tid; e < (TZ + 2) * TX; e += MIXED_THREADS) {
     const int rr = e / TX, cc = e - rr * TX;
     const int k = k0 - 1 + rr;
     if (k < 0 || k >= nz) continue;
@@ -377,22 +384,22 @@ static __device__ __noinline__ void stage_tile_mixed(const StageArgs& a, int til
 
   // ---- 4. faces: own left x face (registers), own lower z face (shared) --
   const int k = k0 + ty;
-  const bool live = k < row_hi;
-  const float mu_c = k < n1 ? g.mu1f : g.mu2f, kap_c = k < n1 ? g.kap1f : g.kap2f;
+  const bool live = ty < TZ && k < row_hi;
   float4 fxl = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (live) {
-    const float4 FI = x_face(a, S, ty, tx);
-    const float4 FV = x_face_visc(a, S, ty, tx, mu_c, kap_c);
-    fxl = make_float4(FI.x - FV.x, FI.y - FV.y, FI.z - FV.z, FI.w - FV.w);
-  }
-  // lower z face of the owned cell (needed by it, and by the cell below)
-  if (k - 1 < row_hi) z_face(a, S, k0, ty, tx);
-  // edge faces: warp 0 the z faces above the tile, warp 1 the right x faces
-  if (ty == 0) {
+  if (ty < TZ) {
+    if (live) {
+      const float mu_c = k < n1 ? g.mu1f : g.mu2f, kap_c = k < n1 ? g.kap1f : g.kap2f;
+      const float4 FI = x_face(a, S, ty, tx);
+      const float4 FV = x_face_visc(a, S, ty, tx, mu_c, kap_c);
+      fxl = make_float4(FI.x - FV.x, FI.y - FV.y, FI.z - FV.z, FI.w - FV.w);
+    }
+    // lower z face of the owned cell (needed by it, and by the cell below)
+    if (k - 1 < row_hi) z_face(a, S, k0, ty, tx);
+  } else {
+    // warp 8: the z faces above the tile, then the x faces on its right edge
     if (k0 + TZ - 1 < row_hi) z_face(a, S, k0, TZ, tx);
-  } else if (ty == 1 && tx < TZ) {
     const int kr = k0 + tx;
-    if (kr < row_hi) {
+    if (tx < TZ && kr < row_hi) {
       const float mu = kr < n1 ? g.mu1f : g.mu2f, kap = kr < n1 ? g.kap1f : g.kap2f;
       const float4 FI = x_face(a, S, tx, TX);
       const float4 FV = x_face_visc(a, S, tx, TX, mu, kap);
@@ -406,7 +413,7 @@ static __device__ __noinline__ void stage_tile_mixed(const StageArgs& a, int til
   fxr.z = __shfl_down_sync(0xffffffffu, fxl.z, 1);
   fxr.w = __shfl_down_sync(0xffffffffu, fxl.w, 1);
   __syncthreads();
-  if (tx == TX - 1) fxr = S.fxr[ty];
+  if (tx == TX - 1 && ty < TZ) fxr = S.fxr[ty];
 
   // ---- 5. R (float) and the stage combination (double) -------------------
   const int i = i0 + tx;

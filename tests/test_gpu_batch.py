@@ -41,6 +41,9 @@ def uneven(count, seed, precision=0):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_batch_equals_each_instance_alone(precision):
+    """FP64: bitwise (both kernels run the same non-inlined tile body).
+    FP32 flux: within the mode's tolerance (the tile is inlined into each
+    kernel, which may contract float operations differently)."""
     from paper_2202_11890_gb300 import mprk as M
     cases = uneven(14, 3 + precision, precision)
     steps = 3
@@ -54,7 +57,10 @@ def test_batch_equals_each_instance_alone(precision):
         M.mprk_step_batch([i.h for i in insts], steps)
         for i, ref in zip(insts, alone):
             out = i.state()
-            assert np.array_equal(out, ref)
+            if precision == 0:
+                assert np.array_equal(out, ref)
+            else:
+                assert np.all(rel_err(out, ref) < 1e-5), rel_err(out, ref)
             assert i.status() == 0
             assert i.diagnostics()[14] == steps
     finally:

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2202_11890_gb300 import workloads as W
-from pairs import pair
+from pairs import pair, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -79,7 +79,10 @@ def test_served_results_equal_solo_results(precision):
             j = order[t]
             assert err == 0
             assert stats["steps_done"] == reqs[j][2]
-            assert np.array_equal(buf, refs[j]), j
+            if precision == 0:
+                assert np.array_equal(buf, refs[j]), j
+            else:  # FP32 flux: batch and solo kernels agree to float rounding
+                assert np.all(rel_err(buf, refs[j]) < 1e-5), (j, rel_err(buf, refs[j]))
         s = M.mprk_server_stats(srv)
         assert s[0] == len(reqs) and s[7] == 0 and s[5] == 0
     finally:
