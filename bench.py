@@ -404,6 +404,51 @@ def run_served(args):
     print(json.dumps(out))
 
 
+def run_speedup(args):
+    """MPRK2 against its single-rate base RK2 on the GPU (Sec. 4, Eq. speedup;
+    the shape of Table 2): 100 rows, 6 buffer rows, N_S/N in {4, 14, ..., 84}
+    per 100, m in {2, 4, 8}, FP64, nx columns. The single-rate run takes m
+    RK2 steps of dt/m over the whole grid per slow step. Reports the measured
+    wall-clock ratio next to the theoretical spd."""
+    import torch
+    from paper_2202_11890_gb300 import build as B
+    from paper_2202_11890_gb300 import mprk as M
+    from paper_2202_11890_gb300 import timing as T
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    nx = args.speedup_nx
+    rows = []
+    for ns in range(4, 85, 10):
+        nB, nF = 6, 100 - ns - 6
+        g = W.Grid(nx, ns, nB, nF, dx=10.0 / nx, dz1=10.0 / 100, dz2=10.0 / 100)
+        q0 = W.gaussian_bumps(g, SEED_SPEEDUP)
+        for m in (2, 4, 8):
+            times = {}
+            for scheme in (M.MPRK_SCHEME_MPRK2, M.MPRK_SCHEME_SR_RK2):
+                cfg = M.mprk_config_default(nx, ns, nB, nF, m, dx=g.dx, dz1=g.dz1, dz2=g.dz2)
+                cfg.scheme = scheme
+                cfg.dt = 1e-3
+                with M.Instance(cfg, q0) as inst:
+                    inst.step(args.warmup)
+                    inst.sync()
+                    times[scheme] = T.time_steps(inst.h, inst.info()["stream"], args.steps) / args.steps
+            spd = 1.0 / (1.0 + (1.0 / m - 1.0) * ns / 100.0)
+            rows.append({"NS_over_N": ns / 100, "m": m, "ms_mprk2": times[M.MPRK_SCHEME_MPRK2],
+                         "ms_rk2": times[M.MPRK_SCHEME_SR_RK2],
+                         "wcr": times[M.MPRK_SCHEME_SR_RK2] / times[M.MPRK_SCHEME_MPRK2], "spd": spd})
+    out = {"metric": "wall-clock ratio RK2/MPRK2 (Table 2 shape)", "value": rows[-1]["wcr"], "unit": "ratio",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "speedup_sweep", "nx": nx, "rows": 100, "buffer_rows": 6},
+           "table": rows}
+    print(json.dumps(out))
+
+
+SEED_SPEEDUP = W.SEED0 + 9
+
+
 def oracle_sample(wl: W.Workload, cols: int):
     """The workload's rows, rate and perturbation on a strip of `cols` columns
     (the oracle's cost per cell-stage does not depend on nx)."""
@@ -483,7 +528,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large_2048",
-                    choices=["large_2048", "plain_64", "mixed_4096", "batched_256", "served"])
+                    choices=["large_2048", "plain_64", "mixed_4096", "batched_256", "served", "speedup"])
+    ap.add_argument("--speedup-nx", type=int, default=2048)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--served-requests", type=int, default=2000)
     ap.add_argument("--served-warmup", type=int, default=200)
@@ -502,6 +548,8 @@ def main():
         run_batched(args)
     elif args.workload == "served":
         run_served(args)
+    elif args.workload == "speedup":
+        run_speedup(args)
     else:
         run_ours(args)
 

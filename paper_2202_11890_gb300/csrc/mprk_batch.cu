@@ -95,7 +95,7 @@ __device__ __forceinline__ void finalize_chunk(const Geom& g, const Bufs& b, int
     else if (k < g.n1_r) v = b.accB[((size_t)c * (g.n1_r - g.nS_r) + (k - g.nS_r)) * g.pitch + i];
     else v = m_odd ? b.qB[o] : b.qA[o];
     b.qA[o] = v;
-    if (mixed) b.dA[o] = narrow(v - (double)b.rowc[c * g.nz + k]);
+    if (mixed) b.dA[o] = narrow(v - (double)b.rowc[4 * k + c]);
   }
 }
 

@@ -71,20 +71,21 @@ __device__ __forceinline__ double ref_pressure(const Geom& g, const double* refd
   return g.gm1 * (E - kk);
 }
 
-__global__ void row_const_kernel(const Geom g, const double* __restrict__ refd, float* rowc) {
+__global__ void row_const_kernel(const Geom g, const double* __restrict__ refd, float4* rowc) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= g.nz) return;
   const int nz = g.nz, n1 = g.n1;
   const bool up_in = (k + 1 < nz) && ((k + 1 < n1) == (k < n1));
   const bool dn_in = (k - 1 >= 0) && ((k - 1 < n1) == (k < n1));
-  for (int c = 0; c < 4; c++) {
-    const double own = refd[c * nz + k];
-    const double mir = (c == 2) ? -own : own;
-    const double up = up_in ? refd[c * nz + k + 1] : mir;
-    const double dn = dn_in ? refd[c * nz + k - 1] : mir;
-    rowc[c * nz + k] = (float)own;
-    rowc[(4 + c) * nz + k] = (float)(0.25 * (up - dn));
-    rowc[(8 + c) * nz + k] = (k + 1 < nz) ? (float)(own - refd[c * nz + k + 1]) : 0.f;
+  float a[4], b[4], c[4];
+  for (int j = 0; j < 4; j++) {
+    const double own = refd[j * nz + k];
+    const double mir = (j == 2) ? -own : own;
+    const double up = up_in ? refd[j * nz + k + 1] : mir;
+    const double dn = dn_in ? refd[j * nz + k - 1] : mir;
+    a[j] = (float)own;
+    b[j] = (float)(0.25 * (up - dn));
+    c[j] = (k + 1 < nz) ? (float)(own - refd[j * nz + k + 1]) : 0.f;
   }
   double ke;
   const double p = ref_pressure(g, refd, k, &ke);
@@ -94,10 +95,11 @@ __global__ void row_const_kernel(const Geom g, const double* __restrict__ refd, 
   const double p_dn = wall_dn ? p : 0.5 * (p + ref_pressure(g, refd, k - 1, nullptr));
   const double p_up = wall_up ? p : 0.5 * (p + ref_pressure(g, refd, k + 1, nullptr));
   const double inv_dz = k < n1 ? g.inv_dz1 : g.inv_dz2;
-  rowc[12 * nz + k] = (float)ke;
-  rowc[13 * nz + k] = (float)((p_dn - p_up) * inv_dz - refd[k] * g.G);
-  rowc[14 * nz + k] = (float)p;
-  rowc[15 * nz + k] = 0.f;
+  rowc[k] = make_float4(a[0], a[1], a[2], a[3]);
+  rowc[nz + k] = make_float4(b[0], b[1], b[2], b[3]);
+  rowc[2 * nz + k] = make_float4(c[0], c[1], c[2], c[3]);
+  rowc[3 * nz + k] =
+      make_float4((float)ke, (float)((p_dn - p_up) * inv_dz - refd[k] * g.G), (float)p, 0.f);
 }
 
 cudaError_t launch_reference(const Geom& g, const double* q, double* refd, float* rowc,
@@ -106,7 +108,7 @@ cudaError_t launch_reference(const Geom& g, const double* q, double* refd, float
   row_mean_kernel<<<b, 128, 0, stream>>>(g, q, refd);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  row_const_kernel<<<b, 128, 0, stream>>>(g, refd, rowc);
+  row_const_kernel<<<b, 128, 0, stream>>>(g, refd, reinterpret_cast<float4*>(rowc));
   return cudaGetLastError();
 }
 
@@ -119,7 +121,7 @@ __global__ void shadow_kernel(const Geom g, const double* __restrict__ q, const 
     const int rem = (int)(e - (long long)c * g.nz * g.nx);
     const int k = rem / g.nx, i = rem - k * g.nx;
     const size_t o = ((size_t)c * g.nz + k) * g.pitch + i;
-    d[o] = narrow(q[o] - (double)rowc[c * g.nz + k]);
+    d[o] = narrow(q[o] - (double)rowc[4 * k + c]);
   }
 }
 
@@ -153,7 +155,7 @@ __global__ void finalize_kernel(const Geom g, const Bufs b, int m_odd) {
     else if (k < g.n1_r) v = b.accB[((size_t)c * (g.n1_r - g.nS_r) + (k - g.nS_r)) * g.pitch + i];
     else v = m_odd ? b.qB[o] : b.qA[o];
     b.qA[o] = v;
-    if (mixed) b.dA[o] = narrow(v - (double)b.rowc[c * g.nz + k]);
+    if (mixed) b.dA[o] = narrow(v - (double)b.rowc[4 * k + c]);
   }
 }
 

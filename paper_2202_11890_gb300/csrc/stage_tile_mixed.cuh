@@ -18,12 +18,13 @@
 // only sees the accumulation into the double state: one DFMA per component
 // per fast substep.
 //
-// Layout for few instructions per cell: one thread owns one cell of the
-// TX x TZ tile and computes the x face on its left and the z face below it;
-// a ninth warp computes the faces on the tile's right and top edges.
-// Per-cell quantities sit in shared memory as float4 (one 16-byte load
-// each). The right x face of a cell comes from the neighbouring lane by a
-// warp shuffle.
+// Layout for few instructions per cell: the halo tile is loaded once with
+// u, w, T computed on the way in (float4 per cell in shared memory). One
+// thread owns one cell of the TX x TZ tile and computes the x face on its
+// left and the z face below it, taking slopes from the staged values as it
+// goes; a ninth warp computes the faces on the tile's right and top edges.
+// The right x face of a cell comes from the neighbouring lane by a warp
+// shuffle. Two barriers per tile.
 #pragma once
 
 #include "mprk_internal.h"
@@ -59,13 +60,12 @@ __device__ __forceinline__ float narrow(double x) {
   return __uint_as_float(f);
 }
 
-// Per-row constants (float), index [j * nz + k]:
-//   0-3   q_ref (rho, rho u, rho w, rho E)
-//   4-7   quarter z difference of q_ref with the mirror rule at walls and Gamma
-//   8-11  q_ref(k) - q_ref(k+1)
-//   12    kinetic energy of q_ref
-//   13    reference pressure divergence and gravity for R(rho w)
-//   14    p_ref
+// Per-row constants: four float4 groups, group j of row k at [j * nz + k]:
+//   A (j = 0)  q_ref (rho, rho u, rho w, rho E)
+//   B (j = 1)  quarter z difference of q_ref with the mirror rule at walls and Gamma
+//   C (j = 2)  q_ref(k) - q_ref(k+1)
+//   D (j = 3)  (kinetic energy of q_ref, reference pressure divergence and
+//              gravity for R(rho w), p_ref, 0)
 constexpr int NROWC = 16;
 
 // Nine warps: warps 0-7 own the TX x TZ cells, warp 8 computes the faces on
@@ -74,17 +74,16 @@ constexpr int NROWC = 16;
 constexpr int MIXED_THREADS = NTHREADS + 32;
 
 struct MixedSmem {
-  float4 q[TZ + 4][TX + 4];   // deviation d of the stage state (rho, mu, mw, E)
-  float4 v[TZ + 2][TX + 2];   // (u, w, T, -) full values on the one-cell ring
-  float4 hx[TZ][TX + 2];      // quarter x differences of d
-  float4 hz[TZ + 2][TX];      // quarter z differences of d plus the reference part
-  float2 tz[TZ][TX + 2];      // d/dz of (u, w)
-  float2 tx[TZ + 2][TX];      // d/dx of (u, w)
-  float4 fz[TZ + 1][TX];      // z face fluxes seen from above (rho, mu, mw, E order)
-  float4 fxr[TZ];             // x face on the tile's right edge, per row
-  float4 fg[TX];              // interface flux seen from fluid 1 (below)
-  float rc[NROWC][TZ + 4];    // row constants of rows k0-2 ..
-  double gam[4][TX + 2];      // sigma_xz, Pi_z, u_w, T_w per column i0-1 ..
+  float4 q[TZ + 4][TX + 4];  // deviation d of the stage state (rho, mu, mw, E) on the halo
+  float4 v[TZ + 4][TX + 4];  // (u, w, T, -) full values on the halo
+  float4 fz[TZ + 1][TX];     // z face fluxes seen from above (rho, mu, mw, E order)
+  float4 fxr[TZ];            // x face on the tile's right edge, per row
+  float4 fg[TX];             // interface flux seen from fluid 1 (below)
+  float4 rcA[TZ + 4];        // q_ref per halo row
+  float4 rcB[TZ + 4];        // quarter z difference of q_ref (mirror rule)
+  float4 rcC[TZ + 4];        // q_ref(k) - q_ref(k+1)
+  float4 rcD[TZ + 4];        // (kinetic energy of q_ref, R(rho w) constant, p_ref, -)
+  double gam[4][TX + 2];     // sigma_xz, Pi_z, u_w, T_w per column i0-1 ..
 };
 
 // Lax–Friedrichs flux in the face frame from references and deviations.
@@ -125,55 +124,125 @@ __device__ __forceinline__ void lf_face_dev(float rL, float mnL_, float mtL_, fl
   out[3] = 0.5f * (unL * (lE + pL) + unR * (rE + pR)) + hl * dq[3];
 }
 
-// One side of a z face in the face frame (normal = z: mn = rho w, mt = rho u).
-struct SideZ {
-  float r, mn, mt, E, ke, p;  // reference of the row
-  float dr, dmn, dmt, dE;     // reconstructed deviation
+// Geometry of a tile row: is the row above / below in the same fluid, and
+// what lies beyond it (outer wall or Gamma).
+struct RowNb {
+  bool up_in, dn_in;      // neighbour row in the same fluid
+  bool top_wall, top_gam; // row above is an outer wall / across Gamma
+  bool bot_wall, bot_gam;
 };
 
-__device__ __forceinline__ SideZ side_z(const MixedSmem& S, int rq, int rh, int cc, float sgn) {
-  SideZ s;
-  s.r = S.rc[0][rq];
-  s.mt = S.rc[1][rq];
-  s.mn = S.rc[2][rq];
-  s.E = S.rc[3][rq];
-  s.ke = S.rc[12][rq];
-  s.p = S.rc[14][rq];
-  const float4 q = S.q[rq][cc + 2];
-  const float4 h = S.hz[rh][cc];
-  s.dr = q.x + sgn * h.x;
-  s.dmt = q.y + sgn * h.y;
-  s.dmn = q.z + sgn * h.z;
-  s.dE = q.w + sgn * h.w;
-  return s;
+__device__ __forceinline__ RowNb row_nb(int k, int nz, int n1) {
+  RowNb r;
+  r.top_wall = (k + 1 == nz);
+  r.top_gam = (k + 1 == n1);
+  r.bot_wall = (k == 0);
+  r.bot_gam = (k == n1);
+  r.up_in = !r.top_wall && !r.top_gam;
+  r.dn_in = !r.bot_wall && !r.bot_gam;
+  return r;
 }
 
-// The z face f of the tile (between halo rows f+1 and f+2, i.e. rows k0+f-1
-// and k0+f) in column cc: writes fz[f][cc], and fg[cc] at the interface.
-__device__ __forceinline__ void z_face(const StageArgs& a, MixedSmem& S, int k0, int f, int cc) {
-  const Geom& g = a.g;
+__device__ __forceinline__ float4 mirror4(float4 q) { return make_float4(q.x, q.y, -q.z, q.w); }
+
+constexpr int HW = TX + 4;  // halo row width: neighbours above and below are +-HW apart
+
+// Quarter z difference of the deviation at the halo cell q (a pointer into
+// S.q), mirror ghost beyond a wall or Gamma, plus the reference part rb of
+// the row.
+__device__ __forceinline__ float4 slope_z(const float4* q, float4 rb, const RowNb& nb) {
+  const float4 own = q[0];
+  const float4 up = nb.up_in ? q[HW] : mirror4(own);
+  const float4 dn = nb.dn_in ? q[-HW] : mirror4(own);
+  return make_float4(0.25f * (up.x - dn.x) + rb.x, 0.25f * (up.y - dn.y) + rb.y,
+                     0.25f * (up.z - dn.z) + rb.z, 0.25f * (up.w - dn.w) + rb.w);
+}
+
+// d/dz of (u, w) at the halo cell v (a pointer into S.v): ghost
+// 2*(wall state) - interior beyond a wall (no-slip or slip) or Gamma (the
+// column's fluid-1 wall velocity uw).
+__device__ __forceinline__ float2 dz_uw(const float4* v, const Geom& g, const RowNb& nb, float uw,
+                                        float hinv_dz) {
+  const float4 vc = v[0];
+  float uu, wu, ud, wd;
+  if (nb.up_in) { const float4 vn = v[HW]; uu = vn.x; wu = vn.y; }
+  else if (nb.top_gam) { uu = 2.0f * uw - vc.x; wu = -vc.y; }
+  else { uu = g.wall ? vc.x : -vc.x; wu = -vc.y; }
+  if (nb.dn_in) { const float4 vs = v[-HW]; ud = vs.x; wd = vs.y; }
+  else if (nb.bot_gam) { ud = 2.0f * uw - vc.x; wd = -vc.y; }
+  else { ud = g.wall ? vc.x : -vc.x; wd = -vc.y; }
+  return make_float2((uu - ud) * hinv_dz, (wu - wd) * hinv_dz);
+}
+
+// d/dx of (u, w) at the halo cell v.
+__device__ __forceinline__ float2 dx_uw(const float4* v, float hinv_dx) {
+  const float4 ve = v[1], vw = v[-1];
+  return make_float2((ve.x - vw.x) * hinv_dx, (ve.y - vw.y) * hinv_dx);
+}
+
+// x face between tile columns f-1 and f (halo columns f+1, f+2) of halo row hr
+// (grid row k): F* = F^{I*} - F^{V*}, in (rho, mu, mw, E) order.
+__device__ __forceinline__ float4 x_face3(const MixedSmem& S, const Geom& g, int hr, int f, const RowNb& nb,
+                                          float mu, float kap, float hinv_dz) {
+  const float4* q = &S.q[hr][f];      // q[0..3]: halo columns f .. f+3
+  const float4* v = &S.v[hr][f + 1];  // v[0], v[1]: the two cells
+  const float4 qa = q[0], qb = q[1], qc = q[2], qd = q[3];
+  const float4 ref = S.rcA[hr], rd = S.rcD[hr];
+  // reconstructed deviations q + (q_{+1} - q_{-1})/4, q - (q_{+1} - q_{-1})/4
+  const float dlr = qb.x + 0.25f * (qc.x - qa.x), dlm = qb.y + 0.25f * (qc.y - qa.y);
+  const float dlw = qb.z + 0.25f * (qc.z - qa.z), dlE = qb.w + 0.25f * (qc.w - qa.w);
+  const float drr = qc.x - 0.25f * (qd.x - qb.x), drm = qc.y - 0.25f * (qd.y - qb.y);
+  const float drw = qc.z - 0.25f * (qd.z - qb.z), drE = qc.w - 0.25f * (qd.w - qb.w);
+  const float dq[4] = {dlr - drr, dlm - drm, dlw - drw, dlE - drE};
+  float FI[4], FV[4];
+  lf_face_dev(ref.x, ref.y, ref.z, ref.w, rd.x, rd.z, dlr, dlm, dlw, dlE, ref.x, ref.y, ref.z, ref.w, rd.x, rd.z,
+              drr, drm, drw, drE, dq, g.gammaf, g.gm1f, FI);
+  float uwL = 0.f, uwR = 0.f;
+  if (nb.top_gam || nb.bot_gam) {
+    uwL = narrow(S.gam[2][f]);
+    uwR = narrow(S.gam[2][f + 1]);
+  }
+  const float4 vL = v[0], vR = v[1];
+  const float2 tL = dz_uw(v, g, nb, uwL, hinv_dz), tR = dz_uw(v + 1, g, nb, uwR, hinv_dz);
+  visc_face<float>(vL.x, vL.y, vL.z, tL.x, tL.y, vR.x, vR.y, vR.z, tR.x, tR.y, g.inv_dxf, mu, kap, FV);
+  return make_float4(FI[0] - FV[0], FI[1] - FV[1], FI[2] - FV[2], FI[3] - FV[3]);
+}
+
+// z face below grid row ku = k0+f (halo rows hd = f+1 below, hu = f+2 above)
+// in tile column cc: writes fz[f][cc], and fg[cc] at the interface.
+__device__ __forceinline__ void z_face3(MixedSmem& S, const Geom& g, int k0, int f, int cc) {
   const int nz = g.nz, n1 = g.n1;
   const int ku = k0 + f, kd = ku - 1;
+  const int hd = f + 1, hu = f + 2, hc = cc + 2;
+  const float4* qd = &S.q[hd][hc];  // cell below the face; the cell above is qd[HW]
+  const float4* vd = &S.v[hd][hc];
   const float gamma = g.gammaf, gm1 = g.gm1f;
+  const float hinv_dx = 0.5f * g.inv_dxf;
   if (ku == 0 || ku == nz) {
     // outer wall: the boundary cell against its mirror (inviscid) and its
     // ghost 2*wall - interior (viscous); no-slip or slip, adiabatic
     const bool below = (ku == 0);
-    const int rq = below ? f + 2 : f + 1, rh = below ? f + 1 : f, rv = below ? f + 1 : f;
-    const SideZ s = side_z(S, rq, rh, cc, below ? -1.f : 1.f);
-    const float dq[4] = {0.f, below ? -2.f * (s.mn + s.dmn) : 2.f * (s.mn + s.dmn), 0.f, 0.f};
+    const int h = below ? hu : hd, k = below ? ku : kd;
+    const float4* qc = below ? qd + HW : qd;
+    const float4* vc = below ? vd + HW : vd;
+    const RowNb nb = row_nb(k, nz, n1);
+    const float4 q = qc[0], hz = slope_z(qc, S.rcB[h], nb);
+    const float sg = below ? -1.f : 1.f;
+    const float4 ref = S.rcA[h], rd = S.rcD[h];
+    const float dr = q.x + sg * hz.x, dmt = q.y + sg * hz.y, dmn = q.z + sg * hz.z, dE = q.w + sg * hz.w;
+    const float mn = ref.z + dmn;
+    const float dq[4] = {0.f, below ? -2.f * mn : 2.f * mn, 0.f, 0.f};
     float FI[4], FV[4];
     if (below)
-      lf_face_dev(s.r, -s.mn, s.mt, s.E, s.ke, s.p, s.dr, -s.dmn, s.dmt, s.dE, s.r, s.mn, s.mt, s.E, s.ke,
-                  s.p, s.dr, s.dmn, s.dmt, s.dE, dq, gamma, gm1, FI);
+      lf_face_dev(ref.x, -ref.z, ref.y, ref.w, rd.x, rd.z, dr, -dmn, dmt, dE, ref.x, ref.z, ref.y, ref.w, rd.x,
+                  rd.z, dr, dmn, dmt, dE, dq, gamma, gm1, FI);
     else
-      lf_face_dev(s.r, s.mn, s.mt, s.E, s.ke, s.p, s.dr, s.dmn, s.dmt, s.dE, s.r, -s.mn, s.mt, s.E, s.ke,
-                  s.p, s.dr, -s.dmn, s.dmt, s.dE, dq, gamma, gm1, FI);
-    const float4 vv = S.v[rv][cc + 1];
-    const float2 t = S.tx[rv][cc];
+      lf_face_dev(ref.x, ref.z, ref.y, ref.w, rd.x, rd.z, dr, dmn, dmt, dE, ref.x, -ref.z, ref.y, ref.w, rd.x,
+                  rd.z, dr, -dmn, dmt, dE, dq, gamma, gm1, FI);
+    const float4 vv = vc[0];
+    const float2 t = dx_uw(vc, hinv_dx);
     const float un = vv.y, ut = vv.x, T = vv.z, gn = t.y, gt = t.x;
     const float utg = g.wall ? ut : -ut, gtg = g.wall ? gt : -gt;
-    const int k = below ? ku : kd;
     const float mu = k < n1 ? g.mu1f : g.mu2f, kap = k < n1 ? g.kap1f : g.kap2f;
     const float inv_dn = k < n1 ? g.inv_dz1f : g.inv_dz2f;
     if (below) visc_face<float>(-un, utg, T, -gn, gtg, un, ut, T, gn, gt, inv_dn, mu, kap, FV);
@@ -185,58 +254,46 @@ __device__ __forceinline__ void z_face(const StageArgs& a, MixedSmem& S, int k0,
     const double sig = S.gam[0][cc + 1], Pi = S.gam[1][cc + 1], uw = S.gam[2][cc + 1];
     const float Vt = narrow(sig), VE = narrow(uw * sig - Pi);
     float FI[4];
-    SideZ s = side_z(S, f + 2, f + 1, cc, -1.f);  // fluid 2, above
-    float dq[4] = {0.f, -2.f * (s.mn + s.dmn), 0.f, 0.f};
-    lf_face_dev(s.r, -s.mn, s.mt, s.E, s.ke, s.p, s.dr, -s.dmn, s.dmt, s.dE, s.r, s.mn, s.mt, s.E, s.ke, s.p,
-                s.dr, s.dmn, s.dmt, s.dE, dq, gamma, gm1, FI);
-    S.fz[f][cc] = make_float4(FI[0], FI[2] - Vt, FI[1], FI[3] - VE);
-    s = side_z(S, f + 1, f, cc, 1.f);  // fluid 1, below
-    dq[1] = 2.f * (s.mn + s.dmn);
-    lf_face_dev(s.r, s.mn, s.mt, s.E, s.ke, s.p, s.dr, s.dmn, s.dmt, s.dE, s.r, -s.mn, s.mt, s.E, s.ke, s.p,
-                s.dr, -s.dmn, s.dmt, s.dE, dq, gamma, gm1, FI);
-    S.fg[cc] = make_float4(FI[0], FI[2] - Vt, FI[1], FI[3] - VE);
+    {  // fluid 2, above: mirror below it
+      const RowNb nb = row_nb(ku, nz, n1);
+      const float4 q = qd[HW], hz = slope_z(qd + HW, S.rcB[hu], nb);
+      const float4 ref = S.rcA[hu], rd = S.rcD[hu];
+      const float dr = q.x - hz.x, dmt = q.y - hz.y, dmn = q.z - hz.z, dE = q.w - hz.w;
+      const float dq[4] = {0.f, -2.f * (ref.z + dmn), 0.f, 0.f};
+      lf_face_dev(ref.x, -ref.z, ref.y, ref.w, rd.x, rd.z, dr, -dmn, dmt, dE, ref.x, ref.z, ref.y, ref.w, rd.x,
+                  rd.z, dr, dmn, dmt, dE, dq, gamma, gm1, FI);
+      S.fz[f][cc] = make_float4(FI[0], FI[2] - Vt, FI[1], FI[3] - VE);
+    }
+    {  // fluid 1, below: mirror above it
+      const RowNb nb = row_nb(kd, nz, n1);
+      const float4 q = qd[0], hz = slope_z(qd, S.rcB[hd], nb);
+      const float4 ref = S.rcA[hd], rd = S.rcD[hd];
+      const float dr = q.x + hz.x, dmt = q.y + hz.y, dmn = q.z + hz.z, dE = q.w + hz.w;
+      const float dq[4] = {0.f, 2.f * (ref.z + dmn), 0.f, 0.f};
+      lf_face_dev(ref.x, ref.z, ref.y, ref.w, rd.x, rd.z, dr, dmn, dmt, dE, ref.x, -ref.z, ref.y, ref.w, rd.x,
+                  rd.z, dr, -dmn, dmt, dE, dq, gamma, gm1, FI);
+      S.fg[cc] = make_float4(FI[0], FI[2] - Vt, FI[1], FI[3] - VE);
+    }
   } else {
-    const SideZ L = side_z(S, f + 1, f, cc, 1.f), R = side_z(S, f + 2, f + 1, cc, -1.f);
+    const RowNb nbd = row_nb(kd, nz, n1), nbu = row_nb(ku, nz, n1);
+    const float4 qL = qd[0], qR = qd[HW];
+    const float4 hL = slope_z(qd, S.rcB[hd], nbd), hR = slope_z(qd + HW, S.rcB[hu], nbu);
+    const float4 refL = S.rcA[hd], rdL = S.rcD[hd], refR = S.rcA[hu], rdR = S.rcD[hu], dref = S.rcC[hd];
+    // face frame: normal momentum rho w (.z), tangential rho u (.y)
+    const float lr = qL.x + hL.x, lmt = qL.y + hL.y, lmn = qL.z + hL.z, lE = qL.w + hL.w;
+    const float rr = qR.x - hR.x, rmt = qR.y - hR.y, rmn = qR.z - hR.z, rE = qR.w - hR.w;
     // q_left - q_right = q_ref(kd) - q_ref(ku) + (d_left - d_right)
-    const float dq[4] = {S.rc[8][f + 1] + (L.dr - R.dr), S.rc[10][f + 1] + (L.dmn - R.dmn),
-                         S.rc[9][f + 1] + (L.dmt - R.dmt), S.rc[11][f + 1] + (L.dE - R.dE)};
+    const float dq[4] = {dref.x + (lr - rr), dref.z + (lmn - rmn), dref.y + (lmt - rmt), dref.w + (lE - rE)};
     float FI[4], FV[4];
-    lf_face_dev(L.r, L.mn, L.mt, L.E, L.ke, L.p, L.dr, L.dmn, L.dmt, L.dE, R.r, R.mn, R.mt, R.E, R.ke, R.p,
-                R.dr, R.dmn, R.dmt, R.dE, dq, gamma, gm1, FI);
+    lf_face_dev(refL.x, refL.z, refL.y, refL.w, rdL.x, rdL.z, lr, lmn, lmt, lE, refR.x, refR.z, refR.y, refR.w,
+                rdR.x, rdR.z, rr, rmn, rmt, rE, dq, gamma, gm1, FI);
     const float mu = kd < n1 ? g.mu1f : g.mu2f, kap = kd < n1 ? g.kap1f : g.kap2f;
     const float inv_dn = kd < n1 ? g.inv_dz1f : g.inv_dz2f;
-    const float4 vL = S.v[f][cc + 1], vR = S.v[f + 1][cc + 1];
-    const float2 tL = S.tx[f][cc], tR = S.tx[f + 1][cc];
+    const float4 vL = vd[0], vR = vd[HW];
+    const float2 tL = dx_uw(vd, hinv_dx), tR = dx_uw(vd + HW, hinv_dx);
     visc_face<float>(vL.y, vL.x, vL.z, tL.y, tL.x, vR.y, vR.x, vR.z, tR.y, tR.x, inv_dn, mu, kap, FV);
     S.fz[f][cc] = make_float4(FI[0] - FV[0], FI[2] - FV[2], FI[1] - FV[1], FI[3] - FV[3]);
   }
-}
-
-// The x face between ring columns f and f+1 (tile columns f-1 and f) of tile
-// row rr; returns the flux in (rho, mu, mw, E) order.
-__device__ __forceinline__ float4 x_face(const StageArgs& a, const MixedSmem& S, int rr, int f) {
-  const Geom& g = a.g;
-  const int rq = rr + 2;
-  const float r0 = S.rc[0][rq], m0 = S.rc[1][rq], w0 = S.rc[2][rq], E0 = S.rc[3][rq];
-  const float ke = S.rc[12][rq], pr = S.rc[14][rq];
-  const float4 qL = S.q[rq][f + 1], qR = S.q[rq][f + 2];
-  const float4 hL = S.hx[rr][f], hR = S.hx[rr][f + 1];
-  const float dlr = qL.x + hL.x, dlmn = qL.y + hL.y, dlmt = qL.z + hL.z, dlE = qL.w + hL.w;
-  const float drr = qR.x - hR.x, drmn = qR.y - hR.y, drmt = qR.z - hR.z, drE = qR.w - hR.w;
-  const float dq[4] = {dlr - drr, dlmn - drmn, dlmt - drmt, dlE - drE};
-  float FI[4];
-  lf_face_dev(r0, m0, w0, E0, ke, pr, dlr, dlmn, dlmt, dlE, r0, m0, w0, E0, ke, pr, drr, drmn, drmt, drE, dq,
-              g.gammaf, g.gm1f, FI);
-  return make_float4(FI[0], FI[1], FI[2], FI[3]);
-}
-
-__device__ __forceinline__ float4 x_face_visc(const StageArgs& a, const MixedSmem& S, int rr, int f, float mu,
-                                              float kap) {
-  const float4 vL = S.v[rr + 1][f], vR = S.v[rr + 1][f + 1];
-  const float2 tL = S.tz[rr][f], tR = S.tz[rr][f + 1];
-  float FV[4];
-  visc_face<float>(vL.x, vL.y, vL.z, tL.x, tL.y, vR.x, vR.y, vR.z, tR.x, tR.y, a.g.inv_dxf, mu, kap, FV);
-  return make_float4(FV[0], FV[1], FV[2], FV[3]);
 }
 
 // Inlined into each kernel: launch constants then stay constant-bank
@@ -246,7 +303,7 @@ __device__ __forceinline__ float4 x_face_visc(const StageArgs& a, const MixedSme
 __device__ __forceinline__ void stage_tile_mixed(const StageArgs& a, int tile, MixedSmem& S) {
   const Geom& g = a.g;
   const int tid = threadIdx.x;
-  const int ty = tid / TX, tx = tid - ty * TX;  // owned cell
+  const int ty = tid / TX, tx = tid - ty * TX;  // owned cell (warp 8: edge faces)
   const int tzi = tile / a.tiles_x;
   const int txi = tile - tzi * a.tiles_x;
   const int k0 = a.row0 + tzi * TZ;
@@ -256,24 +313,27 @@ __device__ __forceinline__ void stage_tile_mixed(const StageArgs& a, int tile, M
   const size_t plane = (size_t)nz * g.pitch;
   const bool odd_stage = !a.rhs_only && (a.stage & 1);
   const float* Ra = reinterpret_cast<const float*>(a.b.Ra);
-  const float* rowc = a.b.rowc;
+  const float4* rowc = reinterpret_cast<const float4*>(a.b.rowc);
+  const float gamma = g.gammaf, gm1 = g.gm1f;
 
-  // ---- 1. deviations of the stage state (tile + halo) and row constants --
+  // ---- 1. stage-state deviations on the halo, with u, w, T per cell ------
   for (int e = tid; e < (TZ + 4) * (TX + 4); e += MIXED_THREADS) {
     const int rr = e / (TX + 4), cc = e - rr * (TX + 4);
     const int k = k0 - 2 + rr;
-    float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 val = make_float4(0.f, 0.f, 0.f, 0.f), vv = make_float4(0.f, 0.f, 0.f, 0.f);
     if (k >= 0 && k < nz) {
       int i = i0 - 2 + cc;
       if (i < 0) i += nx;
       if (i >= nx) i -= nx;
       if (i >= nx) i %= nx;  // only when nx is smaller than the tile
       const size_t off = (size_t)k * g.pitch + i;
+      const float4 ra4 = rowc[k], rd4 = rowc[3 * nz + k];
+      const float r0 = ra4.x, m0 = ra4.y, w0 = ra4.z;
       if (a.rhs_only) {
-        val.x = narrow(a.rhs_in[off] - (double)rowc[k]);
-        val.y = narrow(a.rhs_in[plane + off] - (double)rowc[nz + k]);
-        val.z = narrow(a.rhs_in[2 * plane + off] - (double)rowc[2 * nz + k]);
-        val.w = narrow(a.rhs_in[3 * plane + off] - (double)rowc[3 * nz + k]);
+        val.x = narrow(a.rhs_in[off] - (double)r0);
+        val.y = narrow(a.rhs_in[plane + off] - (double)m0);
+        val.z = narrow(a.rhs_in[2 * plane + off] - (double)w0);
+        val.w = narrow(a.rhs_in[3 * plane + off] - (double)ra4.w);
       } else {
         const float* base = (k < g.n1_r ? a.b.dA : a.dF) + off;
         val = make_float4(base[0], base[plane], base[2 * plane], base[3 * plane]);
@@ -286,32 +346,30 @@ __device__ __forceinline__ void stage_tile_mixed(const StageArgs& a, int tile, M
           val.w += h * ra[3 * plane];
         }
       }
+      const float r = r0 + val.x, mu_ = m0 + val.y, mw = w0 + val.z;
+      const float inv = __frcp_rn(r);
+      const float u = mu_ * inv, w = mw * inv;
+      const float dp = gm1 * (val.w - (0.5f * (mu_ * u + mw * w) - rd4.x));
+      vv = make_float4(u, w, gamma * (rd4.z + dp) * inv, 0.f);
     }
     S.q[rr][cc] = val;
+    S.v[rr][cc] = vv;
   }
-  if (tid < NROWC * (TZ + 4)) {
+  if (tid < 4 * (TZ + 4)) {
     const int j = tid / (TZ + 4), rr = tid - j * (TZ + 4);
     const int k = k0 - 2 + rr;
-    S.rc[j][rr] = (k >= 0 && k < nz) ? rowc[j * nz + k] : 0.f;
+    const float4 c = (k >= 0 && k < nz) ? rowc[j * nz + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j == 0) S.rcA[rr] = c;
+    else if (j == 1) S.rcB[rr] = c;
+    else if (j == 2) S.rcC[rr] = c;
+    else S.rcD[rr] = c;
   }
   const bool has_gamma = (n1 >= k0 && n1 <= k0 + TZ);
-  __syncthreads();
-
-  // ---- 2. u, w, T (full states) on the ring; interface state in double --
-  const float gamma = g.gammaf, gm1 = g.gm1f;
-  for (int e = tid; e < (TZ + 2) * (TX + 2); e += MIXED_THREADS) {
-    const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
-    const int k = k0 - 1 + rr;
-    if (k < 0 || k >= nz) continue;
-    const float4 d = S.q[rr + 1][cc + 1];
-    const float r = S.rc[0][rr + 1] + d.x, mu_ = S.rc[1][rr + 1] + d.y, mw = S.rc[2][rr + 1] + d.z;
-    const float inv = __frcp_rn(r);
-    const float u = mu_ * inv, w = mw * inv;
-    const float dp = gm1 * (d.w - (0.5f * (mu_ * u + mw * w) - S.rc[12][rr + 1]));
-    S.v[rr][cc] = make_float4(u, w, gamma * (S.rc[14][rr + 1] + dp) * inv, 0.f);
-  }
-  if (has_gamma && tid < TX + 2) {
-    int i = i0 - 1 + tid;
+  if (has_gamma && tid >= MIXED_THREADS - 64 && tid - (MIXED_THREADS - 64) < TX + 2) {
+    // interface state of column i0-1+j in double from the two cells touching
+    // Gamma (App. B, Eq. bulk-flux and the wall states)
+    const int j = tid - (MIXED_THREADS - 64);
+    int i = i0 - 1 + j;
     if (i < 0) i += nx;
     if (i >= nx) i %= nx;
     double u[2], T[2];
@@ -338,72 +396,35 @@ __device__ __forceinline__ void stage_tile_mixed(const StageArgs& a, int tile, M
     }
     const double sig = g.bu * (u[1] - u[0]);
     const double Pi = -g.bT * (T[1] - T[0]);
-    S.gam[0][tid] = sig;
-    S.gam[1][tid] = Pi;
-    S.gam[2][tid] = u[0] + sig * g.cu1;
-    S.gam[3][tid] = T[0] - Pi * g.cT1;
+    S.gam[0][j] = sig;
+    S.gam[1][j] = Pi;
+    S.gam[2][j] = u[0] + sig * g.cu1;
+    S.gam[3][j] = T[0] - Pi * g.cT1;
   }
   __syncthreads();
 
-  // ---- 3. slopes ---------------------------------------------------------
-  const float hinv_dx = 0.5f * g.inv_dxf;
-  for (int e = tid; e < TZ * (TX + 2); e += MIXED_THREADS) {
-    const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
-    const int k = k0 + rr;
-    if (k >= row_hi) continue;
-    const float4 qe = S.q[rr + 2][cc + 2], qw = S.q[rr + 2][cc];
-    S.hx[rr][cc] = make_float4(0.25f * (qe.x - qw.x), 0.25f * (qe.y - qw.y), 0.25f * (qe.z - qw.z),
-                               0.25f * (qe.w - qw.w));
-    const float4 vc = S.v[rr + 1][cc];
-    float uu, wu, ud, wd;
-    if (k + 1 == nz) { uu = g.wall ? vc.x : -vc.x; wu = -vc.y; }
-    else if (k + 1 == n1) { uu = 2.0f * narrow(S.gam[2][cc]) - vc.x; wu = -vc.y; }
-    else { const float4 vn = S.v[rr + 2][cc]; uu = vn.x; wu = vn.y; }
-    if (k == 0) { ud = g.wall ? vc.x : -vc.x; wd = -vc.y; }
-    else if (k == n1) { ud = 2.0f * narrow(S.gam[2][cc]) - vc.x; wd = -vc.y; }
-    else { const float4 vs = S.v[rr][cc]; ud = vs.x; wd = vs.y; }
-    const float hinv_dz = 0.5f * (k < n1 ? g.inv_dz1f : g.inv_dz2f);
-    S.tz[rr][cc] = make_float2((uu - ud) * hinv_dz, (wu - wd) * hinv_dz);
-  }
-  for (int e = tid; e < (TZ + 2) * TX; e += MIXED_THREADS) {
-    const int rr = e / TX, cc = e - rr * TX;
-    const int k = k0 - 1 + rr;
-    if (k < 0 || k >= nz) continue;
-    const bool up_in = (k + 1 < nz) && ((k + 1 < n1) == (k < n1));
-    const bool dn_in = (k - 1 >= 0) && ((k - 1 < n1) == (k < n1));
-    const float4 own = S.q[rr + 1][cc + 2];
-    const float4 mir = make_float4(own.x, own.y, -own.z, own.w);  // mirror ghost: rho w odd
-    const float4 up = up_in ? S.q[rr + 2][cc + 2] : mir;
-    const float4 dn = dn_in ? S.q[rr][cc + 2] : mir;
-    S.hz[rr][cc] = make_float4(0.25f * (up.x - dn.x) + S.rc[4][rr + 1], 0.25f * (up.y - dn.y) + S.rc[5][rr + 1],
-                               0.25f * (up.z - dn.z) + S.rc[6][rr + 1], 0.25f * (up.w - dn.w) + S.rc[7][rr + 1]);
-    const float4 ve = S.v[rr][cc + 2], vw = S.v[rr][cc];
-    S.tx[rr][cc] = make_float2((ve.x - vw.x) * hinv_dx, (ve.y - vw.y) * hinv_dx);
-  }
-  __syncthreads();
-
-  // ---- 4. faces: own left x face (registers), own lower z face (shared) --
+  // ---- 2. faces: own left x face (registers), own lower z face (shared) --
   const int k = k0 + ty;
   const bool live = ty < TZ && k < row_hi;
   float4 fxl = make_float4(0.f, 0.f, 0.f, 0.f);
   if (ty < TZ) {
     if (live) {
+      const RowNb nb = row_nb(k, nz, n1);
       const float mu_c = k < n1 ? g.mu1f : g.mu2f, kap_c = k < n1 ? g.kap1f : g.kap2f;
-      const float4 FI = x_face(a, S, ty, tx);
-      const float4 FV = x_face_visc(a, S, ty, tx, mu_c, kap_c);
-      fxl = make_float4(FI.x - FV.x, FI.y - FV.y, FI.z - FV.z, FI.w - FV.w);
+      const float hinv_dz = 0.5f * (k < n1 ? g.inv_dz1f : g.inv_dz2f);
+      fxl = x_face3(S, g, ty + 2, tx, nb, mu_c, kap_c, hinv_dz);
     }
     // lower z face of the owned cell (needed by it, and by the cell below)
-    if (k - 1 < row_hi) z_face(a, S, k0, ty, tx);
+    if (k - 1 < row_hi) z_face3(S, g, k0, ty, tx);
   } else {
     // warp 8: the z faces above the tile, then the x faces on its right edge
-    if (k0 + TZ - 1 < row_hi) z_face(a, S, k0, TZ, tx);
+    if (k0 + TZ - 1 < row_hi) z_face3(S, g, k0, TZ, tx);
     const int kr = k0 + tx;
     if (tx < TZ && kr < row_hi) {
+      const RowNb nb = row_nb(kr, nz, n1);
       const float mu = kr < n1 ? g.mu1f : g.mu2f, kap = kr < n1 ? g.kap1f : g.kap2f;
-      const float4 FI = x_face(a, S, tx, TX);
-      const float4 FV = x_face_visc(a, S, tx, TX, mu, kap);
-      S.fxr[tx] = make_float4(FI.x - FV.x, FI.y - FV.y, FI.z - FV.z, FI.w - FV.w);
+      const float hinv_dz = 0.5f * (kr < n1 ? g.inv_dz1f : g.inv_dz2f);
+      S.fxr[tx] = x_face3(S, g, tx + 2, TX, nb, mu, kap, hinv_dz);
     }
   }
   // right x face of the owned cell: the left face of the next lane
@@ -415,7 +436,7 @@ __device__ __forceinline__ void stage_tile_mixed(const StageArgs& a, int tile, M
   __syncthreads();
   if (tx == TX - 1 && ty < TZ) fxr = S.fxr[ty];
 
-  // ---- 5. R (float) and the stage combination (double) -------------------
+  // ---- 3. R (float) and the stage combination (double) -------------------
   const int i = i0 + tx;
   if (!live || i >= nx) return;
   const float inv_dx = g.inv_dxf;
@@ -429,8 +450,8 @@ __device__ __forceinline__ void stage_tile_mixed(const StageArgs& a, int tile, M
   R[2] = (fxl.z - fxr.z) * inv_dx + (fdn.z - fup.z) * inv_dz;
   R[3] = (fxl.w - fxr.w) * inv_dx + (fdn.w - fup.w) * inv_dz;
   // gravity on the deviation; the reference part sits in the row constant
-  R[2] += S.rc[13][ty + 2] - dc.x * g.Gf;
-  R[3] -= (S.rc[2][ty + 2] + dc.z) * g.Gf;
+  R[2] += S.rcD[ty + 2].y - dc.x * g.Gf;
+  R[3] -= (S.rcA[ty + 2].z + dc.z) * g.Gf;
 
   const size_t row_off = (size_t)k * g.pitch + i;
   if (a.rhs_only) {
