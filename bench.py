@@ -43,6 +43,43 @@ FLOPS_PER_CELL_STAGE = {True: 355.7, False: 381.6}
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 
+# DRAM traffic of the stage kernel (dram__bytes_read.sum + dram__bytes_write.sum)
+# summed over the 2m stage launches of one slow step of the bench workload,
+# from one ncu capture; the profile summaries under profiles/ give the command.
+# A figure holds only for the sources it was taken on (sha256 over the files
+# in order); after any change to them bench.py reports traffic as null.
+CSRC = os.path.join(ROOT, "paper_2202_11890_gb300", "csrc")
+TRAFFIC = {
+    "stage_kernel": {
+        "files": ("stage_tile.cuh", "mprk_internal.h", "mprk_kernels.cu"),
+        "sha256": "872b1166a3d2ecaf91ed26a33c106380a23a2553043f1298fd20d5aabae7c419",
+        "bytes_per_step": 1167967488,
+    },
+    "stage_kernel_mixed": {
+        "files": ("stage_tile_mixed.cuh", "mprk_internal.h", "mprk_kernels.cu"),
+        "sha256": None,
+        "bytes_per_step": None,
+    },
+}
+
+
+def source_hash(files) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str, launches: int):
+    """DRAM bytes per stage launch (mean over one slow step), or None when the
+    kernel's sources changed since the capture."""
+    t = TRAFFIC[kernel]
+    if t["bytes_per_step"] is None or t["sha256"] != source_hash(t["files"]):
+        return None
+    return t["bytes_per_step"] / launches
+
 
 def algorithmic_bytes(g: W.Grid, m: int, fp64: bool):
     """HBM bytes one slow step must move, each array element read or written
@@ -210,6 +247,10 @@ def run_ours(args):
     peaks, src = measured_peaks()
     stage_bytes, fin_bytes = algorithmic_bytes(g, wl.m, fp64)
     ach_gbs = stage_bytes / (stage_ms * 1e-3) / 1e9
+    kname = "stage_kernel" if fp64 else "stage_kernel_mixed"
+    # traffic is per launch like achieved: the mean over the 2m stage launches
+    traffic = measured_traffic(kname, 2 * wl.m) if args.workload in ("large_2048", "mixed_4096") \
+        and not args.precision else None
 
     # end to end through the C ABI with host buffers: pinned host state in,
     # one slow step, state out, every step
@@ -238,17 +279,19 @@ def run_ours(args):
                        "l2": "working set > L2 (about 4 states of 67 MB); no flush"},
             "roofline": (
                 {"bound": "alu", "achieved": ach_gflops, "peak": peak_alu, "unit": "GFLOP/s",
-                 "frac": ach_gflops / peak_alu, "traffic": None,
+                 "frac": ach_gflops / peak_alu, "traffic": traffic,
                  "peak_source": "FP64 unit count x max clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
                  "hbm_achieved_gbs": ach_gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
                  "hbm_frac": ach_gbs / peaks["hbm_gbs"], "hbm_peak_source": src}
                 if fp64 else
                 {"bound": "hbm", "achieved": ach_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                 "frac": ach_gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                 "frac": ach_gbs / peaks["hbm_gbs"], "traffic": traffic, "peak_source": src,
                  "alu_achieved_gflops": ach_gflops, "alu_peak_gflops": peak_alu}),
-            "kernel": {"name": "stage_kernel" if fp64 else "stage_kernel_mixed",
+            "kernel": {"name": kname,
                        "ms_per_step": stage_ms, "cell_stages_per_step": stage_cells,
+                       "launches_per_step": 2 * wl.m,
                        "algorithmic_bytes_per_step": stage_bytes,
+                       "algorithmic_bytes_per_launch": stage_bytes / (2 * wl.m),
                        "completion_bytes_per_step": fin_bytes},
             "e2e": {"value": e2e_value, "unit": "cell-stages/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
