@@ -100,7 +100,7 @@ __device__ __forceinline__ void finalize_chunk(const Geom& g, const Bufs& b, int
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(batch_threads(PREC), PREC == 0 ? 2 : 3) batch_kernel(const BatchArgs A) {
+__global__ void __launch_bounds__(batch_threads(PREC), 2) batch_kernel(const BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
   __shared__ int s_ok;
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(batch_threads(PREC), PREC == 0 ? 2 : 3) batch_
       if (item.stage < 2 * I.g.m) {
         const StageArgs a = stage_args(I.g, I.b, item.stage);
         if (PREC == 0) stage_tile<double, double>(a, item.tile, *reinterpret_cast<TileSmem<double>*>(smem_raw));
-        else stage_tile_mixed(a, item.tile, *reinterpret_cast<MixedSmem*>(smem_raw));
+        else stage_tile_mixed(a, item.tile, *reinterpret_cast<MixedTileSmem*>(smem_raw));
       } else {
         finalize_chunk(I.g, I.b, item.tile);
       }

@@ -12,7 +12,7 @@
 //   accS [4][nS][pitch] double   q_{n+1} on S rows until the step ends
 // FP32-flux mode only:
 //   dA, dB [4][nz][pitch] float  deviations q - q_ref of qA, qB (float shadows)
-//   rowc [16][nz] float          per-row reference constants (stage_tile_mixed.cuh)
+//   rowc [NROWC][nz] float       per-row reference constants (stage_tile_mixed.cuh)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -27,6 +27,11 @@ namespace mprk {
 constexpr int TX = 32;
 constexpr int TZ = 8;
 constexpr int NTHREADS = TX * TZ;
+// The FP32-flux kernel's tile is TX x 2*TZ cells; each thread of its fast
+// path carries two cells of one column, rows k and k + TZ.
+constexpr int MTZ = 2 * TZ;
+// Floats of per-row constants in the FP32-flux mode (layout in stage_tile_mixed.cuh).
+constexpr int NROWC = 48;
 
 // Status bits written by device code.
 constexpr unsigned ST_NONFINITE = 1u;
@@ -83,6 +88,7 @@ struct StageArgs {
   int stage;          // 0-based stage index i in [0, 2m)
   int row0;           // first row of the launch (0 at stages 0, 1; nS_r later)
   int tiles_x;        // tiles across x
+  int tz;             // tile rows: TZ (FP64) or MTZ (FP32-flux)
   int rhs_only;       // test hook: write R to rhs_out instead of combining
   double* rhs_out;    // [4][nz][pitch] when rhs_only
   int rhs_hi;         // last row (exclusive) when rhs_only
@@ -103,11 +109,12 @@ __host__ __device__ inline StageArgs stage_args(const Geom& g, const Bufs& b, in
   a.stage = st;
   a.row0 = st < 2 ? 0 : g.nS_r;
   a.tiles_x = (g.nx + TX - 1) / TX;
+  a.tz = b.dA ? MTZ : TZ;  // float shadows exist only in the FP32-flux mode
   return a;
 }
 __host__ __device__ inline int stage_tiles(const StageArgs& a) {
   const int hi = a.rhs_only ? a.rhs_hi : a.g.nz;
-  return a.tiles_x * ((hi - a.row0 + TZ - 1) / TZ);
+  return a.tiles_x * ((hi - a.row0 + a.tz - 1) / a.tz);
 }
 
 // Launchers (mprk_kernels.cu). All enqueue on `stream` and return the launch error.

@@ -18,14 +18,14 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   stage_tile<Real, Store>(a, blockIdx.x, S);
 }
 
-__global__ void __launch_bounds__(MIXED_THREADS, 4) stage_kernel_mixed(const StageArgs a) {
+__global__ void __launch_bounds__(MIXED_THREADS, 3) stage_kernel_mixed(const StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  MixedSmem& S = *reinterpret_cast<MixedSmem*>(smem_raw);
+  MixedTileSmem& S = *reinterpret_cast<MixedTileSmem*>(smem_raw);
   stage_tile_mixed(a, blockIdx.x, S);
 }
 
 size_t stage_smem_bytes(int precision) {
-  return precision == 0 ? sizeof(TileSmem<double>) : sizeof(MixedSmem);
+  return precision == 0 ? sizeof(TileSmem<double>) : sizeof(MixedTileSmem);
 }
 
 cudaError_t prepare_kernels() {
@@ -34,7 +34,7 @@ cudaError_t prepare_kernels() {
                                        (int)sizeof(TileSmem<double>));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(stage_kernel_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(MixedSmem));
+                              (int)sizeof(MixedTileSmem));
 }
 
 cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStream_t stream) {
@@ -42,7 +42,7 @@ cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStr
   if (precision == 0) {
     stage_kernel<double, double><<<n_tiles, NTHREADS, sizeof(TileSmem<double>), stream>>>(a);
   } else {
-    stage_kernel_mixed<<<n_tiles, MIXED_THREADS, sizeof(MixedSmem), stream>>>(a);
+    stage_kernel_mixed<<<n_tiles, MIXED_THREADS, sizeof(MixedTileSmem), stream>>>(a);
   }
   return cudaGetLastError();
 }
@@ -102,6 +102,25 @@ __global__ void row_const_kernel(const Geom g, const double* __restrict__ refd, 
       make_float4((float)ke, (float)((p_dn - p_up) * inv_dz - refd[k] * g.G), (float)p, 0.f);
 }
 
+// The paired copies of the row constants for the pair path: rows (k, k + TZ)
+// side by side (groups RC_PAIR .. 11; zero where k + TZ is outside the grid).
+__global__ void row_pair_kernel(const Geom g, float4* rowc) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= g.nz) return;
+  const int nz = g.nz;
+  const bool in = k + TZ < nz;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4* P = rowc + RC_PAIR * nz;
+  for (int j = 0; j < 3; j++) {
+    const float4 a = rowc[j * nz + k], b = in ? rowc[j * nz + k + TZ] : z;
+    P[(2 * j) * nz + k] = make_float4(a.x, b.x, a.y, b.y);
+    P[(2 * j + 1) * nz + k] = make_float4(a.z, b.z, a.w, b.w);
+  }
+  const float4 d = rowc[3 * nz + k], e = in ? rowc[3 * nz + k + TZ] : z;
+  P[6 * nz + k] = make_float4(d.x, e.x, d.z, e.z);
+  P[7 * nz + k] = make_float4(d.y, e.y, 0.f, 0.f);
+}
+
 cudaError_t launch_reference(const Geom& g, const double* q, double* refd, float* rowc,
                              cudaStream_t stream) {
   const int b = (g.nz + 127) / 128;
@@ -109,6 +128,8 @@ cudaError_t launch_reference(const Geom& g, const double* q, double* refd, float
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   row_const_kernel<<<b, 128, 0, stream>>>(g, refd, reinterpret_cast<float4*>(rowc));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  row_pair_kernel<<<b, 128, 0, stream>>>(g, reinterpret_cast<float4*>(rowc));
   return cudaGetLastError();
 }
 

@@ -16,9 +16,6 @@
 
 using namespace mprk;
 
-// per-row float constants of the FP32-flux mode (stage_tile_mixed.cuh)
-constexpr int NROWC_HOST = 16;
-
 namespace {
 thread_local std::string g_err;
 }  // namespace
@@ -275,7 +272,7 @@ long long mprk::instance_bytes(const mprk_config& c) {
   const long long rsz = c.precision == MPRK_FP64 ? 8 : 4;
   long long b = 2 * 4 * plane * 8 + 4 * plane * rsz + r16(4 * nB * pitch * 8) + r16(4 * nS * pitch * 8);
   b += 1024 * 16 * 8 + 16 * 8 + 16;  // monitoring partials (upper bound), results, status
-  if (c.precision != MPRK_FP64) b += 2 * 4 * plane * 4 + 16 * nz * 4 + 4 * nz * 8;
+  if (c.precision != MPRK_FP64) b += 2 * 4 * plane * 4 + NROWC * nz * 4 + 4 * nz * 8;
   return b;
 }
 
@@ -369,7 +366,7 @@ int mprk::create_instance(const mprk_config* cfg, const double* q0, int q0_locat
   }
   if (I->precision == MPRK_FP32FLUX &&
       ((rc = alloc((void**)&I->b.dA, 4 * plane * 4)) || (rc = alloc((void**)&I->b.dB, 4 * plane * 4)) ||
-       (rc = alloc((void**)&I->b.rowc, (size_t)NROWC_HOST * g.nz * 4)) ||
+       (rc = alloc((void**)&I->b.rowc, (size_t)NROWC * g.nz * 4)) ||
        (rc = alloc((void**)&I->refd, (size_t)4 * g.nz * 8)))) {
     free_instance(I);
     return rc;

@@ -58,8 +58,6 @@ int setup_device(int dev, void** out) {
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
-constexpr int kRowConsts = 16;  // per-row float constants of the FP32-flux mode
-
 // Scratch bytes a configuration needs: qB | Ra | accB | accS, and in the
 // FP32-flux mode also dA | dB | rowc | refd; pitch = nx.
 size_t scratch_bytes(const mprk_config* c) {
@@ -72,7 +70,7 @@ size_t scratch_bytes(const mprk_config* c) {
   const size_t nB = mprk2 ? (size_t)c->nz_B : 0, nS = mprk2 ? (size_t)c->nz_S : 0;
   size_t b = align256(4 * plane * 8) + align256(4 * plane * rsz) + align256(4 * nB * c->nx * 8) +
              align256(4 * nS * c->nx * 8);
-  if (!fp64) b += 2 * align256(4 * plane * 4) + align256(kRowConsts * nz * 4) + align256(4 * nz * 8);
+  if (!fp64) b += 2 * align256(4 * plane * 4) + align256(NROWC * nz * 4) + align256(4 * nz * 8);
   return b;
 }
 
@@ -137,7 +135,7 @@ int mprk_step_static(const mprk_config* cfg, double* q_dev, int n_slow_steps, vo
     b.dB = reinterpret_cast<float*>(p);
     p += align256(4 * plane * 4);
     b.rowc = reinterpret_cast<float*>(p);
-    p += align256((size_t)kRowConsts * g.nz * 4);
+    p += align256((size_t)NROWC * g.nz * 4);
     refd = reinterpret_cast<double*>(p);
   }
 

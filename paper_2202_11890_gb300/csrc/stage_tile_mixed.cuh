@@ -12,19 +12,28 @@
 // speeds, the viscous terms, the energy flux) uses full float states
 // q_ref + d.
 //
-// The GB300 converts between float and double at the FP64 rate (2 per
-// clock per SM, measured), so the hot loop converts with integer bit
-// operations (IEEE-754 round-to-nearest-even; exact widening). The FP64 pipe
-// only sees the accumulation into the double state: one DFMA per component
-// per fast substep.
+// A tile is TX x MTZ (32 x 16) cells and takes one of two paths:
 //
-// Layout for few instructions per cell: the halo tile is loaded once with
-// u, w, T computed on the way in (float4 per cell in shared memory). One
-// thread owns one cell of the TX x TZ tile and computes the x face on its
-// left and the z face below it, taking slopes from the staged values as it
-// goes; a ninth warp computes the faces on the tile's right and top edges.
-// The right x face of a cell comes from the neighbouring lane by a warp
-// shuffle. Two barriers per tile.
+// * Interior tiles (no wall, no interface and no change of stage region
+//   within two rows) take the pair path. Each thread carries the cells of
+//   rows k and k + TZ of one column. Shared memory interleaves the two
+//   cells' values, so every float operation of the flux is one packed
+//   f32x2 instruction (sm_100 and later) for both. The tile has no branch on
+//   geometry.
+// * Other tiles run the general path twice, on two TX x TZ halves, one cell
+//   per thread, with the ghost rules of walls and the interface.
+//
+// Both paths lay out the work the same way. The halo tile is loaded once,
+// with u, w and T computed on the way in. A thread computes the x face on
+// its cell's left and the z face below it, taking slopes from the staged
+// values as it goes. A ninth warp computes the faces on the tile's right and
+// top edges, and the right x face of a cell comes from the neighbouring lane
+// by a warp shuffle. There are two barriers per tile.
+//
+// The GB300 converts between float and double at the FP64 rate (2 per clock
+// per SM, measured). The general path converts with integer bit operations
+// (IEEE-754 round-to-nearest-even; exact widening). The pair path converts
+// only once per component per combination, in hardware (also exact).
 #pragma once
 
 #include "mprk_internal.h"
@@ -60,13 +69,19 @@ __device__ __forceinline__ float narrow(double x) {
   return __uint_as_float(f);
 }
 
-// Per-row constants: four float4 groups, group j of row k at [j * nz + k]:
+// Per-row constants (NROWC floats per row): float4 group j of row k at
+// [j * nz + k].
 //   A (j = 0)  q_ref (rho, rho u, rho w, rho E)
 //   B (j = 1)  quarter z difference of q_ref with the mirror rule at walls and Gamma
 //   C (j = 2)  q_ref(k) - q_ref(k+1)
 //   D (j = 3)  (kinetic energy of q_ref, reference pressure divergence and
 //              gravity for R(rho w), p_ref, 0)
-constexpr int NROWC = 16;
+// The same values paired for rows (k, k + TZ) for the pair path, each float4
+// holding two pairs:
+//   j = 4, 5   A (rho, rho u), (rho w, rho E)      j = 6, 7   B likewise
+//   j = 8, 9   C likewise                          j = 10     (D.x, D.z) = (ke, p_ref)
+//   j = 11     (D.y, 0): the R(rho w) constant
+constexpr int RC_PAIR = 4;  // first paired group
 
 // Nine warps: warps 0-7 own the TX x TZ cells, warp 8 computes the faces on
 // the tile's top edge (one pass) and right edge (one pass), so every warp
@@ -296,18 +311,11 @@ __device__ __forceinline__ void z_face3(MixedSmem& S, const Geom& g, int k0, int
   }
 }
 
-// Inlined into each kernel: launch constants then stay constant-bank
-// operands. The single-instance and batch kernels may contract floating-point
-// operations differently, so their results agree to float rounding (the
-// FP32-flux tolerance), not bit for bit.
-__device__ __forceinline__ void stage_tile_mixed(const StageArgs& a, int tile, MixedSmem& S) {
+// The general path on the TX x TZ cells from row k0, column i0.
+__device__ __forceinline__ void mixed_subtile(const StageArgs& a, int k0, int i0, MixedSmem& S) {
   const Geom& g = a.g;
   const int tid = threadIdx.x;
   const int ty = tid / TX, tx = tid - ty * TX;  // owned cell (warp 8: edge faces)
-  const int tzi = tile / a.tiles_x;
-  const int txi = tile - tzi * a.tiles_x;
-  const int k0 = a.row0 + tzi * TZ;
-  const int i0 = txi * TX;
   const int nz = g.nz, nx = g.nx, n1 = g.n1;
   const int row_hi = a.rhs_only ? a.rhs_hi : nz;
   const size_t plane = (size_t)nz * g.pitch;
@@ -494,9 +502,457 @@ __device__ __forceinline__ void stage_tile_mixed(const StageArgs& a, int tile, M
 #pragma unroll
     for (int c = 0; c < 4; c++) {
       const size_t o = (size_t)c * plane + row_off;
+      // the two float right-hand sides are summed in float, then combined
+      // with q_n in double (one DFMA)
       if (st == 0) Ra_w[o] = R[c];
-      else a.b.accS[(size_t)c * ps + row_off] = fma(g.hdt, widen(Ra[o]) + widen(R[c]), a.b.qA[o]);
+      else a.b.accS[(size_t)c * ps + row_off] = fma(g.hdt, widen(Ra[o] + R[c]), a.b.qA[o]);
     }
+  }
+}
+
+// ===========================================================================
+// The pair path. A float2 holds one quantity of the two cells a thread
+// carries: .x for row k, .y for row k + TZ (the "A" and "B" cells).
+// ===========================================================================
+
+// f32x2 arithmetic (sm_100 and later), round to nearest: one instruction
+// for both cells.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\t"
+      "sub.rn.f32x2 z, x, y;\n\tmov.b64 {%0, %1}, z;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 sp2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 cat2(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+// reciprocal and reciprocal square root: one MUFU operation each (relative
+// error about 2^-23, far below the mode's tolerance)
+__device__ __forceinline__ float rcp_a(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsq_a(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float2 rcp2(float2 x) { return make_float2(rcp_a(x.x), rcp_a(x.y)); }
+__device__ __forceinline__ float2 rsq2(float2 x) { return make_float2(rsq_a(x.x), rsq_a(x.y)); }
+
+constexpr int PHR = TZ + 4;  // halo pair rows: pair row r holds rows k0-2+r and k0-2+r+TZ
+
+struct PairSmem {
+  float4 qa[PHR][HW];      // deviations: (rho A, rho B, rho u A, rho u B)
+  float4 qb[PHR][HW];      //             (rho w A, rho w B, rho E A, rho E B)
+  float4 vw[PHR][HW];      // (u A, u B, w A, w B)
+  float2 vt[PHR][HW];      // (T A, T B)
+  float4 fza[TZ + 1][TX];  // z face fluxes (rho, rho u) below pair row p of the tile
+  float4 fzb[TZ + 1][TX];  //               (rho w, rho E)
+  float4 fxa[TZ], fxb[TZ]; // x face fluxes on the tile's right edge
+};
+
+// Lax–Friedrichs flux of lf_face_dev for both cells' faces. Each side gives
+// its row's reference (r, mn, mt, E), kinetic energy ke and pressure pr,
+// and its reconstructed deviation. dq is q_left - q_right in the face frame.
+__device__ __forceinline__ void lf_face2(float2 rL, float2 mnL_, float2 mtL_, float2 EL_, float2 keL,
+                                         float2 prL, float2 drL, float2 dmnL, float2 dmtL, float2 dEL,
+                                         float2 rR, float2 mnR_, float2 mtR_, float2 ER_, float2 keR,
+                                         float2 prR, float2 drR, float2 dmnR, float2 dmtR, float2 dER,
+                                         const float2 dq[4], float2 gamma, float2 gm1, float2 out[4]) {
+  const float2 half = sp2(0.5f), mhalf = sp2(-0.5f);
+  const float2 lr = add2(rL, drL), lmn = add2(mnL_, dmnL), lmt = add2(mtL_, dmtL), lE = add2(EL_, dEL);
+  const float2 rr = add2(rR, drR), rmn = add2(mnR_, dmnR), rmt = add2(mtR_, dmtR), rE = add2(ER_, dER);
+  const float2 rsL = rsq2(lr), rsR = rsq2(rr);
+  const float2 invL = mul2(rsL, rsL), invR = mul2(rsR, rsR);
+  const float2 sL = mul2(lr, rsL), sR = mul2(rr, rsR);
+  const float2 unL = mul2(lmn, invL), utL = mul2(lmt, invL);
+  const float2 unR = mul2(rmn, invR), utR = mul2(rmt, invR);
+  // p - p_ref = (gamma - 1) (dE + ke_ref - |m|^2 / (2 rho))
+  const float2 dpL = mul2(gm1, fma2(mhalf, fma2(lmn, unL, mul2(lmt, utL)), add2(dEL, keL)));
+  const float2 dpR = mul2(gm1, fma2(mhalf, fma2(rmn, unR, mul2(rmt, utR)), add2(dER, keR)));
+  const float2 pL = add2(prL, dpL), pR = add2(prR, dpR);
+  const float2 XL = mul2(mul2(gamma, pL), invL), XR = mul2(mul2(gamma, pR), invR);
+  const float2 cL = mul2(XL, rsq2(XL)), cR = mul2(XR, rsq2(XR));
+  const float2 eL = add2(lE, pL), eR = add2(rE, pR);  // rho H on each side
+  const float2 HL = mul2(eL, invL), HR = mul2(eR, invR);
+  // Roe averages
+  const float2 den = rcp2(add2(sL, sR));
+  const float2 un = mul2(fma2(sL, unL, mul2(sR, unR)), den);
+  const float2 ut = mul2(fma2(sL, utL, mul2(sR, utR)), den);
+  const float2 H = mul2(fma2(sL, HL, mul2(sR, HR)), den);
+  const float2 X = mul2(gm1, fma2(mhalf, fma2(un, un, mul2(ut, ut)), H));
+  const float2 c = mul2(X, rsq2(X));
+  const float2 lam = make_float2(fmaxf(fmaxf(fabsf(unL.x) + cL.x, fabsf(unR.x) + cR.x), fabsf(un.x) + c.x),
+                                 fmaxf(fmaxf(fabsf(unL.y) + cL.y, fabsf(unR.y) + cR.y), fabsf(un.y) + c.y));
+  const float2 hl = mul2(half, lam);
+  out[0] = fma2(hl, dq[0], mul2(half, add2(lmn, rmn)));
+  out[1] = fma2(hl, dq[1], mul2(half, add2(fma2(lmn, unL, dpL), fma2(rmn, unR, dpR))));
+  out[2] = fma2(hl, dq[2], mul2(half, fma2(lmt, unL, mul2(rmt, unR))));
+  out[3] = fma2(hl, dq[3], mul2(half, fma2(unL, eL, mul2(unR, eR))));
+}
+
+// Viscous flux of visc_face for both cells' faces; out = (normal momentum,
+// tangential momentum, energy) (the mass flux is zero).
+__device__ __forceinline__ void visc_face2(float2 unL, float2 utL, float2 TL, float2 gnL, float2 gtL,
+                                           float2 unR, float2 utR, float2 TR, float2 gnR, float2 gtR,
+                                           float2 inv_dn, float2 mu, float2 kap, float2 out[3]) {
+  const float2 half = sp2(0.5f);
+  const float2 un = mul2(half, add2(unL, unR)), ut = mul2(half, add2(utL, utR));
+  const float2 dn_un = mul2(sub2(unR, unL), inv_dn);
+  const float2 dn_ut = mul2(sub2(utR, utL), inv_dn);
+  const float2 dn_T = mul2(sub2(TR, TL), inv_dn);
+  const float2 dt_un = mul2(half, add2(gnL, gnR));
+  const float2 dt_ut = mul2(half, add2(gtL, gtR));
+  const float2 snn = mul2(mu, fma2(sp2(2.0f), dn_un, mul2(sp2(-2.0f / 3.0f), add2(dn_un, dt_ut))));
+  const float2 snt = mul2(mu, add2(dn_ut, dt_un));
+  out[0] = snn;
+  out[1] = snt;
+  out[2] = fma2(un, snn, fma2(ut, snt, mul2(kap, dn_T)));
+}
+
+// Constants of an interior tile, the same for all its cells.
+struct PairConst {
+  float2 gamma, gm1, mu, kap, inv_dx, inv_dz, hinv_dx, hinv_dz;
+};
+
+// x face on the left of tile column f (halo columns f+1 | f+2) in halo pair
+// row hr, whose paired reference rows give ref01, ref23 and kp.
+// F = F^{I*} - F^{V*} in (rho, rho u, rho w, rho E) order.
+__device__ __forceinline__ void pair_x_face(const PairSmem& S, const PairConst& C, int hr, int f, float4 ref01,
+                                            float4 ref23, float4 kp, float2 F[4]) {
+  const float2 q25 = sp2(0.25f), m25 = sp2(-0.25f);
+  const float4 a0 = S.qa[hr][f], a1 = S.qa[hr][f + 1], a2 = S.qa[hr][f + 2], a3 = S.qa[hr][f + 3];
+  const float4 b0 = S.qb[hr][f], b1 = S.qb[hr][f + 1], b2 = S.qb[hr][f + 2], b3 = S.qb[hr][f + 3];
+  // reconstructed deviations: left d1 + (d2 - d0)/4, right d2 - (d3 - d1)/4
+  const float2 lr = fma2(q25, sub2(lo2(a2), lo2(a0)), lo2(a1)), rr = fma2(m25, sub2(lo2(a3), lo2(a1)), lo2(a2));
+  const float2 lm = fma2(q25, sub2(hi2(a2), hi2(a0)), hi2(a1)), rm = fma2(m25, sub2(hi2(a3), hi2(a1)), hi2(a2));
+  const float2 lw = fma2(q25, sub2(lo2(b2), lo2(b0)), lo2(b1)), rw = fma2(m25, sub2(lo2(b3), lo2(b1)), lo2(b2));
+  const float2 lE = fma2(q25, sub2(hi2(b2), hi2(b0)), hi2(b1)), rE = fma2(m25, sub2(hi2(b3), hi2(b1)), hi2(b2));
+  const float2 dq[4] = {sub2(lr, rr), sub2(lm, rm), sub2(lw, rw), sub2(lE, rE)};
+  float2 FI[4], FV[3];
+  // face frame: normal momentum rho u, tangential rho w
+  lf_face2(lo2(ref01), hi2(ref01), lo2(ref23), hi2(ref23), lo2(kp), hi2(kp), lr, lm, lw, lE, lo2(ref01),
+           hi2(ref01), lo2(ref23), hi2(ref23), lo2(kp), hi2(kp), rr, rm, rw, rE, dq, C.gamma, C.gm1, FI);
+  // z derivatives of (u, w) at the two cells, central
+  const float4 vL = S.vw[hr][f + 1], vR = S.vw[hr][f + 2];
+  const float4 uL = S.vw[hr + 1][f + 1], dL = S.vw[hr - 1][f + 1];
+  const float4 uR = S.vw[hr + 1][f + 2], dR = S.vw[hr - 1][f + 2];
+  const float2 gnL = mul2(sub2(lo2(uL), lo2(dL)), C.hinv_dz), gtL = mul2(sub2(hi2(uL), hi2(dL)), C.hinv_dz);
+  const float2 gnR = mul2(sub2(lo2(uR), lo2(dR)), C.hinv_dz), gtR = mul2(sub2(hi2(uR), hi2(dR)), C.hinv_dz);
+  visc_face2(lo2(vL), hi2(vL), S.vt[hr][f + 1], gnL, gtL, lo2(vR), hi2(vR), S.vt[hr][f + 2], gnR, gtR, C.inv_dx,
+             C.mu, C.kap, FV);
+  F[0] = FI[0];
+  F[1] = sub2(FI[1], FV[0]);
+  F[2] = sub2(FI[2], FV[1]);
+  F[3] = sub2(FI[3], FV[2]);
+}
+
+// z face below halo pair row hu (rows of pair row hu - 1 below it) in tile
+// column cc: writes fza / fzb [hu - 2][cc]. rowp points at the paired row
+// constants; kd is the A row below the face.
+__device__ __forceinline__ void pair_z_face(PairSmem& S, const PairConst& C, const float4* __restrict__ rowp,
+                                            int nz, int kd, int hu, int cc) {
+  const int hd = hu - 1, c = cc + 2;
+  const float2 q25 = sp2(0.25f);
+  const float4 ref01d = rowp[kd], ref23d = rowp[nz + kd], kpd = rowp[6 * nz + kd];
+  const float4 ref01u = rowp[kd + 1], ref23u = rowp[nz + kd + 1], kpu = rowp[6 * nz + kd + 1];
+  const float4 sb01d = rowp[2 * nz + kd], sb23d = rowp[3 * nz + kd];
+  const float4 sb01u = rowp[2 * nz + kd + 1], sb23u = rowp[3 * nz + kd + 1];
+  const float4 dc01 = rowp[4 * nz + kd], dc23 = rowp[5 * nz + kd];
+  const float4 am = S.qa[hd - 1][c], ad = S.qa[hd][c], au = S.qa[hu][c], ap = S.qa[hu + 1][c];
+  const float4 bm = S.qb[hd - 1][c], bd = S.qb[hd][c], bu = S.qb[hu][c], bp = S.qb[hu + 1][c];
+  // below the face: d + (d_up - d_down)/4 + the reference's quarter difference;
+  // above: d - (...)/4 - (...)
+  const float2 lr = add2(lo2(ad), fma2(q25, sub2(lo2(au), lo2(am)), lo2(sb01d)));
+  const float2 lm = add2(hi2(ad), fma2(q25, sub2(hi2(au), hi2(am)), hi2(sb01d)));
+  const float2 lw = add2(lo2(bd), fma2(q25, sub2(lo2(bu), lo2(bm)), lo2(sb23d)));
+  const float2 lE = add2(hi2(bd), fma2(q25, sub2(hi2(bu), hi2(bm)), hi2(sb23d)));
+  const float2 rr = sub2(lo2(au), fma2(q25, sub2(lo2(ap), lo2(ad)), lo2(sb01u)));
+  const float2 rm = sub2(hi2(au), fma2(q25, sub2(hi2(ap), hi2(ad)), hi2(sb01u)));
+  const float2 rw = sub2(lo2(bu), fma2(q25, sub2(lo2(bp), lo2(bd)), lo2(sb23u)));
+  const float2 rE = sub2(hi2(bu), fma2(q25, sub2(hi2(bp), hi2(bd)), hi2(sb23u)));
+  // q_left - q_right = q_ref(kd) - q_ref(ku) + (d_left - d_right); face frame
+  // (rho, rho w, rho u, rho E)
+  const float2 dq[4] = {add2(lo2(dc01), sub2(lr, rr)), add2(lo2(dc23), sub2(lw, rw)),
+                        add2(hi2(dc01), sub2(lm, rm)), add2(hi2(dc23), sub2(lE, rE))};
+  float2 FI[4], FV[3];
+  lf_face2(lo2(ref01d), lo2(ref23d), hi2(ref01d), hi2(ref23d), lo2(kpd), hi2(kpd), lr, lw, lm, lE, lo2(ref01u),
+           lo2(ref23u), hi2(ref01u), hi2(ref23u), lo2(kpu), hi2(kpu), rr, rw, rm, rE, dq, C.gamma, C.gm1, FI);
+  // x derivatives of (w, u) at the two cells, central
+  const float4 vL = S.vw[hd][c], vR = S.vw[hu][c];
+  const float4 eL = S.vw[hd][c + 1], wL = S.vw[hd][c - 1], eR = S.vw[hu][c + 1], wR = S.vw[hu][c - 1];
+  const float2 gnL = mul2(sub2(hi2(eL), hi2(wL)), C.hinv_dx), gtL = mul2(sub2(lo2(eL), lo2(wL)), C.hinv_dx);
+  const float2 gnR = mul2(sub2(hi2(eR), hi2(wR)), C.hinv_dx), gtR = mul2(sub2(lo2(eR), lo2(wR)), C.hinv_dx);
+  visc_face2(hi2(vL), lo2(vL), S.vt[hd][c], gnL, gtL, hi2(vR), lo2(vR), S.vt[hu][c], gnR, gtR, C.inv_dz, C.mu,
+             C.kap, FV);
+  S.fza[hu - 2][cc] = cat2(FI[0], sub2(FI[2], FV[1]));
+  S.fzb[hu - 2][cc] = cat2(sub2(FI[1], FV[0]), sub2(FI[3], FV[2]));
+}
+
+// An interior tile needs none of the ghost rules: rows k0-2 .. k0+MTZ+1 lie
+// inside the grid and inside one fluid. For a stage (not the right-hand-side
+// hook) they also lie on one side of the F-row bound, and the tile's MTZ rows
+// share one stage region.
+__device__ __forceinline__ bool pair_interior(const StageArgs& a, int k0) {
+  const Geom& g = a.g;
+  const int hi = a.rhs_only ? a.rhs_hi : g.nz;
+  const int lo_h = k0 - 2, hi_h = k0 + MTZ + 2;  // halo rows [lo_h, hi_h)
+  if (lo_h < 0 || hi_h > g.nz || k0 + MTZ > hi || !(g.n1 <= lo_h || g.n1 >= hi_h)) return false;
+  if (a.rhs_only) return true;
+  return (g.n1_r <= lo_h || g.n1_r >= hi_h) && (g.nS_r <= k0 || g.nS_r >= k0 + MTZ);
+}
+
+// Stage combination of one cell outside the F rows (B and S rows), the
+// general path's arithmetic with R in float.
+__device__ __forceinline__ void combine_slow_cell(const StageArgs& a, int k, size_t row_off, const float R[4]) {
+  const Geom& g = a.g;
+  const size_t plane = (size_t)g.nz * g.pitch;
+  const float* Ra = reinterpret_cast<const float*>(a.b.Ra);
+  float* Ra_w = reinterpret_cast<float*>(a.b.Ra);
+  const int st = a.stage;
+  if (k >= g.nS_r) {
+    const size_t pb = (size_t)(g.n1_r - g.nS_r) * g.pitch;
+    const size_t ob = row_off - (size_t)g.nS_r * g.pitch;
+    const bool last = (st == 2 * g.m - 1);
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const size_t o = (size_t)c * plane + row_off;
+      double* acc = a.b.accB + (size_t)c * pb + ob;
+      if (!(st & 1)) Ra_w[o] = R[c];
+      const double r = (double)R[c];
+      if (st == 0) *acc = r;
+      else if (last) *acc = fma(g.h2, *acc + r, a.b.qA[o]);
+      else *acc = *acc + r;
+    }
+  } else {
+    const size_t ps = (size_t)g.nS_r * g.pitch;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const size_t o = (size_t)c * plane + row_off;
+      if (st == 0) Ra_w[o] = R[c];
+      else a.b.accS[(size_t)c * ps + row_off] = fma(g.hdt, (double)(Ra[o] + R[c]), a.b.qA[o]);
+    }
+  }
+}
+
+// The pair path on the TX x MTZ interior tile from row k0, column i0.
+__device__ __forceinline__ void pair_tile(const StageArgs& a, int k0, int i0, PairSmem& S) {
+  const Geom& g = a.g;
+  const int tid = threadIdx.x;
+  const int nz = g.nz, nx = g.nx;
+  const size_t plane = (size_t)nz * g.pitch;
+  const size_t pstep = (size_t)TZ * g.pitch;  // row k -> row k + TZ
+  const float4* __restrict__ rowp = reinterpret_cast<const float4*>(a.b.rowc) + RC_PAIR * nz;
+  const bool fluid1 = k0 < g.n1;
+  PairConst C;
+  C.gamma = sp2(g.gammaf);
+  C.gm1 = sp2(g.gm1f);
+  C.mu = sp2(fluid1 ? g.mu1f : g.mu2f);
+  C.kap = sp2(fluid1 ? g.kap1f : g.kap2f);
+  C.inv_dx = sp2(g.inv_dxf);
+  C.inv_dz = sp2(fluid1 ? g.inv_dz1f : g.inv_dz2f);
+  C.hinv_dx = sp2(0.5f * g.inv_dxf);
+  C.hinv_dz = sp2(0.5f * (fluid1 ? g.inv_dz1f : g.inv_dz2f));
+
+  // ---- 1. deviations on the halo with u, w, T (pair rows r and r + 8 of a thread)
+  {
+    const int r0 = tid / HW, cc = tid - r0 * HW;
+    int i = i0 - 2 + cc;
+    if (i < 0) i += nx;
+    if (i >= nx) i -= nx;
+    if (i >= nx) i %= nx;  // only when nx is smaller than the tile
+    const bool f_rows = k0 >= g.n1_r;
+    const float* __restrict__ dsrc = f_rows ? a.dF : a.b.dA;
+    const float* __restrict__ Ra = reinterpret_cast<const float*>(a.b.Ra);
+    const float2 h = sp2(f_rows ? g.hFf : g.dtf);
+    const bool odd_stage = !a.rhs_only && (a.stage & 1);
+    // a thread stages pair rows r0 and r0 + 8 (the second only when r0 < 4);
+    // every global load is issued before the arithmetic
+    constexpr int RSTEP = MIXED_THREADS / HW;
+    const bool two = r0 + RSTEP < PHR;
+    float2 d[2][4];
+    float4 ref01[2], ref23[2], kp[2];
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+      if (e == 1 && !two) break;
+      const int kA = k0 - 2 + r0 + e * RSTEP;
+      const size_t oA = (size_t)kA * g.pitch + i, oB = oA + pstep;
+      ref01[e] = rowp[kA];
+      ref23[e] = rowp[nz + kA];
+      kp[e] = rowp[6 * nz + kA];
+      if (a.rhs_only) {
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+          d[e][c] = make_float2(__double2float_rn(a.rhs_in[c * plane + oA] - (double)(c == 0 ? ref01[e].x : c == 1 ? ref01[e].z : c == 2 ? ref23[e].x : ref23[e].z)),
+                                __double2float_rn(a.rhs_in[c * plane + oB] - (double)(c == 0 ? ref01[e].y : c == 1 ? ref01[e].w : c == 2 ? ref23[e].y : ref23[e].w)));
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; c++) d[e][c] = make_float2(dsrc[c * plane + oA], dsrc[c * plane + oB]);
+        if (odd_stage) {
+          float2 ra[4];
+#pragma unroll
+          for (int c = 0; c < 4; c++) ra[c] = make_float2(Ra[c * plane + oA], Ra[c * plane + oB]);
+#pragma unroll
+          for (int c = 0; c < 4; c++) d[e][c] = fma2(h, ra[c], d[e][c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+      if (e == 1 && !two) break;
+      const int r = r0 + e * RSTEP;
+      const float2 rho = add2(lo2(ref01[e]), d[e][0]), mu_ = add2(hi2(ref01[e]), d[e][1]);
+      const float2 mw = add2(lo2(ref23[e]), d[e][2]);
+      const float2 inv = rcp2(rho);
+      const float2 u = mul2(mu_, inv), w = mul2(mw, inv);
+      const float2 dp = mul2(C.gm1, fma2(sp2(-0.5f), fma2(mu_, u, mul2(mw, w)), add2(d[e][3], lo2(kp[e]))));
+      S.qa[r][cc] = cat2(d[e][0], d[e][1]);
+      S.qb[r][cc] = cat2(d[e][2], d[e][3]);
+      S.vw[r][cc] = cat2(u, w);
+      S.vt[r][cc] = mul2(mul2(C.gamma, add2(hi2(kp[e]), dp)), inv);
+    }
+  }
+  __syncthreads();
+
+  // ---- 2. faces: own left x face (registers), own lower z face (shared) ----
+  const int p = tid / TX, tx = tid - p * TX;  // pair row of the tile (warp 8: edges)
+  float2 fxl[4];
+  if (p < TZ) {
+    const int kA = k0 + p;
+    pair_z_face(S, C, rowp, nz, kA - 1, p + 2, tx);
+    pair_x_face(S, C, p + 2, tx, rowp[kA], rowp[nz + kA], rowp[6 * nz + kA], fxl);
+  } else {
+    // warp 8: the z faces below pair row TZ (its B half is the tile's top
+    // face), then the x faces on the tile's right edge
+    pair_z_face(S, C, rowp, nz, k0 + TZ - 1, TZ + 2, tx);
+    if (tx < TZ) {
+      const int kA = k0 + tx;
+      float2 F[4];
+      pair_x_face(S, C, tx + 2, TX, rowp[kA], rowp[nz + kA], rowp[6 * nz + kA], F);
+      S.fxa[tx] = cat2(F[0], F[1]);
+      S.fxb[tx] = cat2(F[2], F[3]);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++) fxl[c] = make_float2(0.f, 0.f);
+  }
+  // right x face of the owned cells: the left face of the next lane
+  float2 fxr[4];
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    fxr[c].x = __shfl_down_sync(0xffffffffu, fxl[c].x, 1);
+    fxr[c].y = __shfl_down_sync(0xffffffffu, fxl[c].y, 1);
+  }
+  // the combination's global operands (F rows of an odd stage), loaded
+  // before the barrier so that their latency overlaps the wait
+  const int kA = k0 + p;
+  const int i = i0 + tx;
+  const bool own = p < TZ && i < nx;
+  const size_t offA = (size_t)kA * g.pitch + i, offB = offA + pstep;
+  const int st = a.stage;
+  const bool f_odd = !a.rhs_only && kA >= g.n1_r && (st & 1);
+  float2 ra[4], dfo[4];
+  double qa[4], qb[4];
+  if (own && f_odd) {
+    const float* Ra = reinterpret_cast<const float*>(a.b.Ra);
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const size_t oA = c * plane + offA, oB = c * plane + offB;
+      ra[c] = make_float2(Ra[oA], Ra[oB]);
+      qa[c] = a.qF[oA];
+      qb[c] = a.qF[oB];
+      dfo[c] = make_float2(a.dF[oA], a.dF[oB]);
+    }
+  }
+  __syncthreads();
+  if (!own) return;
+  if (tx == TX - 1) {
+    const float4 ea = S.fxa[p], eb = S.fxb[p];
+    fxr[0] = lo2(ea);
+    fxr[1] = hi2(ea);
+    fxr[2] = lo2(eb);
+    fxr[3] = hi2(eb);
+  }
+
+  // ---- 3. R (float pairs) and the stage combination (double) -------------
+  const float4 da = S.fza[p][tx], db = S.fzb[p][tx], ua = S.fza[p + 1][tx], ub = S.fzb[p + 1][tx];
+  const float2 fdn[4] = {lo2(da), hi2(da), lo2(db), hi2(db)};
+  const float2 fup[4] = {lo2(ua), hi2(ua), lo2(ub), hi2(ub)};
+  float2 R[4];
+#pragma unroll
+  for (int c = 0; c < 4; c++) R[c] = fma2(sub2(fxl[c], fxr[c]), C.inv_dx, mul2(sub2(fdn[c], fup[c]), C.inv_dz));
+  // gravity on the deviation; the reference part sits in the row constant
+  const float4 dca = S.qa[p + 2][tx + 2], dcb = S.qb[p + 2][tx + 2];
+  const float2 mG = sp2(-g.Gf);
+  R[2] = add2(R[2], fma2(mG, lo2(dca), lo2(rowp[7 * nz + kA])));
+  R[3] = fma2(mG, add2(lo2(rowp[nz + kA]), lo2(dcb)), R[3]);
+
+  if (a.rhs_only) {
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      a.rhs_out[c * plane + offA] = (double)R[c].x;
+      a.rhs_out[c * plane + offB] = (double)R[c].y;
+    }
+    return;
+  }
+  if (f_odd) {
+    const float2 h2f = sp2(g.h2f);
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const size_t oA = c * plane + offA, oB = c * plane + offB;
+      const float2 s = add2(ra[c], R[c]);
+      a.qF_next[oA] = fma(g.h2, (double)s.x, qa[c]);
+      a.qF_next[oB] = fma(g.h2, (double)s.y, qb[c]);
+      // float shadow; resynchronised each slow step
+      const float2 dn = fma2(h2f, s, dfo[c]);
+      a.dF_next[oA] = dn.x;
+      a.dF_next[oB] = dn.y;
+    }
+  } else if (kA >= g.n1_r) {
+    float* Ra_w = reinterpret_cast<float*>(a.b.Ra);
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      Ra_w[c * plane + offA] = R[c].x;
+      Ra_w[c * plane + offB] = R[c].y;
+    }
+  } else {
+    const float RA[4] = {R[0].x, R[1].x, R[2].x, R[3].x}, RB[4] = {R[0].y, R[1].y, R[2].y, R[3].y};
+    combine_slow_cell(a, kA, offA, RA);
+    combine_slow_cell(a, kA + TZ, offB, RB);
+  }
+}
+
+// One tile of the FP32-flux stage kernel (TX x MTZ cells). Inlined into
+// each kernel: launch constants then stay constant-bank operands. The
+// single-instance and batch kernels may contract floating-point operations
+// differently, so their results agree to float rounding (the FP32-flux
+// tolerance), not bit for bit.
+union MixedTileSmem {
+  MixedSmem gen;
+  PairSmem pair;
+};
+
+__device__ __forceinline__ void stage_tile_mixed(const StageArgs& a, int tile, MixedTileSmem& S) {
+  const int tzi = tile / a.tiles_x;
+  const int txi = tile - tzi * a.tiles_x;
+  const int k0 = a.row0 + tzi * MTZ;
+  const int i0 = txi * TX;
+  if (pair_interior(a, k0)) {
+    pair_tile(a, k0, i0, S.pair);
+    return;
+  }
+  mixed_subtile(a, k0, i0, S.gen);
+  const int hi = a.rhs_only ? a.rhs_hi : a.g.nz;
+  if (k0 + TZ < hi) {
+    __syncthreads();  // the first half's phase 3 reads shared memory
+    mixed_subtile(a, k0 + TZ, i0, S.gen);
   }
 }
 

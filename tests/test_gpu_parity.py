@@ -297,10 +297,13 @@ def test_bit_operation_conversions_match_hardware():
     assert np.array_equal(a, b)
 
 
-def test_fp32_flux_rhs_close_to_oracle():
+@pytest.mark.parametrize("dims", [(64, 30, 4, 30), (100, 40, 8, 48)])
+def test_fp32_flux_rhs_close_to_oracle(dims):
     """The FP32-flux right-hand side (deviation form) against the FP64
-    oracle's."""
-    g = W.Grid(64, 30, 4, 30)
+    oracle's. On the 100 x 96 grid, tile rows 16-31 (fluid 1) and 64-79
+    (fluid 2) take the packed pair path, the rest the general path. x is
+    ragged (100 columns) and wraps at both ends."""
+    g = W.Grid(*dims)
     q = W.gaussian_bumps(g, 17, sigma_cells=3.0)
     cfg, P, _ = pair(g, 2, dt=0.01, precision=1)
     R_or = O.rhs(P, q)
@@ -308,3 +311,22 @@ def test_fp32_flux_rhs_close_to_oracle():
     err = rel_err(R_gpu, R_or)
     print("fp32flux RHS error per component:", err)
     assert np.all(err < 1e-4), err
+
+
+@pytest.mark.parametrize("m,wall", [(3, 0), (4, 1)])
+def test_fp32_flux_pair_path_in_every_band(m, wall):
+    """A grid whose 16-row tiles take the packed pair path in the slow band
+    (rows 16-31), the buffer (32-47) and the fast band (64-79), next to
+    general-path tiles at the walls and at Gamma: 20 slow steps within
+    1e-5 of the FP64 oracle."""
+    mp = M()
+    g = W.Grid(100, 32, 24, 40)
+    q0 = W.gaussian_bumps(g, 29 + m, sigma_cells=3.0)
+    cfg, P, dt = pair(g, m, q0=q0, precision=mp.MPRK_FP32FLUX, wall=wall)
+    q_or, _ = O.mprk_step(P, q0, 20)
+    with mp.Instance(cfg, q0) as inst:
+        inst.step(20)
+        q_gpu = inst.state()
+    err = rel_err(q_gpu, q_or)
+    print("fp32flux pair-path grid error per component:", err)
+    assert np.all(err < 1e-5), err
