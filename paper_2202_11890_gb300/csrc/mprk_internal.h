@@ -15,6 +15,7 @@
 //   rowc [NROWC][nz] float       per-row reference constants (stage_tile_mixed.cuh)
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (types only; the encoder is looked up at run time)
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -93,6 +94,9 @@ struct StageArgs {
   double* rhs_out;    // [4][nz][pitch] when rhs_only
   int rhs_hi;         // last row (exclusive) when rhs_only
   const double* rhs_in;  // full stage state when rhs_only
+  int bulk;           // FP32-flux: interior tiles stage their float planes by
+                      // tensor copies (set by launch_stage when maps exist)
+  unsigned* status;   // status word for device-side errors, or null
 };
 
 // Arguments of stage st of one slow step: F rows ping-pong between the A and
@@ -117,8 +121,22 @@ __host__ __device__ inline int stage_tiles(const StageArgs& a) {
   return a.tiles_x * ((hi - a.row0 + a.tz - 1) / a.tz);
 }
 
+// Tensor maps of the FP32-flux float planes ([4][nz][pitch] float each) for
+// the bulk tensor copies of the stage kernel (mprk_kernels.cu).
+struct StageMaps {
+  CUtensorMap dA, dB, Ra;
+  bool valid;
+};
+// Encodes the maps of b's float planes. Sets valid = false (and returns
+// cudaSuccess) where the planes cannot be tensor-copied (pitch not a
+// multiple of 4 floats, or no encoder in the driver); tiles then load
+// directly.
+cudaError_t make_stage_maps(const Geom& g, const Bufs& b, StageMaps* out);
+
 // Launchers (mprk_kernels.cu). All enqueue on `stream` and return the launch error.
-cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStream_t stream);
+// maps (FP32-flux only, may be null) enables the staged tiles.
+cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStream_t stream,
+                         const StageMaps* maps = nullptr);
 cudaError_t launch_finalize(const Geom& g, const Bufs& b, int m_odd, cudaStream_t stream);
 // FP32-flux mode: per-row reference of q (row means, refd [4][nz] scratch)
 // and the float shadow dA = q - q_ref of qA.

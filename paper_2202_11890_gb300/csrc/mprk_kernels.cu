@@ -4,6 +4,10 @@
 //                   odd number of substeps) into the state buffer
 //   diag_*          deterministic monitoring reductions (Sec. 5.1 mass and
 //                   energy; Courant numbers; non-finite count)
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
 #include "mprk_internal.h"
 #include "stage_tile.cuh"
 #include "stage_tile_mixed.cuh"
@@ -13,15 +17,33 @@ namespace mprk {
 template <typename Real, typename Store>
 __global__ void __launch_bounds__(NTHREADS, 2)
     stage_kernel(const StageArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   TileSmem<Real>& S = *reinterpret_cast<TileSmem<Real>*>(smem_raw);
   stage_tile<Real, Store>(a, blockIdx.x, S);
 }
 
-__global__ void __launch_bounds__(MIXED_THREADS, 3) stage_kernel_mixed(const StageArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  MixedTileSmem& S = *reinterpret_cast<MixedTileSmem*>(smem_raw);
-  stage_tile_mixed(a, blockIdx.x, S);
+// FP32-flux stage kernel: one CTA per tile, blockIdx = (tile column, tile
+// row). An interior tile away from the x wrap has its float planes
+// tensor-copied (TMA) into shared memory: one thread issues the copies at
+// the start, and the row constants are fetched while they fly.
+__global__ void __launch_bounds__(MIXED_THREADS, 3)
+    stage_kernel_mixed(const StageArgs a, const __grid_constant__ CUtensorMap tm_sb,
+                       const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_ra) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  MixedKernelSmem& S = *reinterpret_cast<MixedKernelSmem*>(smem_raw);
+  const int k0 = a.row0 + blockIdx.y * MTZ, i0 = blockIdx.x * TX;
+  const bool staged = tile_bulk_ok(a, k0, i0);
+  if (staged && threadIdx.x == MIXED_THREADS - 32) {
+    mbar_init(&S.bar);
+    stage_issue(a, k0, i0, S.stg, &S.bar, &tm_sb, &tm_f, &tm_ra);
+  }
+  if (staged) __syncthreads();  // the mbarrier is initialised before anyone waits on it
+  if (!stage_tile_mixed(a, k0, i0, S.work, staged ? &S.stg : nullptr, &S.bar)) {
+    // a tensor copy never completed within the bound: flag it, give the
+    // copies one more bounded wait, and leave
+    if (threadIdx.x == 0 && a.status) atomicOr(a.status, ST_TIMEOUT);
+    (void)mbar_wait(&S.bar, 0);
+  }
 }
 
 size_t stage_smem_bytes(int precision) {
@@ -34,15 +56,65 @@ cudaError_t prepare_kernels() {
                                        (int)sizeof(TileSmem<double>));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(stage_kernel_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(MixedTileSmem));
+                              (int)sizeof(MixedKernelSmem));
 }
 
-cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStream_t stream) {
+namespace {
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link-time
+// dependency on the driver library); null if the driver lacks it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+}  // namespace
+
+cudaError_t make_stage_maps(const Geom& g, const Bufs& b, StageMaps* out) {
+  out->valid = false;
+  if (!b.dA || g.pitch % 4 != 0 || g.nx < SCOLS || g.nz < SROWS) return cudaSuccess;
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaSuccess;
+  // [4][nz][pitch] float: x = column (nx of pitch used), y = row, z = component
+  const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.nz, 4};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.nz * g.pitch * 4};
+  const cuuint32_t box[3] = {SCOLS, SROWS, 4};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  void* planes[3] = {b.dA, b.dB, b.Ra};
+  CUtensorMap* maps[3] = {&out->dA, &out->dB, &out->Ra};
+  for (int j = 0; j < 3; j++) {
+    if (((unsigned long long)planes[j] & 15ull) != 0) return cudaSuccess;
+    const CUresult r = enc(maps[j], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, planes[j], dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  out->valid = true;
+  return cudaSuccess;
+}
+
+cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStream_t stream,
+                         const StageMaps* maps) {
   if (n_tiles <= 0) return cudaSuccess;
   if (precision == 0) {
     stage_kernel<double, double><<<n_tiles, NTHREADS, sizeof(TileSmem<double>), stream>>>(a);
   } else {
-    stage_kernel_mixed<<<n_tiles, MIXED_THREADS, sizeof(MixedTileSmem), stream>>>(a);
+    StageArgs s = a;
+    CUtensorMap none;
+    memset(&none, 0, sizeof(none));
+    const bool staged = maps && maps->valid;
+    s.bulk = staged ? 1 : 0;
+    const CUtensorMap& sb = staged ? maps->dA : none;
+    const CUtensorMap& f = staged ? (a.dF == a.b.dA ? maps->dA : maps->dB) : none;
+    const CUtensorMap& ra = staged ? maps->Ra : none;
+    const dim3 grid(a.tiles_x, n_tiles / a.tiles_x);
+    stage_kernel_mixed<<<grid, MIXED_THREADS, sizeof(MixedKernelSmem), stream>>>(s, sb, f, ra);
   }
   return cudaGetLastError();
 }

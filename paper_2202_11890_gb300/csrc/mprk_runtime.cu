@@ -77,6 +77,7 @@ struct mprk_instance {
   long long steps_done;
   long long bytes;
   bool stream_ordered;  // buffers from cudaMallocAsync on `stream` (server instances)
+  StageMaps maps;       // FP32-flux mode: tensor maps of the float planes
 };
 
 namespace {
@@ -137,8 +138,9 @@ void free_instance(mprk_instance* I) {
 int enqueue_step(mprk_instance* I, cudaStream_t s) {
   const Geom& g = I->g;
   for (int st = 0; st < 2 * g.m; st++) {
-    const StageArgs a = stage_args(g, I->b, st);
-    CU(launch_stage(a, I->precision, stage_tiles(a), s));
+    StageArgs a = stage_args(g, I->b, st);
+    a.status = I->status_dev;
+    CU(launch_stage(a, I->precision, stage_tiles(a), s, &I->maps));
   }
   CU(launch_finalize(g, I->b, g.m & 1, s));
   return MPRK_OK;
@@ -389,6 +391,7 @@ int mprk::create_instance(const mprk_config* cfg, const double* q0, int q0_locat
     // reference rows from the initial state, then the shadow of qA
     cudaError_t e = launch_reference(g, I->b.qA, I->refd, I->b.rowc, I->stream);
     if (e == cudaSuccess) e = launch_shadow(g, I->b.qA, I->b.rowc, I->b.dA, I->stream);
+    if (e == cudaSuccess) e = make_stage_maps(g, I->b, &I->maps);
     if (e != cudaSuccess) return fin(fail(MPRK_ECUDA, "reference set-up: %s", cudaGetErrorString(e)));
   }
 
@@ -527,6 +530,7 @@ int mprk_rhs(mprk_instance* I, const double* W_dev, double* R_dev, int k_lo, int
   a.rhs_out = I->rhs_out;
   a.rhs_hi = k_hi;
   a.rhs_in = I->rhs_in;
+  a.status = I->status_dev;
   CU(launch_stage(a, I->precision, stage_tiles(a), I->stream));
   for (int c = 0; c < 4; c++) {
     CU(cudaMemcpy2DAsync(R_dev + ((size_t)c * g.nz + k_lo) * g.nx, (size_t)g.nx * 8,
@@ -546,8 +550,9 @@ int mprk_profile_step(mprk_instance* I, double* launch_ms, long long* launch_cel
   int rc = MPRK_OK;
   CU(cudaEventRecord(ev[0], I->stream));
   for (int st = 0; st < 2 * g.m && rc == MPRK_OK; st++) {
-    const StageArgs a = stage_args(g, I->b, st);
-    cudaError_t e = launch_stage(a, I->precision, stage_tiles(a), I->stream);
+    StageArgs a = stage_args(g, I->b, st);
+    a.status = I->status_dev;
+    cudaError_t e = launch_stage(a, I->precision, stage_tiles(a), I->stream, &I->maps);
     if (e != cudaSuccess) rc = fail(MPRK_ECUDA, "stage launch: %s", cudaGetErrorString(e));
     cudaEventRecord(ev[st + 1], I->stream);
     if (st < cap && launch_cells) launch_cells[st] = (long long)(g.nz - a.row0) * g.nx;

@@ -145,15 +145,18 @@ int mprk_step_static(const mprk_config* cfg, double* q_dev, int n_slow_steps, vo
   // result, the FP32-flux reference rows and shadow are rebuilt from q_dev
   // below, and padding does not exist because the pitch is nx).
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  StageMaps maps;
+  maps.valid = false;
   if (b.dA) {
     e = launch_reference(g, q_dev, refd, b.rowc, s);
     if (e == cudaSuccess) e = launch_shadow(g, q_dev, b.rowc, b.dA, s);
+    if (e == cudaSuccess) e = make_stage_maps(g, b, &maps);  // host-side encoding, no allocation
     if (e != cudaSuccess) return sfail(MPRK_ECUDA, std::string("reference set-up: ") + cudaGetErrorString(e));
   }
   for (int step = 0; step < n_slow_steps; step++) {
     for (int st = 0; st < 2 * g.m; st++) {
       const StageArgs a = stage_args(g, b, st);
-      e = launch_stage(a, cfg->precision, stage_tiles(a), s);
+      e = launch_stage(a, cfg->precision, stage_tiles(a), s, &maps);
       if (e != cudaSuccess) return sfail(MPRK_ECUDA, std::string("stage launch: ") + cudaGetErrorString(e));
     }
     e = launch_finalize(g, b, g.m & 1, s);

@@ -549,6 +549,17 @@ __device__ __forceinline__ float2 rsq2(float2 x) { return make_float2(rsq_a(x.x)
 
 constexpr int PHR = TZ + 4;  // halo pair rows: pair row r holds rows k0-2+r and k0-2+r+TZ
 
+// A staging buffer that tensor copies (TMA) fill with the float planes of
+// one interior tile: the box of columns i0-4 .. i0+TX+3 (160 bytes, so the
+// box starts on a 16-byte boundary), rows k0-2 .. k0+MTZ+1 and the four
+// components.
+constexpr int SROWS = MTZ + 4;
+constexpr int SCOLS = TX + 8;
+struct __align__(128) Stage {
+  float d[4][SROWS][SCOLS];   // float shadow of the stage's base state
+  float ra[4][SROWS][SCOLS];  // R_a (odd stages only)
+};
+
 struct PairSmem {
   float4 qa[PHR][HW];      // deviations: (rho A, rho B, rho u A, rho u B)
   float4 qb[PHR][HW];      //             (rho w A, rho w B, rho E A, rho E B)
@@ -558,6 +569,52 @@ struct PairSmem {
   float4 fzb[TZ + 1][TX];  //               (rho w, rho E)
   float4 fxa[TZ], fxb[TZ]; // x face fluxes on the tile's right edge
 };
+
+// ---- bulk copies and their mbarriers (PTX) -------------------------------
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase of the given parity to complete; gives up after about
+// one second (2^31 clocks) and returns false.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
+}
+// Orders this thread's earlier shared-memory accesses before later bulk
+// copies into shared memory.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// One 3D tensor copy (tile mode) of the box at (x, y, z) of tmap into dst.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tmap, int x, int y, int z,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
 
 // Lax–Friedrichs flux of lf_face_dev for both cells' faces. Each side gives
 // its row's reference (r, mn, mt, E), kinetic energy ke and pressure pr,
@@ -743,8 +800,11 @@ __device__ __forceinline__ void combine_slow_cell(const StageArgs& a, int k, siz
   }
 }
 
-// The pair path on the TX x MTZ interior tile from row k0, column i0.
-__device__ __forceinline__ void pair_tile(const StageArgs& a, int k0, int i0, PairSmem& S) {
+// The pair path on the TX x MTZ interior tile from row k0, column i0. stg,
+// when not null, receives the tile's float planes by tensor copies that
+// complete on bar (phase 0). Returns false if the wait for them gave up.
+__device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, PairSmem& S, const Stage* stg,
+                                          unsigned long long* bar) {
   const Geom& g = a.g;
   const int tid = threadIdx.x;
   const int nz = g.nz, nx = g.nx;
@@ -752,6 +812,7 @@ __device__ __forceinline__ void pair_tile(const StageArgs& a, int k0, int i0, Pa
   const size_t pstep = (size_t)TZ * g.pitch;  // row k -> row k + TZ
   const float4* __restrict__ rowp = reinterpret_cast<const float4*>(a.b.rowc) + RC_PAIR * nz;
   const bool fluid1 = k0 < g.n1;
+  bool ok = true;
   PairConst C;
   C.gamma = sp2(g.gammaf);
   C.gm1 = sp2(g.gm1f);
@@ -784,15 +845,33 @@ __device__ __forceinline__ void pair_tile(const StageArgs& a, int k0, int i0, Pa
     for (int e = 0; e < 2; e++) {
       if (e == 1 && !two) break;
       const int kA = k0 - 2 + r0 + e * RSTEP;
-      const size_t oA = (size_t)kA * g.pitch + i, oB = oA + pstep;
       ref01[e] = rowp[kA];
       ref23[e] = rowp[nz + kA];
       kp[e] = rowp[6 * nz + kA];
-      if (a.rhs_only) {
+    }
+    if (stg) ok = mbar_wait(bar, 0);  // the row constants above are in flight meanwhile
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+      if (e == 1 && !two) break;
+      const int kA = k0 - 2 + r0 + e * RSTEP;
+      const size_t oA = (size_t)kA * g.pitch + i, oB = oA + pstep;
+      if (stg) {
+        // staged row of halo pair row r: r (A) and r + TZ (B); column cc + 2
+        const int r = r0 + e * RSTEP;
+#pragma unroll
+        for (int c = 0; c < 4; c++) d[e][c] = make_float2(stg->d[c][r][cc + 2], stg->d[c][r + TZ][cc + 2]);
+        if (odd_stage) {
+#pragma unroll
+          for (int c = 0; c < 4; c++)
+            d[e][c] = fma2(h, make_float2(stg->ra[c][r][cc + 2], stg->ra[c][r + TZ][cc + 2]), d[e][c]);
+        }
+      } else if (a.rhs_only) {
+        const float refA[4] = {ref01[e].x, ref01[e].z, ref23[e].x, ref23[e].z};
+        const float refB[4] = {ref01[e].y, ref01[e].w, ref23[e].y, ref23[e].w};
 #pragma unroll
         for (int c = 0; c < 4; c++)
-          d[e][c] = make_float2(__double2float_rn(a.rhs_in[c * plane + oA] - (double)(c == 0 ? ref01[e].x : c == 1 ? ref01[e].z : c == 2 ? ref23[e].x : ref23[e].z)),
-                                __double2float_rn(a.rhs_in[c * plane + oB] - (double)(c == 0 ? ref01[e].y : c == 1 ? ref01[e].w : c == 2 ? ref23[e].y : ref23[e].w)));
+          d[e][c] = make_float2(__double2float_rn(a.rhs_in[c * plane + oA] - (double)refA[c]),
+                                __double2float_rn(a.rhs_in[c * plane + oB] - (double)refB[c]));
       } else {
 #pragma unroll
         for (int c = 0; c < 4; c++) d[e][c] = make_float2(dsrc[c * plane + oA], dsrc[c * plane + oB]);
@@ -820,7 +899,7 @@ __device__ __forceinline__ void pair_tile(const StageArgs& a, int k0, int i0, Pa
       S.vt[r][cc] = mul2(mul2(C.gamma, add2(hi2(kp[e]), dp)), inv);
     }
   }
-  __syncthreads();
+  if (__syncthreads_or(!ok)) return false;
 
   // ---- 2. faces: own left x face (registers), own lower z face (shared) ----
   const int p = tid / TX, tx = tid - p * TX;  // pair row of the tile (warp 8: edges)
@@ -865,14 +944,19 @@ __device__ __forceinline__ void pair_tile(const StageArgs& a, int k0, int i0, Pa
 #pragma unroll
     for (int c = 0; c < 4; c++) {
       const size_t oA = c * plane + offA, oB = c * plane + offB;
-      ra[c] = make_float2(Ra[oA], Ra[oB]);
       qa[c] = a.qF[oA];
       qb[c] = a.qF[oB];
-      dfo[c] = make_float2(a.dF[oA], a.dF[oB]);
+      if (stg) {  // staged rows p + 2 and p + 2 + TZ, column tx + 4 (dF is the staged shadow)
+        ra[c] = make_float2(stg->ra[c][p + 2][tx + 4], stg->ra[c][p + 2 + TZ][tx + 4]);
+        dfo[c] = make_float2(stg->d[c][p + 2][tx + 4], stg->d[c][p + 2 + TZ][tx + 4]);
+      } else {
+        ra[c] = make_float2(Ra[oA], Ra[oB]);
+        dfo[c] = make_float2(a.dF[oA], a.dF[oB]);
+      }
     }
   }
   __syncthreads();
-  if (!own) return;
+  if (!own) return true;
   if (tx == TX - 1) {
     const float4 ea = S.fxa[p], eb = S.fxb[p];
     fxr[0] = lo2(ea);
@@ -900,7 +984,7 @@ __device__ __forceinline__ void pair_tile(const StageArgs& a, int k0, int i0, Pa
       a.rhs_out[c * plane + offA] = (double)R[c].x;
       a.rhs_out[c * plane + offB] = (double)R[c].y;
     }
-    return;
+    return true;
   }
   if (f_odd) {
     const float2 h2f = sp2(g.h2f);
@@ -927,33 +1011,64 @@ __device__ __forceinline__ void pair_tile(const StageArgs& a, int k0, int i0, Pa
     combine_slow_cell(a, kA, offA, RA);
     combine_slow_cell(a, kA + TZ, offB, RB);
   }
+  return true;
 }
 
-// One tile of the FP32-flux stage kernel (TX x MTZ cells). Inlined into
-// each kernel: launch constants then stay constant-bank operands. The
-// single-instance and batch kernels may contract floating-point operations
-// differently, so their results agree to float rounding (the FP32-flux
-// tolerance), not bit for bit.
+// One tile of the FP32-flux stage kernel: TX x MTZ cells from row k0,
+// column i0. Inlined into each kernel: launch constants then stay
+// constant-bank operands. The single-instance and batch kernels may contract
+// floating-point operations differently, so their results agree to float
+// rounding (the FP32-flux tolerance), not bit for bit. stg and bar as for
+// pair_tile (stg only for tiles that tile_bulk_ok accepts); returns false if
+// the wait for the tensor copies gave up.
 union MixedTileSmem {
   MixedSmem gen;
   PairSmem pair;
 };
 
-__device__ __forceinline__ void stage_tile_mixed(const StageArgs& a, int tile, MixedTileSmem& S) {
-  const int tzi = tile / a.tiles_x;
-  const int txi = tile - tzi * a.tiles_x;
-  const int k0 = a.row0 + tzi * MTZ;
-  const int i0 = txi * TX;
-  if (pair_interior(a, k0)) {
-    pair_tile(a, k0, i0, S.pair);
-    return;
-  }
+__device__ __forceinline__ bool stage_tile_mixed(const StageArgs& a, int k0, int i0, MixedTileSmem& S,
+                                                 const Stage* stg, unsigned long long* bar) {
+  if (pair_interior(a, k0)) return pair_tile(a, k0, i0, S.pair, stg, bar);
   mixed_subtile(a, k0, i0, S.gen);
   const int hi = a.rhs_only ? a.rhs_hi : a.g.nz;
   if (k0 + TZ < hi) {
     __syncthreads();  // the first half's phase 3 reads shared memory
     mixed_subtile(a, k0 + TZ, i0, S.gen);
   }
+  return true;
 }
+
+// The same by linear tile index (row-major over tiles_x), without staging.
+__device__ __forceinline__ void stage_tile_mixed(const StageArgs& a, int tile, MixedTileSmem& S) {
+  const int tzi = tile / a.tiles_x;
+  const int txi = tile - tzi * a.tiles_x;
+  (void)stage_tile_mixed(a, a.row0 + tzi * MTZ, txi * TX, S, nullptr, nullptr);
+}
+
+// Tiles whose float planes are tensor-copied: interior tiles of a stage
+// away from the x wrap (the 40 staged columns lie inside the row).
+__device__ __forceinline__ bool tile_bulk_ok(const StageArgs& a, int k0, int i0) {
+  return a.bulk && !a.rhs_only && i0 >= 4 && i0 + TX + 4 <= a.g.nx && pair_interior(a, k0);
+}
+
+// Issued by one thread: the tensor copies of the tile's float planes into B
+// (the shadow box, and R_a's on odd stages), completing on bar. tm_sb / tm_f
+// map the shadow of the S and B rows / of the F rows, tm_ra R_a.
+__device__ __forceinline__ void stage_issue(const StageArgs& a, int k0, int i0, Stage& B, unsigned long long* bar,
+                                            const CUtensorMap* tm_sb, const CUtensorMap* tm_f,
+                                            const CUtensorMap* tm_ra) {
+  const bool odd = a.stage & 1;
+  mbar_expect_tx(bar, (unsigned)((odd ? 2 : 1) * sizeof(B.d)));
+  tma_load_3d(&B.d[0][0][0], k0 >= a.g.n1_r ? tm_f : tm_sb, i0 - 4, k0 - 2, 0, bar);
+  if (odd) tma_load_3d(&B.ra[0][0][0], tm_ra, i0 - 4, k0 - 2, 0, bar);
+}
+
+// Shared memory of the single-instance FP32-flux kernel: the staging
+// buffer, its mbarrier and the tile's working set.
+struct MixedKernelSmem {
+  Stage stg;
+  unsigned long long bar;
+  MixedTileSmem work;
+};
 
 }  // namespace mprk
