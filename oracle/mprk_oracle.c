@@ -27,6 +27,10 @@
  *    flux between the reconstructed boundary state and its mirror;
  *  - the viscous flux through an outer wall is the common-value recipe of
  *    App. B applied between the cell and its ghost;
+ *  - x walls (xwall = 1; Sec. 5.2 puts adiabatic no-slip walls on all
+ *    boundaries) follow the z-wall rules with x as the normal: the mirror
+ *    ghost flips rho u, and the (u, w, T) ghost flips u, flips w for no-slip
+ *    and keeps it for slip;
  *  - the viscous flux through the interface is (0, sigma_xz, 0,
  *    u_w*sigma_xz - Pi_z) from the bulk formulas of App. B (w = 0,
  *    sigma_zz = 0);
@@ -210,11 +214,27 @@ static void nb_uwT_z(const or_problem* P, const double* W, int k, int i, int s, 
   }
 }
 
+/* Is column i+s beyond an x wall? */
+static int beyond_x(const or_problem* P, int i, int s) {
+  return P->xwall && (i + s < 0 || i + s >= P->nx);
+}
+
+/* conserved neighbour of (k,i) in x at offset s: periodic, or the mirror
+ * ghost (rho u flipped) beyond an x wall */
+static void nb_cons_x(const or_problem* P, const double* W, int k, int i, int s, double q[4]) {
+  if (!beyond_x(P, i, s)) {
+    load(P, W, k, wrap(P, i + s), q);
+  } else {
+    load(P, W, k, i, q);
+    q[1] = -q[1];
+  }
+}
+
 /* Cell gradients by central differences (App. B, LS gradient on a uniform grid) */
 static void grad_x_cons(const or_problem* P, const double* W, int k, int i, double g[4]) {
   double qe[4], qw[4];
-  load(P, W, k, wrap(P, i + 1), qe);
-  load(P, W, k, wrap(P, i - 1), qw);
+  nb_cons_x(P, W, k, i, +1, qe);
+  nb_cons_x(P, W, k, i, -1, qw);
   for (int c = 0; c < 4; c++) g[c] = (qe[c] - qw[c]) / (2.0 * P->dx);
 }
 static void grad_z_cons(const or_problem* P, const double* W, int k, int i, double g[4]) {
@@ -229,10 +249,22 @@ static void uwT_at(const or_problem* P, const double* W, int k, int i, double v[
   prim c = to_prim(q, P->gamma);
   v[0] = c.u; v[1] = c.w; v[2] = c.T;
 }
+/* (u, w, T) of the x-neighbour of (k,i) at offset s; beyond an x wall the
+ * ghost is 2*(wall state) - (interior value): u flips (normal), w flips for
+ * no-slip and stays for slip, T stays (adiabatic) */
+static void nb_uwT_x(const or_problem* P, const double* W, int k, int i, int s, double v[3]) {
+  if (!beyond_x(P, i, s)) {
+    uwT_at(P, W, k, wrap(P, i + s), v);
+    return;
+  }
+  uwT_at(P, W, k, i, v);
+  v[0] = -v[0];
+  if (P->wall != OR_WALL_SLIP) v[1] = -v[1];
+}
 static void grad_x_uwT(const or_problem* P, const double* W, int k, int i, double g[3]) {
   double ve[3], vw[3];
-  uwT_at(P, W, k, wrap(P, i + 1), ve);
-  uwT_at(P, W, k, wrap(P, i - 1), vw);
+  nb_uwT_x(P, W, k, i, +1, ve);
+  nb_uwT_x(P, W, k, i, -1, vw);
   for (int c = 0; c < 3; c++) g[c] = (ve[c] - vw[c]) / (2.0 * P->dx);
 }
 static void grad_z_uwT(const or_problem* P, const double* W, int k, int i, double g[3]) {
@@ -282,7 +314,7 @@ static void viscous_flux(const vside* L, const vside* R, int d, double dn, doubl
 /* Face fluxes F* = F^{I*} - F^{V*}                                           */
 /* ------------------------------------------------------------------------ */
 
-/* x face between (k,i) and (k,i+1), periodic */
+/* x face between (k,i) and (k,i+1) (periodic wrap when x is periodic) */
 static void xface(const or_problem* P, const double* W, int k, int i, double F[4]) {
   int ip = wrap(P, i + 1);
   double qL[4], qR[4], gL[4], gR[4], ql[4], qr[4], FI[4], FV[4];
@@ -334,6 +366,36 @@ static void zface_interior(const or_problem* P, const double* W, int k, int i, d
 
 static void mirror(const double q[4], double g[4]) {
   g[0] = q[0]; g[1] = q[1]; g[2] = -q[2]; g[3] = q[3];
+}
+
+/* x wall on the left of column 0 (s = -1) or on the right of column nx-1
+ * (s = +1): the z-wall construction with x as the normal direction. */
+static void xface_wall(const or_problem* P, const double* W, int k, int i, int s, double F[4]) {
+  double q[4], g[4], qb[4], qg[4], FI[4], FV[4];
+  load(P, W, k, i, q);
+  grad_x_cons(P, W, k, i, g);
+  for (int c = 0; c < 4; c++) qb[c] = q[c] + (double)s * g[c] * (P->dx / 2.0);
+  for (int c = 0; c < 4; c++) qg[c] = qb[c];
+  qg[1] = -qb[1];
+  if (s < 0) or_lf_flux(qg, qb, 0, P->gamma, FI);
+  else or_lf_flux(qb, qg, 0, P->gamma, FI);
+  /* viscous: the cell and its ghost (2*wall - interior; adiabatic) */
+  double v[3], t[3];
+  uwT_at(P, W, k, i, v);
+  grad_z_uwT(P, W, k, i, t);
+  vside C = {v[0], v[1], v[2], t[0], t[1]};
+  vside Gh;
+  Gh.u = -v[0]; Gh.dut = -t[0];
+  if (P->wall == OR_WALL_SLIP) {
+    Gh.w = v[1]; Gh.dwt = t[1];
+  } else {
+    Gh.w = -v[1]; Gh.dwt = -t[1];
+  }
+  Gh.T = v[2];
+  int f = fluid_of(P, k);
+  if (s < 0) viscous_flux(&Gh, &C, 0, P->dx, mu_of_fluid(P, f), kappa_of_fluid(P, f), FV);
+  else viscous_flux(&C, &Gh, 0, P->dx, mu_of_fluid(P, f), kappa_of_fluid(P, f), FV);
+  for (int c = 0; c < 4; c++) F[c] = FI[c] - FV[c];
 }
 
 /* Outer wall below row 0 (s = -1) or above the top row (s = +1). */
@@ -411,8 +473,10 @@ static void rhs_cell(const or_problem* P, const double* W, int k, int i, double 
     return;
   }
   double Fe[4], Fw[4], Hn[4], Hs[4], q[4];
-  xface(P, W, k, i, Fe);
-  xface(P, W, k, wrap(P, i - 1), Fw);
+  if (P->xwall && i == P->nx - 1) xface_wall(P, W, k, i, +1, Fe);
+  else xface(P, W, k, i, Fe);
+  if (P->xwall && i == 0) xface_wall(P, W, k, i, -1, Fw);
+  else xface(P, W, k, wrap(P, i - 1), Fw);
   zflux_of_cell(P, W, k, i, +1, Hn);
   zflux_of_cell(P, W, k, i, -1, Hs);
   load(P, W, k, i, q);

@@ -32,9 +32,10 @@ enum { OR_RHS_NS = 0, OR_RHS_LINEAR = 1 };
 typedef struct {
   int nx, nS, nB, nF;  /* columns; rows of the S, B and F bands                */
   int m;               /* rate ratio: slow step = m fast steps (Sec. 3)          */
-  int wall;            /* outer z walls: OR_WALL_NOSLIP or OR_WALL_SLIP (adiabatic) */
+  int wall;            /* outer walls: OR_WALL_NOSLIP or OR_WALL_SLIP (adiabatic) */
   int rhs_mode;        /* OR_RHS_NS, or OR_RHS_LINEAR (R = lin_lambda*q, tests)  */
-  int pad_;
+  int xwall;           /* 0: x periodic; 1: walls of the same kind at both x ends
+                        * (Sec. 5.2, walls on all boundaries)                    */
   double dt;           /* slow step Delta t                                     */
   double dx, dz1, dz2; /* cell sizes: x, fluid-1 rows, fluid-2 rows             */
   double gamma, Pr;    /* ratio of specific heats, Prandtl number               */

@@ -28,7 +28,7 @@ RHS_NS, RHS_LINEAR = 0, 1
 class Problem(C.Structure):
     _fields_ = [
         ("nx", C.c_int), ("nS", C.c_int), ("nB", C.c_int), ("nF", C.c_int),
-        ("m", C.c_int), ("wall", C.c_int), ("rhs_mode", C.c_int), ("pad_", C.c_int),
+        ("m", C.c_int), ("wall", C.c_int), ("rhs_mode", C.c_int), ("xwall", C.c_int),
         ("dt", C.c_double), ("dx", C.c_double), ("dz1", C.c_double), ("dz2", C.c_double),
         ("gamma", C.c_double), ("Pr", C.c_double), ("mu1", C.c_double), ("mu2", C.c_double),
         ("G", C.c_double), ("lin_lambda", C.c_double),
@@ -95,10 +95,10 @@ def _p(a: np.ndarray):
 
 def make_problem(nx, nS, nB, nF, m, dt, dx, dz1=None, dz2=None, gamma=1.4, Pr=0.72,
                  mu1=1.0 / 20000.0, mu2=1.0 / 5000.0, G=0.008140864714, wall=WALL_NOSLIP,
-                 rhs_mode=RHS_NS, lin_lambda=0.0) -> Problem:
+                 rhs_mode=RHS_NS, lin_lambda=0.0, xwall=0) -> Problem:
     dz1 = dx if dz1 is None else dz1
     dz2 = dx if dz2 is None else dz2
-    return Problem(nx=nx, nS=nS, nB=nB, nF=nF, m=m, wall=wall, rhs_mode=rhs_mode, pad_=0,
+    return Problem(nx=nx, nS=nS, nB=nB, nF=nF, m=m, wall=wall, rhs_mode=rhs_mode, xwall=xwall,
                    dt=dt, dx=dx, dz1=dz1, dz2=dz2, gamma=gamma, Pr=Pr, mu1=mu1, mu2=mu2, G=G,
                    lin_lambda=lin_lambda)
 

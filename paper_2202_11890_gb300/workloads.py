@@ -153,11 +153,32 @@ def thermal_bubble(grid: Grid, gamma=GAMMA, g=G_SIGNED, theta0=300.0,
                    centre=(0.0, -2.5), radius=2.5, amp=0.25) -> np.ndarray:
     """Warm bubble in fluid 1 of Sec. 5.2: delta theta = amp(1 + cos(pi r)) for
     r <= radius around centre, 0 elsewhere and in fluid 2."""
+    return _potential_temperature_state(grid, [(1, centre, radius, amp)], gamma, g, theta0)
+
+
+def thermal_convection(grid: Grid, gamma=GAMMA, g=G_SIGNED, theta0=300.0) -> np.ndarray:
+    """The second thermal-convection case of Sec. 5.2 (the one of Table 6): a
+    warm perturbation in fluid 1, delta theta_1 = 1.25 (1 + cos(pi r_1)) for
+    r_1 <= 2.5 around (0, -2.5), and a cold one in fluid 2, delta theta_2 =
+    -7.5 (1 + cos(pi r_2)) for r_2 <= 1 around (0, 1.5)."""
+    return _potential_temperature_state(
+        grid, [(1, (0.0, -2.5), 2.5, 1.25), (2, (0.0, 1.5), 1.0, -7.5)], gamma, g, theta0)
+
+
+def _potential_temperature_state(grid: Grid, bumps, gamma, g, theta0) -> np.ndarray:
+    """The initial state of Sec. 5.2 at rest from potential-temperature
+    perturbations: T = (1 + dth/theta0) Psi, p = Psi^(gamma/(gamma-1))/gamma,
+    rho = theta0/(theta0 + dth) Psi^(1/(gamma-1)), Psi = 1 + g z/(cp (1 +
+    dth/theta0)). bumps: (fluid, centre, radius, amplitude) with
+    dth = amplitude (1 + cos(pi r)) for r <= radius."""
     x = grid.x_centres()[None, :] * np.ones((grid.nz, 1))
     z = grid.z_centres()[:, None] * np.ones((1, grid.nx))
-    r = np.sqrt((x - centre[0]) ** 2 + (z - centre[1]) ** 2)
     k = np.arange(grid.nz)[:, None] * np.ones((1, grid.nx))
-    dth = np.where((r <= radius) & (k < grid.n1), amp * (1.0 + np.cos(np.pi * r)), 0.0)
+    dth = np.zeros((grid.nz, grid.nx))
+    for fluid, centre, radius, amp in bumps:
+        r = np.sqrt((x - centre[0]) ** 2 + (z - centre[1]) ** 2)
+        inside = (k < grid.n1) if fluid == 1 else (k >= grid.n1)
+        dth = np.where((r <= radius) & inside, amp * (1.0 + np.cos(np.pi * r)), dth)
     cp = 1.0 / (gamma - 1.0)
     fac = 1.0 + dth / theta0
     psi = 1.0 + g * z / (cp * fac)
