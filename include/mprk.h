@@ -57,21 +57,26 @@ extern "C" {
 #define MPRK_WALL_NOSLIP 0 /* outer z walls: no-slip, adiabatic               */
 #define MPRK_WALL_SLIP 1   /* outer z walls: free slip, adiabatic             */
 
+#define MPRK_X_PERIODIC 0 /* x is periodic                       */
+#define MPRK_X_WALLS 1    /* walls at both ends of x              */
+
 #define MPRK_HOST 0   /* pointer is host memory   */
 #define MPRK_DEVICE 1 /* pointer is device memory */
 
 /* ---- configuration ----------------------------------------------------- */
 typedef struct {
-  int nx;         /* columns (periodic), >= 4                                 */
+  int nx;         /* columns, >= 4                                            */
   int nz_S;       /* rows of the slow band, >= 2                              */
   int nz_B;       /* rows of the buffer band, >= 4 (buffer condition, Sec. 3) */
   int nz_F;       /* rows of the fast band, >= 2                              */
   int m;          /* rate ratio, 1..64: dt_fast = dt / m                      */
   int precision;  /* MPRK_FP64 or MPRK_FP32FLUX                               */
   int scheme;     /* MPRK_SCHEME_MPRK2 or MPRK_SCHEME_SR_RK2                  */
-  int wall;       /* MPRK_WALL_NOSLIP or MPRK_WALL_SLIP                       */
+  int wall;       /* MPRK_WALL_NOSLIP or MPRK_WALL_SLIP (adiabatic)           */
   int diag_every; /* monitor the state every this many slow steps (0 = never) */
-  int reserved;   /* must be 0                                                */
+  int x_walls;    /* MPRK_X_PERIODIC (0) or MPRK_X_WALLS: adiabatic walls of
+                     kind `wall` at both x ends, as in Sec. 5.2's thermal
+                     convection (walls on all boundaries)                     */
   double dt;      /* slow step; 0 = from the initial state at Courant cfl     */
   double cfl;     /* used when dt == 0; 0 means 0.4                           */
   double dx;      /* cell width                                              */

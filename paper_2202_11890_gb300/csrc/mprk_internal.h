@@ -48,6 +48,7 @@ struct Geom {
   int nS_g;        // rows of the slow band of the grid (Courant numbers per band)
   int m;           // fast substeps per slow step
   int wall;        // 0 no-slip, 1 slip
+  int xwall;       // 0 periodic x, 1 walls (of kind `wall`) at both x ends
   double dt;
   double inv_dx, inv_dz1, inv_dz2;
   double gamma, gm1;

@@ -114,7 +114,7 @@ cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStr
     const CUtensorMap& f = staged ? (a.dF == a.b.dA ? maps->dA : maps->dB) : none;
     const CUtensorMap& ra = staged ? maps->Ra : none;
     const dim3 grid(a.tiles_x, n_tiles / a.tiles_x);
-    stage_kernel_mixed<<<grid, MIXED_THREADS, sizeof(MixedKernelSmem), stream>>>(s, sb, f, ra);
+    stage_kernel_mixed<<<grid, MIXED_THREADS, mixed_kernel_smem(a.stage & 1), stream>>>(s, sb, f, ra);
   }
   return cudaGetLastError();
 }

@@ -100,7 +100,8 @@ int mprk::validate_config(const mprk_config* c) {
   if (c->wall != MPRK_WALL_NOSLIP && c->wall != MPRK_WALL_SLIP)
     return fail(MPRK_EINVAL, "unknown wall type %d", c->wall);
   if (c->diag_every < 0) return fail(MPRK_EINVAL, "diag_every must be >= 0");
-  if (c->reserved != 0) return fail(MPRK_EINVAL, "reserved must be 0");
+  if (c->x_walls != MPRK_X_PERIODIC && c->x_walls != MPRK_X_WALLS)
+    return fail(MPRK_EINVAL, "unknown x boundary %d", c->x_walls);
   if (!(c->dt >= 0.0) || !std::isfinite(c->dt)) return fail(MPRK_EINVAL, "dt must be >= 0");
   if (!(c->cfl >= 0.0) || c->cfl > 10.0) return fail(MPRK_EINVAL, "cfl out of range");
   if (!(c->dx > 0) || !(c->dz1 > 0) || !(c->dz2 > 0))
@@ -227,6 +228,7 @@ void mprk::geom_from_config(const mprk_config& c, int pitch, Geom* gp) {
   g.nS_g = c.nz_S;
   g.m = c.m;
   g.wall = c.wall;
+  g.xwall = c.x_walls;
   g.dt = c.dt;
   g.inv_dx = 1.0 / c.dx;
   g.inv_dz1 = 1.0 / c.dz1;

@@ -82,8 +82,8 @@ int mprk_step_static(const mprk_config* cfg, double* q_dev, int n_slow_steps, vo
   if (!cfg || !q_dev) return sfail(MPRK_EINVAL, "NULL argument");
   if (n_slow_steps < 0) return sfail(MPRK_EINVAL, "negative step count");
   if (cfg->nx < 4 || cfg->nz_S < 2 || cfg->nz_B < 4 || cfg->nz_F < 2 || cfg->m < 1 ||
-      cfg->m > 64 || cfg->reserved != 0)
-    return sfail(MPRK_EINVAL, "invalid grid, buffer width (>= 4), rate ratio or reserved field");
+      cfg->m > 64 || (cfg->x_walls != MPRK_X_PERIODIC && cfg->x_walls != MPRK_X_WALLS))
+    return sfail(MPRK_EINVAL, "invalid grid, buffer width (>= 4), rate ratio or x boundary");
   if (cfg->precision != MPRK_FP64 && cfg->precision != MPRK_FP32FLUX)
     return sfail(MPRK_EINVAL, "unknown precision");
   if (cfg->scheme != MPRK_SCHEME_MPRK2 && cfg->scheme != MPRK_SCHEME_SR_RK2)

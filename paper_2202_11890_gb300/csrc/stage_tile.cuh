@@ -105,6 +105,27 @@ __device__ __forceinline__ int wrap_col(int i, int nx) {
   return i;
 }
 
+// The cell that halo column i stands for: its periodic image, or with x
+// walls its mirror image across the nearer wall. In that case *ghost is set
+// and the caller builds the wall ghosts: rho u flips (mirror state), u flips
+// and, at a no-slip wall, w flips ((u, w, T) ghost = 2 wall state - cell).
+// Far ghosts of a tile wider than the grid feed no cell of the grid and are
+// clamped into it.
+__device__ __forceinline__ int halo_col(int i, int nx, int xwall, bool* ghost) {
+  *ghost = false;
+  if (!xwall) return wrap_col(i, nx);
+  if (i < 0) {
+    *ghost = true;
+    i = -1 - i;
+  } else if (i >= nx) {
+    *ghost = true;
+    i = 2 * nx - 1 - i;
+  }
+  return i < 0 ? 0 : (i >= nx ? nx - 1 : i);
+}
+// Is halo column i an x-wall ghost?
+__device__ __forceinline__ bool x_ghost(int i, int nx, int xwall) { return xwall && (i < 0 || i >= nx); }
+
 // The tile body. tile = linear tile index within the launch's row range.
 // Not inlined: the single-instance kernel and the persistent batch kernel
 // then run the very same compiled body, so an instance's results are bitwise
@@ -135,7 +156,8 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
     const int k = k0 - 2 + rr;
     Real val = Real(0);
     if (k >= 0 && k < nz) {
-      const int i = wrap_col(i0 - 2 + cc, nx);
+      bool gh;
+      const int i = halo_col(i0 - 2 + cc, nx, g.xwall, &gh);
       const size_t off = (size_t)c * plane + (size_t)k * g.pitch + i;
       if (a.rhs_only) {
         val = (Real)a.rhs_in[off];
@@ -148,6 +170,7 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
           val = (Real)base[off];
         }
       }
+      if (gh && c == 1) val = -val;  // mirror state beyond an x wall
     }
     S.q[c][rr][cc] = val;
   }
@@ -166,13 +189,15 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
     const Real u = mu_ * inv, w = mw * inv;
     const Real p = gm1 * (E - Real(0.5) * (mu_ * u + mw * w));
     S.v[0][rr][cc] = u;
-    S.v[1][rr][cc] = w;
+    // the mirror state's u is already flipped; a no-slip wall flips w too
+    S.v[1][rr][cc] = (x_ghost(i0 - 1 + cc, nx, g.xwall) && g.wall == 0) ? -w : w;
     S.v[2][rr][cc] = gamma * p * inv;
   }
   if (has_gamma && tid < TX + 2) {
     // Interface state of column i0-1+tid in double precision from the two
     // cells touching Gamma (App. B, Eq. bulk-flux and the wall states).
-    const int i = wrap_col(i0 - 1 + tid, nx);
+    bool gh;
+    const int i = halo_col(i0 - 1 + tid, nx, g.xwall, &gh);
     double u[2], T[2];
 #pragma unroll
     for (int s = 0; s < 2; s++) {
@@ -192,6 +217,7 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
           }
         }
       }
+      if (gh) qq[1] = -qq[1];  // mirror state beyond an x wall
       const double inv = 1.0 / qq[0];
       u[s] = qq[1] * inv;
       const double w = qq[2] * inv;

@@ -330,16 +330,14 @@ __device__ __forceinline__ void mixed_subtile(const StageArgs& a, int k0, int i0
     const int k = k0 - 2 + rr;
     float4 val = make_float4(0.f, 0.f, 0.f, 0.f), vv = make_float4(0.f, 0.f, 0.f, 0.f);
     if (k >= 0 && k < nz) {
-      int i = i0 - 2 + cc;
-      if (i < 0) i += nx;
-      if (i >= nx) i -= nx;
-      if (i >= nx) i %= nx;  // only when nx is smaller than the tile
+      bool gh;
+      const int i = halo_col(i0 - 2 + cc, nx, g.xwall, &gh);
       const size_t off = (size_t)k * g.pitch + i;
       const float4 ra4 = rowc[k], rd4 = rowc[3 * nz + k];
       const float r0 = ra4.x, m0 = ra4.y, w0 = ra4.z;
       if (a.rhs_only) {
         val.x = narrow(a.rhs_in[off] - (double)r0);
-        val.y = narrow(a.rhs_in[plane + off] - (double)m0);
+        val.y = narrow((gh ? -a.rhs_in[plane + off] : a.rhs_in[plane + off]) - (double)m0);
         val.z = narrow(a.rhs_in[2 * plane + off] - (double)w0);
         val.w = narrow(a.rhs_in[3 * plane + off] - (double)ra4.w);
       } else {
@@ -353,12 +351,15 @@ __device__ __forceinline__ void mixed_subtile(const StageArgs& a, int k0, int i0
           val.z += h * ra[2 * plane];
           val.w += h * ra[3 * plane];
         }
+        // mirror state beyond an x wall: rho u = m0 + d flips
+        if (gh) val.y = -val.y - 2.0f * m0;
       }
       const float r = r0 + val.x, mu_ = m0 + val.y, mw = w0 + val.z;
       const float inv = __frcp_rn(r);
       const float u = mu_ * inv, w = mw * inv;
       const float dp = gm1 * (val.w - (0.5f * (mu_ * u + mw * w) - rd4.x));
-      vv = make_float4(u, w, gamma * (rd4.z + dp) * inv, 0.f);
+      // the mirror state's u is already flipped; a no-slip wall flips w too
+      vv = make_float4(u, (gh && g.wall == 0) ? -w : w, gamma * (rd4.z + dp) * inv, 0.f);
     }
     S.q[rr][cc] = val;
     S.v[rr][cc] = vv;
@@ -377,9 +378,8 @@ __device__ __forceinline__ void mixed_subtile(const StageArgs& a, int k0, int i0
     // interface state of column i0-1+j in double from the two cells touching
     // Gamma (App. B, Eq. bulk-flux and the wall states)
     const int j = tid - (MIXED_THREADS - 64);
-    int i = i0 - 1 + j;
-    if (i < 0) i += nx;
-    if (i >= nx) i %= nx;
+    bool gh;
+    const int i = halo_col(i0 - 1 + j, nx, g.xwall, &gh);
     double u[2], T[2];
 #pragma unroll
     for (int s = 0; s < 2; s++) {
@@ -396,6 +396,7 @@ __device__ __forceinline__ void mixed_subtile(const StageArgs& a, int k0, int i0
           if (odd_stage) qq[c] += (k < g.n1_r ? g.dt : g.hF) * widen(Ra[off]);
         }
       }
+      if (gh) qq[1] = -qq[1];  // mirror state beyond an x wall
       const double inv = 1.0 / qq[0];
       u[s] = qq[1] * inv;
       const double w = qq[2] * inv;
@@ -755,14 +756,16 @@ __device__ __forceinline__ void pair_z_face(PairSmem& S, const PairConst& C, con
 }
 
 // An interior tile needs none of the ghost rules: rows k0-2 .. k0+MTZ+1 lie
-// inside the grid and inside one fluid. For a stage (not the right-hand-side
+// inside the grid and inside one fluid, and with x walls its halo columns
+// i0-2 .. i0+TX+1 lie between them. For a stage (not the right-hand-side
 // hook) they also lie on one side of the F-row bound, and the tile's MTZ rows
 // share one stage region.
-__device__ __forceinline__ bool pair_interior(const StageArgs& a, int k0) {
+__device__ __forceinline__ bool pair_interior(const StageArgs& a, int k0, int i0) {
   const Geom& g = a.g;
   const int hi = a.rhs_only ? a.rhs_hi : g.nz;
   const int lo_h = k0 - 2, hi_h = k0 + MTZ + 2;  // halo rows [lo_h, hi_h)
   if (lo_h < 0 || hi_h > g.nz || k0 + MTZ > hi || !(g.n1 <= lo_h || g.n1 >= hi_h)) return false;
+  if (g.xwall && (i0 < 2 || i0 + TX + 2 > g.nx)) return false;  // halo columns inside the walls
   if (a.rhs_only) return true;
   return (g.n1_r <= lo_h || g.n1_r >= hi_h) && (g.nS_r <= k0 || g.nS_r >= k0 + MTZ);
 }
@@ -1028,7 +1031,7 @@ union MixedTileSmem {
 
 __device__ __forceinline__ bool stage_tile_mixed(const StageArgs& a, int k0, int i0, MixedTileSmem& S,
                                                  const Stage* stg, unsigned long long* bar) {
-  if (pair_interior(a, k0)) return pair_tile(a, k0, i0, S.pair, stg, bar);
+  if (pair_interior(a, k0, i0)) return pair_tile(a, k0, i0, S.pair, stg, bar);
   mixed_subtile(a, k0, i0, S.gen);
   const int hi = a.rhs_only ? a.rhs_hi : a.g.nz;
   if (k0 + TZ < hi) {
@@ -1048,7 +1051,7 @@ __device__ __forceinline__ void stage_tile_mixed(const StageArgs& a, int tile, M
 // Tiles whose float planes are tensor-copied: interior tiles of a stage
 // away from the x wrap (the 40 staged columns lie inside the row).
 __device__ __forceinline__ bool tile_bulk_ok(const StageArgs& a, int k0, int i0) {
-  return a.bulk && !a.rhs_only && i0 >= 4 && i0 + TX + 4 <= a.g.nx && pair_interior(a, k0);
+  return a.bulk && !a.rhs_only && i0 >= 4 && i0 + TX + 4 <= a.g.nx && pair_interior(a, k0, i0);
 }
 
 // Issued by one thread: the tensor copies of the tile's float planes into B
@@ -1063,12 +1066,18 @@ __device__ __forceinline__ void stage_issue(const StageArgs& a, int k0, int i0, 
   if (odd) tma_load_3d(&B.ra[0][0][0], tm_ra, i0 - 4, k0 - 2, 0, bar);
 }
 
-// Shared memory of the single-instance FP32-flux kernel: the staging
-// buffer, its mbarrier and the tile's working set.
+// Shared memory of the single-instance FP32-flux kernel: the tile's working
+// set, the staging buffer's mbarrier and the staging buffer. The buffer
+// comes last, so that even stages (no R_a box) launch without its second
+// half.
 struct MixedKernelSmem {
-  Stage stg;
-  unsigned long long bar;
   MixedTileSmem work;
+  unsigned long long bar;
+  Stage stg;
 };
+// Dynamic shared memory of a launch of the stage kernel for stage parity odd.
+constexpr size_t mixed_kernel_smem(bool odd) {
+  return odd ? sizeof(MixedKernelSmem) : offsetof(MixedKernelSmem, stg) + sizeof(Stage::d);
+}
 
 }  // namespace mprk

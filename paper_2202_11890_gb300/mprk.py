@@ -34,6 +34,8 @@ MPRK_SCHEME_MPRK2 = 0
 MPRK_SCHEME_SR_RK2 = 1
 MPRK_WALL_NOSLIP = 0
 MPRK_WALL_SLIP = 1
+MPRK_X_PERIODIC = 0
+MPRK_X_WALLS = 1
 MPRK_HOST = 0
 MPRK_DEVICE = 1
 
@@ -46,7 +48,7 @@ class mprk_config(C.Structure):
     _fields_ = [
         ("nx", C.c_int), ("nz_S", C.c_int), ("nz_B", C.c_int), ("nz_F", C.c_int),
         ("m", C.c_int), ("precision", C.c_int), ("scheme", C.c_int), ("wall", C.c_int),
-        ("diag_every", C.c_int), ("reserved", C.c_int),
+        ("diag_every", C.c_int), ("x_walls", C.c_int),
         ("dt", C.c_double), ("cfl", C.c_double), ("dx", C.c_double), ("dz1", C.c_double),
         ("dz2", C.c_double), ("gamma", C.c_double), ("Pr", C.c_double), ("mu1", C.c_double),
         ("mu2", C.c_double), ("G", C.c_double),

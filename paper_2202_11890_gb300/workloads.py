@@ -207,6 +207,8 @@ class Workload:
             return fourier_modes(self.grid, self.seed)
         if self.perturbation == "rest":
             return rest_state(self.grid)
+        if self.perturbation == "convection":
+            return thermal_convection(self.grid)
         raise ValueError(self.perturbation)
 
     def cell_stages_per_step(self) -> int:
@@ -230,6 +232,20 @@ def mixed_4096():
     """4096x2048 grid, S 960 / B 128 / F 960 rows, m = 8, 500 slow steps, FP32 flux."""
     return Workload("mixed_4096x2048_m8_fp32flux", Grid(4096, 960, 128, 960), 8, 500, "fp32flux",
                     "fourier", SEED0 + 2)
+
+
+def convection_grid() -> Grid:
+    """The thermal-convection mesh of Table 6 (Sec. 5.2, second set-up):
+    Omega_1 = (-5,5) x (-7,0) with 100 x 100 cells, Omega_2 = (-5,5) x (0,3)
+    with 100 x 200 cells; fluid 1 split into 96 slow and 4 buffer rows."""
+    return Grid(100, 96, 4, 200, dx=0.1, dz1=0.07, dz2=0.015)
+
+
+def convection_100() -> Workload:
+    """Table 6's thermal convection: walls on all boundaries, MPRK2 with
+    m = 4, dt = 0.025, to t = 2.5 (100 slow steps), FP64."""
+    return Workload("convection_100x300_m4_fp64", convection_grid(), 4, 100, "fp64", "convection", 0,
+                    extra={"x_walls": 1, "dt": 0.025})
 
 
 def batched_256(count: int = 256, seed: int = SEED0 + 3, steps: int = 100):

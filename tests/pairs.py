@@ -12,12 +12,12 @@ def oracle_threads():
 
 
 def pair(grid: W.Grid, m: int, dt: float = 0.0, precision: int = 0, scheme: int = 0, wall: int = 0,
-         mu1=W.MU1, mu2=W.MU2, G=-W.G_SIGNED, diag_every: int = 0, q0=None, cfl=0.4):
+         mu1=W.MU1, mu2=W.MU2, G=-W.G_SIGNED, diag_every: int = 0, q0=None, cfl=0.4, xwall: int = 0):
     """(mprk_config, oracle Problem, dt) for the same problem. dt == 0 picks
     the oracle's Courant-number step for q0."""
     from paper_2202_11890_gb300 import mprk as M
     P = O.make_problem(grid.nx, grid.nS, grid.nB, grid.nF, m, dt, grid.dx, dz1=grid.dz1,
-                       dz2=grid.dz2, mu1=mu1, mu2=mu2, G=G, wall=wall)
+                       dz2=grid.dz2, mu1=mu1, mu2=mu2, G=G, wall=wall, xwall=xwall)
     if dt == 0.0:
         assert q0 is not None
         dt = O.stable_dt(P, q0, cfl)
@@ -27,6 +27,7 @@ def pair(grid: W.Grid, m: int, dt: float = 0.0, precision: int = 0, scheme: int 
     cfg.dx, cfg.dz1, cfg.dz2 = grid.dx, grid.dz1, grid.dz2
     cfg.mu1, cfg.mu2, cfg.G = mu1, mu2, G
     cfg.precision, cfg.scheme, cfg.wall, cfg.diag_every = precision, scheme, wall, diag_every
+    cfg.x_walls = xwall
     return cfg, P, dt
 
 

@@ -44,7 +44,7 @@ def test_invalid_configs_are_rejected_without_a_device(lib):
     from paper_2202_11890_gb300 import mprk as M
     q = np.ones((4, 12, 8))
     cases = [dict(nz_B=3), dict(nz_B=2), dict(m=0), dict(nx=3), dict(precision=7),
-             dict(scheme=9), dict(wall=5), dict(dt=-1.0), dict(mu1=0.0), dict(reserved=1)]
+             dict(scheme=9), dict(wall=5), dict(dt=-1.0), dict(mu1=0.0), dict(x_walls=2)]
     for over in cases:
         base = dict(nx=8, nz_S=4, nz_B=4, nz_F=4, m=2)
         geo = {k: over.pop(k) for k in list(over) if k in base}
