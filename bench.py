@@ -57,8 +57,8 @@ TRAFFIC = {
     },
     "stage_kernel_mixed": {
         "files": ("stage_tile_mixed.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": None,
-        "bytes_per_step": None,
+        "sha256": "3e5d5c025b6de49b323530dea2c9ac3d1048fc3345099d967940b58a06433ec9",
+        "bytes_per_step": 5211695616,
     },
 }
 
@@ -492,6 +492,78 @@ def run_speedup(args):
 SEED_SPEEDUP = W.SEED0 + 9
 
 
+def run_convection(args):
+    """Table 6's thermal convection (Sec. 5.2, second set-up) on the GPU:
+    walls on all boundaries, 100 x (100 + 200) cells, MPRK2 with m = 4.
+    Throughput of the dt = 0.025 run to t = 2.5 (100 slow steps) in FP64 and
+    in the FP32-flux mode, and the temporal-convergence study: L2 errors of
+    rho, momentum and rho E at t = 2.5 for dt = 0.025 {1, 1/2, 1/4, 1/8}
+    against a single-rate RK2 run on the GPU with dt = 0.003125/64 (the
+    paper's reference is RK45 with dt = 0.00125; the oracle check of the same
+    study is tests/test_gpu_xwall.py)."""
+    import torch
+    from paper_2202_11890_gb300 import build as B
+    from paper_2202_11890_gb300 import mprk as M
+    from paper_2202_11890_gb300 import timing as T
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    wl = W.convection_100()
+    g = wl.grid
+    q0 = wl.initial_state()
+    t_end = 2.5
+
+    def config(dt, m=wl.m, scheme=M.MPRK_SCHEME_MPRK2, precision=M.MPRK_FP64):
+        cfg = M.mprk_config_default(g.nx, g.nS, g.nB, g.nF, m, dx=g.dx, dz1=g.dz1, dz2=g.dz2)
+        cfg.dt, cfg.scheme, cfg.precision, cfg.x_walls = dt, scheme, precision, M.MPRK_X_WALLS
+        return cfg
+
+    # throughput of the dt = 0.025 run, FP64 and FP32 flux
+    rates = {}
+    for name, prec in (("fp64", M.MPRK_FP64), ("fp32flux", M.MPRK_FP32FLUX)):
+        with M.Instance(config(0.025, precision=prec), q0) as inst:
+            cs = inst.info()["cell_stages_per_step"]
+            inst.step(args.warmup)
+            inst.sync()
+            sampler = ClockSampler(torch.cuda.current_device())
+            with sampler:
+                t_ms = T.time_steps(inst.h, inst.info()["stream"], wl.steps)
+            rates[name] = {"value": cs * wl.steps / (t_ms * 1e-3), "ms_per_step": t_ms / wl.steps,
+                           "clocks": sampler.summary()}
+
+    # reference: single-rate RK2 with a tiny step (fast-band Courant ~0.01)
+    ref_dt = 0.003125 / 64
+    with M.Instance(config(ref_dt, m=1, scheme=M.MPRK_SCHEME_SR_RK2), q0) as inst:
+        inst.step(int(round(t_end / ref_dt)))
+        ref = inst.state()
+    cell = g.dx * np.concatenate([np.full(g.n1, g.dz1), np.full(g.nF, g.dz2)])[:, None]
+
+    def l2(a):
+        return float(np.sqrt((a * a * cell).sum()))
+
+    dts, errs = [0.025, 0.0125, 0.00625, 0.003125], []
+    for dt in dts:
+        with M.Instance(config(dt), q0) as inst:
+            inst.step(int(round(t_end / dt)))
+            d = inst.state() - ref
+        errs.append([l2(d[0]), l2(np.stack([d[1], d[2]])), l2(d[3])])
+    e = np.array(errs)
+    orders = np.log2(e[:-1] / e[1:]).tolist()
+    out = {"metric": METRIC, "value": rates["fp64"]["value"], "unit": "cell-stages/s", "n_gpus": 1,
+           "steps": wl.steps, "warmup": args.warmup, "ms_per_step": rates["fp64"]["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": wl.name, "nx": g.nx, "rows_S_B_F": [g.nS, g.nB, g.nF], "m": wl.m,
+                      "dt": 0.025, "x_walls": True, "dz1": g.dz1, "dz2": g.dz2},
+           "fp32flux": rates["fp32flux"], "clocks": rates["fp64"]["clocks"],
+           "convergence": {"t": t_end, "dt": dts, "l2_rho_momentum_energy": errs, "orders": orders,
+                           "reference": f"SR-RK2 on the GPU, dt = {ref_dt}",
+                           "paper_orders": [[2.04, 2.04, 2.04], [2.00, 2.00, 2.00], [2.00, 2.00, 2.00]]},
+           "gpu_launches": (2 * wl.m + 1) * wl.steps}
+    print(json.dumps(out))
+
+
 def oracle_sample(wl: W.Workload, cols: int):
     """The workload's rows, rate and perturbation on a strip of `cols` columns
     (the oracle's cost per cell-stage does not depend on nx)."""
@@ -571,7 +643,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large_2048",
-                    choices=["large_2048", "plain_64", "mixed_4096", "batched_256", "served", "speedup"])
+                    choices=["large_2048", "plain_64", "mixed_4096", "batched_256", "served", "speedup",
+                             "convection"])
     ap.add_argument("--speedup-nx", type=int, default=2048)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--served-requests", type=int, default=2000)
@@ -591,6 +664,8 @@ def main():
         run_batched(args)
     elif args.workload == "served":
         run_served(args)
+    elif args.workload == "convection":
+        run_convection(args)
     elif args.workload == "speedup":
         run_speedup(args)
     else:
