@@ -52,8 +52,8 @@ CSRC = os.path.join(ROOT, "paper_2202_11890_gb300", "csrc")
 TRAFFIC = {
     "stage_kernel": {
         "files": ("stage_tile.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "872b1166a3d2ecaf91ed26a33c106380a23a2553043f1298fd20d5aabae7c419",
-        "bytes_per_step": 1167967488,
+        "sha256": "e05c30d7ae781d6b69fa8f3147d1ff62280ccabbbc388581c35d171fd84f5b1c",
+        "bytes_per_step": 1169889536,
     },
     "stage_kernel_mixed": {
         "files": ("stage_tile_mixed.cuh", "mprk_internal.h", "mprk_kernels.cu"),
