@@ -123,6 +123,96 @@ def gaussian_bumps(grid: Grid, seed: int, k_bumps: int = 4, sigma_cells: float =
     return conserved(rho0 * (1.0 + drho), u, w, p0, gamma)
 
 
+# ---- three dimensions (App. B in full): state [5][nz][ny][nx] -------------
+
+@dataclass
+class Grid3:
+    """x-y-z grid: nx x ny columns (both periodic), rows S | B | F in z."""
+    nx: int
+    ny: int
+    nS: int
+    nB: int
+    nF: int
+    dx: float = 0.0
+    dy: float = 0.0
+    dz1: float = 0.0
+    dz2: float = 0.0
+
+    def __post_init__(self):
+        if self.dx <= 0.0:
+            self.dx = 10.0 / self.nx
+        if self.dy <= 0.0:
+            self.dy = self.dx
+        if self.dz1 <= 0.0:
+            self.dz1 = self.dx
+        if self.dz2 <= 0.0:
+            self.dz2 = self.dx
+
+    @property
+    def nz(self) -> int:
+        return self.nS + self.nB + self.nF
+
+    @property
+    def n1(self) -> int:
+        return self.nS + self.nB
+
+    def column_grid(self) -> Grid:
+        """The x-z grid of one y column (same rows and cell sizes)."""
+        return Grid(self.nx, self.nS, self.nB, self.nF, dx=self.dx, dz1=self.dz1, dz2=self.dz2)
+
+    def y_centres(self) -> np.ndarray:
+        return -0.5 * self.ny * self.dy + (np.arange(self.ny) + 0.5) * self.dy
+
+
+def conserved3(rho, u, v, w, p, gamma=GAMMA) -> np.ndarray:
+    """Stack (rho, rho u, rho v, rho w, rho E) from fields of shape [nz][ny][nx]."""
+    q = np.empty((5,) + rho.shape)
+    q[0] = rho
+    q[1] = rho * u
+    q[2] = rho * v
+    q[3] = rho * w
+    q[4] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+    return q
+
+
+def rest_state3(grid: Grid3, gamma=GAMMA, g=G_SIGNED) -> np.ndarray:
+    rho, p = rest_primitives(grid.column_grid(), gamma, g)
+    rho = np.repeat(rho[:, None, :], grid.ny, axis=1)
+    p = np.repeat(p[:, None, :], grid.ny, axis=1)
+    zero = np.zeros_like(rho)
+    return conserved3(rho, zero, zero, zero, p, gamma)
+
+
+def gaussian_bumps3(grid: Grid3, seed: int, k_bumps: int = 4, sigma_cells: float = 3.0,
+                    amp: float = 1e-2, gamma=GAMMA, g=G_SIGNED) -> np.ndarray:
+    """The rest state with k seeded Gaussian bumps in density and velocity
+    (random direction in 3-D), pressure kept."""
+    rng = np.random.default_rng(seed)
+    cg = grid.column_grid()
+    rho0, p0 = rest_primitives(cg, gamma, g)
+    rho0 = np.repeat(rho0[:, None, :], grid.ny, axis=1)
+    p0 = np.repeat(p0[:, None, :], grid.ny, axis=1)
+    x = cg.x_centres()[None, None, :]
+    y = grid.y_centres()[None, :, None]
+    z = cg.z_centres()[:, None, None]
+    Lx, Ly = grid.nx * grid.dx, grid.ny * grid.dy
+    zlo, zhi = -grid.n1 * grid.dz1, (grid.nz - grid.n1) * grid.dz2
+    sig = sigma_cells * grid.dx
+    drho = np.zeros_like(rho0)
+    vel = [np.zeros_like(rho0) for _ in range(3)]
+    for _ in range(k_bumps):
+        c = (rng.uniform(-Lx / 2, Lx / 2), rng.uniform(-Ly / 2, Ly / 2), rng.uniform(zlo, zhi))
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        ddx = (x - c[0] + Lx / 2) % Lx - Lx / 2  # periodic distances
+        ddy = (y - c[1] + Ly / 2) % Ly - Ly / 2
+        env = np.exp(-(ddx ** 2 + ddy ** 2 + (z - c[2]) ** 2) / (2.0 * sig * sig))
+        drho += amp * env
+        for a in range(3):
+            vel[a] += amp * env * d[a]
+    return conserved3(rho0 * (1.0 + drho), vel[0], vel[1], vel[2], p0, gamma)
+
+
 def _modes(rng, xi, zeta, n_modes, amp):
     f = np.zeros((zeta.shape[0], xi.shape[1]))
     for _ in range(n_modes):
