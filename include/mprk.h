@@ -18,6 +18,13 @@
  * structure of arrays [4][nz][nx] of double, contiguous, nz = nz_S + nz_B +
  * nz_F, components (rho, rho*u, rho*w, rho*E), rows bottom to top.
  *
+ * Three dimensions (ny > 1 in the configuration; App. B in full): the same
+ * x-z rows with y added, periodic in x and y, FP64 only. Every state buffer
+ * is then [5][nz][ny][nx] of double with components (rho, rho*u, rho*v,
+ * rho*w, rho*E). Every single-instance call below takes that layout where
+ * the 2-D text says [4][nz][nx]. The batch, server and static entry points
+ * are 2-D only.
+ *
  * Conventions. Every call returns 0 (MPRK_OK) or a negative MPRK_E* code, and
  * on error mprk_last_error() returns a message for the calling thread.
  * Nothing runs on the CPU: without a usable CUDA device every compute call
@@ -87,13 +94,17 @@ typedef struct {
   double mu1;     /* nondimensional viscosity of fluid 1 (App. A)             */
   double mu2;     /* nondimensional viscosity of fluid 2                      */
   double G;       /* gravity magnitude: source (0, 0, -rho G, -rho w G)       */
+  int ny;         /* columns in y: 1 for the 2-D model; >= 4 for 3-D (App. B):
+                     y periodic, 5 components, FP64, MPRK_X_PERIODIC          */
+  double dy;      /* cell depth in y (3-D)                                    */
 } mprk_config;
 
 typedef struct mprk_instance mprk_instance;
 
 /* Fill cfg with the paper's constants (Sec. 5.2: gamma 1.4, Pr 0.72,
  * mu1 1/20000, mu2 1/5000, G 0.008140864714), dx = 10/nx, dz1 = dz2 = dx,
- * MPRK2, FP64, no-slip walls, dt = 0 (automatic, cfl 0.4), no monitoring. */
+ * MPRK2, FP64, no-slip walls, dt = 0 (automatic, cfl 0.4), no monitoring,
+ * 2-D (ny = 1, dy = dx). */
 int mprk_config_default(mprk_config* cfg, int nx, int nz_S, int nz_B, int nz_F, int m);
 
 /* Create an instance: allocate its device buffers (about 3 to 4 states of
@@ -147,7 +158,11 @@ int mprk_set_state(mprk_instance* inst, const double* q, int location);
  * the cell area over fluid 1, out[4..7] over fluid 2, out[8..10] Courant
  * numbers of S, B and F ((max(|u|,|w|)+a) dt_region / min(dx, dz)),
  * out[11] count of non-finite entries, out[12] minimum density, out[13]
- * minimum pressure, out[14] slow steps taken, out[15] dt. Synchronises. */
+ * minimum pressure, out[14] slow steps taken, out[15] dt. In 3-D: out[0..4]
+ * sums of rho, rho u, rho v, rho w, rho E times the cell volume over fluid 1,
+ * out[5..9] over fluid 2, out[10..12] the Courant numbers
+ * ((max(|u|,|v|,|w|)+a) dt_region / min(dx, dy, dz)), out[13] non-finite
+ * entries, out[14] minimum density, out[15] minimum pressure. Synchronises. */
 int mprk_diagnostics(mprk_instance* inst, double out[16]);
 
 /* Wait for the instance's queued work. */
@@ -158,7 +173,7 @@ int mprk_sync(mprk_instance* inst);
 int mprk_status(mprk_instance* inst);
 
 /* Read-only facts: dt, the number of cell right-hand-side evaluations per
- * slow step (nx (2 nz_S + 2 m (nz_B + nz_F)) for MPRK2, Sec. 4), device bytes
+ * slow step (nx ny (2 nz_S + 2 m (nz_B + nz_F)) for MPRK2, Sec. 4), device bytes
  * held, and the CUDA stream. Any out pointer may be NULL. */
 int mprk_info(const mprk_instance* inst, double* dt, long long* cell_stages_per_step,
               long long* device_bytes, void** cuda_stream);

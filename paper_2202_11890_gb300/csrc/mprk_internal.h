@@ -56,6 +56,10 @@ struct Geom {
   double G;
   double bu, bT;       // interface bulk coefficients (App. B)
   double cu1, cT1;     // dz1/(2 mu1), dz1/(2 kappa1): wall states from fluid 1
+  double cu2, cT2;     // dz2/(2 mu2), dz2/(2 kappa2): wall states from fluid 2
+  int ny;              // columns in y: 1 in 2-D
+  int nc;              // conserved components: 4 (2-D) or 5 (3-D)
+  double inv_dy;       // 3-D only
   double hF;           // dt / m
   double h2;           // dt / (2 m)
   double hdt;          // dt / 2
@@ -95,6 +99,7 @@ struct StageArgs {
   double* rhs_out;    // [4][nz][pitch] when rhs_only
   int rhs_hi;         // last row (exclusive) when rhs_only
   const double* rhs_in;  // full stage state when rhs_only
+  double* gy;         // 3-D: y-face fluxes [5][nz][ny][pitch] (face j+1/2 at j)
   int bulk;           // FP32-flux: interior tiles stage their float planes by
                       // tensor copies (set by launch_stage when maps exist)
   unsigned* status;   // status word for device-side errors, or null
@@ -139,6 +144,9 @@ cudaError_t make_stage_maps(const Geom& g, const Bufs& b, StageMaps* out);
 cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStream_t stream,
                          const StageMaps* maps = nullptr);
 cudaError_t launch_finalize(const Geom& g, const Bufs& b, int m_odd, cudaStream_t stream);
+// 3-D (g.ny > 1): the y-face launch and the stage launch of one stage; a.gy
+// must point at a state-sized buffer.
+cudaError_t launch_stage3(const StageArgs& a, cudaStream_t stream);
 // FP32-flux mode: per-row reference of q (row means, refd [4][nz] scratch)
 // and the float shadow dA = q - q_ref of qA.
 cudaError_t launch_reference(const Geom& g, const double* q, double* refd, float* rowc,

@@ -10,6 +10,7 @@
 
 #include "mprk_internal.h"
 #include "stage_tile.cuh"
+#include "stage_tile3d.cuh"
 #include "stage_tile_mixed.cuh"
 
 namespace mprk {
@@ -46,6 +47,31 @@ __global__ void __launch_bounds__(MIXED_THREADS, 3)
   }
 }
 
+// 3-D stage (App. B in full): the y faces of a plane pair, then the x and z
+// faces, the divergence and the combination of a plane; one CTA per TX x TZ
+// tile of an x-z plane, blockIdx = (tile column, tile row, plane).
+__global__ void __launch_bounds__(NTHREADS, 2) yface3_kernel(const StageArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  yface_tile(a, a.row0 + blockIdx.y * TZ, blockIdx.x * TX, blockIdx.z, *reinterpret_cast<YfaceSmem*>(smem_raw));
+}
+
+__global__ void __launch_bounds__(NTHREADS, 2) stage3_kernel(const StageArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  stage_tile3(a, a.row0 + blockIdx.y * TZ, blockIdx.x * TX, blockIdx.z, *reinterpret_cast<Tile3Smem*>(smem_raw));
+}
+
+cudaError_t launch_stage3(const StageArgs& a, cudaStream_t stream) {
+  const int hi = a.rhs_only ? a.rhs_hi : a.g.nz;
+  const int tz = (hi - a.row0 + TZ - 1) / TZ;
+  if (tz <= 0) return cudaSuccess;
+  const dim3 grid(a.tiles_x, tz, a.g.ny);
+  yface3_kernel<<<grid, NTHREADS, sizeof(YfaceSmem), stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  stage3_kernel<<<grid, NTHREADS, sizeof(Tile3Smem), stream>>>(a);
+  return cudaGetLastError();
+}
+
 size_t stage_smem_bytes(int precision) {
   return precision == 0 ? sizeof(TileSmem<double>) : sizeof(MixedTileSmem);
 }
@@ -54,6 +80,10 @@ cudaError_t prepare_kernels() {
   cudaError_t e = cudaFuncSetAttribute(stage_kernel<double, double>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(TileSmem<double>));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(yface3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(YfaceSmem));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(stage3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Tile3Smem));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(stage_kernel_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(MixedKernelSmem));
@@ -233,19 +263,24 @@ cudaError_t launch_shadow(const Geom& g, const double* q, const float* rowc, flo
 // shadow is also resynchronised to the new double state. One thread per
 // (component, row, column).
 // ---------------------------------------------------------------------------
+// An x-row r of a component is (k, j) with r = k ny + j (ny = 1 in 2-D);
+// the buffers' rows of the S and B bands are numbered the same way.
 __global__ void finalize_kernel(const Geom g, const Bufs b, int m_odd) {
   const bool mixed = b.dA != nullptr;
   const int rows = (m_odd || mixed) ? g.nz : g.n1_r;
-  const long long total = 4LL * rows * g.nx;
+  const long long xrows = (long long)rows * g.ny;
+  const long long total = (long long)g.nc * xrows * g.nx;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(e / ((long long)rows * g.nx));
-    const int rem = (int)(e - (long long)c * rows * g.nx);
-    const int k = rem / g.nx, i = rem - k * g.nx;
-    const size_t o = ((size_t)c * g.nz + k) * g.pitch + i;
+    const int c = (int)(e / (xrows * g.nx));
+    const long long rem = e - (long long)c * xrows * g.nx;
+    const int r = (int)(rem / g.nx), i = (int)(rem - (long long)r * g.nx);
+    const int k = r / g.ny;
+    const size_t o = ((size_t)c * g.nz * g.ny + r) * g.pitch + i;
     double v;
-    if (k < g.nS_r) v = b.accS[((size_t)c * g.nS_r + k) * g.pitch + i];
-    else if (k < g.n1_r) v = b.accB[((size_t)c * (g.n1_r - g.nS_r) + (k - g.nS_r)) * g.pitch + i];
+    if (k < g.nS_r) v = b.accS[((size_t)c * g.nS_r * g.ny + r) * g.pitch + i];
+    else if (k < g.n1_r)
+      v = b.accB[((size_t)c * (g.n1_r - g.nS_r) * g.ny + (r - (size_t)g.nS_r * g.ny)) * g.pitch + i];
     else v = m_odd ? b.qB[o] : b.qA[o];
     b.qA[o] = v;
     if (mixed) b.dA[o] = narrow(v - (double)b.rowc[4 * k + c]);
@@ -255,7 +290,7 @@ __global__ void finalize_kernel(const Geom g, const Bufs b, int m_odd) {
 cudaError_t launch_finalize(const Geom& g, const Bufs& b, int m_odd, cudaStream_t stream) {
   const int rows = (m_odd || b.dA != nullptr) ? g.nz : g.n1_r;
   if (rows == 0) return cudaSuccess;
-  const long long total = 4LL * rows * g.nx;
+  const long long total = (long long)g.nc * rows * g.ny * g.nx;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   finalize_kernel<<<blocks, 256, 0, stream>>>(g, b, m_odd);
@@ -295,127 +330,163 @@ cudaError_t launch_convert_check(const double* in, int n, float* nar, float* nar
 constexpr int DIAG_THREADS = 256;
 
 int diag_blocks(const Geom& g) {
-  long long cells = (long long)g.nz * g.nx;
+  long long cells = (long long)g.nz * g.ny * g.nx;
   long long b = (cells + DIAG_THREADS * 8 - 1) / (DIAG_THREADS * 8);
   if (b < 1) b = 1;
   if (b > 1024) b = 1024;
   return (int)b;
 }
 
-__device__ __forceinline__ void combine16(double* d, const double* s) {
+// Monitoring slots for NC components: sums over fluid 1 [0, NC), fluid 2
+// [NC, 2NC), the maximal wave speed of the S, B, F bands [2NC, 2NC+3), the
+// non-finite count 2NC+3, the minimum density 2NC+4 and pressure 2NC+5
+// (NC = 4: the 2-D layout; NC = 5: the 3-D one).
+template <int NC>
+__device__ __forceinline__ void combine_diag(double* d, const double* s) {
 #pragma unroll
-  for (int j = 0; j < 8; j++) d[j] += s[j];
+  for (int j = 0; j < 2 * NC; j++) d[j] += s[j];
 #pragma unroll
-  for (int j = 8; j < 11; j++) d[j] = fmax(d[j], s[j]);
-  d[11] += s[11];
-  d[12] = fmin(d[12], s[12]);
-  d[13] = fmin(d[13], s[13]);
+  for (int j = 2 * NC; j < 2 * NC + 3; j++) d[j] = fmax(d[j], s[j]);
+  d[2 * NC + 3] += s[2 * NC + 3];
+  d[2 * NC + 4] = fmin(d[2 * NC + 4], s[2 * NC + 4]);
+  d[2 * NC + 5] = fmin(d[2 * NC + 5], s[2 * NC + 5]);
 }
 
+template <int NC>
 __global__ void diag_partial_kernel(const Geom g, const double* __restrict__ q, double* partials) {
-  double acc[16];
+  constexpr int NS = 2 * NC + 6;
+  double acc[NS];
 #pragma unroll
-  for (int j = 0; j < 16; j++) acc[j] = 0.0;
-  acc[12] = INFINITY;
-  acc[13] = INFINITY;
-  const long long cells = (long long)g.nz * g.nx;
-  const size_t plane = (size_t)g.nz * g.pitch;
+  for (int j = 0; j < NS; j++) acc[j] = 0.0;
+  acc[2 * NC + 4] = INFINITY;
+  acc[2 * NC + 5] = INFINITY;
+  const long long xrows = (long long)g.nz * g.ny;
+  const long long cells = xrows * g.nx;
+  const size_t plane = (size_t)xrows * g.pitch;
   for (long long e = blockIdx.x * (long long)DIAG_THREADS + threadIdx.x; e < cells;
        e += (long long)gridDim.x * DIAG_THREADS) {
-    const int k = (int)(e / g.nx), i = (int)(e - (long long)k * g.nx);
-    const size_t o = (size_t)k * g.pitch + i;
-    const double r = q[o], mu = q[plane + o], mw = q[2 * plane + o], E = q[3 * plane + o];
-    const int f = k < g.n1 ? 0 : 4;
-    acc[f + 0] += r;
-    acc[f + 1] += mu;
-    acc[f + 2] += mw;
-    acc[f + 3] += E;
-    const double bad = (double)(!isfinite(r)) + (double)(!isfinite(mu)) + (double)(!isfinite(mw)) +
-                       (double)(!isfinite(E));
-    acc[11] += bad;
-    const double u = mu / r, w = mw / r;
-    const double p = g.gm1 * (E - 0.5 * (mu * u + mw * w));
-    const double c = sqrt(g.gamma * p / r);
-    const double ws = fmax(fabs(u), fabs(w)) + c;
-    const int band = (k < g.nS_g) ? 8 : (k < g.n1 ? 9 : 10);  // S, B, F bands of the grid
+    const int r = (int)(e / g.nx), i = (int)(e - (long long)r * g.nx);
+    const int k = r / g.ny;
+    const size_t o = (size_t)r * g.pitch + i;
+    double v[NC];
+#pragma unroll
+    for (int c = 0; c < NC; c++) v[c] = q[c * plane + o];
+    const int f = k < g.n1 ? 0 : NC;
+    double bad = 0.0;
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      acc[f + c] += v[c];
+      bad += (double)(!isfinite(v[c]));
+    }
+    acc[2 * NC + 3] += bad;
+    const double rho = v[0], E = v[NC - 1];
+    double ke = 0.0, umax = 0.0;
+#pragma unroll
+    for (int c = 1; c < NC - 1; c++) {
+      const double u = v[c] / rho;
+      ke += v[c] * u;
+      umax = fmax(umax, fabs(u));
+    }
+    const double p = g.gm1 * (E - 0.5 * ke);
+    const double ws = umax + sqrt(g.gamma * p / rho);
+    const int band = 2 * NC + ((k < g.nS_g) ? 0 : (k < g.n1 ? 1 : 2));  // S, B, F bands of the grid
     if (ws == ws) acc[band] = fmax(acc[band], ws);
-    acc[12] = fmin(acc[12], r);
-    acc[13] = fmin(acc[13], p);
+    acc[2 * NC + 4] = fmin(acc[2 * NC + 4], rho);
+    acc[2 * NC + 5] = fmin(acc[2 * NC + 5], p);
   }
   // warp tree (fixed order)
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    double o[16];
+    double o[NS];
 #pragma unroll
-    for (int j = 0; j < 16; j++) o[j] = __shfl_down_sync(0xffffffffu, acc[j], off);
-    combine16(acc, o);
+    for (int j = 0; j < NS; j++) o[j] = __shfl_down_sync(0xffffffffu, acc[j], off);
+    combine_diag<NC>(acc, o);
   }
-  __shared__ double warp_part[DIAG_THREADS / 32][16];
+  __shared__ double warp_part[DIAG_THREADS / 32][NS];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
 #pragma unroll
-    for (int j = 0; j < 16; j++) warp_part[wid][j] = acc[j];
+    for (int j = 0; j < NS; j++) warp_part[wid][j] = acc[j];
   }
   __syncthreads();
-  if (threadIdx.x < 16) {
+  if (threadIdx.x < NS) {
     const int j = threadIdx.x;
     double v = warp_part[0][j];
     for (int w = 1; w < DIAG_THREADS / 32; w++) {
       const double s = warp_part[w][j];
-      if (j < 8 || j == 11) v += s;
-      else if (j < 11) v = fmax(v, s);
+      if (j < 2 * NC || j == 2 * NC + 3) v += s;
+      else if (j < 2 * NC + 3) v = fmax(v, s);
       else v = fmin(v, s);
     }
     partials[(size_t)blockIdx.x * 16 + j] = v;
   }
 }
 
+// Final combination and scaling. 2-D: out = the 14 slots scaled to sums
+// times the cell area and Courant numbers, then out[14] = 0 (steps, filled
+// by the host) and out[15] = dt. 3-D: the 16 slots, sums times the cell
+// volume.
+template <int NC>
 __global__ void diag_final_kernel(const Geom g, const double* partials, int nblocks, double* out,
                                   unsigned* status, double cfl_limit) {
-  __shared__ double res[16];
+  constexpr int NS = 2 * NC + 6;
+  __shared__ double res[NS];
   const int j = threadIdx.x;
-  if (j < 16) {
+  if (j < NS) {
     double v = partials[j];
     for (int b = 1; b < nblocks; b++) {
       const double s = partials[(size_t)b * 16 + j];
-      if (j < 8 || j == 11) v += s;
-      else if (j < 11) v = fmax(v, s);
-      else if (j < 14) v = fmin(v, s);
+      if (j < 2 * NC || j == 2 * NC + 3) v += s;
+      else if (j < 2 * NC + 3) v = fmax(v, s);
+      else v = fmin(v, s);
     }
     res[j] = v;
   }
   __syncthreads();
   if (j == 0) {
-    const double a1 = 1.0 / (g.inv_dx * g.inv_dz1), a2 = 1.0 / (g.inv_dx * g.inv_dz2);
-    double o[16];
-    for (int c = 0; c < 4; c++) {
-      o[c] = res[c] * a1;
-      o[4 + c] = res[4 + c] * a2;
-    }
     const double dx = 1.0 / g.inv_dx, dz1 = 1.0 / g.inv_dz1, dz2 = 1.0 / g.inv_dz2;
+    const double dy = NC == 5 ? 1.0 / g.inv_dy : 1.0;
+    const double a1 = dx * dy * dz1, a2 = dx * dy * dz2;
+    const double h = NC == 5 ? fmin(dx, dy) : dx;
+    double o[16];
+    for (int c = 0; c < NC; c++) {
+      o[c] = res[c] * a1;
+      o[NC + c] = res[NC + c] * a2;
+    }
     const double dtS = (g.n1_r > 0) ? g.dt : g.dt / g.m;
-    o[8] = dtS * res[8] / fmin(dx, dz1);
-    o[9] = dtS * res[9] / fmin(dx, dz1);
-    o[10] = (g.dt / g.m) * res[10] / fmin(dx, dz2);
-    o[11] = res[11];
-    o[12] = res[12];
-    o[13] = res[13];
-    o[14] = 0.0;  // slow steps taken: filled in by the host
-    o[15] = g.dt;
+    o[2 * NC] = dtS * res[2 * NC] / fmin(h, dz1);
+    o[2 * NC + 1] = dtS * res[2 * NC + 1] / fmin(h, dz1);
+    o[2 * NC + 2] = (g.dt / g.m) * res[2 * NC + 2] / fmin(h, dz2);
+    o[2 * NC + 3] = res[2 * NC + 3];
+    o[2 * NC + 4] = res[2 * NC + 4];
+    o[2 * NC + 5] = res[2 * NC + 5];
+    if (NC == 4) {
+      o[14] = 0.0;  // slow steps taken: filled in by the host
+      o[15] = g.dt;
+    }
     for (int c = 0; c < 16; c++) out[c] = o[c];
     unsigned st = 0;
-    if (o[11] > 0.0 || !(o[12] > 0.0) || !(o[13] > 0.0)) st |= ST_NONFINITE;
-    if (cfl_limit > 0.0 && (o[8] > cfl_limit || o[9] > cfl_limit || o[10] > cfl_limit)) st |= ST_CFL;
+    if (o[2 * NC + 3] > 0.0 || !(o[2 * NC + 4] > 0.0) || !(o[2 * NC + 5] > 0.0)) st |= ST_NONFINITE;
+    if (cfl_limit > 0.0 &&
+        (o[2 * NC] > cfl_limit || o[2 * NC + 1] > cfl_limit || o[2 * NC + 2] > cfl_limit))
+      st |= ST_CFL;
     if (st) atomicOr(status, st);
   }
 }
 
 cudaError_t launch_diag(const Geom& g, const double* q, double* partials, int nblocks, double* out,
                         unsigned* status, double cfl_limit, cudaStream_t stream) {
-  diag_partial_kernel<<<nblocks, DIAG_THREADS, 0, stream>>>(g, q, partials);
+  if (g.nc == 5) {
+    diag_partial_kernel<5><<<nblocks, DIAG_THREADS, 0, stream>>>(g, q, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diag_final_kernel<5><<<1, 32, 0, stream>>>(g, partials, nblocks, out, status, cfl_limit);
+    return cudaGetLastError();
+  }
+  diag_partial_kernel<4><<<nblocks, DIAG_THREADS, 0, stream>>>(g, q, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  diag_final_kernel<<<1, 32, 0, stream>>>(g, partials, nblocks, out, status, cfl_limit);
+  diag_final_kernel<4><<<1, 32, 0, stream>>>(g, partials, nblocks, out, status, cfl_limit);
   return cudaGetLastError();
 }
 

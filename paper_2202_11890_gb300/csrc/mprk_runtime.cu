@@ -78,6 +78,7 @@ struct mprk_instance {
   long long bytes;
   bool stream_ordered;  // buffers from cudaMallocAsync on `stream` (server instances)
   StageMaps maps;       // FP32-flux mode: tensor maps of the float planes
+  double* gy;           // 3-D: y-face fluxes of the current stage
 };
 
 namespace {
@@ -109,7 +110,14 @@ int mprk::validate_config(const mprk_config* c) {
   if (!(c->gamma > 1.0) || !(c->Pr > 0.0)) return fail(MPRK_EINVAL, "need gamma > 1 and Pr > 0");
   if (!(c->mu1 > 0.0) || !(c->mu2 > 0.0)) return fail(MPRK_EINVAL, "viscosities must be positive");
   if (!(c->G >= 0.0)) return fail(MPRK_EINVAL, "G must be >= 0");
-  long long cells = (long long)c->nx * (c->nz_S + c->nz_B + c->nz_F);
+  if (c->ny < 1) return fail(MPRK_EINVAL, "ny = %d: need ny >= 1", c->ny);
+  if (c->ny > 1) {
+    if (c->ny < 4) return fail(MPRK_EINVAL, "ny = %d: a 3-D grid needs at least 4 columns in y", c->ny);
+    if (c->precision != MPRK_FP64) return fail(MPRK_EINVAL, "the 3-D model runs in FP64 only");
+    if (c->x_walls != MPRK_X_PERIODIC) return fail(MPRK_EINVAL, "the 3-D model is periodic in x and y");
+    if (!(c->dy > 0)) return fail(MPRK_EINVAL, "dy must be positive");
+  }
+  long long cells = (long long)c->nx * c->ny * (c->nz_S + c->nz_B + c->nz_F);
   if (cells > (1LL << 31)) return fail(MPRK_EINVAL, "grid too large");
   return MPRK_OK;
 }
@@ -124,7 +132,8 @@ void free_instance(mprk_instance* I) {
   if (I->exec) cudaGraphExecDestroy(I->exec);
   if (I->exec_diag) cudaGraphExecDestroy(I->exec_diag);
   void* bufs[] = {I->b.qA,     I->b.qB,     I->b.Ra,     I->b.accB, I->b.accS, I->partials, I->diag_dev,
-                  I->status_dev, I->rhs_in, I->rhs_out, I->b.dA,   I->b.dB,   I->b.rowc,   I->refd};
+                  I->status_dev, I->rhs_in, I->rhs_out, I->b.dA,   I->b.dB,   I->b.rowc,   I->refd,
+                  I->gy};
   for (void* p : bufs) {
     if (!p) continue;
     // stream-ordered buffers go back to the pool after the stream's queued work
@@ -141,7 +150,12 @@ int enqueue_step(mprk_instance* I, cudaStream_t s) {
   for (int st = 0; st < 2 * g.m; st++) {
     StageArgs a = stage_args(g, I->b, st);
     a.status = I->status_dev;
-    CU(launch_stage(a, I->precision, stage_tiles(a), s, &I->maps));
+    if (g.ny > 1) {
+      a.gy = I->gy;
+      CU(launch_stage3(a, s));
+    } else {
+      CU(launch_stage(a, I->precision, stage_tiles(a), s, &I->maps));
+    }
   }
   CU(launch_finalize(g, I->b, g.m & 1, s));
   return MPRK_OK;
@@ -172,7 +186,7 @@ int copy_state_in(mprk_instance* I, const double* q, int loc) {
   const Geom& g = I->g;
   cudaMemcpyKind kind = loc == MPRK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CU(cudaMemcpy2DAsync(I->b.qA, (size_t)g.pitch * 8, q, (size_t)g.nx * 8, (size_t)g.nx * 8,
-                       (size_t)4 * g.nz, kind, I->stream));
+                       (size_t)g.nc * g.nz * g.ny, kind, I->stream));
   if (I->b.dA && I->b.rowc) CU(launch_shadow(g, I->b.qA, I->b.rowc, I->b.dA, I->stream));
   return MPRK_OK;
 }
@@ -183,7 +197,7 @@ int run_diag(mprk_instance* I, double out[16]) {
                  I->stream));
   CU(cudaMemcpyAsync(out, I->diag_dev, 16 * sizeof(double), cudaMemcpyDeviceToHost, I->stream));
   CU(cudaStreamSynchronize(I->stream));
-  out[14] = (double)I->steps_done;
+  if (I->g.nc == 4) out[14] = (double)I->steps_done;
   return MPRK_OK;
 }
 
@@ -246,6 +260,11 @@ void mprk::geom_from_config(const mprk_config& c, int pitch, Geom* gp) {
   g.bT = 2.0 * g.kap1 * g.kap2 / (c.dz2 * g.kap1 + c.dz1 * g.kap2);
   g.cu1 = c.dz1 / (2.0 * c.mu1);
   g.cT1 = c.dz1 / (2.0 * g.kap1);
+  g.cu2 = c.dz2 / (2.0 * c.mu2);
+  g.cT2 = c.dz2 / (2.0 * g.kap2);
+  g.ny = c.ny > 1 ? c.ny : 1;
+  g.nc = c.ny > 1 ? 5 : 4;
+  g.inv_dy = c.ny > 1 ? 1.0 / c.dy : 0.0;
   g.hF = c.dt / c.m;
   g.h2 = c.dt / (2.0 * c.m);
   g.hdt = 0.5 * c.dt;
@@ -270,11 +289,14 @@ long long mprk::instance_bytes(const mprk_config& c) {
   auto r16 = [](long long b) { return b == 0 ? 16LL : b; };
   const long long pitch = (c.nx + 31) / 32 * 32;
   const long long nz = (long long)c.nz_S + c.nz_B + c.nz_F;
-  const long long plane = nz * pitch;
+  const long long ny = c.ny > 1 ? c.ny : 1, nc = c.ny > 1 ? 5 : 4;
+  const long long plane = nz * ny * pitch;
   const bool mprk2 = c.scheme == MPRK_SCHEME_MPRK2;
   const long long nB = mprk2 ? c.nz_B : 0, nS = mprk2 ? c.nz_S : 0;
   const long long rsz = c.precision == MPRK_FP64 ? 8 : 4;
-  long long b = 2 * 4 * plane * 8 + 4 * plane * rsz + r16(4 * nB * pitch * 8) + r16(4 * nS * pitch * 8);
+  long long b = 2 * nc * plane * 8 + nc * plane * rsz + r16(nc * nB * ny * pitch * 8) +
+                r16(nc * nS * ny * pitch * 8);
+  if (ny > 1) b += nc * plane * 8;  // y-face fluxes
   b += 1024 * 16 * 8 + 16 * 8 + 16;  // monitoring partials (upper bound), results, status
   if (c.precision != MPRK_FP64) b += 2 * 4 * plane * 4 + NROWC * nz * 4 + 4 * nz * 8;
   return b;
@@ -305,6 +327,8 @@ int mprk_config_default(mprk_config* cfg, int nx, int nz_S, int nz_B, int nz_F, 
   cfg->mu1 = 1.0 / 20000.0;
   cfg->mu2 = 1.0 / 5000.0;
   cfg->G = 0.008140864714;
+  cfg->ny = 1;
+  cfg->dy = cfg->dx;
   return MPRK_OK;
 }
 
@@ -356,13 +380,15 @@ int mprk::create_instance(const mprk_config* cfg, const double* q0, int q0_locat
     I->bytes += (long long)bytes;
     return MPRK_OK;
   };
-  const size_t plane = (size_t)g.nz * g.pitch;
+  const size_t plane = (size_t)g.nz * g.ny * g.pitch;  // elements of one component
+  const size_t nc = g.nc;
   const size_t rsz = I->precision == MPRK_FP64 ? sizeof(double) : sizeof(float);
   I->diag_nblocks = diag_blocks(g);
-  if ((rc = alloc((void**)&I->b.qA, 4 * plane * 8)) || (rc = alloc((void**)&I->b.qB, 4 * plane * 8)) ||
-      (rc = alloc(&I->b.Ra, 4 * plane * rsz)) ||
-      (rc = alloc((void**)&I->b.accB, 4 * (size_t)(g.n1_r - g.nS_r) * g.pitch * 8)) ||
-      (rc = alloc((void**)&I->b.accS, 4 * (size_t)g.nS_r * g.pitch * 8)) ||
+  if ((rc = alloc((void**)&I->b.qA, nc * plane * 8)) || (rc = alloc((void**)&I->b.qB, nc * plane * 8)) ||
+      (rc = alloc(&I->b.Ra, nc * plane * rsz)) ||
+      (rc = alloc((void**)&I->b.accB, nc * (size_t)(g.n1_r - g.nS_r) * g.ny * g.pitch * 8)) ||
+      (rc = alloc((void**)&I->b.accS, nc * (size_t)g.nS_r * g.ny * g.pitch * 8)) ||
+      (g.ny > 1 && (rc = alloc((void**)&I->gy, nc * plane * 8))) ||
       (rc = alloc((void**)&I->partials, (size_t)I->diag_nblocks * 16 * 8)) ||
       (rc = alloc((void**)&I->diag_dev, 16 * 8)) || (rc = alloc((void**)&I->status_dev, 16))) {
     free_instance(I);
@@ -379,9 +405,9 @@ int mprk::create_instance(const mprk_config* cfg, const double* q0, int q0_locat
     free_instance(I);
     return code;
   };
-  if (cudaMemsetAsync(I->b.qA, 0, 4 * plane * 8, I->stream) != cudaSuccess ||
-      cudaMemsetAsync(I->b.qB, 0, 4 * plane * 8, I->stream) != cudaSuccess ||
-      cudaMemsetAsync(I->b.Ra, 0, 4 * plane * rsz, I->stream) != cudaSuccess ||
+  if (cudaMemsetAsync(I->b.qA, 0, nc * plane * 8, I->stream) != cudaSuccess ||
+      cudaMemsetAsync(I->b.qB, 0, nc * plane * 8, I->stream) != cudaSuccess ||
+      cudaMemsetAsync(I->b.Ra, 0, nc * plane * rsz, I->stream) != cudaSuccess ||
       cudaMemsetAsync(I->status_dev, 0, 16, I->stream) != cudaSuccess)
     return fin(fail(MPRK_ECUDA, "memset failed"));
   if (I->b.dA &&
@@ -401,9 +427,10 @@ int mprk::create_instance(const mprk_config* cfg, const double* q0, int q0_locat
   double d[16];
   I->g.dt = 1.0;  // placeholder for the Courant numbers of the check
   if ((rc = run_diag(I, d))) return fin(rc);
-  if (d[11] > 0.0 || !(d[12] > 0.0) || !(d[13] > 0.0))
-    return fin(fail(MPRK_ENONFINITE, "q0 has %g non-finite entries, min rho %g, min p %g", d[11],
-                    d[12], d[13]));
+  const int o = 2 * g.nc;  // first Courant slot (8 in 2-D, 10 in 3-D)
+  if (d[o + 3] > 0.0 || !(d[o + 4] > 0.0) || !(d[o + 5] > 0.0))
+    return fin(fail(MPRK_ENONFINITE, "q0 has %g non-finite entries, min rho %g, min p %g", d[o + 3],
+                    d[o + 4], d[o + 5]));
   if (cudaMemsetAsync(I->status_dev, 0, 16, I->stream) != cudaSuccess)
     return fin(fail(MPRK_ECUDA, "memset failed"));
   double dt = cfg->dt;
@@ -411,11 +438,12 @@ int mprk::create_instance(const mprk_config* cfg, const double* q0, int q0_locat
     // wave speeds: d[8..10] hold max(|u|,|w|)+a per band times dt/min(dx,dz)
     // with dt = 1 (S, B at dt, F at dt/m)
     const double sr = cfg->scheme == MPRK_SCHEME_MPRK2 ? 1.0 : (double)cfg->m;
-    const double c1 = fmax(d[8], d[9]) * sr * fmin(cfg->dx, cfg->dz1);
-    const double c2 = d[10] * cfg->m * fmin(cfg->dx, cfg->dz2);
+    const double h = g.ny > 1 ? fmin(cfg->dx, cfg->dy) : cfg->dx;
+    const double c1 = fmax(d[o], d[o + 1]) * sr * fmin(h, cfg->dz1);
+    const double c2 = d[o + 2] * cfg->m * fmin(h, cfg->dz2);
     const double cfl = I->cfg.cfl;
-    const double d1 = cfl * fmin(cfg->dx, cfg->dz1) / c1;
-    const double d2 = cfg->m * cfl * fmin(cfg->dx, cfg->dz2) / c2;
+    const double d1 = cfl * fmin(h, cfg->dz1) / c1;
+    const double d2 = cfg->m * cfl * fmin(h, cfg->dz2) / c2;
     dt = cfg->scheme == MPRK_SCHEME_MPRK2 ? fmin(d1, d2) : cfg->m * fmin(d1, d2 / cfg->m);
   }
   I->cfg.dt = dt;
@@ -462,7 +490,7 @@ int mprk_get_state(mprk_instance* I, double* q_out, int location) {
   const Geom& g = I->g;
   cudaMemcpyKind kind = location == MPRK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   CU(cudaMemcpy2DAsync(q_out, (size_t)g.nx * 8, I->b.qA, (size_t)g.pitch * 8, (size_t)g.nx * 8,
-                       (size_t)4 * g.nz, kind, I->stream));
+                       (size_t)g.nc * g.nz * g.ny, kind, I->stream));
   CU(cudaStreamSynchronize(I->stream));
   return MPRK_OK;
 }
@@ -505,9 +533,9 @@ int mprk_info(const mprk_instance* I, double* dt, long long* cell_stages, long l
   if (dt) *dt = I->g.dt;
   if (cell_stages) {
     const long long nz = c.nz_S + c.nz_B + c.nz_F;
-    *cell_stages = c.scheme == MPRK_SCHEME_MPRK2
-                       ? (long long)c.nx * (2LL * c.nz_S + 2LL * c.m * (c.nz_B + c.nz_F))
-                       : (long long)c.nx * 2LL * c.m * nz;
+    const long long cols = (long long)c.nx * (c.ny > 1 ? c.ny : 1);
+    *cell_stages = c.scheme == MPRK_SCHEME_MPRK2 ? cols * (2LL * c.nz_S + 2LL * c.m * (c.nz_B + c.nz_F))
+                                                 : cols * 2LL * c.m * nz;
   }
   if (bytes) *bytes = I->bytes;
   if (stream) *stream = (void*)I->stream;
@@ -518,14 +546,15 @@ int mprk_rhs(mprk_instance* I, const double* W_dev, double* R_dev, int k_lo, int
   if (!I || !W_dev || !R_dev) return fail(MPRK_EINVAL, "NULL argument");
   const Geom& g = I->g;
   if (k_lo < 0 || k_hi > g.nz || k_lo >= k_hi) return fail(MPRK_EINVAL, "bad row range");
-  const size_t plane = (size_t)g.nz * g.pitch;
+  const size_t plane = (size_t)g.nz * g.ny * g.pitch;
+  const size_t nc = g.nc;
   if (!I->rhs_in) {
-    CU(cudaMalloc((void**)&I->rhs_in, 4 * plane * 8));
-    CU(cudaMalloc((void**)&I->rhs_out, 4 * plane * 8));
-    CU(cudaMemsetAsync(I->rhs_in, 0, 4 * plane * 8, I->stream));
+    CU(cudaMalloc((void**)&I->rhs_in, nc * plane * 8));
+    CU(cudaMalloc((void**)&I->rhs_out, nc * plane * 8));
+    CU(cudaMemsetAsync(I->rhs_in, 0, nc * plane * 8, I->stream));
   }
   CU(cudaMemcpy2DAsync(I->rhs_in, (size_t)g.pitch * 8, W_dev, (size_t)g.nx * 8, (size_t)g.nx * 8,
-                       (size_t)4 * g.nz, cudaMemcpyDeviceToDevice, I->stream));
+                       nc * g.nz * g.ny, cudaMemcpyDeviceToDevice, I->stream));
   StageArgs a = stage_args(g, I->b, 0);
   a.row0 = k_lo;
   a.rhs_only = 1;
@@ -533,12 +562,16 @@ int mprk_rhs(mprk_instance* I, const double* W_dev, double* R_dev, int k_lo, int
   a.rhs_hi = k_hi;
   a.rhs_in = I->rhs_in;
   a.status = I->status_dev;
-  CU(launch_stage(a, I->precision, stage_tiles(a), I->stream));
-  for (int c = 0; c < 4; c++) {
-    CU(cudaMemcpy2DAsync(R_dev + ((size_t)c * g.nz + k_lo) * g.nx, (size_t)g.nx * 8,
-                         I->rhs_out + (size_t)c * plane + (size_t)k_lo * g.pitch,
-                         (size_t)g.pitch * 8, (size_t)g.nx * 8, (size_t)(k_hi - k_lo),
-                         cudaMemcpyDeviceToDevice, I->stream));
+  if (g.ny > 1) {
+    a.gy = I->gy;
+    CU(launch_stage3(a, I->stream));
+  } else {
+    CU(launch_stage(a, I->precision, stage_tiles(a), I->stream));
+  }
+  for (size_t c = 0; c < nc; c++) {
+    CU(cudaMemcpy2DAsync(R_dev + ((size_t)c * g.nz + k_lo) * g.ny * g.nx, (size_t)g.nx * 8,
+                         I->rhs_out + c * plane + (size_t)k_lo * g.ny * g.pitch, (size_t)g.pitch * 8,
+                         (size_t)g.nx * 8, (size_t)(k_hi - k_lo) * g.ny, cudaMemcpyDeviceToDevice, I->stream));
   }
   return MPRK_OK;
 }
@@ -554,10 +587,12 @@ int mprk_profile_step(mprk_instance* I, double* launch_ms, long long* launch_cel
   for (int st = 0; st < 2 * g.m && rc == MPRK_OK; st++) {
     StageArgs a = stage_args(g, I->b, st);
     a.status = I->status_dev;
-    cudaError_t e = launch_stage(a, I->precision, stage_tiles(a), I->stream, &I->maps);
+    a.gy = I->gy;
+    cudaError_t e = g.ny > 1 ? launch_stage3(a, I->stream)
+                             : launch_stage(a, I->precision, stage_tiles(a), I->stream, &I->maps);
     if (e != cudaSuccess) rc = fail(MPRK_ECUDA, "stage launch: %s", cudaGetErrorString(e));
     cudaEventRecord(ev[st + 1], I->stream);
-    if (st < cap && launch_cells) launch_cells[st] = (long long)(g.nz - a.row0) * g.nx;
+    if (st < cap && launch_cells) launch_cells[st] = (long long)(g.nz - a.row0) * g.ny * g.nx;
   }
   if (rc == MPRK_OK) {
     cudaError_t e = launch_finalize(g, I->b, g.m & 1, I->stream);

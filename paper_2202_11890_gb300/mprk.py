@@ -51,7 +51,7 @@ class mprk_config(C.Structure):
         ("diag_every", C.c_int), ("x_walls", C.c_int),
         ("dt", C.c_double), ("cfl", C.c_double), ("dx", C.c_double), ("dz1", C.c_double),
         ("dz2", C.c_double), ("gamma", C.c_double), ("Pr", C.c_double), ("mu1", C.c_double),
-        ("mu2", C.c_double), ("G", C.c_double),
+        ("mu2", C.c_double), ("G", C.c_double), ("ny", C.c_int), ("dy", C.c_double),
     ]
 
     @property
@@ -60,6 +60,8 @@ class mprk_config(C.Structure):
 
     @property
     def shape(self):
+        if self.ny > 1:
+            return (5, self.nz, self.ny, self.nx)
         return (4, self.nz, self.nx)
 
 
