@@ -491,6 +491,120 @@ def run_speedup(args):
 
 SEED_SPEEDUP = W.SEED0 + 9
 
+# Algorithmic floating-point operations per cell-stage of the 3-D stage
+# (yface3 + stage3), counted from their formulas like the 2-D figure:
+# 176 per face (Lax–Friedrichs flux of five components 110, viscous flux
+# with the full stress tensor 41, reconstruction 20, F* assembly 5) times
+# 3.16 faces per cell (x 33/32, z 9/8, y 1), plus ring primitives of both
+# kernels and the y derivatives 91, slopes and tangential derivatives 70,
+# divergence and source 32, stage combination 10.
+FLOPS_PER_CELL_STAGE_3D = 759.0
+
+
+def algorithmic_bytes3(g, m: int) -> tuple[int, int]:
+    """HBM bytes one 3-D slow step must move, like algorithmic_bytes with
+    five doubles per state (40 B), plus the y-face buffer written once and
+    read once per cell-stage (80 B)."""
+    cols = g.nx * g.ny
+    s = 40
+    tot = 0
+    for st in range(2 * m):
+        odd = st % 2 == 1
+        B = s + s + (s if st == 0 else 2 * s)
+        S = (s + s) if st == 0 else ((s + s + s) if st == 1 else 0)
+        F = (s + s + s) if odd else (s + s)
+        rows = g.nS * (1 if st < 2 else 0) + g.nB + g.nF
+        tot += cols * (g.nS * S + g.nB * B + g.nF * F) + cols * rows * 80
+    fin = cols * (g.nS + g.nB) * 80 + (cols * g.nF * 80 if m % 2 else 0)
+    return tot, fin
+
+
+def run_cube(args):
+    """The 3-D model on one GPU: `cube_512` (512 x 64 x 200 cells, m = 4,
+    FP64). Reports the FP64-ALU roofline of the stage launches, e2e through
+    the C ABI with host buffers, and the 3-D oracle on a strip of columns."""
+    import torch
+    from paper_2202_11890_gb300 import build as B
+    from paper_2202_11890_gb300 import mprk as M
+    from paper_2202_11890_gb300 import timing as T
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    wl = W.cube_512()
+    g = wl.grid
+    q0 = wl.initial_state()
+    cfg = M.mprk_config_default(g.nx, g.nS, g.nB, g.nF, wl.m, dx=g.dx, dz1=g.dz1, dz2=g.dz2)
+    cfg.ny, cfg.dy = g.ny, g.dy
+    steps = args.steps if args.steps != 200 else wl.steps
+    with M.Instance(cfg, q0) as inst:
+        info = inst.info()
+        cs = info["cell_stages_per_step"]
+        inst.step(args.warmup)
+        inst.sync()
+        sampler = ClockSampler(torch.cuda.current_device())
+        torch.cuda.synchronize()
+        with sampler:
+            t_ms = T.time_steps(inst.h, info["stream"], steps)
+        torch.cuda.synchronize()
+        stage_ms, stage_cells = T.stage_kernel_times(inst.h, info["stream"], reps=3)
+        pin_in = torch.from_numpy(q0).pin_memory()
+        pin_out = torch.empty_like(pin_in).pin_memory()
+        e2e_steps = 3
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            M.mprk_set_state(inst.h, pin_in)
+            M.mprk_step(inst.h, 1)
+            M.mprk_get_state(inst.h, pin_out)
+        e2e_s = time.perf_counter() - t0
+    value = cs * steps / (t_ms * 1e-3)
+    ach = stage_cells * FLOPS_PER_CELL_STAGE_3D / (stage_ms * 1e-3) / 1e9
+    stage_bytes, fin_bytes = algorithmic_bytes3(g, wl.m)
+    peaks, src = measured_peaks()
+    out = {"metric": METRIC, "value": value, "unit": "cell-stages/s", "n_gpus": ws, "steps": steps,
+           "warmup": args.warmup, "ms_per_step": t_ms / steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl.name, "nx": g.nx, "ny": g.ny, "rows_S_B_F": [g.nS, g.nB, g.nF], "m": wl.m,
+                      "cell_stages_per_step": cs, "parallelism": f"replicas x{ws}",
+                      "l2": "working set > L2 (a state is 262 MB); no flush"},
+           "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                        "frac": ach / FP64_PEAK_GFLOPS, "traffic": None,
+                        "peak_source": "FP64 unit count x max clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                        "hbm_achieved_gbs": stage_bytes / (stage_ms * 1e-3) / 1e9,
+                        "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": src},
+           "kernel": {"name": "yface3_kernel + stage3_kernel", "ms_per_step": stage_ms,
+                      "cell_stages_per_step": stage_cells, "launches_per_step": 4 * wl.m,
+                      "algorithmic_bytes_per_step": stage_bytes, "completion_bytes_per_step": fin_bytes},
+           "e2e": {"value": cs * e2e_steps / e2e_s, "unit": "cell-stages/s", "h2d_bytes_per_step": q0.nbytes,
+                   "d2h_bytes_per_step": q0.nbytes, "steps": e2e_steps},
+           "gpu_launches": (4 * wl.m + 1) * steps, "clocks": sampler.summary()}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline3(wl)
+    print(json.dumps(out))
+
+
+def cpu_baseline3(wl, cols=(16, 8), budget_s: float = 10.0, max_steps: int = 200):
+    """The 3-D oracle, all host cores, on slow steps of a 16 x 8 column strip
+    of the workload's rows."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    g = wl.grid
+    sg = W.Grid3(cols[0], cols[1], g.nS, g.nB, g.nF, dx=g.dx, dy=g.dy, dz1=g.dz1, dz2=g.dz2)
+    q = W.gaussian_bumps3(sg, wl.seed)
+    P = O.make_problem3(sg.nx, sg.ny, sg.nS, sg.nB, sg.nF, wl.m, 0.0, sg.dx, dy=sg.dy, dz1=sg.dz1, dz2=sg.dz2)
+    P.dt = O.stable_dt3(P, q, 0.4)
+    per_step = sg.nx * sg.ny * (2 * sg.nS + 2 * wl.m * (sg.nB + sg.nF))
+    n, t0 = 0, time.perf_counter()
+    while n < max_steps and time.perf_counter() - t0 < budget_s:
+        q = O.mprk_step3(P, q)
+        n += 1
+    el = time.perf_counter() - t0
+    return {"value": per_step * n / el, "unit": "cell-stages/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} slow steps of the {wl.name} rows on a {cols[0]}x{cols[1]}-column strip "
+                      f"({per_step * n} cell-stages, {el:.1f} s)"}
+
 
 def run_convection(args):
     """Table 6's thermal convection (Sec. 5.2, second set-up) on the GPU:
@@ -644,7 +758,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large_2048",
                     choices=["large_2048", "plain_64", "mixed_4096", "batched_256", "served", "speedup",
-                             "convection"])
+                             "convection", "cube"])
     ap.add_argument("--speedup-nx", type=int, default=2048)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--served-requests", type=int, default=2000)
@@ -666,6 +780,8 @@ def main():
         run_served(args)
     elif args.workload == "convection":
         run_convection(args)
+    elif args.workload == "cube":
+        run_cube(args)
     elif args.workload == "speedup":
         run_speedup(args)
     else:

@@ -299,6 +299,8 @@ class Workload:
             return rest_state(self.grid)
         if self.perturbation == "convection":
             return thermal_convection(self.grid)
+        if self.perturbation == "bumps3":
+            return gaussian_bumps3(self.grid, self.seed)
         raise ValueError(self.perturbation)
 
     def cell_stages_per_step(self) -> int:
@@ -336,6 +338,13 @@ def convection_100() -> Workload:
     m = 4, dt = 0.025, to t = 2.5 (100 slow steps), FP64."""
     return Workload("convection_100x300_m4_fp64", convection_grid(), 4, 100, "fp64", "convection", 0,
                     extra={"x_walls": 1, "dt": 0.025})
+
+
+def cube_512() -> Workload:
+    """The 3-D model (App. B): 512 x 64 columns, S/B/F = 96/8/96 rows, m = 4,
+    seeded bumps, FP64, 20 slow steps."""
+    return Workload("cube_512x64x200_m4_fp64", Grid3(512, 64, 96, 8, 96), 4, 20, "fp64", "bumps3",
+                    SEED0 + 11)
 
 
 def batched_256(count: int = 256, seed: int = SEED0 + 3, steps: int = 100):
