@@ -652,6 +652,114 @@ int or_mprk_step(const or_problem* P, double* q, long long* rhs_cells) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* MPRK with a general base method (Sec. 3 remark: the base of the MPRK2     */
+/* framework can be any Runge–Kutta method; the coupled method stays second  */
+/* order at most)                                                             */
+/* ------------------------------------------------------------------------ */
+
+/* The three region tableaus for an s-stage base method (A s x s row-major,
+ * b, c) and rate ratio m, built the way Table 1 builds them from RK2; stage
+ * i = k s + p is stage p of fast substep k:
+ *  F: m base steps of dt/m: a_{i, k's+q} = b_q/m for k' < k,
+ *     a_{i, ks+q} = A_pq/m, c_i = (k + c_p)/m, b_i = b_p/m;
+ *  B: the base restarted from q_n every substep: a_{i, ks+q} = A_pq,
+ *     c_i = c_p, b_i = b_p/m;
+ *  S: the base once; stages past s repeat stage p of the first substep:
+ *     a_{i, q} = A_pq, c_i = c_p, b = (b, 0, ..., 0).
+ * With Heun's base these are or_tableau's entries exactly. */
+int or_tableau_base(int m, int region, int s, const double* A, const double* bb, const double* cc, double* a,
+                    double* b, double* c) {
+  if (m < 1 || s < 1 || region < 0 || region > 2) return -1;
+  const int ms = m * s;
+  for (int e = 0; e < ms * ms; e++) a[e] = 0.0;
+  for (int k = 0; k < m; k++)
+    for (int p = 0; p < s; p++) {
+      const int i = k * s + p;
+      if (region == OR_REGION_F) {
+        for (int kk = 0; kk < k; kk++)
+          for (int q = 0; q < s; q++) a[i * ms + kk * s + q] = bb[q] / m;
+        for (int q = 0; q < p; q++) a[i * ms + k * s + q] = A[p * s + q] / m;
+        c[i] = (k + cc[p]) / m;
+        b[i] = bb[p] / m;
+      } else if (region == OR_REGION_B) {
+        for (int q = 0; q < p; q++) a[i * ms + k * s + q] = A[p * s + q];
+        c[i] = cc[p];
+        b[i] = bb[p] / m;
+      } else {
+        for (int q = 0; q < p; q++) a[i * ms + q] = A[p * s + q];
+        c[i] = cc[p];
+        b[i] = k == 0 ? bb[p] : 0.0;
+      }
+    }
+  return 0;
+}
+
+/* One slow step of MPRK with the s-stage base (A, b, c): Algorithm 1 with s
+ * in place of 2 (S stages past s copy stage mod(i-1, s)+1 of the first
+ * substep and skip their RHS). */
+int or_mprk_step_base(const or_problem* P, int s, const double* A, const double* bb, const double* cc, double* q) {
+  if (check_problem(P) || s < 1 || s > 8) return -1;
+  const int m = P->m, ms = s * m;
+  const int nS = P->nS, n1 = n1_of(P), nz = nz_of(P);
+  const size_t N = (size_t)4 * nz * P->nx;
+  double* Q = malloc(sizeof(double) * N * ms);
+  double* R = calloc(N * ms, sizeof(double));
+  double* qn = malloc(sizeof(double) * N);
+  double* tab = malloc(sizeof(double) * (3 * ms * ms + 4 * ms));
+  if (!Q || !R || !qn || !tab) { free(Q); free(R); free(qn); free(tab); return -2; }
+  double *aS = tab, *aB = tab + ms * ms, *aF = tab + 2 * ms * ms;
+  double *bS = tab + 3 * ms * ms, *bB = bS + ms, *bF = bS + 2 * ms, *cx = bS + 3 * ms;
+  or_tableau_base(m, OR_REGION_S, s, A, bb, cc, aS, bS, cx);
+  or_tableau_base(m, OR_REGION_B, s, A, bb, cc, aB, bB, cx);
+  or_tableau_base(m, OR_REGION_F, s, A, bb, cc, aF, bF, cx);
+  for (int i = 0; i < ms; i++) {
+    double* Qi = Q + (size_t)i * N;
+    double* Ri = R + (size_t)i * N;
+    stage_value(P, q, R, Qi, aB, ms, i, nS, n1);
+    if (i < s) stage_value(P, q, R, Qi, aS, ms, i, 0, nS);
+    else copy_rows(P, Q + (size_t)(i % s) * N, Qi, 0, nS);
+    stage_value(P, q, R, Qi, aF, ms, i, n1, nz);
+    or_rhs(P, Qi, Ri, nS, n1);
+    if (i < s) or_rhs(P, Qi, Ri, 0, nS);
+    or_rhs(P, Qi, Ri, n1, nz);
+  }
+  completion(P, q, R, qn, bS, ms, 0, nS);
+  completion(P, q, R, qn, bB, ms, nS, n1);
+  completion(P, q, R, qn, bF, ms, n1, nz);
+  memcpy(q, qn, sizeof(double) * N);
+  free(Q); free(R); free(qn); free(tab);
+  return 0;
+}
+
+/* The s-stage base method alone over the whole grid, step h:
+ * K_i = R(q + h sum_{j<i} A_ij K_j), q <- q + h sum_i b_i K_i. */
+int or_rk_step_base(const or_problem* P, int s, const double* A, const double* bb, double* q, double h) {
+  if (check_problem(P) || s < 1 || s > 8) return -1;
+  const int nz = nz_of(P);
+  const size_t N = (size_t)4 * nz * P->nx;
+  double* K = malloc(sizeof(double) * N * (s + 1));
+  if (!K) return -2;
+  double* y = K + (size_t)s * N;
+  for (int i = 0; i < s; i++) {
+    for (size_t e = 0; e < N; e++) {
+      double sum = 0.0;
+      for (int j = 0; j < i; j++)
+        if (A[i * s + j] != 0.0) sum += A[i * s + j] * K[(size_t)j * N + e];
+      y[e] = q[e] + h * sum;
+    }
+    or_rhs(P, y, K + (size_t)i * N, 0, nz);
+  }
+  for (size_t e = 0; e < N; e++) {
+    double sum = 0.0;
+    for (int i = 0; i < s; i++)
+      if (bb[i] != 0.0) sum += bb[i] * K[(size_t)i * N + e];
+    q[e] = q[e] + h * sum;
+  }
+  free(K);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Single-rate integrators over the whole grid                                */
 /* ------------------------------------------------------------------------ */
 

@@ -62,6 +62,15 @@ int or_mprk_step(const or_problem* P, double* q, long long* rhs_cells);
 int or_mprk_step_trace(const or_problem* P, const double* q, double* Q, double* R,
                        double* q_next);
 
+/* MPRK with a general s-stage base method (A s x s row-major, b, c; the
+ * Sec. 3 remark): the region tableaus built from the base as Table 1 builds
+ * them from RK2 (or_tableau's entries for Heun's base), one slow step, and
+ * the base method alone over the whole grid. */
+int or_tableau_base(int m, int region, int s, const double* A, const double* b, const double* c, double* a_out,
+                    double* b_out, double* c_out);
+int or_mprk_step_base(const or_problem* P, int s, const double* A, const double* b, const double* c, double* q);
+int or_rk_step_base(const or_problem* P, int s, const double* A, const double* b, double* q, double h);
+
 /* Single-rate base RK2 (Heun, Table 1 "Base RK2") over the whole grid, step h. */
 int or_rk2_step(const or_problem* P, double* q, double h);
 

@@ -106,6 +106,9 @@ def lib():
         _lib.or_set_threads.restype = None
         _lib.or_get_threads.restype = C.c_int
         _lib.or_rhs_cell_count.restype = C.c_longlong
+        _lib.or_tableau_base.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp, dp]
+        _lib.or_mprk_step_base.argtypes = [pp, C.c_int, dp, dp, dp, dp]
+        _lib.or_rk_step_base.argtypes = [pp, C.c_int, dp, dp, dp, C.c_double]
         p3 = C.POINTER(Problem3)
         _lib.or3_rhs.argtypes = [p3, dp, dp, C.c_int, C.c_int]
         _lib.or3_mprk_step.argtypes = [p3, dp]
@@ -304,3 +307,46 @@ def lf_flux3(ql, qr, d: int, gamma: float = 1.4) -> np.ndarray:
     F = np.zeros(5)
     lib().or3_lf_flux(_p(ql), _p(qr), d, gamma, _p(F))
     return F
+
+
+# ---- MPRK with a general base method (Sec. 3 remark) ------------------------
+
+# (A, b, c) of the base methods: Heun (the RK2 of Table 1), the third-order
+# strong-stability-preserving method of Shu and Osher, classical RK4.
+BASES = {
+    "rk2": (np.array([[0.0, 0.0], [1.0, 0.0]]), np.array([0.5, 0.5]), np.array([0.0, 1.0])),
+    "rk3": (np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.25, 0.25, 0.0]]), np.array([1 / 6, 1 / 6, 2 / 3]),
+            np.array([0.0, 1.0, 0.5])),
+    "rk4": (np.array([[0.0, 0.0, 0.0, 0.0], [0.5, 0.0, 0.0, 0.0], [0.0, 0.5, 0.0, 0.0], [0.0, 0.0, 1.0, 0.0]]),
+            np.array([1 / 6, 1 / 3, 1 / 3, 1 / 6]), np.array([0.0, 0.5, 0.5, 1.0])),
+}
+
+
+def _base(base):
+    A, b, c = BASES[base] if isinstance(base, str) else base
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    return A.shape[0], A, np.ascontiguousarray(b, dtype=np.float64), np.ascontiguousarray(c, dtype=np.float64)
+
+
+def tableau_base(m: int, region: int, base="rk2"):
+    s, A, b, c = _base(base)
+    ms = m * s
+    a_out, b_out, c_out = np.zeros((ms, ms)), np.zeros(ms), np.zeros(ms)
+    assert lib().or_tableau_base(m, region, s, _p(A), _p(b), _p(c), _p(a_out), _p(b_out), _p(c_out)) == 0
+    return a_out, b_out, c_out
+
+
+def mprk_step_base(P: Problem, q: np.ndarray, base="rk2", n: int = 1) -> np.ndarray:
+    s, A, b, c = _base(base)
+    q = np.array(q, dtype=np.float64, order="C", copy=True)
+    for _ in range(n):
+        assert lib().or_mprk_step_base(C.byref(P), s, _p(A), _p(b), _p(c), _p(q)) == 0
+    return q
+
+
+def rk_step_base(P: Problem, q: np.ndarray, h: float, base="rk2", n: int = 1) -> np.ndarray:
+    s, A, b, c = _base(base)
+    q = np.array(q, dtype=np.float64, order="C", copy=True)
+    for _ in range(n):
+        assert lib().or_rk_step_base(C.byref(P), s, _p(A), _p(b), _p(q), h) == 0
+    return q
