@@ -678,6 +678,98 @@ def run_convection(args):
     print(json.dumps(out))
 
 
+def run_base(args):
+    """MPRK with the classical RK4 base (Sec. 3 remark) on the GPU. Throughput
+    of the 2048x1024, m = 8, FP64 workload with the RK4 base (4m stages per
+    slow step), and the accuracy experiment the remark calls for: on the
+    thermal convection set-up (walls on all sides, m = 4, to t = 2.5), the L2
+    errors of rho, momentum and rho E for the RK2, RK3 and RK4 bases at dt =
+    0.025 {1, 1/2, 1/4, 1/8} against single-rate RK4 with dt = 0.003125/16,
+    and their observed orders (the coupling keeps every base at second order
+    or below)."""
+    import torch
+    from paper_2202_11890_gb300 import build as B
+    from paper_2202_11890_gb300 import mprk as M
+    from paper_2202_11890_gb300 import timing as T
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    bases = {"rk2": M.MPRK_BASE_RK2, "rk3": M.MPRK_BASE_RK3, "rk4": M.MPRK_BASE_RK4}
+    stages = {"rk2": 2, "rk3": 3, "rk4": 4}
+
+    # throughput: the large FP64 workload with the RK4 base
+    wl = W.large_2048()
+    g = wl.grid
+    q0 = wl.initial_state()
+    cfg = M.mprk_config_default(g.nx, g.nS, g.nB, g.nF, wl.m)
+    cfg.base = M.MPRK_BASE_RK4
+    steps = min(args.steps, 60)
+    with M.Instance(cfg, q0) as inst:
+        cs = inst.info()["cell_stages_per_step"]
+        stream = inst.info()["stream"]
+        inst.step(args.warmup)
+        inst.sync()
+        sampler = ClockSampler(torch.cuda.current_device())
+        torch.cuda.synchronize()
+        with sampler:
+            t_ms = T.time_steps(inst.h, stream, steps)
+        torch.cuda.synchronize()
+        stage_ms, stage_cells = T.stage_kernel_times(inst.h, stream, reps=3)
+    value = cs * steps / (t_ms * 1e-3)
+    ach = stage_cells * FLOPS_PER_CELL_STAGE[True] / (stage_ms * 1e-3) / 1e9
+
+    # accuracy: the thermal convection with each base
+    cw = W.convection_100()
+    cg = cw.grid
+    cq = cw.initial_state()
+    t_end = 2.5
+
+    def config(dt, base, m=cw.m, scheme=M.MPRK_SCHEME_MPRK2):
+        c = M.mprk_config_default(cg.nx, cg.nS, cg.nB, cg.nF, m, dx=cg.dx, dz1=cg.dz1, dz2=cg.dz2)
+        c.dt, c.scheme, c.x_walls, c.base = dt, scheme, M.MPRK_X_WALLS, bases[base]
+        return c
+
+    ref_dt = 0.003125 / 16
+    with M.Instance(config(ref_dt, "rk4", m=1, scheme=M.MPRK_SCHEME_SR_RK2), cq) as inst:
+        inst.step(int(round(t_end / ref_dt)))
+        ref = inst.state()
+    cell = cg.dx * np.concatenate([np.full(cg.n1, cg.dz1), np.full(cg.nF, cg.dz2)])[:, None]
+
+    def l2(a):
+        return float(np.sqrt((a * a * cell).sum()))
+
+    dts = [0.025, 0.0125, 0.00625, 0.003125]
+    study = {}
+    for base in bases:
+        errs = []
+        for dt in dts:
+            with M.Instance(config(dt, base), cq) as inst:
+                inst.step(int(round(t_end / dt)))
+                d = inst.state() - ref
+            errs.append([l2(d[0]), l2(np.stack([d[1], d[2]])), l2(d[3])])
+        e = np.array(errs)
+        study[base] = {"l2_rho_momentum_energy": errs, "orders": np.log2(e[:-1] / e[1:]).tolist()}
+
+    out = {"metric": METRIC, "value": value, "unit": "cell-stages/s", "n_gpus": 1, "steps": steps,
+           "warmup": args.warmup, "ms_per_step": t_ms / steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl.name.replace("_m8", "_m8_rk4base"), "nx": g.nx,
+                      "rows_S_B_F": [g.nS, g.nB, g.nF], "m": wl.m, "base": "rk4",
+                      "cell_stages_per_step": cs, "l2": "working set > L2; no flush"},
+           "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                        "frac": ach / FP64_PEAK_GFLOPS, "traffic": None,
+                        "peak_source": "FP64 unit count x max clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                        "flops": "the Heun stage's count; the RK4 stage values and weights add < 2 %"},
+           "kernel": {"name": "stage_kernel<GEN>", "ms_per_step": stage_ms,
+                      "cell_stages_per_step": stage_cells, "launches_per_step": 4 * wl.m},
+           "clocks": sampler.summary(),
+           "accuracy": {"setup": cw.name, "t": t_end, "dt": dts, "m": cw.m,
+                        "reference": f"single-rate RK4 on the GPU, dt = {ref_dt}", "bases": study},
+           "gpu_launches": (4 * wl.m + 1) * steps}
+    print(json.dumps(out))
+
+
 def oracle_sample(wl: W.Workload, cols: int):
     """The workload's rows, rate and perturbation on a strip of `cols` columns
     (the oracle's cost per cell-stage does not depend on nx)."""
@@ -758,7 +850,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large_2048",
                     choices=["large_2048", "plain_64", "mixed_4096", "batched_256", "served", "speedup",
-                             "convection", "cube"])
+                             "convection", "cube", "base_rk4"])
     ap.add_argument("--speedup-nx", type=int, default=2048)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--served-requests", type=int, default=2000)
@@ -782,6 +874,8 @@ def main():
         run_convection(args)
     elif args.workload == "cube":
         run_cube(args)
+    elif args.workload == "base_rk4":
+        run_base(args)
     elif args.workload == "speedup":
         run_speedup(args)
     else:

@@ -67,6 +67,14 @@ extern "C" {
 #define MPRK_X_PERIODIC 0 /* x is periodic                       */
 #define MPRK_X_WALLS 1    /* walls at both ends of x              */
 
+/* Base Runge-Kutta method of the MPRK framework. Sec. 3 builds the coupled
+ * method from any base; the coupling keeps it second order at most, so the
+ * higher-order bases serve accuracy experiments. RK3 and RK4 run in FP64 on
+ * the 2-D model through mprk_create/mprk_step only. */
+#define MPRK_BASE_RK2 0 /* Heun's method: the Table 1 tableaus           */
+#define MPRK_BASE_RK3 1 /* the three-stage third-order SSP method        */
+#define MPRK_BASE_RK4 2 /* the classical four-stage fourth-order method  */
+
 #define MPRK_HOST 0   /* pointer is host memory   */
 #define MPRK_DEVICE 1 /* pointer is device memory */
 
@@ -96,6 +104,9 @@ typedef struct {
   double G;       /* gravity magnitude: source (0, 0, -rho G, -rho w G)       */
   int ny;         /* columns in y: 1 for the 2-D model; >= 4 for 3-D (App. B):
                      y periodic, 5 components, FP64, MPRK_X_PERIODIC          */
+  int base;       /* MPRK_BASE_RK2 (default), MPRK_BASE_RK3 or MPRK_BASE_RK4:
+                     the s-stage base of every region (s = 2, 3, 4); a slow
+                     step then has s*m stages                                 */
   double dy;      /* cell depth in y (3-D)                                    */
 } mprk_config;
 
@@ -188,7 +199,8 @@ int mprk_rhs(mprk_instance* inst, const double* W_dev, double* R_dev, int k_lo, 
  * enqueued on its own, bracketed by CUDA events on the instance stream.
  * launch_ms[j] receives the duration of launch j and launch_cells[j] the
  * cell right-hand-side evaluations it made (0 for the step completion); the
- * launches are the 2m stages in order, then the completion. Returns the
+ * launches are the s*m stages in order (s = 2 for the Heun base), then the
+ * completion. Returns the
  * number of launches (at most cap are written) or a negative error code.
  * Synchronises. */
 int mprk_profile_step(mprk_instance* inst, double* launch_ms, long long* launch_cells, int cap);

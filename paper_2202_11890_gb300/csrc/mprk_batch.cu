@@ -199,9 +199,9 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
     int prec;
     int rc = instance_view(insts[j], &hinst[j].g, &hinst[j].b, &prec, &s, &st);
     if (rc) { free_plan(p); return rc; }
-    if (hinst[j].g.ny > 1) {
+    if (hinst[j].g.ny > 1 || hinst[j].g.gen) {
       free_plan(p);
-      return bfail(MPRK_EINVAL, "batches take 2-D instances only");
+      return bfail(MPRK_EINVAL, "batches take 2-D instances with the Heun base only");
     }
     hinst[j].status = st;
     if (j == 0) {
@@ -430,7 +430,8 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
       int rc = instance_view(insts[j], &hinst[j].g, &hinst[j].b, &prec, &s, &st);
       if (rc) return rc;
       if (prec != r->precision) return bfail(MPRK_EINVAL, "batch runner: precision mismatch");
-      if (hinst[j].g.ny > 1) return bfail(MPRK_EINVAL, "batch runner: 2-D instances only");
+      if (hinst[j].g.ny > 1 || hinst[j].g.gen)
+        return bfail(MPRK_EINVAL, "batch runner: 2-D instances with the Heun base only");
       hinst[j].status = st;
       hinst[j].precision = prec;
       hinst[j].counter_base = n_counters;

@@ -60,6 +60,11 @@ struct Geom {
   int ny;              // columns in y: 1 in 2-D
   int nc;              // conserved components: 4 (2-D) or 5 (3-D)
   double inv_dy;       // 3-D only
+  // base method of the MPRK framework (Sec. 3 remark): s stages, A, b.
+  // gen = 0 for Heun (Table 1), which runs the dedicated RK2 low-storage
+  // path; otherwise the general s-stage path with s R_a slots.
+  int s, gen;
+  double bA[4][4], bb[4];
   double hF;           // dt / m
   double h2;           // dt / (2 m)
   double hdt;          // dt / 2
@@ -111,13 +116,13 @@ __host__ __device__ inline StageArgs stage_args(const Geom& g, const Bufs& b, in
   StageArgs a{};
   a.g = g;
   a.b = b;
-  const bool even_sub = ((st / 2) % 2) == 0;
+  const bool even_sub = ((st / g.s) % 2) == 0;
   a.qF = even_sub ? b.qA : b.qB;
   a.qF_next = even_sub ? b.qB : b.qA;
   a.dF = even_sub ? b.dA : b.dB;
   a.dF_next = even_sub ? b.dB : b.dA;
   a.stage = st;
-  a.row0 = st < 2 ? 0 : g.nS_r;
+  a.row0 = st < g.s ? 0 : g.nS_r;  // S rows only during the first substep
   a.tiles_x = (g.nx + TX - 1) / TX;
   a.tz = b.dA ? MTZ : TZ;  // float shadows exist only in the FP32-flux mode
   return a;

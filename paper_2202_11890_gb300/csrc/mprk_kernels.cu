@@ -15,12 +15,14 @@
 
 namespace mprk {
 
-template <typename Real, typename Store>
+// GEN: the general s-stage base (RK3, RK4) in place of Heun's low-storage
+// combination.
+template <typename Real, typename Store, bool GEN = false>
 __global__ void __launch_bounds__(NTHREADS, 2)
     stage_kernel(const StageArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   TileSmem<Real>& S = *reinterpret_cast<TileSmem<Real>*>(smem_raw);
-  stage_tile<Real, Store>(a, blockIdx.x, S);
+  stage_tile<Real, Store, GEN>(a, blockIdx.x, S);
 }
 
 // FP32-flux stage kernel: one CTA per tile, blockIdx = (tile column, tile
@@ -81,6 +83,9 @@ cudaError_t prepare_kernels() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(TileSmem<double>));
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(stage_kernel<double, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(TileSmem<double>));
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(yface3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(YfaceSmem));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(stage3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Tile3Smem));
@@ -132,7 +137,9 @@ cudaError_t make_stage_maps(const Geom& g, const Bufs& b, StageMaps* out) {
 cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStream_t stream,
                          const StageMaps* maps) {
   if (n_tiles <= 0) return cudaSuccess;
-  if (precision == 0) {
+  if (precision == 0 && a.g.gen) {
+    stage_kernel<double, double, true><<<n_tiles, NTHREADS, sizeof(TileSmem<double>), stream>>>(a);
+  } else if (precision == 0) {
     stage_kernel<double, double><<<n_tiles, NTHREADS, sizeof(TileSmem<double>), stream>>>(a);
   } else {
     StageArgs s = a;

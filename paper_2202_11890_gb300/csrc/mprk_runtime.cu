@@ -111,6 +111,10 @@ int mprk::validate_config(const mprk_config* c) {
   if (!(c->mu1 > 0.0) || !(c->mu2 > 0.0)) return fail(MPRK_EINVAL, "viscosities must be positive");
   if (!(c->G >= 0.0)) return fail(MPRK_EINVAL, "G must be >= 0");
   if (c->ny < 1) return fail(MPRK_EINVAL, "ny = %d: need ny >= 1", c->ny);
+  if (c->base < MPRK_BASE_RK2 || c->base > MPRK_BASE_RK4)
+    return fail(MPRK_EINVAL, "unknown base method %d", c->base);
+  if (c->base != MPRK_BASE_RK2 && (c->precision != MPRK_FP64 || c->ny > 1))
+    return fail(MPRK_EINVAL, "the RK3 and RK4 bases run in FP64 on the 2-D model only");
   if (c->ny > 1) {
     if (c->ny < 4) return fail(MPRK_EINVAL, "ny = %d: a 3-D grid needs at least 4 columns in y", c->ny);
     if (c->precision != MPRK_FP64) return fail(MPRK_EINVAL, "the 3-D model runs in FP64 only");
@@ -147,7 +151,7 @@ void free_instance(mprk_instance* I) {
 // Enqueue the stage launches and the completion of one slow step.
 int enqueue_step(mprk_instance* I, cudaStream_t s) {
   const Geom& g = I->g;
-  for (int st = 0; st < 2 * g.m; st++) {
+  for (int st = 0; st < g.s * g.m; st++) {
     StageArgs a = stage_args(g, I->b, st);
     a.status = I->status_dev;
     if (g.ny > 1) {
@@ -225,6 +229,41 @@ void mprk::destroy_instance(mprk_instance* I) {
   free_instance(I);
 }
 
+// The base tableau (A, b) of Sec. 3's remark. Heun keeps gen = 0: its
+// low-storage path needs no tableau.
+static void set_base(int base, Geom* g) {
+  for (int p = 0; p < 4; p++) {
+    g->bb[p] = 0.0;
+    for (int q = 0; q < 4; q++) g->bA[p][q] = 0.0;
+  }
+  if (base == MPRK_BASE_RK3) {
+    // three-stage SSP: stages at 0, 1 and 1/2 of the step
+    g->s = 3;
+    g->bA[1][0] = 1.0;
+    g->bA[2][0] = 0.25;
+    g->bA[2][1] = 0.25;
+    g->bb[0] = 1.0 / 6.0;
+    g->bb[1] = 1.0 / 6.0;
+    g->bb[2] = 2.0 / 3.0;
+  } else if (base == MPRK_BASE_RK4) {
+    // classical RK4: stages at 0, 1/2, 1/2 and 1
+    g->s = 4;
+    g->bA[1][0] = 0.5;
+    g->bA[2][1] = 0.5;
+    g->bA[3][2] = 1.0;
+    g->bb[0] = 1.0 / 6.0;
+    g->bb[1] = 1.0 / 3.0;
+    g->bb[2] = 1.0 / 3.0;
+    g->bb[3] = 1.0 / 6.0;
+  } else {
+    g->s = 2;
+    g->bA[1][0] = 1.0;
+    g->bb[0] = 0.5;
+    g->bb[1] = 0.5;
+  }
+  g->gen = base != MPRK_BASE_RK2;
+}
+
 void mprk::geom_from_config(const mprk_config& c, int pitch, Geom* gp) {
   Geom& g = *gp;
   memset(&g, 0, sizeof g);
@@ -265,6 +304,7 @@ void mprk::geom_from_config(const mprk_config& c, int pitch, Geom* gp) {
   g.ny = c.ny > 1 ? c.ny : 1;
   g.nc = c.ny > 1 ? 5 : 4;
   g.inv_dy = c.ny > 1 ? 1.0 / c.dy : 0.0;
+  set_base(c.base, &g);
   g.hF = c.dt / c.m;
   g.h2 = c.dt / (2.0 * c.m);
   g.hdt = 0.5 * c.dt;
@@ -294,7 +334,8 @@ long long mprk::instance_bytes(const mprk_config& c) {
   const bool mprk2 = c.scheme == MPRK_SCHEME_MPRK2;
   const long long nB = mprk2 ? c.nz_B : 0, nS = mprk2 ? c.nz_S : 0;
   const long long rsz = c.precision == MPRK_FP64 ? 8 : 4;
-  long long b = 2 * nc * plane * 8 + nc * plane * rsz + r16(nc * nB * ny * pitch * 8) +
+  const long long ra_slots = c.base == MPRK_BASE_RK4 ? 3 : c.base == MPRK_BASE_RK3 ? 2 : 1;
+  long long b = 2 * nc * plane * 8 + ra_slots * nc * plane * rsz + r16(nc * nB * ny * pitch * 8) +
                 r16(nc * nS * ny * pitch * 8);
   if (ny > 1) b += nc * plane * 8;  // y-face fluxes
   b += 1024 * 16 * 8 + 16 * 8 + 16;  // monitoring partials (upper bound), results, status
@@ -385,7 +426,7 @@ int mprk::create_instance(const mprk_config* cfg, const double* q0, int q0_locat
   const size_t rsz = I->precision == MPRK_FP64 ? sizeof(double) : sizeof(float);
   I->diag_nblocks = diag_blocks(g);
   if ((rc = alloc((void**)&I->b.qA, nc * plane * 8)) || (rc = alloc((void**)&I->b.qB, nc * plane * 8)) ||
-      (rc = alloc(&I->b.Ra, nc * plane * rsz)) ||
+      (rc = alloc(&I->b.Ra, (size_t)(g.s - 1) * nc * plane * rsz)) ||
       (rc = alloc((void**)&I->b.accB, nc * (size_t)(g.n1_r - g.nS_r) * g.ny * g.pitch * 8)) ||
       (rc = alloc((void**)&I->b.accS, nc * (size_t)g.nS_r * g.ny * g.pitch * 8)) ||
       (g.ny > 1 && (rc = alloc((void**)&I->gy, nc * plane * 8))) ||
@@ -407,7 +448,7 @@ int mprk::create_instance(const mprk_config* cfg, const double* q0, int q0_locat
   };
   if (cudaMemsetAsync(I->b.qA, 0, nc * plane * 8, I->stream) != cudaSuccess ||
       cudaMemsetAsync(I->b.qB, 0, nc * plane * 8, I->stream) != cudaSuccess ||
-      cudaMemsetAsync(I->b.Ra, 0, nc * plane * rsz, I->stream) != cudaSuccess ||
+      cudaMemsetAsync(I->b.Ra, 0, (size_t)(g.s - 1) * nc * plane * rsz, I->stream) != cudaSuccess ||
       cudaMemsetAsync(I->status_dev, 0, 16, I->stream) != cudaSuccess)
     return fin(fail(MPRK_ECUDA, "memset failed"));
   if (I->b.dA &&
@@ -534,8 +575,9 @@ int mprk_info(const mprk_instance* I, double* dt, long long* cell_stages, long l
   if (cell_stages) {
     const long long nz = c.nz_S + c.nz_B + c.nz_F;
     const long long cols = (long long)c.nx * (c.ny > 1 ? c.ny : 1);
-    *cell_stages = c.scheme == MPRK_SCHEME_MPRK2 ? cols * (2LL * c.nz_S + 2LL * c.m * (c.nz_B + c.nz_F))
-                                                 : cols * 2LL * c.m * nz;
+    const long long s = I->g.s;
+    *cell_stages = c.scheme == MPRK_SCHEME_MPRK2 ? cols * (s * c.nz_S + s * c.m * (c.nz_B + c.nz_F))
+                                                 : cols * s * c.m * nz;
   }
   if (bytes) *bytes = I->bytes;
   if (stream) *stream = (void*)I->stream;
@@ -579,12 +621,12 @@ int mprk_rhs(mprk_instance* I, const double* W_dev, double* R_dev, int k_lo, int
 int mprk_profile_step(mprk_instance* I, double* launch_ms, long long* launch_cells, int cap) {
   if (!I) return fail(MPRK_EINVAL, "instance is NULL");
   const Geom& g = I->g;
-  const int n = 2 * g.m + 1;
-  cudaEvent_t ev[2 * 64 + 2];
+  const int n = g.s * g.m + 1;
+  cudaEvent_t ev[4 * 64 + 2];
   for (int j = 0; j <= n; j++) CU(cudaEventCreate(&ev[j]));
   int rc = MPRK_OK;
   CU(cudaEventRecord(ev[0], I->stream));
-  for (int st = 0; st < 2 * g.m && rc == MPRK_OK; st++) {
+  for (int st = 0; st < g.s * g.m && rc == MPRK_OK; st++) {
     StageArgs a = stage_args(g, I->b, st);
     a.status = I->status_dev;
     a.gy = I->gy;

@@ -336,6 +336,7 @@ int mprk_submit(mprk_server* S, const mprk_config* cfg, const double* q0_host, i
   int rc = validate_config(cfg);
   if (rc) return rc;
   if (cfg->ny > 1) return sfail(MPRK_EINVAL, "the server takes 2-D requests only");
+  if (cfg->base != MPRK_BASE_RK2) return sfail(MPRK_EINVAL, "the server takes the Heun base only");
   const long long bytes = instance_bytes(*cfg);
   if (bytes > S->cfg.hbm_budget_bytes)
     return sfail(MPRK_EBUDGET, "request needs " + std::to_string(bytes) + " device bytes, budget is " +

@@ -130,7 +130,22 @@ __device__ __forceinline__ bool x_ghost(int i, int nx, int xwall) { return xwall
 // Not inlined: the single-instance kernel and the persistent batch kernel
 // then run the very same compiled body, so an instance's results are bitwise
 // the same alone and in a batch.
-template <typename Real, typename Store>
+// The stage value of a general s-stage base (GEN): base + h sum_{q<p}
+// A_pq R_q over the R_a slots of the current substep (slot q at
+// Ra + q * slot); p = 0 gives the base value.
+__device__ __forceinline__ double gen_stage_value(const Geom& g, const double* base, const double* Ra, size_t slot,
+                                                  size_t off, int p, double h) {
+  if (p == 0) return base[off];
+  double sum = 0.0;
+  for (int q = 0; q < p; q++)
+    if (g.bA[p][q] != 0.0) sum += g.bA[p][q] * Ra[(size_t)q * slot + off];
+  return base[off] + h * sum;
+}
+
+// GEN selects the general s-stage base method (Sec. 3 remark) in place of
+// Heun's low-storage path: s R_a slots, the stage values of the region
+// tableaus built from the base, and its weights b in the combinations.
+template <typename Real, typename Store, bool GEN = false>
 __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int tile,
                                        TileSmem<Real>& __restrict__ S) {
   // __restrict__: the argument block and shared memory never alias, so its
@@ -163,7 +178,10 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
         val = (Real)a.rhs_in[off];
       } else {
         const double* base = k < g.n1_r ? a.b.qA : a.qF;
-        if (odd_stage) {
+        if (GEN) {
+          val = (Real)gen_stage_value(g, base, reinterpret_cast<const double*>(Ra), 4 * plane, off,
+                                      a.stage % g.s, k < g.n1_r ? g.dt : hF);
+        } else if (odd_stage) {
           const Real h = (Real)(k < g.n1_r ? g.dt : hF);
           val = (Real)base[off] + h * (Real)Ra[off];
         } else {
@@ -210,7 +228,10 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
           qq[c] = a.rhs_in[off];
         } else {
           const double* base = k < g.n1_r ? a.b.qA : a.qF;
-          if (odd_stage) {
+          if (GEN) {
+            qq[c] = gen_stage_value(g, base, reinterpret_cast<const double*>(Ra), 4 * plane, off, a.stage % g.s,
+                                    k < g.n1_r ? g.dt : hF);
+          } else if (odd_stage) {
             qq[c] = base[off] + (k < g.n1_r ? g.dt : hF) * (double)Ra[off];
           } else {
             qq[c] = base[off];
@@ -412,6 +433,40 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
     Store* Ra_w = reinterpret_cast<Store*>(a.b.Ra);
     const int st = a.stage;
     const double h2 = g.h2;
+    if (GEN) {
+      // general s-stage base: R to slot p; F rows finish a substep with the
+      // weights b/m, B rows accumulate b_p R over the slow step, S rows finish
+      // after the first substep
+      double* Rs = reinterpret_cast<double*>(a.b.Ra);
+      const size_t slot = 4 * plane;
+      const int s = g.s, p = st % s;
+      const bool sub_end = (p == s - 1);
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const size_t o = (size_t)c * plane + row_off;
+        const double r = (double)R[c];
+        if (!sub_end) Rs[(size_t)p * slot + o] = r;
+        if (k >= g.n1_r) {
+          if (sub_end) {
+            double sum = 0.0;
+            for (int q = 0; q < s - 1; q++) sum += g.bb[q] * Rs[(size_t)q * slot + o];
+            sum += g.bb[s - 1] * r;
+            a.qF_next[o] = a.qF[o] + g.hF * sum;
+          }
+        } else if (k >= g.nS_r) {
+          const size_t pb = (size_t)(g.n1_r - g.nS_r) * g.pitch;
+          double* acc = a.b.accB + (size_t)c * pb + (size_t)(k - g.nS_r) * g.pitch + i;
+          const double v = (st == 0) ? g.bb[p] * r : *acc + g.bb[p] * r;
+          *acc = (st == s * g.m - 1) ? a.b.qA[o] + g.hF * v : v;
+        } else if (sub_end) {
+          double sum = 0.0;
+          for (int q = 0; q < s - 1; q++) sum += g.bb[q] * Rs[(size_t)q * slot + o];
+          sum += g.bb[s - 1] * r;
+          a.b.accS[(size_t)c * ((size_t)g.nS_r * g.pitch) + row_off] = a.b.qA[o] + g.dt * sum;
+        }
+      }
+      return;
+    }
     if (k >= g.n1_r) {
       // fast region: m Heun substeps of dt/m
       if (!(st & 1)) {

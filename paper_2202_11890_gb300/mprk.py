@@ -36,6 +36,9 @@ MPRK_WALL_NOSLIP = 0
 MPRK_WALL_SLIP = 1
 MPRK_X_PERIODIC = 0
 MPRK_X_WALLS = 1
+MPRK_BASE_RK2 = 0
+MPRK_BASE_RK3 = 1
+MPRK_BASE_RK4 = 2
 MPRK_HOST = 0
 MPRK_DEVICE = 1
 
@@ -51,7 +54,7 @@ class mprk_config(C.Structure):
         ("diag_every", C.c_int), ("x_walls", C.c_int),
         ("dt", C.c_double), ("cfl", C.c_double), ("dx", C.c_double), ("dz1", C.c_double),
         ("dz2", C.c_double), ("gamma", C.c_double), ("Pr", C.c_double), ("mu1", C.c_double),
-        ("mu2", C.c_double), ("G", C.c_double), ("ny", C.c_int), ("dy", C.c_double),
+        ("mu2", C.c_double), ("G", C.c_double), ("ny", C.c_int), ("base", C.c_int), ("dy", C.c_double),
     ]
 
     @property
@@ -222,7 +225,7 @@ def mprk_rhs(h: int, W, R, k_lo: int, k_hi: int) -> None:
 
 def mprk_profile_step(h: int):
     """Per-launch durations (ms) and cell-stages of one un-captured slow step."""
-    cap = 2 * 64 + 1
+    cap = 4 * 64 + 1
     ms = np.zeros(cap)
     cells = np.zeros(cap, dtype=np.int64)
     n = lib().mprk_profile_step(C.c_void_p(h), ms.ctypes.data_as(C.POINTER(C.c_double)),

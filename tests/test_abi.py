@@ -44,7 +44,8 @@ def test_invalid_configs_are_rejected_without_a_device(lib):
     from paper_2202_11890_gb300 import mprk as M
     q = np.ones((4, 12, 8))
     cases = [dict(nz_B=3), dict(nz_B=2), dict(m=0), dict(nx=3), dict(precision=7),
-             dict(scheme=9), dict(wall=5), dict(dt=-1.0), dict(mu1=0.0), dict(x_walls=2)]
+             dict(scheme=9), dict(wall=5), dict(dt=-1.0), dict(mu1=0.0), dict(x_walls=2), dict(base=3),
+             dict(base=2, precision=1), dict(base=1, ny=4)]
     for over in cases:
         base = dict(nx=8, nz_S=4, nz_B=4, nz_F=4, m=2)
         geo = {k: over.pop(k) for k in list(over) if k in base}
@@ -65,3 +66,22 @@ def test_config_default_matches_the_paper_constants(lib):
     assert cfg.gamma == 1.4 and cfg.Pr == 0.72
     assert cfg.mu1 == 1.0 / 20000 and cfg.mu2 == 1.0 / 5000
     assert cfg.G == 0.008140864714 and cfg.dx == 10.0 / 64
+
+
+def test_python_config_layout_matches_the_header(tmp_path):
+    """Every field of the ctypes mirror sits at the offset the C compiler
+    gives the header's struct, and the sizes agree."""
+    import subprocess
+    from paper_2202_11890_gb300 import mprk as M
+    names = [f[0] for f in M.mprk_config._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join(f'  printf("%s %zu\\n", "{n}", offsetof(mprk_config, {n}));\n' for n in names)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "mprk.h"\nint main(void) {\n' + body +
+                   '  printf("sizeof %zu\\n", sizeof(mprk_config));\n  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for n in names:
+        assert int(got[n]) == getattr(M.mprk_config, n).offset, n
+    assert int(got["sizeof"]) == C.sizeof(M.mprk_config)
