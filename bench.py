@@ -52,8 +52,8 @@ CSRC = os.path.join(ROOT, "paper_2202_11890_gb300", "csrc")
 TRAFFIC = {
     "stage_kernel": {
         "files": ("stage_tile.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "e05c30d7ae781d6b69fa8f3147d1ff62280ccabbbc388581c35d171fd84f5b1c",
-        "bytes_per_step": 1169889536,
+        "sha256": "020a1b55a3b48228f1655a8392c6cf3c7e65067d9d98d7c3e6364b4e7b3320db",
+        "bytes_per_step": 1175056384,
     },
     "stage_kernel_mixed": {
         "files": ("stage_tile_mixed.cuh", "mprk_internal.h", "mprk_kernels.cu"),
