@@ -307,9 +307,9 @@ def run_ours(args):
 
 def run_batched(args):
     """256 uneven instances (sides log-uniform in [64, 512], m in {2, 4, 8},
-    buffer 4-16 rows, FP64): one persistent launch per slow step
-    (mprk_step_batch) against the same instances stepped one after another
-    with mprk_step on the same stream."""
+    buffer 4-16 rows, FP64, or FP32 flux with --precision fp32flux): one
+    persistent launch per slow step (mprk_step_batch) against the same
+    instances stepped one after another with mprk_step on the same stream."""
     import torch
     from paper_2202_11890_gb300 import build as B
     from paper_2202_11890_gb300 import mprk as M
@@ -325,6 +325,8 @@ def run_batched(args):
     for wl in wls:
         g = wl.grid
         cfg = M.mprk_config_default(g.nx, g.nS, g.nB, g.nF, wl.m)
+        if args.precision == "fp32flux":
+            cfg.precision = M.MPRK_FP32FLUX
         q0 = wl.initial_state()
         q0s.append(q0)
         insts.append(M.Instance(cfg, q0, stream=sp))
@@ -357,8 +359,12 @@ def run_batched(args):
     for i, q0 in zip(insts[:8], q0s[:8]):
         i.set_state(q0)
         i.step(2)
+    maxrel = 0.0
     for i, ob in zip(insts[:8], out_b):
-        same = same and bool(np.array_equal(i.state(), ob))
+        op = i.state()
+        same = same and bool(np.array_equal(op, ob))
+        scale = np.abs(ob).max(axis=(1, 2))
+        maxrel = max(maxrel, float((np.abs(op - ob).max(axis=(1, 2)) / scale).max()))
     value = cs * args.steps / (t_batch * 1e-3)
     plain_value = cs * args.steps / (t_plain * 1e-3)
     for i in insts:
@@ -366,12 +372,14 @@ def run_batched(args):
     out = {
         "metric": METRIC, "value": value, "unit": "cell-stages/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": f"batched_{len(wls)}_uneven_fp64", "instances": len(wls), "cells": cells,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 flux / f64 accumulate" if args.precision == "fp32flux" else "f64", "data": "synthetic",
+        "config": {"workload": f"batched_{len(wls)}_uneven_{args.precision or 'fp64'}", "instances": len(wls),
+                   "cells": cells,
                    "cell_stages_per_step": cs, "parallelism": "replicas x1"},
         "batched_vs_plain": {"batched": value, "plain_sequential": plain_value,
                              "speedup": value / plain_value, "bitwise_equal": same,
+                             "max_rel_diff": maxrel,
                              "plain_ms_per_step": t_plain / args.steps},
         "gpu_launches": args.steps,
         "clocks": sampler.summary(),

@@ -40,9 +40,15 @@ struct BatchInst {
 struct BatchItem {
   int inst;
   int stage;  // 0 .. 2m-1, or 2m for a completion item
-  int tile;   // tile index of the stage, or chunk index of the completion
+  int tile;   // first tile of the stage, or first chunk of the completion
+  int count;  // consecutive tiles (chunks) the item covers
   int need;   // items of the previous stage this one waits for (0: none)
 };
+
+// Tiles per work item. An FP32-flux tile takes a few microseconds, about
+// what an item's scheduling costs (counter, wait, barriers, argument copy),
+// so four tiles share one item; FP64 tiles take an item each.
+constexpr int batch_group(int prec) { return prec == 0 ? 2 : 8; }
 
 struct BatchArgs {
   const BatchInst* insts;
@@ -104,6 +110,9 @@ __global__ void __launch_bounds__(batch_threads(PREC), 2) batch_kernel(const Bat
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
   __shared__ int s_ok;
+  // the item's stage arguments, one copy for the CTA: the tile reads its
+  // launch constants from shared memory instead of a per-thread local copy
+  __shared__ StageArgs s_a;
   cuda::atomic_ref<int, cuda::thread_scope_device> nxt(*A.next);
   for (;;) {
     if (threadIdx.x == 0) s_item = nxt.fetch_add(1, cuda::memory_order_relaxed);
@@ -117,15 +126,20 @@ __global__ void __launch_bounds__(batch_threads(PREC), 2) batch_kernel(const Bat
       if (item.need > 0) s_ok = wait_for(A, I.counter_base + item.stage - 1, item.need) ? 1 : 0;
       else if (*(volatile int*)A.abort_flag) s_ok = 0;
       if (!s_ok) atomicOr(I.status, ST_TIMEOUT);  // this instance's step is incomplete
+      else if (item.stage < 2 * I.g.m) s_a = stage_args(I.g, I.b, item.stage);
     }
     __syncthreads();
     if (s_ok) {
       if (item.stage < 2 * I.g.m) {
-        const StageArgs a = stage_args(I.g, I.b, item.stage);
-        if (PREC == 0) stage_tile<double, double>(a, item.tile, *reinterpret_cast<TileSmem<double>*>(smem_raw));
-        else stage_tile_mixed(a, item.tile, *reinterpret_cast<MixedTileSmem*>(smem_raw));
+        for (int t = 0; t < item.count; t++) {
+          if (t > 0) __syncthreads();  // the previous tile is done with shared memory
+          if (PREC == 0)
+            stage_tile<double, double>(s_a, item.tile + t, *reinterpret_cast<TileSmem<double>*>(smem_raw));
+          else
+            stage_tile_mixed(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
+        }
       } else {
-        finalize_chunk(I.g, I.b, item.tile);
+        for (int t = 0; t < item.count; t++) finalize_chunk(I.g, I.b, item.tile + t);
       }
     }
     __syncthreads();  // the tile's writes are done; shared memory is free again
@@ -184,6 +198,36 @@ void free_plan(Plan* p) {
 
 namespace {
 
+// The stage-major work list: all first-stage items of all instances, then
+// all second-stage items, ...; each instance's completion items follow its
+// last stage. Items group batch_group(precision) consecutive tiles.
+void build_items(const std::vector<BatchInst>& hinst, int precision, std::vector<BatchItem>& items,
+                 long long* cell_stages) {
+  const int G = batch_group(precision);
+  int max_stages = 0;
+  for (const BatchInst& bi : hinst) max_stages = std::max(max_stages, 2 * bi.g.m);
+  long long cs = 0;
+  items.clear();
+  for (int st = 0; st <= max_stages; st++) {
+    for (int j = 0; j < (int)hinst.size(); j++) {
+      const Geom& g = hinst[j].g;
+      const int ms = 2 * g.m;
+      if (st > ms) continue;
+      auto ntiles = [&](int s) {
+        if (s < ms) return stage_tiles(stage_args(g, hinst[j].b, s));
+        const int rows = ((g.m & 1) || hinst[j].b.dA) ? g.nz : g.n1_r;
+        const long long total = 4LL * rows * g.nx;
+        return (int)((total + FIN_CHUNK - 1) / FIN_CHUNK);
+      };
+      const int nt = ntiles(st);
+      const int need = st == 0 ? 0 : (ntiles(st - 1) + G - 1) / G;
+      for (int t = 0; t < nt; t += G) items.push_back({j, st, t, std::min(G, nt - t), need});
+      if (st < ms) cs += (long long)(g.nz - stage_args(g, hinst[j].b, st).row0) * g.nx;
+    }
+  }
+  *cell_stages = cs;
+}
+
 int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, int wi, int ws,
                cudaStream_t stream, Plan** out) {
   Plan* p = new Plan();
@@ -192,7 +236,6 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
   p->withhold_stage = ws;
   std::vector<BatchInst> hinst(count);
   unsigned* status = nullptr;
-  int max_stages = 0;
   for (int j = 0; j < count; j++) {
     cudaStream_t s;
     unsigned* st;
@@ -215,28 +258,10 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
     hinst[j].precision = prec;
     hinst[j].counter_base = p->n_counters;
     p->n_counters += 2 * hinst[j].g.m + 1;
-    max_stages = std::max(max_stages, 2 * hinst[j].g.m);
     p->key.push_back(insts[j]);
   }
-  // stage-major work list; completion items follow each instance's last stage
   std::vector<BatchItem> items;
-  for (int st = 0; st <= max_stages; st++) {
-    for (int j = 0; j < count; j++) {
-      const Geom& g = hinst[j].g;
-      const int ms = 2 * g.m;
-      if (st > ms) continue;
-      auto ntiles = [&](int s) {
-        if (s < ms) return stage_tiles(stage_args(g, hinst[j].b, s));
-        const int rows = ((g.m & 1) || hinst[j].b.dA) ? g.nz : g.n1_r;
-        const long long total = 4LL * rows * g.nx;
-        return (int)((total + FIN_CHUNK - 1) / FIN_CHUNK);
-      };
-      const int nt = ntiles(st);
-      const int need = st == 0 ? 0 : ntiles(st - 1);
-      for (int t = 0; t < nt; t++) items.push_back({j, st, t, need});
-      if (st < ms) p->cell_stages += (long long)(g.nz - stage_args(g, hinst[j].b, st).row0) * g.nx;
-    }
-  }
+  build_items(hinst, p->precision, items, &p->cell_stages);
   p->n_items = (int)items.size();
   cudaError_t e;
   if ((e = cudaMalloc(&p->d_insts, sizeof(BatchInst) * count)) != cudaSuccess ||
@@ -422,7 +447,7 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
   for (int j = 0; j < count && same; j++) same = r->key[j] == insts[j];
   if (!same) {
     std::vector<BatchInst> hinst(count);
-    int max_stages = 0, n_counters = 0;
+    int n_counters = 0;
     for (int j = 0; j < count; j++) {
       cudaStream_t s;
       unsigned* st;
@@ -436,27 +461,11 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
       hinst[j].precision = prec;
       hinst[j].counter_base = n_counters;
       n_counters += 2 * hinst[j].g.m + 1;
-      max_stages = std::max(max_stages, 2 * hinst[j].g.m);
       if (j == 0) r->status = st;
     }
     std::vector<BatchItem> items;
     long long cs = 0;
-    for (int st = 0; st <= max_stages; st++) {
-      for (int j = 0; j < count; j++) {
-        const Geom& g = hinst[j].g;
-        const int ms = 2 * g.m;
-        if (st > ms) continue;
-        auto ntiles = [&](int s) {
-          if (s < ms) return stage_tiles(stage_args(g, hinst[j].b, s));
-          const int rows = ((g.m & 1) || hinst[j].b.dA) ? g.nz : g.n1_r;
-          return (int)((4LL * rows * g.nx + FIN_CHUNK - 1) / FIN_CHUNK);
-        };
-        const int nt = ntiles(st);
-        const int need = st == 0 ? 0 : ntiles(st - 1);
-        for (int t = 0; t < nt; t++) items.push_back({j, st, t, need});
-        if (st < ms) cs += (long long)(g.nz - stage_args(g, hinst[j].b, st).row0) * g.nx;
-      }
-    }
+    build_items(hinst, r->precision, items, &cs);
     cudaError_t e = grow(&r->d_insts, &r->cap_insts, (size_t)count, r->stream);
     if (e == cudaSuccess) e = grow(&r->d_items, &r->cap_items, items.size(), r->stream);
     if (e == cudaSuccess) e = grow(&r->d_ctr, &r->cap_ctr, (size_t)(2 + n_counters), r->stream);
