@@ -16,9 +16,9 @@
 namespace mprk {
 
 // GEN: the general s-stage base (RK3, RK4) in place of Heun's low-storage
-// combination.
+// combination. Three CTAs per SM: 80 registers, a few spilled in the tile.
 template <typename Real, typename Store, bool GEN = false>
-__global__ void __launch_bounds__(NTHREADS, 2)
+__global__ void __launch_bounds__(NTHREADS, 3)
     stage_kernel(const StageArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   TileSmem<Real>& S = *reinterpret_cast<TileSmem<Real>*>(smem_raw);
