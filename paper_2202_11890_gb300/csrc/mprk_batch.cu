@@ -105,9 +105,10 @@ __device__ __forceinline__ void finalize_chunk(const Geom& g, const Bufs& b, int
   }
 }
 
-// three FP64 CTAs per SM (80 registers), two FP32-flux ones
+// three CTAs per SM in both precisions (80 and 72 registers; the FP32-flux
+// form spills some, and still runs faster than at two CTAs)
 template <int PREC>
-__global__ void __launch_bounds__(batch_threads(PREC), PREC == 0 ? 3 : 2) batch_kernel(const BatchArgs A) {
+__global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
   __shared__ int s_ok;
