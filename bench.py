@@ -367,6 +367,20 @@ def run_batched(args):
         maxrel = max(maxrel, float((np.abs(op - ob).max(axis=(1, 2)) / scale).max()))
     value = cs * args.steps / (t_batch * 1e-3)
     plain_value = cs * args.steps / (t_plain * 1e-3)
+    # roofline of the whole batched launch (stage tiles and completions)
+    fp64 = args.precision != "fp32flux"
+    peaks, src = measured_peaks()
+    if fp64:
+        ach = cs * FLOPS_PER_CELL_STAGE[True] * args.steps / (t_batch * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": ach / FP64_PEAK_GFLOPS, "traffic": None,
+                "peak_source": "FP64 unit count x max clock (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
+    else:
+        nbytes = sum(sum(algorithmic_bytes(wl.grid, wl.m, False)) for wl in wls)
+        ach = nbytes * args.steps / (t_batch * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                "algorithmic_bytes_per_step": nbytes}
     for i in insts:
         i.close()
     out = {
@@ -381,6 +395,7 @@ def run_batched(args):
                              "speedup": value / plain_value, "bitwise_equal": same,
                              "max_rel_diff": maxrel,
                              "plain_ms_per_step": t_plain / args.steps},
+        "roofline": roof,
         "gpu_launches": args.steps,
         "clocks": sampler.summary(),
     }
@@ -407,7 +422,8 @@ def run_served(args):
         g = wl.grid
         cfg = M.mprk_config_default(g.nx, g.nS, g.nB, g.nF, wl.m)
         cfg.precision = M.MPRK_FP32FLUX
-        reqs.append((cfg, wl.initial_state(), wl.steps, wl.cell_stages_per_step() * wl.steps))
+        reqs.append((cfg, wl.initial_state(), wl.steps, wl.cell_stages_per_step() * wl.steps,
+                     sum(algorithmic_bytes(g, wl.m, False)) * wl.steps))
     srv = M.mprk_server_create(hbm_budget_bytes=int(args.budget_gb * 1e9), max_slots=args.slots)
     sampler = ClockSampler(torch.cuda.current_device())
     tickets = {}
@@ -418,7 +434,7 @@ def run_served(args):
         while len(done) < len(reqs):
             now = time.perf_counter() - t0
             while nxt < len(reqs) and arrivals[nxt] <= now:
-                cfg, q, n, _ = reqs[nxt]
+                cfg, q, n, _, _ = reqs[nxt]
                 tickets[M.mprk_submit(srv, cfg, q, n)] = nxt
                 nxt += 1
             for t, j in list(tickets.items()):
@@ -439,6 +455,8 @@ def run_served(args):
     cells = sum(reqs[j][3] for j in range(n_warm, len(reqs)))
     value = cells / (t_last - t_first)
     offered = sum(r[3] for r in reqs) / arrivals[-1]
+    peaks, src = measured_peaks()
+    gbs = sum(reqs[j][4] for j in range(n_warm, len(reqs))) / (t_last - t_first) / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": "cell-stages/s", "n_gpus": ws,
         "steps": n_meas, "warmup": n_warm, "ms_per_step": None, "higher_is_better": True,
@@ -449,6 +467,9 @@ def run_served(args):
         "served": {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                    "mean_latency_s": float(lat.mean()), "errors": errors, "offered_cell_stages_per_s": offered,
                    "batched_steps": sstats[2], "wall_s": wall},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                     "note": "algorithmic bytes of the measured requests over their first submit to last finish"},
         "gpu_launches": int(sstats[2]),
         "clocks": sampler.summary(),
     }
@@ -806,9 +827,27 @@ def cpu_baseline(wl: W.Workload, cols: int = 512, budget_s: float = 10.0, max_st
         total += cnt
         steps += 1
     dt = time.perf_counter() - t0
-    return {"value": total / dt, "unit": "cell-stages/s", "cores": O.get_threads(), "kind": "oracle",
-            "sample": f"{steps} slow steps of the {wl.name} rows on a {cols}-column strip "
-                      f"({total} cell-stages, {dt:.1f} s)"}
+    out = {"value": total / dt, "unit": "cell-stages/s", "cores": O.get_threads(), "kind": "oracle",
+           "sample": f"{steps} slow steps of the {wl.name} rows on a {cols}-column strip "
+                     f"({total} cell-stages, {dt:.1f} s)"}
+    # the same oracle on one thread, on a narrower strip
+    O.set_threads(1)
+    s1 = oracle_sample(wl, 64)
+    g1 = s1.grid
+    q1 = s1.initial_state()
+    P1 = O.make_problem(g1.nx, g1.nS, g1.nB, g1.nF, s1.m, P.dt, g1.dx, dz1=g1.dz1, dz2=g1.dz2)
+    t0 = time.perf_counter()
+    total1, steps1 = 0, 0
+    while steps1 < max_steps and (time.perf_counter() - t0) < budget_s / 2:
+        q1, cnt = O.mprk_step(P1, q1, 1)
+        total1 += cnt
+        steps1 += 1
+    dt1 = time.perf_counter() - t0
+    O.set_threads(cores)
+    out["single_thread"] = {"value": total1 / dt1, "unit": "cell-stages/s", "cores": 1,
+                            "sample": f"{steps1} slow steps on a 64-column strip ({total1} cell-stages, "
+                                      f"{dt1:.1f} s)"}
+    return out
 
 
 def run_reference(args):
