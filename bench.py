@@ -125,6 +125,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device: str) -> float:
+    """The largest x over the ranks of the default process group (x itself
+    without one): the job's time is its slowest replica's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, ranks: int, seconds: float) -> float:
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed over the slowest rank's time."""
+    return units_per_rank * ranks / seconds
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -231,11 +249,8 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_ms = float(t.item())
-    value = cs * args.steps * ws / (t_ms * 1e-3)
+    t_ms = max_over_ranks(t_ms, "cuda")
+    value = replica_value(cs * args.steps, ws, t_ms * 1e-3)
 
     # dominant kernel: average duration of one stage launch (events on the
     # instance stream around each launch of one un-captured slow step)
@@ -258,14 +273,16 @@ def run_ours(args):
     pin_out = torch.empty_like(pin_in).pin_memory()
     e2e_steps = max(3, min(args.steps, 20))
     torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         M.mprk_set_state(inst.h, pin_in)
         M.mprk_step(inst.h, 1)
         M.mprk_get_state(inst.h, pin_out)
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
     nbytes = q0.nbytes
-    e2e_value = cs * e2e_steps * ws / e2e_s
+    e2e_value = replica_value(cs * e2e_steps, ws, e2e_s)
     inst.close()
 
     if rank == 0:
@@ -911,8 +928,11 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    ws, rank, _ = dist_env()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload not in ("large_2048", "plain_64", "mixed_4096") and rank != 0:
+        return  # the other workloads are single-GPU studies: rank 0 runs them alone
     elif args.workload == "batched_256":
         run_batched(args)
     elif args.workload == "served":
