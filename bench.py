@@ -359,8 +359,14 @@ def run_batched(args):
     def batched(n):
         M.mprk_step_batch(hs, n)
 
-    # warm-up both paths (graphs, plan)
+    # warm-up both paths (graphs, plan), the default launch, then the tuned
+    # one (mprk_batch_tune restores the states it advances)
+    M.mprk_tune_clear()
     plain(args.warmup)
+    batched(args.warmup)
+    torch.cuda.synchronize()
+    t_default = T.time_region(sp, lambda: batched(args.steps))
+    tune = M.mprk_batch_tune(hs, reps=3)
     batched(args.warmup)
     torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device())
@@ -410,8 +416,9 @@ def run_batched(args):
                    "cell_stages_per_step": cs, "parallelism": "replicas x1"},
         "batched_vs_plain": {"batched": value, "plain_sequential": plain_value,
                              "speedup": value / plain_value, "bitwise_equal": same,
-                             "max_rel_diff": maxrel,
-                             "plain_ms_per_step": t_plain / args.steps},
+                             "max_rel_diff": maxrel, "plain_ms_per_step": t_plain / args.steps,
+                             "default_launch": cs * args.steps / (t_default * 1e-3)},
+        "tuned_launch": {**tune, "defaults": "2 FP64 or 8 FP32-flux tiles per item, all CTAs that fit"},
         "roofline": roof,
         "gpu_launches": args.steps,
         "clocks": sampler.summary(),

@@ -149,6 +149,35 @@ int mprk_step(mprk_instance* inst, int n_slow_steps);
  * in batched steps. Errors: MPRK_EINVAL, MPRK_ENOMEM, MPRK_ECUDA. */
 int mprk_step_batch(mprk_instance* const* insts, int count, int n_slow_steps);
 
+/* ---- launch tuning ------------------------------------------------------
+ * Two choices of the batched launch change no result, only its speed: the
+ * stage tiles per work item (1, 2, 4, 8 or 16) and the CTAs per SM (1 to 3).
+ * A process-wide table keeps, per precision and size bucket (floor(log2) of
+ * the mean cells per instance), the fastest pair measured; batches without
+ * an entry use 2 (FP64) or 8 (FP32 flux) tiles per item and every CTA that
+ * fits. mprk_step_batch and the server read the table when they build a
+ * work list. */
+
+/* Time every choice on these instances (reps batched slow steps each after
+ * one warm-up step), record the fastest in the table and return it in out:
+ * {tiles per item, CTAs per SM, ms per slow step}. The instances' states and
+ * step counts are restored afterwards. Synchronises. Errors: MPRK_EINVAL,
+ * MPRK_ENOMEM, MPRK_ECUDA. */
+int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out[3]);
+
+/* The table's choice for a precision and a mean instance size in cells:
+ * writes it and returns 1, or writes the defaults (ctas_per_sm 0: every CTA
+ * that fits) and returns 0. Needs no device. */
+int mprk_tune_lookup(int precision, double mean_cells, int* group, int* ctas_per_sm);
+
+/* Save the table to a JSON file, {"gpu": <device name>, "entries": [...]}, or
+ * replace it from one. Loading a table measured on a GPU of another name
+ * fails with MPRK_EINVAL when a device is present. mprk_tune_clear empties
+ * the table. No device is needed to save or clear. */
+int mprk_tune_save(const char* path);
+int mprk_tune_load(const char* path);
+int mprk_tune_clear(void);
+
 /* Test hook for the bounded waits of mprk_step_batch: one batched slow step
  * in which the tiles of stage `stage` of instance inst_index never report
  * completion, and each wait gives up after wait_cycles clock cycles. The

@@ -16,8 +16,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <fstream>
 #include <map>
+#include <sstream>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -45,9 +49,10 @@ struct BatchItem {
   int need;   // items of the previous stage this one waits for (0: none)
 };
 
-// Tiles per work item. An FP32-flux tile takes a few microseconds, about
-// what an item's scheduling costs (counter, wait, barriers, argument copy),
-// so four tiles share one item; FP64 tiles take an item each.
+// Default tiles per work item. An FP32-flux tile takes a few microseconds,
+// about what an item's scheduling costs (counter, wait, barriers, argument
+// copy), so eight tiles share one item; FP64 tiles go two to an item.
+// mprk_batch_tune may pick others per size bucket.
 constexpr int batch_group(int prec) { return prec == 0 ? 2 : 8; }
 
 struct BatchArgs {
@@ -165,6 +170,10 @@ namespace {
 struct Plan {
   std::vector<const void*> key;
   int precision = 0;
+  int bucket = 0;      // size bucket of the instance set (tuning key)
+  int group = 0;       // tiles per work item
+  int per_sm = 0;      // CTAs per SM of the persistent launch
+  int per_sm_req = 0;  // CTAs per SM asked for (0: as many as fit)
   int n_items = 0;
   int n_counters = 0;
   int grid = 0;
@@ -180,6 +189,51 @@ struct Plan {
 
 std::mutex g_batch_mu;
 std::vector<Plan*> g_plans;
+
+// ---- launch tuning ---------------------------------------------------------
+// Two choices of the persistent launch change no result: the tiles per work
+// item and the CTAs per SM. The table holds, per precision and size bucket
+// (floor(log2) of the mean cells per instance), the fastest pair
+// mprk_batch_tune measured, with the name of the GPU it ran on. Plans
+// without an entry take the defaults (batch_group tiles, every CTA that fits).
+struct TuneVal {
+  int group, per_sm;
+  double ms;
+};
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, TuneVal> g_tune;
+std::string g_tune_gpu;
+
+int size_bucket(const std::vector<BatchInst>& hinst) {
+  double cells = 0;
+  for (const BatchInst& bi : hinst) cells += (double)bi.g.nx * bi.g.nz;
+  const double mean = hinst.empty() ? 1.0 : cells / hinst.size();
+  return std::max(0, std::min(40, (int)std::floor(std::log2(std::max(mean, 1.0)))));
+}
+
+// The tuned (group, per_sm) of a precision and bucket, or the defaults
+// (per_sm 0: as many as fit).
+void tuned_choice(int prec, int bucket, int* group, int* per_sm) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find({prec, bucket});
+  if (it != g_tune.end()) {
+    *group = it->second.group;
+    *per_sm = it->second.per_sm;
+  } else {
+    *group = batch_group(prec);
+    *per_sm = 0;
+  }
+}
+
+std::string device_name() {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "";
+  }
+  return prop.name;
+}
 
 int bfail(int code, const std::string& msg) {
   set_last_error(msg);
@@ -202,10 +256,9 @@ namespace {
 
 // The stage-major work list: all first-stage items of all instances, then
 // all second-stage items, ...; each instance's completion items follow its
-// last stage. Items group batch_group(precision) consecutive tiles.
-void build_items(const std::vector<BatchInst>& hinst, int precision, std::vector<BatchItem>& items,
+// last stage. Items group G consecutive tiles.
+void build_items(const std::vector<BatchInst>& hinst, int G, std::vector<BatchItem>& items,
                  long long* cell_stages) {
-  const int G = batch_group(precision);
   int max_stages = 0;
   for (const BatchInst& bi : hinst) max_stages = std::max(max_stages, 2 * bi.g.m);
   long long cs = 0;
@@ -230,8 +283,9 @@ void build_items(const std::vector<BatchInst>& hinst, int precision, std::vector
   *cell_stages = cs;
 }
 
+// group / per_sm: the launch choices, or 0 for the tuned (else default) ones.
 int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, int wi, int ws,
-               cudaStream_t stream, Plan** out) {
+               cudaStream_t stream, int group, int per_sm_want, Plan** out) {
   Plan* p = new Plan();
   p->wait_cycles = wait_cycles;
   p->withhold_inst = wi;
@@ -262,8 +316,11 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
     p->n_counters += 2 * hinst[j].g.m + 1;
     p->key.push_back(insts[j]);
   }
+  p->bucket = size_bucket(hinst);
+  if (group <= 0) tuned_choice(p->precision, p->bucket, &group, &per_sm_want);
+  p->group = group;
   std::vector<BatchItem> items;
-  build_items(hinst, p->precision, items, &p->cell_stages);
+  build_items(hinst, group, items, &p->cell_stages);
   p->n_items = (int)items.size();
   cudaError_t e;
   if ((e = cudaMalloc(&p->d_insts, sizeof(BatchInst) * count)) != cudaSuccess ||
@@ -294,6 +351,9 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
     return bfail(MPRK_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e) + ", " +
                                  std::to_string(per_sm) + " blocks per SM");
   }
+  p->per_sm_req = per_sm_want;
+  if (per_sm_want > 0) per_sm = std::min(per_sm, per_sm_want);
+  p->per_sm = per_sm;
   p->grid = std::min(per_sm * sms, p->n_items);
   // capture: reset the counters, then the persistent launch
   BatchArgs A;
@@ -327,15 +387,25 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
   return MPRK_OK;
 }
 
+// A cached plan for this instance set whose launch choice is still the
+// tuned one (a plan built before a tuning run is rebuilt).
 Plan* find_plan(mprk_instance* const* insts, int count, long long wait_cycles, int wi, int ws,
                 cudaStream_t stream) {
-  for (Plan* p : g_plans) {
+  for (size_t k = 0; k < g_plans.size(); k++) {
+    Plan* p = g_plans[k];
     if ((int)p->key.size() != count || p->wait_cycles != wait_cycles || p->withhold_inst != wi ||
         p->withhold_stage != ws || (stream && p->stream != stream))
       continue;
     bool same = true;
     for (int j = 0; j < count && same; j++) same = p->key[j] == insts[j];
-    if (same) return p;
+    if (!same) continue;
+    int group, per_sm;
+    tuned_choice(p->precision, p->bucket, &group, &per_sm);
+    if (group == p->group && per_sm == p->per_sm_req) return p;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    free_plan(p);
+    g_plans.erase(g_plans.begin() + k);
+    return nullptr;
   }
   return nullptr;
 }
@@ -349,7 +419,7 @@ int step_batch(mprk_instance* const* insts, int count, int n, long long wait_cyc
   std::lock_guard<std::mutex> lk(g_batch_mu);
   Plan* p = find_plan(insts, count, wait_cycles, wi, ws, stream);
   if (!p) {
-    int rc = build_plan(insts, count, wait_cycles, wi, ws, stream, &p);
+    int rc = build_plan(insts, count, wait_cycles, wi, ws, stream, 0, 0, &p);
     if (rc) return rc;
     if (g_plans.size() >= 64) {
       free_plan(g_plans.front());
@@ -407,7 +477,7 @@ struct BatchRunner {
   BatchItem* d_items = nullptr;
   int* d_ctr = nullptr;
   size_t cap_insts = 0, cap_items = 0, cap_ctr = 0;
-  int n_items = 0, n_counters = 0, grid = 0, per_sm = 0;
+  int n_items = 0, n_counters = 0, grid = 0, per_sm = 0, sms = 0;
   long long cell_stages = 0;
   unsigned* status = nullptr;
 };
@@ -465,9 +535,11 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
       n_counters += 2 * hinst[j].g.m + 1;
       if (j == 0) r->status = st;
     }
+    int group, per_sm_want;
+    tuned_choice(r->precision, size_bucket(hinst), &group, &per_sm_want);
     std::vector<BatchItem> items;
     long long cs = 0;
-    build_items(hinst, r->precision, items, &cs);
+    build_items(hinst, group, items, &cs);
     cudaError_t e = grow(&r->d_insts, &r->cap_insts, (size_t)count, r->stream);
     if (e == cudaSuccess) e = grow(&r->d_items, &r->cap_items, items.size(), r->stream);
     if (e == cudaSuccess) e = grow(&r->d_ctr, &r->cap_ctr, (size_t)(2 + n_counters), r->stream);
@@ -484,9 +556,9 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
     r->cell_stages = cs;
     if (r->per_sm == 0) {
       const size_t smem = stage_smem_bytes(r->precision);
-      int dev = 0, sms = 0;
+      int dev = 0;
       cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaDeviceGetAttribute(&r->sms, cudaDevAttrMultiProcessorCount, dev);
       if (r->precision == 0) {
         e = cudaFuncSetAttribute(batch_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r->per_sm, batch_kernel<0>, batch_threads(0), smem);
@@ -495,8 +567,8 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r->per_sm, batch_kernel<1>, batch_threads(1), smem);
       }
       if (e != cudaSuccess || r->per_sm < 1) return bfail(MPRK_ECUDA, "batch runner: occupancy query failed");
-      r->grid = r->per_sm * sms;
     }
+    r->grid = (per_sm_want > 0 ? std::min(per_sm_want, r->per_sm) : r->per_sm) * r->sms;
   }
   BatchArgs A;
   A.insts = r->d_insts;
@@ -547,6 +619,173 @@ extern "C" {
 int mprk_step_batch(mprk_instance* const* insts, int count, int n_slow_steps) {
   // about one second at 2 GHz per wait
   return step_batch(insts, count, n_slow_steps, 2000000000LL, -1, -1, nullptr, nullptr);
+}
+
+int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out[3]) {
+  if (!insts || count <= 0 || reps < 1 || !out) return bfail(MPRK_EINVAL, "bad tuning arguments");
+  // the runs advance the states: keep them (and the step counts) to restore
+  std::vector<std::vector<double>> saved(count);
+  std::vector<long long> steps(count);
+  for (int j = 0; j < count; j++) {
+    if (!insts[j]) return bfail(MPRK_EINVAL, "NULL instance in batch");
+    Geom g;
+    Bufs b;
+    int prec;
+    cudaStream_t st;
+    unsigned* sw;
+    int rc = instance_view(insts[j], &g, &b, &prec, &st, &sw);
+    if (rc) return rc;
+    saved[j].resize((size_t)4 * g.nz * g.ny * g.nx);
+    if ((rc = mprk_get_state(insts[j], saved[j].data(), MPRK_HOST))) return rc;
+    steps[j] = instance_steps(insts[j]);
+  }
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  int best_g = 0, best_c = 0, prec = 0, bucket = 0;
+  double best_ms = 1e300;
+  int rc = MPRK_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = bfail(MPRK_ECUDA, "event create");
+  for (int G : {1, 2, 4, 8, 16}) {
+    for (int c = 1; c <= 3 && rc == MPRK_OK; c++) {
+      Plan* p = nullptr;
+      rc = build_plan(insts, count, 2000000000LL, -1, -1, nullptr, G, c, &p);
+      if (rc) break;
+      prec = p->precision;
+      bucket = p->bucket;
+      if (p->per_sm < c) {  // more CTAs than fit
+        free_plan(p);
+        continue;
+      }
+      cudaGraphLaunch(p->exec, p->stream);  // warm-up
+      cudaEventRecord(e0, p->stream);
+      for (int k = 0; k < reps; k++) cudaGraphLaunch(p->exec, p->stream);
+      cudaEventRecord(e1, p->stream);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        rc = bfail(MPRK_ECUDA, "tuning run failed");
+      free_plan(p);
+      if (rc == MPRK_OK && ms / reps < best_ms) {
+        best_ms = ms / reps;
+        best_g = G;
+        best_c = c;
+      }
+    }
+    if (rc) break;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  for (int j = 0; j < count; j++) {
+    const int r2 = mprk_set_state(insts[j], saved[j].data(), MPRK_HOST);
+    if (!rc) rc = r2;
+    instance_count_steps(insts[j], (int)(steps[j] - instance_steps(insts[j])));
+  }
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> tl(g_tune_mu);
+    g_tune[{prec, bucket}] = TuneVal{best_g, best_c, best_ms};
+    g_tune_gpu = device_name();
+  }
+  out[0] = best_g;
+  out[1] = best_c;
+  out[2] = best_ms;
+  return MPRK_OK;
+}
+
+int mprk_tune_lookup(int precision, double mean_cells, int* group, int* ctas_per_sm) {
+  if (!group || !ctas_per_sm || precision < 0 || precision > 1 || !(mean_cells >= 1.0))
+    return bfail(MPRK_EINVAL, "bad tuning lookup");
+  const int bucket = std::max(0, std::min(40, (int)std::floor(std::log2(mean_cells))));
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find({precision, bucket});
+  if (it == g_tune.end()) {
+    *group = batch_group(precision);
+    *ctas_per_sm = 0;
+    return 0;
+  }
+  *group = it->second.group;
+  *ctas_per_sm = it->second.per_sm;
+  return 1;
+}
+
+int mprk_tune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+  g_tune_gpu.clear();
+  return MPRK_OK;
+}
+
+int mprk_tune_save(const char* path) {
+  if (!path) return bfail(MPRK_EINVAL, "NULL path");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::string gpu;
+  for (char ch : g_tune_gpu) {
+    if (ch == '"' || ch == '\\') gpu += '\\';
+    gpu += ch;
+  }
+  std::ofstream f(path);
+  if (!f) return bfail(MPRK_EINVAL, std::string("cannot write ") + path);
+  f << "{\"gpu\": \"" << gpu << "\", \"entries\": [";
+  bool first = true;
+  char buf[256];
+  for (const auto& kv : g_tune) {
+    snprintf(buf, sizeof buf, "%s\n  {\"precision\": %d, \"bucket\": %d, \"group\": %d, \"ctas_per_sm\": %d, \"ms\": %.6g}",
+             first ? "" : ",", kv.first.first, kv.first.second, kv.second.group, kv.second.per_sm, kv.second.ms);
+    f << buf;
+    first = false;
+  }
+  f << "\n]}\n";
+  return f.good() ? MPRK_OK : bfail(MPRK_EINVAL, std::string("write failed: ") + path);
+}
+
+int mprk_tune_load(const char* path) {
+  if (!path) return bfail(MPRK_EINVAL, "NULL path");
+  std::ifstream f(path);
+  if (!f) return bfail(MPRK_EINVAL, std::string("cannot read ") + path);
+  std::stringstream ss;
+  ss << f.rdbuf();
+  const std::string t = ss.str();
+  // the GPU name: the string after "gpu":
+  size_t k = t.find("\"gpu\"");
+  if (k == std::string::npos || (k = t.find('"', t.find(':', k) + 1)) == std::string::npos)
+    return bfail(MPRK_EINVAL, "tuning file: no gpu name");
+  std::string gpu;
+  for (size_t j = k + 1; j < t.size() && t[j] != '"'; j++) {
+    if (t[j] == '\\' && j + 1 < t.size()) j++;
+    gpu += t[j];
+  }
+  const std::string here = device_name();
+  if (!here.empty() && gpu != here)
+    return bfail(MPRK_EINVAL, "tuning file measured on " + gpu + ", this device is " + here);
+  auto num = [&](const std::string& obj, const char* key, double* v) {
+    const size_t a = obj.find(std::string("\"") + key + "\"");
+    if (a == std::string::npos) return false;
+    const size_t c = obj.find(':', a);
+    if (c == std::string::npos) return false;
+    char* end = nullptr;
+    *v = strtod(obj.c_str() + c + 1, &end);
+    return end != obj.c_str() + c + 1;
+  };
+  std::map<std::pair<int, int>, TuneVal> table;
+  size_t pos = t.find("\"entries\"");
+  if (pos == std::string::npos) return bfail(MPRK_EINVAL, "tuning file: no entries");
+  for (;;) {
+    const size_t a = t.find('{', pos), b = a == std::string::npos ? a : t.find('}', a);
+    if (a == std::string::npos || b == std::string::npos) break;
+    const std::string obj = t.substr(a, b - a + 1);
+    double pr, bu, gr, ct, ms = 0.0;
+    if (!num(obj, "precision", &pr) || !num(obj, "bucket", &bu) || !num(obj, "group", &gr) ||
+        !num(obj, "ctas_per_sm", &ct))
+      return bfail(MPRK_EINVAL, "tuning file: incomplete entry");
+    num(obj, "ms", &ms);
+    if ((pr != 0 && pr != 1) || bu < 0 || bu > 40 || gr < 1 || gr > 64 || ct < 0 || ct > 8)
+      return bfail(MPRK_EINVAL, "tuning file: value out of range");
+    table[{(int)pr, (int)bu}] = TuneVal{(int)gr, (int)ct, ms};
+    pos = b + 1;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.swap(table);
+  g_tune_gpu = gpu;
+  return MPRK_OK;
 }
 
 int mprk_batch_test_withhold(mprk_instance* const* insts, int count, int inst_index, int stage,

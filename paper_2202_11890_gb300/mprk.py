@@ -122,6 +122,11 @@ def lib():
         "mprk_step_batch": (ip, [C.POINTER(vp), ip, ip]),
         "mprk_batch_test_withhold": (ip, [C.POINTER(vp), ip, ip, ip, C.c_longlong]),
         "mprk_selftest_convert": (ip, [vp, ip, vp, vp, vp, vp]),
+        "mprk_batch_tune": (ip, [C.POINTER(vp), ip, ip, dp]),
+        "mprk_tune_lookup": (ip, [ip, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "mprk_tune_save": (ip, [C.c_char_p]),
+        "mprk_tune_load": (ip, [C.c_char_p]),
+        "mprk_tune_clear": (ip, []),
         "mprk_server_create": (ip, [C.POINTER(mprk_server_config), C.POINTER(vp)]),
         "mprk_submit": (ip, [vp, cfgp, vp, ip, C.POINTER(C.c_uint64)]),
         "mprk_poll": (ip, [vp, C.c_uint64, C.POINTER(C.c_int), vp, C.POINTER(mprk_stats)]),
@@ -255,6 +260,34 @@ def mprk_selftest_convert(x_dev, narrow, narrow_hw, widen, widen_hw) -> None:
     _check(lib().mprk_selftest_convert(C.c_void_p(x_dev.data_ptr()), int(x_dev.numel()),
                                        C.c_void_p(narrow.data_ptr()), C.c_void_p(narrow_hw.data_ptr()),
                                        C.c_void_p(widen.data_ptr()), C.c_void_p(widen_hw.data_ptr())))
+
+
+def mprk_batch_tune(handles, reps: int = 3) -> dict:
+    """Time the batched launch choices on these instances; the fastest goes
+    to the table and is returned."""
+    out = (C.c_double * 3)()
+    _check(lib().mprk_batch_tune(_handles(handles), len(handles), int(reps), out))
+    return {"tiles_per_item": int(out[0]), "ctas_per_sm": int(out[1]), "ms_per_step": float(out[2])}
+
+
+def mprk_tune_lookup(precision: int, mean_cells: float):
+    g, c = C.c_int(), C.c_int()
+    rc = lib().mprk_tune_lookup(int(precision), float(mean_cells), C.byref(g), C.byref(c))
+    if rc < 0:
+        raise MprkError(rc, mprk_last_error())
+    return {"tiles_per_item": g.value, "ctas_per_sm": c.value, "tuned": bool(rc)}
+
+
+def mprk_tune_save(path: str) -> None:
+    _check(lib().mprk_tune_save(str(path).encode()))
+
+
+def mprk_tune_load(path: str) -> None:
+    _check(lib().mprk_tune_load(str(path).encode()))
+
+
+def mprk_tune_clear() -> None:
+    _check(lib().mprk_tune_clear())
 
 
 MPRK_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024

@@ -85,3 +85,31 @@ def test_python_config_layout_matches_the_header(tmp_path):
     for n in names:
         assert int(got[n]) == getattr(M.mprk_config, n).offset, n
     assert int(got["sizeof"]) == C.sizeof(M.mprk_config)
+
+
+def test_tuning_table_round_trip_without_a_device(lib, tmp_path):
+    """The launch-tuning table loads from JSON, answers lookups by size
+    bucket (floor log2 of the mean cells), saves the same entries back, and
+    rejects out-of-range values; none of it needs a GPU."""
+    from paper_2202_11890_gb300 import mprk as M
+    M.mprk_tune_clear()
+    assert M.mprk_tune_lookup(1, 5000.0) == {"tiles_per_item": 8, "ctas_per_sm": 0, "tuned": False}
+    assert M.mprk_tune_lookup(0, 5000.0)["tiles_per_item"] == 2
+    src = tmp_path / "t.json"
+    src.write_text('{"gpu": "", "entries": [\n'
+                   ' {"precision": 1, "bucket": 12, "group": 4, "ctas_per_sm": 2, "ms": 1.5},\n'
+                   ' {"precision": 0, "bucket": 16, "group": 1, "ctas_per_sm": 3, "ms": 9}\n]}\n')
+    M.mprk_tune_load(str(src))
+    assert M.mprk_tune_lookup(1, 5000.0) == {"tiles_per_item": 4, "ctas_per_sm": 2, "tuned": True}  # 2^12 <= 5000
+    assert M.mprk_tune_lookup(1, 9000.0)["tuned"] is False                                            # bucket 13
+    assert M.mprk_tune_lookup(0, 70000.0) == {"tiles_per_item": 1, "ctas_per_sm": 3, "tuned": True}
+    out = tmp_path / "u.json"
+    M.mprk_tune_save(str(out))
+    M.mprk_tune_clear()
+    M.mprk_tune_load(str(out))
+    assert M.mprk_tune_lookup(0, 70000.0)["tiles_per_item"] == 1
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"gpu": "", "entries": [{"precision": 1, "bucket": 12, "group": 0, "ctas_per_sm": 2}]}')
+    with pytest.raises(M.MprkError):
+        M.mprk_tune_load(str(bad))
+    M.mprk_tune_clear()

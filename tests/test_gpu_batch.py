@@ -117,3 +117,40 @@ def test_batch_rejects_mixed_precisions():
     finally:
         ia.close()
         ib.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tuned_launch_leaves_states_and_results_unchanged(precision, tmp_path):
+    """mprk_batch_tune restores every state and step count it advanced, its
+    choice lands in the table (and in a saved file keyed by this GPU's
+    name), and batched steps with the tuned launch equal those with the
+    default launch bitwise: the choice moves work, not arithmetic."""
+    from paper_2202_11890_gb300 import mprk as M
+    M.mprk_tune_clear()
+    cases = uneven(6, 11 + precision, precision)
+    a = [M.Instance(cfg, q) for cfg, P, q in cases]
+    b = [M.Instance(cfg, q) for cfg, P, q in cases]
+    try:
+        M.mprk_step_batch([i.h for i in b], 2)  # default launch
+        before = [i.state() for i in a]
+        best = M.mprk_batch_tune([i.h for i in a], reps=2)
+        assert best["tiles_per_item"] in (1, 2, 4, 8, 16) and 1 <= best["ctas_per_sm"] <= 3
+        assert best["ms_per_step"] > 0
+        for i, q in zip(a, before):
+            assert np.array_equal(i.state(), q) and i.info()["cell_stages_per_step"] > 0
+        mean = np.mean([c.nx * (c.nz_S + c.nz_B + c.nz_F) for c, P, q in cases])
+        look = M.mprk_tune_lookup(precision, mean)
+        assert look["tuned"] and look["tiles_per_item"] == best["tiles_per_item"]
+        M.mprk_step_batch([i.h for i in a], 2)  # tuned launch
+        for x, y in zip(a, b):
+            assert np.array_equal(x.state(), y.state())
+        path = tmp_path / "tune.json"
+        M.mprk_tune_save(str(path))
+        assert torch.cuda.get_device_name(0) in path.read_text()
+        M.mprk_tune_clear()
+        M.mprk_tune_load(str(path))
+        assert M.mprk_tune_lookup(precision, mean) == look
+    finally:
+        for i in a + b:
+            i.close()
+        M.mprk_tune_clear()
