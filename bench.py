@@ -52,13 +52,13 @@ CSRC = os.path.join(ROOT, "paper_2202_11890_gb300", "csrc")
 TRAFFIC = {
     "stage_kernel": {
         "files": ("stage_tile.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "020a1b55a3b48228f1655a8392c6cf3c7e65067d9d98d7c3e6364b4e7b3320db",
-        "bytes_per_step": 1175056384,
+        "sha256": "057e9e9c62fbc53a9e239965a3cc4f9879802246093c7d4e5d3954f0f6630edd",
+        "bytes_per_step": 1192898048,
     },
     "stage_kernel_mixed": {
         "files": ("stage_tile_mixed.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "3e5d5c025b6de49b323530dea2c9ac3d1048fc3345099d967940b58a06433ec9",
-        "bytes_per_step": 5211695616,
+        "sha256": "06a0f40b7d6f3322798dc211a5042c9894ba47c4583c363e1d41addefbea4114",
+        "bytes_per_step": 5197837056,
     },
 }
 
