@@ -17,12 +17,14 @@ namespace mprk {
 
 // GEN: the general s-stage base (RK3, RK4) in place of Heun's low-storage
 // combination. Three CTAs per SM: 80 registers, a few spilled in the tile.
-template <typename Real, typename Store, bool GEN = false>
-__global__ void __launch_bounds__(NTHREADS, 3)
+// NT = 2 NTHREADS: two threads per cell for launches of few tiles (one CTA
+// per SM).
+template <typename Real, typename Store, bool GEN = false, int NT = NTHREADS>
+__global__ void __launch_bounds__(NT, NT == NTHREADS ? 3 : 1)
     stage_kernel(const StageArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   TileSmem<Real>& S = *reinterpret_cast<TileSmem<Real>*>(smem_raw);
-  stage_tile<Real, Store, GEN>(a, blockIdx.x, S);
+  stage_tile<Real, Store, GEN, NT>(a, blockIdx.x, S);
 }
 
 // FP32-flux stage kernel: one CTA per tile, blockIdx = (tile column, tile
@@ -86,6 +88,12 @@ cudaError_t prepare_kernels() {
   e = cudaFuncSetAttribute(stage_kernel<double, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(TileSmem<double>));
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(stage_kernel<double, double, false, 2 * NTHREADS>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem<double>));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(stage_kernel<double, double, true, 2 * NTHREADS>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem<double>));
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(yface3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(YfaceSmem));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(stage3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Tile3Smem));
@@ -134,10 +142,32 @@ cudaError_t make_stage_maps(const Geom& g, const Bufs& b, StageMaps* out) {
   return cudaSuccess;
 }
 
+namespace {
+// SMs of the current device (queried once per device)
+int sm_count() {
+  static int counts[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (counts[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    counts[dev] = n;
+  }
+  return counts[dev];
+}
+}  // namespace
+
 cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStream_t stream,
                          const StageMaps* maps) {
   if (n_tiles <= 0) return cudaSuccess;
-  if (precision == 0 && a.g.gen) {
+  // a launch of no more tiles than SMs runs two threads per cell
+  constexpr int WIDE = 2 * NTHREADS;
+  const bool wide = precision == 0 && n_tiles <= sm_count();
+  if (wide && a.g.gen) {
+    stage_kernel<double, double, true, WIDE><<<n_tiles, WIDE, sizeof(TileSmem<double>), stream>>>(a);
+  } else if (wide) {
+    stage_kernel<double, double, false, WIDE><<<n_tiles, WIDE, sizeof(TileSmem<double>), stream>>>(a);
+  } else if (precision == 0 && a.g.gen) {
     stage_kernel<double, double, true><<<n_tiles, NTHREADS, sizeof(TileSmem<double>), stream>>>(a);
   } else if (precision == 0) {
     stage_kernel<double, double><<<n_tiles, NTHREADS, sizeof(TileSmem<double>), stream>>>(a);

@@ -145,7 +145,12 @@ __device__ __forceinline__ double gen_stage_value(const Geom& g, const double* b
 // GEN selects the general s-stage base method (Sec. 3 remark) in place of
 // Heun's low-storage path: s R_a slots, the stage values of the region
 // tableaus built from the base, and its weights b in the combinations.
-template <typename Real, typename Store, bool GEN = false>
+// NT: threads of the CTA. NTHREADS gives one thread per cell; launches with
+// fewer tiles than the GPU has SMs take 2 NTHREADS, so that each SM holds
+// more warps of the few tiles there are: every phase but the last spreads
+// its work over all threads, and the last (one cell per thread) uses the
+// first NTHREADS.
+template <typename Real, typename Store, bool GEN = false, int NT = NTHREADS>
 __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int tile,
                                        TileSmem<Real>& __restrict__ S) {
   // __restrict__: the argument block and shared memory never alias, so its
@@ -164,7 +169,7 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
   const double hF = g.hF;
 
   // ---- 1. stage state of the tile and its halo --------------------------
-  for (int e = tid; e < 4 * (TZ + 4) * (TX + 4); e += NTHREADS) {
+  for (int e = tid; e < 4 * (TZ + 4) * (TX + 4); e += NT) {
     const int c = e / ((TZ + 4) * (TX + 4));
     const int rem = e - c * ((TZ + 4) * (TX + 4));
     const int rr = rem / (TX + 4), cc = rem - rr * (TX + 4);
@@ -197,7 +202,7 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
 
   // ---- 2. u, w, T on the one-cell ring; interface state -----------------
   const Real gamma = (Real)g.gamma, gm1 = (Real)g.gm1;
-  for (int e = tid; e < (TZ + 2) * (TX + 2); e += NTHREADS) {
+  for (int e = tid; e < (TZ + 2) * (TX + 2); e += NT) {
     const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
     const int k = k0 - 1 + rr;
     if (k < 0 || k >= nz) continue;
@@ -258,7 +263,7 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
   const Real quarter = Real(0.25);
   const Real hinv_dx = Real(0.5) * (Real)g.inv_dx;
   // (a) quarter x differences of q on tile rows, cols i0-1 .. i0+TX
-  for (int e = tid; e < TZ * (TX + 2); e += NTHREADS) {
+  for (int e = tid; e < TZ * (TX + 2); e += NT) {
     const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
     if (k0 + rr >= row_hi) continue;
 #pragma unroll
@@ -280,7 +285,7 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
     S.tz[1][rr][cc] = (wu - wd) * hinv_dz;
   }
   // (b) quarter z differences of q on ring rows k0-1 .. k0+TZ, tile cols
-  for (int e = tid; e < (TZ + 2) * TX; e += NTHREADS) {
+  for (int e = tid; e < (TZ + 2) * TX; e += NT) {
     const int rr = e / TX, cc = e - rr * TX;
     const int k = k0 - 1 + rr;
     if (k < 0 || k >= nz) continue;
@@ -304,7 +309,7 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
   // faces. Every warp sees one face kind.
   const Real mu1 = (Real)g.mu1, mu2 = (Real)g.mu2, kap1 = (Real)g.kap1, kap2 = (Real)g.kap2;
   constexpr int NZF = (TZ + 1) * TX, NXF = TZ * (TX + 1);
-  for (int e = tid; e < NZF + NXF; e += NTHREADS) {
+  for (int e = tid; e < NZF + NXF; e += NT) {
     Real F[4];
     if (e < NZF) {
       const int f = e / TX, cc = e - f * TX;
@@ -410,7 +415,7 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
   {
     const int rr = tid / TX, cc = tid - rr * TX;
     const int k = k0 + rr, i = i0 + cc;
-    if (k >= row_hi || i >= nx) return;
+    if (rr >= TZ || k >= row_hi || i >= nx) return;
     const Real inv_dx = (Real)g.inv_dx;
     const Real inv_dz = (Real)(k < n1 ? g.inv_dz1 : g.inv_dz2);
     const bool under_gamma = (k == n1 - 1);
