@@ -94,18 +94,19 @@ __device__ __forceinline__ void finalize_chunk(const Geom& g, const Bufs& b, int
   const int m_odd = g.m & 1;
   const bool mixed = b.dA != nullptr;
   const int rows = (m_odd || mixed) ? g.nz : g.n1_r;
-  const long long total = 4LL * rows * g.nx;
+  const long long per_c = (long long)rows * g.nx;  // elements of one component (< 2^31)
+  const long long total = 4LL * per_c;
   for (long long e = (long long)chunk * FIN_CHUNK + threadIdx.x; e < total && e < (long long)(chunk + 1) * FIN_CHUNK;
        e += blockDim.x) {
-    const int c = (int)(e / ((long long)rows * g.nx));
-    const int rem = (int)(e - (long long)c * rows * g.nx);
+    const int c = (e >= per_c) + (e >= 2 * per_c) + (e >= 3 * per_c);
+    const int rem = (int)(e - c * per_c);
     const int k = rem / g.nx, i = rem - k * g.nx;
     const size_t o = ((size_t)c * g.nz + k) * g.pitch + i;
     double v;
     if (k < g.nS_r) v = b.accS[((size_t)c * g.nS_r + k) * g.pitch + i];
     else if (k < g.n1_r) v = b.accB[((size_t)c * (g.n1_r - g.nS_r) + (k - g.nS_r)) * g.pitch + i];
     else v = m_odd ? b.qB[o] : b.qA[o];
-    b.qA[o] = v;
+    if (k < g.n1_r || m_odd) b.qA[o] = v;  // F rows after an even m hold q_{n+1} already
     if (mixed) b.dA[o] = narrow(v - (double)b.rowc[4 * k + c]);
   }
 }

@@ -8,6 +8,8 @@
 
 #include <cstring>
 
+#include <algorithm>
+
 #include "mprk_internal.h"
 #include "stage_tile.cuh"
 #include "stage_tile3d.cuh"
@@ -302,35 +304,36 @@ cudaError_t launch_shadow(const Geom& g, const double* q, const float* rowc, flo
 // ---------------------------------------------------------------------------
 // An x-row r of a component is (k, j) with r = k ny + j (ny = 1 in 2-D);
 // the buffers' rows of the S and B bands are numbered the same way.
+// One row of one component per block row: blockIdx.z the component,
+// rows r = blockIdx.y + n gridDim.y (r = k ny + j, k the z row), threads
+// over x. F rows after an even m already hold q_{n+1} in qA and only
+// refresh the float shadow.
 __global__ void finalize_kernel(const Geom g, const Bufs b, int m_odd) {
   const bool mixed = b.dA != nullptr;
   const int rows = (m_odd || mixed) ? g.nz : g.n1_r;
-  const long long xrows = (long long)rows * g.ny;
-  const long long total = (long long)g.nc * xrows * g.nx;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(e / (xrows * g.nx));
-    const long long rem = e - (long long)c * xrows * g.nx;
-    const int r = (int)(rem / g.nx), i = (int)(rem - (long long)r * g.nx);
+  const int c = blockIdx.z;
+  for (int r = blockIdx.y; r < rows * g.ny; r += gridDim.y) {
     const int k = r / g.ny;
-    const size_t o = ((size_t)c * g.nz * g.ny + r) * g.pitch + i;
-    double v;
-    if (k < g.nS_r) v = b.accS[((size_t)c * g.nS_r * g.ny + r) * g.pitch + i];
-    else if (k < g.n1_r)
-      v = b.accB[((size_t)c * (g.n1_r - g.nS_r) * g.ny + (r - (size_t)g.nS_r * g.ny)) * g.pitch + i];
-    else v = m_odd ? b.qB[o] : b.qA[o];
-    b.qA[o] = v;
-    if (mixed) b.dA[o] = narrow(v - (double)b.rowc[4 * k + c]);
+    const size_t o = ((size_t)c * g.nz * g.ny + r) * g.pitch;
+    const double* src;
+    if (k < g.nS_r) src = b.accS + ((size_t)c * g.nS_r * g.ny + r) * g.pitch;
+    else if (k < g.n1_r) src = b.accB + ((size_t)c * (g.n1_r - g.nS_r) * g.ny + (r - (size_t)g.nS_r * g.ny)) * g.pitch;
+    else src = (m_odd ? b.qB : b.qA) + o;
+    const bool store_q = k < g.n1_r || m_odd;
+    const double ref = mixed ? (double)b.rowc[4 * k + c] : 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nx; i += gridDim.x * blockDim.x) {
+      const double v = src[i];
+      if (store_q) b.qA[o + i] = v;
+      if (mixed) b.dA[o + i] = narrow(v - ref);
+    }
   }
 }
 
 cudaError_t launch_finalize(const Geom& g, const Bufs& b, int m_odd, cudaStream_t stream) {
   const int rows = (m_odd || b.dA != nullptr) ? g.nz : g.n1_r;
   if (rows == 0) return cudaSuccess;
-  const long long total = (long long)g.nc * rows * g.ny * g.nx;
-  int blocks = (int)((total + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  finalize_kernel<<<blocks, 256, 0, stream>>>(g, b, m_odd);
+  const dim3 grid((g.nx + 255) / 256, (unsigned)std::min(rows * g.ny, 65535), (unsigned)g.nc);
+  finalize_kernel<<<grid, 256, 0, stream>>>(g, b, m_odd);
   return cudaGetLastError();
 }
 
