@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const Bat
           if (PREC == 0)
             stage_tile<double, double>(s_a, item.tile + t, *reinterpret_cast<TileSmem<double>*>(smem_raw));
           else
-            stage_tile_mixed(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
+            stage_tile_mixed<PAR_RT>(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
         }
       } else {
         for (int t = 0; t < item.count; t++) finalize_chunk(I.g, I.b, item.tile + t);

@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(NT, NT == NTHREADS ? 3 : 1)
 // row). An interior tile away from the x wrap has its float planes
 // tensor-copied (TMA) into shared memory: one thread issues the copies at
 // the start, and the row constants are fetched while they fly.
+template <int PAR>
 __global__ void __launch_bounds__(MIXED_THREADS, 3)
     stage_kernel_mixed(const StageArgs a, const __grid_constant__ CUtensorMap tm_sb,
                        const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_ra) {
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(MIXED_THREADS, 3)
     stage_issue(a, k0, i0, S.stg, &S.bar, &tm_sb, &tm_f, &tm_ra);
   }
   if (staged) __syncthreads();  // the mbarrier is initialised before anyone waits on it
-  if (!stage_tile_mixed(a, k0, i0, S.work, staged ? &S.stg : nullptr, &S.bar)) {
+  if (!stage_tile_mixed<PAR>(a, k0, i0, S.work, staged ? &S.stg : nullptr, &S.bar)) {
     // a tensor copy never completed within the bound: flag it, give the
     // copies one more bounded wait, and leave
     if (threadIdx.x == 0 && a.status) atomicOr(a.status, ST_TIMEOUT);
@@ -100,8 +101,13 @@ cudaError_t prepare_kernels() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(stage3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Tile3Smem));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(stage_kernel_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(MixedKernelSmem));
+  // one FP32-flux kernel per stage parity, and one that reads it (and the
+  // right-hand-side hook) from its arguments
+  for (auto k : {stage_kernel_mixed<0>, stage_kernel_mixed<1>, stage_kernel_mixed<PAR_RT>}) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MixedKernelSmem));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 namespace {
@@ -183,7 +189,13 @@ cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStr
     const CUtensorMap& f = staged ? (a.dF == a.b.dA ? maps->dA : maps->dB) : none;
     const CUtensorMap& ra = staged ? maps->Ra : none;
     const dim3 grid(a.tiles_x, n_tiles / a.tiles_x);
-    stage_kernel_mixed<<<grid, MIXED_THREADS, mixed_kernel_smem(a.stage & 1), stream>>>(s, sb, f, ra);
+    const size_t smem = mixed_kernel_smem(a.stage & 1);
+    if (a.rhs_only)
+      stage_kernel_mixed<PAR_RT><<<grid, MIXED_THREADS, smem, stream>>>(s, sb, f, ra);
+    else if (a.stage & 1)
+      stage_kernel_mixed<1><<<grid, MIXED_THREADS, smem, stream>>>(s, sb, f, ra);
+    else
+      stage_kernel_mixed<0><<<grid, MIXED_THREADS, smem, stream>>>(s, sb, f, ra);
   }
   return cudaGetLastError();
 }

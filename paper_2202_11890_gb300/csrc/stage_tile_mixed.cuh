@@ -311,15 +311,29 @@ __device__ __forceinline__ void z_face3(MixedSmem& S, const Geom& g, int k0, int
   }
 }
 
+// PAR: a launch's stage parity when the kernel is compiled for it (0 even,
+// 1 odd), or PAR_RT to read the parity and the right-hand-side hook from the
+// arguments at run time (the batch kernel's callers pick 0 or 1 too).
+constexpr int PAR_RT = 2;
+template <int PAR>
+__device__ __forceinline__ bool rhs_mode(const StageArgs& a) {
+  return PAR == PAR_RT ? a.rhs_only != 0 : false;
+}
+template <int PAR>
+__device__ __forceinline__ bool odd_mode(const StageArgs& a) {
+  return PAR == PAR_RT ? (!a.rhs_only && (a.stage & 1)) : PAR == 1;
+}
+
 // The general path on the TX x TZ cells from row k0, column i0.
+template <int PAR>
 __device__ __forceinline__ void mixed_subtile(const StageArgs& a, int k0, int i0, MixedSmem& S) {
   const Geom& g = a.g;
   const int tid = threadIdx.x;
   const int ty = tid / TX, tx = tid - ty * TX;  // owned cell (warp 8: edge faces)
   const int nz = g.nz, nx = g.nx, n1 = g.n1;
-  const int row_hi = a.rhs_only ? a.rhs_hi : nz;
+  const int row_hi = rhs_mode<PAR>(a) ? a.rhs_hi : nz;
   const size_t plane = (size_t)nz * g.pitch;
-  const bool odd_stage = !a.rhs_only && (a.stage & 1);
+  const bool odd_stage = odd_mode<PAR>(a);
   const float* Ra = reinterpret_cast<const float*>(a.b.Ra);
   const float4* rowc = reinterpret_cast<const float4*>(a.b.rowc);
   const float gamma = g.gammaf, gm1 = g.gm1f;
@@ -335,7 +349,7 @@ __device__ __forceinline__ void mixed_subtile(const StageArgs& a, int k0, int i0
       const size_t off = (size_t)k * g.pitch + i;
       const float4 ra4 = rowc[k], rd4 = rowc[3 * nz + k];
       const float r0 = ra4.x, m0 = ra4.y, w0 = ra4.z;
-      if (a.rhs_only) {
+      if (rhs_mode<PAR>(a)) {
         val.x = narrow(a.rhs_in[off] - (double)r0);
         val.y = narrow((gh ? -a.rhs_in[plane + off] : a.rhs_in[plane + off]) - (double)m0);
         val.z = narrow(a.rhs_in[2 * plane + off] - (double)w0);
@@ -388,7 +402,7 @@ __device__ __forceinline__ void mixed_subtile(const StageArgs& a, int k0, int i0
 #pragma unroll
       for (int c = 0; c < 4; c++) {
         const size_t off = (size_t)c * plane + (size_t)k * g.pitch + i;
-        if (a.rhs_only) {
+        if (rhs_mode<PAR>(a)) {
           qq[c] = a.rhs_in[off];
         } else {
           const double* base = k < g.n1_r ? a.b.qA : a.qF;
@@ -463,7 +477,7 @@ __device__ __forceinline__ void mixed_subtile(const StageArgs& a, int k0, int i0
   R[3] -= (S.rcA[ty + 2].z + dc.z) * g.Gf;
 
   const size_t row_off = (size_t)k * g.pitch + i;
-  if (a.rhs_only) {
+  if (rhs_mode<PAR>(a)) {
 #pragma unroll
     for (int c = 0; c < 4; c++) a.rhs_out[(size_t)c * plane + row_off] = widen(R[c]);
     return;
@@ -472,7 +486,7 @@ __device__ __forceinline__ void mixed_subtile(const StageArgs& a, int k0, int i0
   const int st = a.stage;
   const double h2 = g.h2;
   if (k >= g.n1_r) {
-    if (!(st & 1)) {
+    if (!odd_stage) {
 #pragma unroll
       for (int c = 0; c < 4; c++) Ra_w[(size_t)c * plane + row_off] = R[c];
     } else {
@@ -492,7 +506,7 @@ __device__ __forceinline__ void mixed_subtile(const StageArgs& a, int k0, int i0
     for (int c = 0; c < 4; c++) {
       const size_t o = (size_t)c * plane + row_off;
       double* acc = a.b.accB + (size_t)c * pb + ob;
-      if (!(st & 1)) Ra_w[o] = R[c];
+      if (!odd_stage) Ra_w[o] = R[c];
       const double r = widen(R[c]);
       if (st == 0) *acc = r;
       else if (last) *acc = fma(h2, *acc + r, a.b.qA[o]);
@@ -772,6 +786,7 @@ __device__ __forceinline__ bool pair_interior(const StageArgs& a, int k0, int i0
 
 // Stage combination of one cell outside the F rows (B and S rows), the
 // general path's arithmetic with R in float.
+template <int PAR>
 __device__ __forceinline__ void combine_slow_cell(const StageArgs& a, int k, size_t row_off, const float R[4]) {
   const Geom& g = a.g;
   const size_t plane = (size_t)g.nz * g.pitch;
@@ -786,7 +801,7 @@ __device__ __forceinline__ void combine_slow_cell(const StageArgs& a, int k, siz
     for (int c = 0; c < 4; c++) {
       const size_t o = (size_t)c * plane + row_off;
       double* acc = a.b.accB + (size_t)c * pb + ob;
-      if (!(st & 1)) Ra_w[o] = R[c];
+      if (!odd_mode<PAR>(a)) Ra_w[o] = R[c];
       const double r = (double)R[c];
       if (st == 0) *acc = r;
       else if (last) *acc = fma(g.h2, *acc + r, a.b.qA[o]);
@@ -806,6 +821,7 @@ __device__ __forceinline__ void combine_slow_cell(const StageArgs& a, int k, siz
 // The pair path on the TX x MTZ interior tile from row k0, column i0. stg,
 // when not null, receives the tile's float planes by tensor copies that
 // complete on bar (phase 0). Returns false if the wait for them gave up.
+template <int PAR>
 __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, PairSmem& S, const Stage* stg,
                                           unsigned long long* bar) {
   const Geom& g = a.g;
@@ -837,7 +853,7 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
     const float* __restrict__ dsrc = f_rows ? a.dF : a.b.dA;
     const float* __restrict__ Ra = reinterpret_cast<const float*>(a.b.Ra);
     const float2 h = sp2(f_rows ? g.hFf : g.dtf);
-    const bool odd_stage = !a.rhs_only && (a.stage & 1);
+    const bool odd_stage = odd_mode<PAR>(a);
     // a thread stages pair rows r0 and r0 + 8 (the second only when r0 < 4);
     // every global load is issued before the arithmetic
     constexpr int RSTEP = MIXED_THREADS / HW;
@@ -868,7 +884,7 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
           for (int c = 0; c < 4; c++)
             d[e][c] = fma2(h, make_float2(stg->ra[c][r][cc + 2], stg->ra[c][r + TZ][cc + 2]), d[e][c]);
         }
-      } else if (a.rhs_only) {
+      } else if (rhs_mode<PAR>(a)) {
         const float refA[4] = {ref01[e].x, ref01[e].z, ref23[e].x, ref23[e].z};
         const float refB[4] = {ref01[e].y, ref01[e].w, ref23[e].y, ref23[e].w};
 #pragma unroll
@@ -939,7 +955,7 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
   const bool own = p < TZ && i < nx;
   const size_t offA = (size_t)kA * g.pitch + i, offB = offA + pstep;
   const int st = a.stage;
-  const bool f_odd = !a.rhs_only && kA >= g.n1_r && (st & 1);
+  const bool f_odd = odd_mode<PAR>(a) && kA >= g.n1_r;
   float2 ra[4], dfo[4];
   double qa[4], qb[4];
   if (own && f_odd) {
@@ -981,7 +997,7 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
   R[2] = add2(R[2], fma2(mG, lo2(dca), lo2(rowp[7 * nz + kA])));
   R[3] = fma2(mG, add2(lo2(rowp[nz + kA]), lo2(dcb)), R[3]);
 
-  if (a.rhs_only) {
+  if (rhs_mode<PAR>(a)) {
 #pragma unroll
     for (int c = 0; c < 4; c++) {
       a.rhs_out[c * plane + offA] = (double)R[c].x;
@@ -1011,8 +1027,8 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
     }
   } else {
     const float RA[4] = {R[0].x, R[1].x, R[2].x, R[3].x}, RB[4] = {R[0].y, R[1].y, R[2].y, R[3].y};
-    combine_slow_cell(a, kA, offA, RA);
-    combine_slow_cell(a, kA + TZ, offB, RB);
+    combine_slow_cell<PAR>(a, kA, offA, RA);
+    combine_slow_cell<PAR>(a, kA + TZ, offB, RB);
   }
   return true;
 }
@@ -1029,23 +1045,25 @@ union MixedTileSmem {
   PairSmem pair;
 };
 
+template <int PAR>
 __device__ __forceinline__ bool stage_tile_mixed(const StageArgs& a, int k0, int i0, MixedTileSmem& S,
                                                  const Stage* stg, unsigned long long* bar) {
-  if (pair_interior(a, k0, i0)) return pair_tile(a, k0, i0, S.pair, stg, bar);
-  mixed_subtile(a, k0, i0, S.gen);
-  const int hi = a.rhs_only ? a.rhs_hi : a.g.nz;
+  if (pair_interior(a, k0, i0)) return pair_tile<PAR>(a, k0, i0, S.pair, stg, bar);
+  mixed_subtile<PAR>(a, k0, i0, S.gen);
+  const int hi = rhs_mode<PAR>(a) ? a.rhs_hi : a.g.nz;
   if (k0 + TZ < hi) {
     __syncthreads();  // the first half's phase 3 reads shared memory
-    mixed_subtile(a, k0 + TZ, i0, S.gen);
+    mixed_subtile<PAR>(a, k0 + TZ, i0, S.gen);
   }
   return true;
 }
 
 // The same by linear tile index (row-major over tiles_x), without staging.
+template <int PAR>
 __device__ __forceinline__ void stage_tile_mixed(const StageArgs& a, int tile, MixedTileSmem& S) {
   const int tzi = tile / a.tiles_x;
   const int txi = tile - tzi * a.tiles_x;
-  (void)stage_tile_mixed(a, a.row0 + tzi * MTZ, txi * TX, S, nullptr, nullptr);
+  (void)stage_tile_mixed<PAR>(a, a.row0 + tzi * MTZ, txi * TX, S, nullptr, nullptr);
 }
 
 // Tiles whose float planes are tensor-copied: interior tiles of a stage
