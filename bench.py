@@ -52,13 +52,13 @@ CSRC = os.path.join(ROOT, "paper_2202_11890_gb300", "csrc")
 TRAFFIC = {
     "stage_kernel": {
         "files": ("stage_tile.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "057e9e9c62fbc53a9e239965a3cc4f9879802246093c7d4e5d3954f0f6630edd",
-        "bytes_per_step": 1192898048,
+        "sha256": "16e12dd343ffbec04af1315ab7ddd6a52bdb546c9060c0031433251155e592e2",
+        "bytes_per_step": 1191586304,
     },
     "stage_kernel_mixed": {
         "files": ("stage_tile_mixed.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "06a0f40b7d6f3322798dc211a5042c9894ba47c4583c363e1d41addefbea4114",
-        "bytes_per_step": 5197837056,
+        "sha256": "dbc7e7db5f488c98a33421819ea18b635bbd8dbe7cf61e9cb0904ee22611041c",
+        "bytes_per_step": 5195528448,
     },
 }
 
