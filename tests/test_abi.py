@@ -45,7 +45,11 @@ def test_invalid_configs_are_rejected_without_a_device(lib):
     q = np.ones((4, 12, 8))
     cases = [dict(nz_B=3), dict(nz_B=2), dict(m=0), dict(nx=3), dict(precision=7),
              dict(scheme=9), dict(wall=5), dict(dt=-1.0), dict(mu1=0.0), dict(x_walls=2), dict(base=3),
-             dict(base=2, precision=1), dict(base=1, ny=4)]
+             dict(base=2, precision=1), dict(base=1, ny=4), dict(m=65), dict(nz_S=1), dict(nz_F=1),
+             dict(ny=2), dict(ny=4, precision=1), dict(ny=4, x_walls=1), dict(ny=4, dy=0.0), dict(cfl=11.0),
+             dict(gamma=1.0), dict(G=-1.0), dict(diag_every=-1),
+             # the largest grid the ABI takes has 2^31 cells
+             dict(nx=65536, nz_S=16384, nz_F=16384)]
     for over in cases:
         base = dict(nx=8, nz_S=4, nz_B=4, nz_F=4, m=2)
         geo = {k: over.pop(k) for k in list(over) if k in base}

@@ -330,3 +330,21 @@ def test_fp32_flux_pair_path_in_every_band(m, wall):
     err = rel_err(q_gpu, q_or)
     print("fp32flux pair-path grid error per component:", err)
     assert np.all(err < 1e-5), err
+
+
+def test_both_fp64_launch_forms_in_one_step():
+    """512 x 96 cells with a thin buffer and fast band: the two full-row
+    stages launch 192 tiles (one thread per cell), the later B+F stages 32
+    tiles (more SMs than tiles, so two threads per cell). Three slow steps
+    within 1e-12 of the oracle, and bitwise equal to the batch kernel's."""
+    mp = M()
+    g = W.Grid(512, 80, 4, 12)
+    q = W.gaussian_bumps(g, 31, sigma_cells=3.0, amp=0.03)
+    cfg, P, dt = pair(g, 2, q0=q)
+    q_or, _ = O.mprk_step(P, q, 3)
+    with mp.Instance(cfg, q) as a, mp.Instance(cfg, q) as b:
+        a.step(3)
+        mp.mprk_step_batch([b.h], 3)
+        qa, qb = a.state(), b.state()
+    assert np.all(rel_err(qa, q_or) < 1e-12)
+    assert np.array_equal(qa, qb)
