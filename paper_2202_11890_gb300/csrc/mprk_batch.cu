@@ -2,11 +2,13 @@
 // persistent launch per slow step covers every instance's stage tiles and
 // step completions (mprk_step_batch).
 //
-// Work items (instance, stage, tile) are listed stage-major: all first-stage
-// tiles of all instances, then all second-stage tiles, and so on, with each
-// instance's completion items after its last stage. CTAs take items in list
-// order from one atomic counter. An item of stage s of instance I first waits
-// until every tile of stage s-1 of I has finished (a per-instance counter).
+// Work items (instance, stage, a run of consecutive tiles) are listed
+// stage-major: all first-stage items of all instances, then all second-stage
+// items, and so on, with each instance's completion items after its last
+// stage. CTAs take items in list order from one atomic counter. An item of
+// stage s of instance I first waits until every item of stage s-1 of I has
+// finished (a per-instance counter). The tiles per item and the CTAs per SM
+// come from a tuning table (mprk_batch_tune) or defaults.
 // Since items are taken in list order, every item an item waits on was taken
 // earlier by a CTA that is already running, so the waits always end. Waits
 // are bounded all the same: after a fixed number of clock cycles a CTA sets

@@ -1,9 +1,13 @@
 // mprk_kernels.cu — CUDA kernels of one MPRK2 slow step for sm_103a:
-//   stage_kernel    fused RHS + stage combination over the rows of one stage
-//   finalize_kernel moves q_{n+1} of the S and B rows (and of F rows after an
-//                   odd number of substeps) into the state buffer
-//   diag_*          deterministic monitoring reductions (Sec. 5.1 mass and
-//                   energy; Courant numbers; non-finite count)
+//   stage_kernel        FP64 fused RHS + stage combination over the rows of
+//                       one stage (one thread per cell, or two in launches
+//                       with fewer tiles than SMs; Heun or a general base)
+//   stage_kernel_mixed  the FP32-flux form, one instantiation per stage parity
+//   yface3_kernel, stage3_kernel  the 3-D model (App. B)
+//   finalize_kernel     moves q_{n+1} of the S and B rows (and of F rows after
+//                       an odd number of substeps) into the state buffer
+//   diag_*              deterministic monitoring reductions (Sec. 5.1 mass
+//                       and energy; Courant numbers; non-finite count)
 #include <cudaTypedefs.h>
 
 #include <cstring>
