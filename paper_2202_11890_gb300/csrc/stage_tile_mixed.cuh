@@ -818,6 +818,41 @@ __device__ __forceinline__ void combine_slow_cell(const StageArgs& a, int k, siz
   }
 }
 
+// One bulk L2 prefetch of bytes (a multiple of 16) from a 16-byte aligned
+// global address.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// L2 prefetch of the double rows that the stage combination of the tile's
+// rows k0 .. k0+MTZ-1, columns i0 .. i0+TX-1 will read after the tile's
+// second barrier: q_F (F rows, odd stages), the buffer accumulator (B rows,
+// every stage but the first) and q_n (S rows at the second stage, B rows at
+// the last). Thread t < 4 MTZ issues the 256-byte segment of row t / 4,
+// component t % 4; every segment is 256-byte aligned and inside its row's
+// pitch. Issued as the tile starts, so that those loads find L2. Only the
+// kernels compiled for one stage parity prefetch: in the batch kernel (the
+// run-time form, short of registers) it measured slower.
+template <int PAR>
+__device__ __forceinline__ void prefetch_combination(const StageArgs& a, int k0, int i0) {
+  const int t = threadIdx.x;
+  if (PAR == PAR_RT || t >= 4 * MTZ) return;
+  const Geom& g = a.g;
+  const int k = k0 + t / 4, c = t % 4;
+  if (k >= g.nz) return;
+  const size_t off = (size_t)c * g.nz * g.pitch + (size_t)k * g.pitch + i0;
+  const int st = a.stage;
+  if (k >= g.n1_r) {
+    if (odd_mode<PAR>(a)) prefetch_l2(a.qF + off, TX * 8);
+  } else if (k >= g.nS_r) {
+    if (st > 0)
+      prefetch_l2(a.b.accB + ((size_t)c * (g.n1_r - g.nS_r) + (k - g.nS_r)) * g.pitch + i0, TX * 8);
+    if (st == 2 * g.m - 1) prefetch_l2(a.b.qA + off, TX * 8);
+  } else if (st == 1) {
+    prefetch_l2(a.b.qA + off, TX * 8);
+  }
+}
+
 // The pair path on the TX x MTZ interior tile from row k0, column i0. stg,
 // when not null, receives the tile's float planes by tensor copies that
 // complete on bar (phase 0). Returns false if the wait for them gave up.
@@ -826,6 +861,7 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
                                           unsigned long long* bar) {
   const Geom& g = a.g;
   const int tid = threadIdx.x;
+  prefetch_combination<PAR>(a, k0, i0);
   const int nz = g.nz, nx = g.nx;
   const size_t plane = (size_t)nz * g.pitch;
   const size_t pstep = (size_t)TZ * g.pitch;  // row k -> row k + TZ
