@@ -583,6 +583,7 @@ struct PairSmem {
   float4 fza[TZ + 1][TX];  // z face fluxes (rho, rho u) below pair row p of the tile
   float4 fzb[TZ + 1][TX];  //               (rho w, rho E)
   float4 fxa[TZ], fxb[TZ]; // x face fluxes on the tile's right edge
+  float4 rc[8][PHR];       // paired row constants (groups RC_PAIR ..) of the halo pair rows
 };
 
 // ---- bulk copies and their mbarriers (PTX) -------------------------------
@@ -728,17 +729,16 @@ __device__ __forceinline__ void pair_x_face(const PairSmem& S, const PairConst& 
 }
 
 // z face below halo pair row hu (rows of pair row hu - 1 below it) in tile
-// column cc: writes fza / fzb [hu - 2][cc]. rowp points at the paired row
-// constants; kd is the A row below the face.
-__device__ __forceinline__ void pair_z_face(PairSmem& S, const PairConst& C, const float4* __restrict__ rowp,
-                                            int nz, int kd, int hu, int cc) {
+// column cc: writes fza / fzb [hu - 2][cc]. The paired row constants of both
+// pair rows come from S.rc.
+__device__ __forceinline__ void pair_z_face(PairSmem& S, const PairConst& C, int hu, int cc) {
   const int hd = hu - 1, c = cc + 2;
   const float2 q25 = sp2(0.25f);
-  const float4 ref01d = rowp[kd], ref23d = rowp[nz + kd], kpd = rowp[6 * nz + kd];
-  const float4 ref01u = rowp[kd + 1], ref23u = rowp[nz + kd + 1], kpu = rowp[6 * nz + kd + 1];
-  const float4 sb01d = rowp[2 * nz + kd], sb23d = rowp[3 * nz + kd];
-  const float4 sb01u = rowp[2 * nz + kd + 1], sb23u = rowp[3 * nz + kd + 1];
-  const float4 dc01 = rowp[4 * nz + kd], dc23 = rowp[5 * nz + kd];
+  const float4 ref01d = S.rc[0][hd], ref23d = S.rc[1][hd], kpd = S.rc[6][hd];
+  const float4 ref01u = S.rc[0][hu], ref23u = S.rc[1][hu], kpu = S.rc[6][hu];
+  const float4 sb01d = S.rc[2][hd], sb23d = S.rc[3][hd];
+  const float4 sb01u = S.rc[2][hu], sb23u = S.rc[3][hu];
+  const float4 dc01 = S.rc[4][hd], dc23 = S.rc[5][hd];
   const float4 am = S.qa[hd - 1][c], ad = S.qa[hd][c], au = S.qa[hu][c], ap = S.qa[hu + 1][c];
   const float4 bm = S.qb[hd - 1][c], bd = S.qb[hd][c], bu = S.qb[hu][c], bp = S.qb[hu + 1][c];
   // below the face: d + (d_up - d_down)/4 + the reference's quarter difference;
@@ -904,6 +904,12 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
       ref23[e] = rowp[nz + kA];
       kp[e] = rowp[6 * nz + kA];
     }
+    // the paired row constants of the halo pair rows, which the face and
+    // combination phases read from shared memory
+    if (tid < 8 * PHR) {
+      const int j = tid / PHR, r = tid - j * PHR;
+      S.rc[j][r] = rowp[j * nz + k0 - 2 + r];
+    }
     if (stg) ok = mbar_wait(bar, 0);  // the row constants above are in flight meanwhile
 #pragma unroll
     for (int e = 0; e < 2; e++) {
@@ -960,17 +966,15 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
   const int p = tid / TX, tx = tid - p * TX;  // pair row of the tile (warp 8: edges)
   float2 fxl[4];
   if (p < TZ) {
-    const int kA = k0 + p;
-    pair_z_face(S, C, rowp, nz, kA - 1, p + 2, tx);
-    pair_x_face(S, C, p + 2, tx, rowp[kA], rowp[nz + kA], rowp[6 * nz + kA], fxl);
+    pair_z_face(S, C, p + 2, tx);
+    pair_x_face(S, C, p + 2, tx, S.rc[0][p + 2], S.rc[1][p + 2], S.rc[6][p + 2], fxl);
   } else {
     // warp 8: the z faces below pair row TZ (its B half is the tile's top
     // face), then the x faces on the tile's right edge
-    pair_z_face(S, C, rowp, nz, k0 + TZ - 1, TZ + 2, tx);
+    pair_z_face(S, C, TZ + 2, tx);
     if (tx < TZ) {
-      const int kA = k0 + tx;
       float2 F[4];
-      pair_x_face(S, C, tx + 2, TX, rowp[kA], rowp[nz + kA], rowp[6 * nz + kA], F);
+      pair_x_face(S, C, tx + 2, TX, S.rc[0][tx + 2], S.rc[1][tx + 2], S.rc[6][tx + 2], F);
       S.fxa[tx] = cat2(F[0], F[1]);
       S.fxb[tx] = cat2(F[2], F[3]);
     }
@@ -990,7 +994,6 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
   const int i = i0 + tx;
   const bool own = p < TZ && i < nx;
   const size_t offA = (size_t)kA * g.pitch + i, offB = offA + pstep;
-  const int st = a.stage;
   const bool f_odd = odd_mode<PAR>(a) && kA >= g.n1_r;
   float2 ra[4], dfo[4];
   double qa[4], qb[4];
@@ -1030,8 +1033,8 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
   // gravity on the deviation; the reference part sits in the row constant
   const float4 dca = S.qa[p + 2][tx + 2], dcb = S.qb[p + 2][tx + 2];
   const float2 mG = sp2(-g.Gf);
-  R[2] = add2(R[2], fma2(mG, lo2(dca), lo2(rowp[7 * nz + kA])));
-  R[3] = fma2(mG, add2(lo2(rowp[nz + kA]), lo2(dcb)), R[3]);
+  R[2] = add2(R[2], fma2(mG, lo2(dca), lo2(S.rc[7][p + 2])));
+  R[3] = fma2(mG, add2(lo2(S.rc[1][p + 2]), lo2(dcb)), R[3]);
 
   if (rhs_mode<PAR>(a)) {
 #pragma unroll
