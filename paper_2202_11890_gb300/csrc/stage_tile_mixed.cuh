@@ -988,29 +988,19 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
     fxr[c].x = __shfl_down_sync(0xffffffffu, fxl[c].x, 1);
     fxr[c].y = __shfl_down_sync(0xffffffffu, fxl[c].y, 1);
   }
-  // the combination's global operands (F rows of an odd stage), loaded
+  // the combination's double operands (F rows of an odd stage), loaded
   // before the barrier so that their latency overlaps the wait
   const int kA = k0 + p;
   const int i = i0 + tx;
   const bool own = p < TZ && i < nx;
   const size_t offA = (size_t)kA * g.pitch + i, offB = offA + pstep;
   const bool f_odd = odd_mode<PAR>(a) && kA >= g.n1_r;
-  float2 ra[4], dfo[4];
   double qa[4], qb[4];
   if (own && f_odd) {
-    const float* Ra = reinterpret_cast<const float*>(a.b.Ra);
 #pragma unroll
     for (int c = 0; c < 4; c++) {
-      const size_t oA = c * plane + offA, oB = c * plane + offB;
-      qa[c] = a.qF[oA];
-      qb[c] = a.qF[oB];
-      if (stg) {  // staged rows p + 2 and p + 2 + TZ, column tx + 4 (dF is the staged shadow)
-        ra[c] = make_float2(stg->ra[c][p + 2][tx + 4], stg->ra[c][p + 2 + TZ][tx + 4]);
-        dfo[c] = make_float2(stg->d[c][p + 2][tx + 4], stg->d[c][p + 2 + TZ][tx + 4]);
-      } else {
-        ra[c] = make_float2(Ra[oA], Ra[oB]);
-        dfo[c] = make_float2(a.dF[oA], a.dF[oB]);
-      }
+      qa[c] = a.qF[c * plane + offA];
+      qb[c] = a.qF[c * plane + offB];
     }
   }
   __syncthreads();
@@ -1045,6 +1035,21 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
     return true;
   }
   if (f_odd) {
+    // R_a and the float shadow of the two cells: the staged rows p + 2 and
+    // p + 2 + TZ, column tx + 4 (the staging buffer is not written again
+    // in this tile), else global memory
+    const float* Ra = reinterpret_cast<const float*>(a.b.Ra);
+    float2 ra[4], dfo[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      if (stg) {
+        ra[c] = make_float2(stg->ra[c][p + 2][tx + 4], stg->ra[c][p + 2 + TZ][tx + 4]);
+        dfo[c] = make_float2(stg->d[c][p + 2][tx + 4], stg->d[c][p + 2 + TZ][tx + 4]);
+      } else {
+        ra[c] = make_float2(Ra[c * plane + offA], Ra[c * plane + offB]);
+        dfo[c] = make_float2(a.dF[c * plane + offA], a.dF[c * plane + offB]);
+      }
+    }
     const float2 h2f = sp2(g.h2f);
 #pragma unroll
     for (int c = 0; c < 4; c++) {
