@@ -828,15 +828,16 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 // rows k0 .. k0+MTZ-1, columns i0 .. i0+TX-1 will read after the tile's
 // second barrier: q_F (F rows, odd stages), the buffer accumulator (B rows,
 // every stage but the first) and q_n (S rows at the second stage, B rows at
-// the last). Thread t < 4 MTZ issues the 256-byte segment of row t / 4,
-// component t % 4; every segment is 256-byte aligned and inside its row's
-// pitch. Issued as the tile starts, so that those loads find L2. Only the
-// kernels compiled for one stage parity prefetch: in the batch kernel (the
-// run-time form, short of registers) it measured slower.
+// the last). The last 4 MTZ threads (which stage one pair row rather than
+// two) each issue one 256-byte segment: thread t counted from there takes
+// row t / 4, component t % 4. Every segment is 256-byte aligned and inside
+// its row's pitch. Issued as the tile starts, so that those loads find L2.
+// Only the kernels compiled for one stage parity prefetch: in the batch
+// kernel (the run-time form, short of registers) it measured slower.
 template <int PAR>
 __device__ __forceinline__ void prefetch_combination(const StageArgs& a, int k0, int i0) {
-  const int t = threadIdx.x;
-  if (PAR == PAR_RT || t >= 4 * MTZ) return;
+  const int t = (int)threadIdx.x - (MIXED_THREADS - 4 * MTZ);
+  if (PAR == PAR_RT || t < 0) return;
   const Geom& g = a.g;
   const int k = k0 + t / 4, c = t % 4;
   if (k >= g.nz) return;
@@ -905,9 +906,11 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
       kp[e] = rowp[6 * nz + kA];
     }
     // the paired row constants of the halo pair rows, which the face and
-    // combination phases read from shared memory
-    if (tid < 8 * PHR) {
-      const int j = tid / PHR, r = tid - j * PHR;
+    // combination phases read from shared memory; the last threads, which
+    // stage one pair row instead of two, load them
+    const int t2 = tid - (MIXED_THREADS - 8 * PHR);
+    if (t2 >= 0) {
+      const int j = t2 / PHR, r = t2 - j * PHR;
       S.rc[j][r] = rowp[j * nz + k0 - 2 + r];
     }
     if (stg) ok = mbar_wait(bar, 0);  // the row constants above are in flight meanwhile
