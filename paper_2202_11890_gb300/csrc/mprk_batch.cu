@@ -145,8 +145,10 @@ __global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const Bat
           if (t > 0) __syncthreads();  // the previous tile is done with shared memory
           if (PREC == 0)
             stage_tile<double, double>(s_a, item.tile + t, *reinterpret_cast<TileSmem<double>*>(smem_raw));
+          else if (s_a.stage & 1)  // the FP32-flux tile compiled per stage parity
+            stage_tile_mixed<1>(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
           else
-            stage_tile_mixed<PAR_RT>(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
+            stage_tile_mixed<0>(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
         }
       } else {
         for (int t = 0; t < item.count; t++) finalize_chunk(I.g, I.b, item.tile + t);

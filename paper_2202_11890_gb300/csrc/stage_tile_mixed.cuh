@@ -312,8 +312,8 @@ __device__ __forceinline__ void z_face3(MixedSmem& S, const Geom& g, int k0, int
 }
 
 // PAR: a launch's stage parity when the kernel is compiled for it (0 even,
-// 1 odd), or PAR_RT to read the parity and the right-hand-side hook from the
-// arguments at run time (the batch kernel's callers pick 0 or 1 too).
+// 1 odd; the batch kernel picks one per work item), or PAR_RT to read the
+// parity and the right-hand-side hook from the arguments at run time.
 constexpr int PAR_RT = 2;
 template <int PAR>
 __device__ __forceinline__ bool rhs_mode(const StageArgs& a) {
@@ -832,8 +832,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 // two) each issue one 256-byte segment: thread t counted from there takes
 // row t / 4, component t % 4. Every segment is 256-byte aligned and inside
 // its row's pitch. Issued as the tile starts, so that those loads find L2.
-// Only the kernels compiled for one stage parity prefetch: in the batch
-// kernel (the run-time form, short of registers) it measured slower.
+// The run-time form (the right-hand-side hook) does not prefetch.
 template <int PAR>
 __device__ __forceinline__ void prefetch_combination(const StageArgs& a, int k0, int i0) {
   const int t = (int)threadIdx.x - (MIXED_THREADS - 4 * MTZ);
