@@ -58,8 +58,8 @@ TRAFFIC = {
     },
     "stage_kernel_mixed": {
         "files": ("stage_tile_mixed.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "15d73bacc7ecfbcdea55a9b1b27575f9cc2b30fb978a07e0db9ce287a9fd6d28",
-        "bytes_per_step": 5195528448,
+        "sha256": "6ec23e9fe334fec5d02ccc34981df2fda2de32b4dbfa5d430da8c98096d4d711",
+        "bytes_per_step": 5197735680,
     },
 }
 
