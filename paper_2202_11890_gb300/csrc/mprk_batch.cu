@@ -53,9 +53,10 @@ struct BatchItem {
 
 // Default tiles per work item. An FP32-flux tile takes a few microseconds,
 // about what an item's scheduling costs (counter, wait, barriers, argument
-// copy), so eight tiles share one item; FP64 tiles go two to an item.
-// mprk_batch_tune may pick others per size bucket.
-constexpr int batch_group(int prec) { return prec == 0 ? 2 : 8; }
+// copy), so four tiles share one item (the tuner's pick on mixed batches);
+// FP64 tiles go two to an item. mprk_batch_tune may pick others per size
+// bucket.
+constexpr int batch_group(int prec) { return prec == 0 ? 2 : 4; }
 
 struct BatchArgs {
   const BatchInst* insts;
