@@ -53,8 +53,8 @@ CSRC = os.path.join(ROOT, "paper_2202_11890_gb300", "csrc")
 TRAFFIC = {
     "stage_kernel": {
         "files": ("stage_tile.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "b0a29d14d8b916f906a693f631e3548014f539d97c67455392a6faaebbc5e0f3",
-        "bytes_per_step": 1191586304,
+        "sha256": "ea26998041765ff8bec403170af5538b73882691bf90e1be84400f6370963e9a",
+        "bytes_per_step": 1179626496,
     },
     "stage_kernel_mixed": {
         "files": ("stage_tile_mixed.cuh", "mprk_internal.h", "mprk_kernels.cu"),

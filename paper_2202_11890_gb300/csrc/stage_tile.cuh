@@ -8,10 +8,13 @@
 //      state (bulk fluxes and wall states of App. B) when the tile touches it,
 //   3. computes the cell slopes: central differences of the conserved
 //      variables (reconstruction) and of u, w (tangential viscous gradients),
-//      with mirror or wall-state ghosts beyond walls and the interface,
+//      with mirror or wall-state ghosts beyond walls and the interface; the
+//      differences are stored unscaled and their factors (1/4 for the
+//      reconstruction, 1/(2 d) for a derivative) taken up where they are used,
 //   4. computes every x and z face flux of the tile once (Lax–Friedrichs
 //      inviscid flux of Sec. 2.1 minus the common-value viscous flux of
-//      App. B), in one direction-generic routine written in the face frame,
+//      App. B), in one direction-generic routine written in the face frame;
+//      each flux comes out multiplied by the 1/dx or 1/dz of the divergence,
 //   5. forms R = -div F* + s per cell and applies the partition's stage
 //      combination (Eq. MRK2 in low-storage form) in double precision.
 //
@@ -23,18 +26,34 @@
 
 namespace mprk {
 
+// Face constants of one face direction in one fluid (scaled by the divergence
+// factor sc = 1/dx at x faces, 1/dz of the fluid at z faces; d_n and d_t are
+// the spacings normal and tangential to the face).
+enum {
+  FC_HS,  // sc / 2: the averages of the Lax–Friedrichs flux
+  FC_A,   // (4/3) mu sc / d_n: sigma_nn from the normal difference of u_n
+  FC_B,   // mu sc / (6 d_t): sigma_nn from the two cells' tangential differences of u_t
+  FC_C,   // mu sc / d_n: sigma_nt from the normal difference of u_t
+  FC_D,   // mu sc / (4 d_t): sigma_nt from the two cells' tangential differences of u_n
+  FC_K,   // kappa sc / d_n: heat flux from the normal difference of T
+  FC_SC,  // sc
+  FC_N
+};
+
 template <typename Real>
 struct TileSmem {
   Real q[4][TZ + 4][TX + 4];   // stage state, rows k0-2.., cols i0-2..
   Real v[3][TZ + 2][TX + 2];   // u, w, T, rows k0-1.., cols i0-1..
-  Real hx[4][TZ][TX + 2];      // quarter x differences of q, cols i0-1..
-  Real hz[4][TZ + 2][TX];      // quarter z differences of q, rows k0-1..
-  Real tz[2][TZ][TX + 2];      // d/dz of u, w (tangential at x faces)
-  Real tx[2][TZ + 2][TX];      // d/dx of u, w (tangential at z faces)
-  Real fx[4][TZ][TX + 1];      // x face fluxes, face f between cols f-1, f
-  Real fz[4][TZ + 1][TX];      // z face fluxes seen from above
-  Real fg[4][TX];              // interface flux seen from fluid 1 (below)
+  Real hx[4][TZ][TX + 2];      // central x differences of q, cols i0-1..
+  Real hz[4][TZ + 2][TX];      // central z differences of q, rows k0-1..
+  Real tz[2][TZ][TX + 2];      // central z differences of u, w (tangential at x faces)
+  Real tx[2][TZ + 2][TX];      // central x differences of u, w (tangential at z faces)
+  Real fx[4][TZ][TX + 1];      // x face fluxes / dx, face f between cols f-1, f
+  Real fz[4][TZ + 1][TX];      // z face fluxes / dz seen from above
+  Real fg[4][TX];              // interface flux / dz1 seen from fluid 1 (below)
   double gam[4][TX + 2];       // sigma_xz, Pi_z, u_w, T_w per column i0-1..
+  Real fc[2][2][FC_N];         // face constants per direction (x, z) and fluid (1, 2)
+  Real gg;                     // gamma (gamma - 1)
 };
 
 template <typename Real>
@@ -46,11 +65,13 @@ __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
 
 // Lax–Friedrichs flux in the face frame. A state is (rho, m_n, m_t, rho E):
 // m_n is the momentum along the face normal, m_t along the face. Output is
-// (F_rho, F_mn, F_mt, F_E). lambda is the largest |u_n| + a over the left,
-// right and Roe-averaged states (Sec. 2.1).
+// hs = sc/2 times twice the flux, i.e. sc (F_rho, F_mn, F_mt, F_E). lambda is
+// the largest |u_n| + a over the left, right and Roe-averaged states
+// (Sec. 2.1); the Roe weights sqrt(rho)/(sqrt(rho_L) + sqrt(rho_R)) times
+// the enthalpy H = (rho E + p)/rho are formed as (rho E + p)/sqrt(rho).
 template <typename Real>
 __device__ __forceinline__ void lf_face(Real lr, Real lmn, Real lmt, Real lE, Real rr, Real rmn,
-                                        Real rmt, Real rE, Real gamma, Real gm1, Real out[4]) {
+                                        Real rmt, Real rE, Real gamma, Real gm1, Real hs, Real out[4]) {
   const Real half = Real(0.5);
   const Real rsL = rsq(lr), rsR = rsq(rr);
   const Real invL = rsL * rsL, invR = rsR * rsR;
@@ -61,19 +82,19 @@ __device__ __forceinline__ void lf_face(Real lr, Real lmn, Real lmt, Real lE, Re
   const Real pR = gm1 * (rE - half * (rmn * unR + rmt * utR));
   const Real XL = gamma * pL * invL, XR = gamma * pR * invR;
   const Real cL = XL * rsq(XL), cR = XR * rsq(XR);
-  const Real HL = (lE + pL) * invL, HR = (rE + pR) * invR;
+  const Real eL = lE + pL, eR = rE + pR;
   const Real den = Real(1) / (sL + sR);
   const Real un = (sL * unL + sR * unR) * den;
   const Real ut = (sL * utL + sR * utR) * den;
-  const Real H = (sL * HL + sR * HR) * den;
+  const Real H = (eL * rsL + eR * rsR) * den;
   const Real X = gm1 * (H - half * (un * un + ut * ut));
   const Real c = X * rsq(X);
   const Real lam = fmax(fmax(fabs(unL) + cL, fabs(unR) + cR), fabs(un) + c);
-  const Real hl = half * lam;
-  out[0] = half * (lmn + rmn) + hl * (lr - rr);
-  out[1] = half * ((lmn * unL + pL) + (rmn * unR + pR)) + hl * (lmn - rmn);
-  out[2] = half * (lmt * unL + rmt * unR) + hl * (lmt - rmt);
-  out[3] = half * (unL * (lE + pL) + unR * (rE + pR)) + hl * (lE - rE);
+  const Real hl = hs * lam;
+  out[0] = hs * (lmn + rmn) + hl * (lr - rr);
+  out[1] = hs * ((lmn * unL + pL) + (rmn * unR + pR)) + hl * (lmn - rmn);
+  out[2] = hs * (lmt * unL + rmt * unR) + hl * (lmt - rmt);
+  out[3] = hs * (unL * eL + unR * eR) + hl * (lE - rE);
 }
 
 // Viscous flux in the face frame from the common values of App. B: face
@@ -97,6 +118,23 @@ __device__ __forceinline__ void visc_face(Real unL, Real utL, Real TL, Real gnL,
   out[1] = snn;
   out[2] = snt;
   out[3] = un * snn + ut * snt + kap * dn_T;
+}
+
+// visc_face with the spacings, viscosity and divergence factor folded into
+// the face constants fc (FC_*): the tangential inputs gn, gt are the cells'
+// unscaled central differences of u_n, u_t along the face. Output
+// sc (0, sigma_nn, sigma_nt, u.sigma_n + kappa dT/dn); the same sums as
+// visc_face, regrouped.
+template <typename Real>
+__device__ __forceinline__ void visc_face_fc(Real unL, Real utL, Real TL, Real gnL, Real gtL, Real unR,
+                                             Real utR, Real TR, Real gnR, Real gtR, const Real* fc,
+                                             Real out[4]) {
+  const Real snn = fc[FC_A] * (unR - unL) - fc[FC_B] * (gtL + gtR);
+  const Real snt = fc[FC_C] * (utR - utL) + fc[FC_D] * (gnL + gnR);
+  out[0] = Real(0);
+  out[1] = snn;
+  out[2] = snt;
+  out[3] = Real(0.5) * ((unL + unR) * snn + (utL + utR) * snt) + fc[FC_K] * (TR - TL);
 }
 
 __device__ __forceinline__ int wrap_col(int i, int nx) {
@@ -169,6 +207,23 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
   const double hF = g.hF;
 
   // ---- 1. stage state of the tile and its halo --------------------------
+  if (tid < 4) {
+    // face constants of direction tid >> 1 (x, z) in fluid tid & 1
+    const int dir = tid >> 1, fl = tid & 1;
+    const double inv_dz = fl ? g.inv_dz2 : g.inv_dz1;
+    const double mu = fl ? g.mu2 : g.mu1, kap = fl ? g.kap2 : g.kap1;
+    const double inv_dn = dir ? inv_dz : g.inv_dx, inv_dt = dir ? g.inv_dx : inv_dz;
+    const double sc = inv_dn;  // the divergence factor is the normal one
+    Real* fc = S.fc[dir][fl];
+    fc[FC_HS] = (Real)(0.5 * sc);
+    fc[FC_A] = (Real)(4.0 / 3.0 * mu * inv_dn * sc);
+    fc[FC_B] = (Real)(mu * inv_dt * sc / 6.0);
+    fc[FC_C] = (Real)(mu * inv_dn * sc);
+    fc[FC_D] = (Real)(0.25 * mu * inv_dt * sc);
+    fc[FC_K] = (Real)(kap * inv_dn * sc);
+    fc[FC_SC] = (Real)sc;
+    if (tid == 0) S.gg = (Real)(g.gamma * g.gm1);
+  }
   for (int e = tid; e < 4 * (TZ + 4) * (TX + 4); e += NT) {
     const int c = e / ((TZ + 4) * (TX + 4));
     const int rem = e - c * ((TZ + 4) * (TX + 4));
@@ -201,7 +256,7 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
   __syncthreads();
 
   // ---- 2. u, w, T on the one-cell ring; interface state -----------------
-  const Real gamma = (Real)g.gamma, gm1 = (Real)g.gm1;
+  const Real gamma = (Real)g.gamma, gm1 = (Real)g.gm1, gg = S.gg;
   for (int e = tid; e < (TZ + 2) * (TX + 2); e += NT) {
     const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
     const int k = k0 - 1 + rr;
@@ -210,11 +265,10 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
     const Real mw = S.q[2][rr + 1][cc + 1], E = S.q[3][rr + 1][cc + 1];
     const Real inv = Real(1) / r;
     const Real u = mu_ * inv, w = mw * inv;
-    const Real p = gm1 * (E - Real(0.5) * (mu_ * u + mw * w));
     S.v[0][rr][cc] = u;
     // the mirror state's u is already flipped; a no-slip wall flips w too
     S.v[1][rr][cc] = (x_ghost(i0 - 1 + cc, nx, g.xwall) && g.wall == 0) ? -w : w;
-    S.v[2][rr][cc] = gamma * p * inv;
+    S.v[2][rr][cc] = gg * (E - Real(0.5) * (mu_ * u + mw * w)) * inv;  // T = gamma p / rho
   }
   if (has_gamma && tid < TX + 2) {
     // Interface state of column i0-1+tid in double precision from the two
@@ -260,15 +314,13 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
   __syncthreads();
 
   // ---- 3. slopes ---------------------------------------------------------
-  const Real quarter = Real(0.25);
-  const Real hinv_dx = Real(0.5) * (Real)g.inv_dx;
-  // (a) quarter x differences of q on tile rows, cols i0-1 .. i0+TX
+  // (a) central x differences of q on tile rows, cols i0-1 .. i0+TX
   for (int e = tid; e < TZ * (TX + 2); e += NT) {
     const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
     if (k0 + rr >= row_hi) continue;
 #pragma unroll
-    for (int c = 0; c < 4; c++) S.hx[c][rr][cc] = quarter * (S.q[c][rr + 2][cc + 2] - S.q[c][rr + 2][cc]);
-    // d/dz of u, w at the same cells (tangential at x faces)
+    for (int c = 0; c < 4; c++) S.hx[c][rr][cc] = S.q[c][rr + 2][cc + 2] - S.q[c][rr + 2][cc];
+    // z differences of u, w at the same cells (tangential at x faces)
     const int k = k0 + rr;
     const Real u = S.v[0][rr + 1][cc], w = S.v[1][rr + 1][cc];
     Real uu, wu, ud, wd;  // values above and below, or their ghosts
@@ -280,11 +332,10 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
     if (bot_wall) { ud = g.wall ? u : -u; wd = -w; }
     else if (bot_gam) { ud = Real(2) * (Real)S.gam[2][cc] - u; wd = -w; }
     else { ud = S.v[0][rr][cc]; wd = S.v[1][rr][cc]; }
-    const Real hinv_dz = Real(0.5) * (Real)(k < n1 ? g.inv_dz1 : g.inv_dz2);
-    S.tz[0][rr][cc] = (uu - ud) * hinv_dz;
-    S.tz[1][rr][cc] = (wu - wd) * hinv_dz;
+    S.tz[0][rr][cc] = uu - ud;
+    S.tz[1][rr][cc] = wu - wd;
   }
-  // (b) quarter z differences of q on ring rows k0-1 .. k0+TZ, tile cols
+  // (b) central z differences of q on ring rows k0-1 .. k0+TZ, tile cols
   for (int e = tid; e < (TZ + 2) * TX; e += NT) {
     const int rr = e / TX, cc = e - rr * TX;
     const int k = k0 - 1 + rr;
@@ -297,17 +348,17 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
       const Real mir = (c == 2) ? -own : own;  // mirror ghost: rho w odd
       const Real up = up_in ? S.q[c][rr + 2][cc + 2] : mir;
       const Real dn = dn_in ? S.q[c][rr][cc + 2] : mir;
-      S.hz[c][rr][cc] = quarter * (up - dn);
+      S.hz[c][rr][cc] = up - dn;
     }
-    S.tx[0][rr][cc] = (S.v[0][rr][cc + 2] - S.v[0][rr][cc]) * hinv_dx;
-    S.tx[1][rr][cc] = (S.v[1][rr][cc + 2] - S.v[1][rr][cc]) * hinv_dx;
+    S.tx[0][rr][cc] = S.v[0][rr][cc + 2] - S.v[0][rr][cc];
+    S.tx[1][rr][cc] = S.v[1][rr][cc + 2] - S.v[1][rr][cc];
   }
   __syncthreads();
 
   // ---- 4. face fluxes ----------------------------------------------------
   // z faces first: (TZ+1) rows of TX faces, one warp per face row; then x
   // faces. Every warp sees one face kind.
-  const Real mu1 = (Real)g.mu1, mu2 = (Real)g.mu2, kap1 = (Real)g.kap1, kap2 = (Real)g.kap2;
+  const Real quarter = Real(0.25);
   constexpr int NZF = (TZ + 1) * TX, NXF = TZ * (TX + 1);
   for (int e = tid; e < NZF + NXF; e += NT) {
     Real F[4];
@@ -318,12 +369,13 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
       // needed by a cell of the tile: the cell below (f >= 1) or above (f == 0)
       if (kd >= row_hi) continue;
       // reconstructed state of the cell at tile row rq (halo rows) / ring row
-      // rh in the face frame (normal = z): q + sgn * (quarter z difference)
-      auto load_side = [&](int rq, int rh, Real& r, Real& mn, Real& mt, Real& E, Real sgn) {
-        r = S.q[0][rq][cc + 2] + sgn * S.hz[0][rh][cc];
-        mt = S.q[1][rq][cc + 2] + sgn * S.hz[1][rh][cc];
-        mn = S.q[2][rq][cc + 2] + sgn * S.hz[2][rh][cc];
-        E = S.q[3][rq][cc + 2] + sgn * S.hz[3][rh][cc];
+      // rh in the face frame (normal = z): q + sq * (central z difference),
+      // sq = +-1/4
+      auto load_side = [&](int rq, int rh, Real& r, Real& mn, Real& mt, Real& E, Real sq) {
+        r = S.q[0][rq][cc + 2] + sq * S.hz[0][rh][cc];
+        mt = S.q[1][rq][cc + 2] + sq * S.hz[1][rh][cc];
+        mn = S.q[2][rq][cc + 2] + sq * S.hz[2][rh][cc];
+        E = S.q[3][rq][cc + 2] + sq * S.hz[3][rh][cc];
       };
       if (ku == 0 || ku == nz) {
         // outer wall: the boundary cell against its mirror (inviscid) and its
@@ -332,19 +384,18 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
         const int rq = below ? f + 2 : f + 1;
         const int rh = below ? f + 1 : f;
         const int rv = below ? f + 1 : f;
+        const int k = below ? ku : kd;
+        const Real* fc = S.fc[1][k >= n1];
         Real r, mn, mt, E;
-        load_side(rq, rh, r, mn, mt, E, below ? Real(-1) : Real(1));
+        load_side(rq, rh, r, mn, mt, E, below ? -quarter : quarter);
         Real FI[4], FV[4];
-        if (below) lf_face(r, -mn, mt, E, r, mn, mt, E, gamma, gm1, FI);
-        else lf_face(r, mn, mt, E, r, -mn, mt, E, gamma, gm1, FI);
+        if (below) lf_face(r, -mn, mt, E, r, mn, mt, E, gamma, gm1, fc[FC_HS], FI);
+        else lf_face(r, mn, mt, E, r, -mn, mt, E, gamma, gm1, fc[FC_HS], FI);
         const Real un = S.v[1][rv][cc + 1], ut = S.v[0][rv][cc + 1], T = S.v[2][rv][cc + 1];
         const Real gn = S.tx[1][rv][cc], gt = S.tx[0][rv][cc];
         const Real utg = g.wall ? ut : -ut, gtg = g.wall ? gt : -gt;
-        const int k = below ? ku : kd;
-        const Real mu = k < n1 ? mu1 : mu2, kap = k < n1 ? kap1 : kap2;
-        const Real inv_dn = (Real)(k < n1 ? g.inv_dz1 : g.inv_dz2);
-        if (below) visc_face(-un, utg, T, -gn, gtg, un, ut, T, gn, gt, inv_dn, mu, kap, FV);
-        else visc_face(un, ut, T, gn, gt, -un, utg, T, -gn, gtg, inv_dn, mu, kap, FV);
+        if (below) visc_face_fc(-un, utg, T, -gn, gtg, un, ut, T, gn, gt, fc, FV);
+        else visc_face_fc(un, ut, T, gn, gt, -un, utg, T, -gn, gtg, fc, FV);
         S.fz[0][f][cc] = FI[0] - FV[0];
         S.fz[1][f][cc] = FI[2] - FV[2];
         S.fz[2][f][cc] = FI[1] - FV[1];
@@ -354,30 +405,29 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
         // fluxes of App. B (viscous, shared by both fluids)
         const double sig = S.gam[0][cc + 1], Pi = S.gam[1][cc + 1], uw = S.gam[2][cc + 1];
         const Real Vt = (Real)sig, VE = (Real)(uw * sig - Pi);
+        const Real *fc2 = S.fc[1][1], *fc1 = S.fc[1][0];
         Real r, mn, mt, E, FI[4];
-        load_side(f + 2, f + 1, r, mn, mt, E, Real(-1));  // fluid 2, above
-        lf_face(r, -mn, mt, E, r, mn, mt, E, gamma, gm1, FI);
+        load_side(f + 2, f + 1, r, mn, mt, E, -quarter);  // fluid 2, above
+        lf_face(r, -mn, mt, E, r, mn, mt, E, gamma, gm1, fc2[FC_HS], FI);
         S.fz[0][f][cc] = FI[0];
-        S.fz[1][f][cc] = FI[2] - Vt;
+        S.fz[1][f][cc] = FI[2] - Vt * fc2[FC_SC];
         S.fz[2][f][cc] = FI[1];
-        S.fz[3][f][cc] = FI[3] - VE;
-        load_side(f + 1, f, r, mn, mt, E, Real(1));  // fluid 1, below
-        lf_face(r, mn, mt, E, r, -mn, mt, E, gamma, gm1, FI);
+        S.fz[3][f][cc] = FI[3] - VE * fc2[FC_SC];
+        load_side(f + 1, f, r, mn, mt, E, quarter);  // fluid 1, below
+        lf_face(r, mn, mt, E, r, -mn, mt, E, gamma, gm1, fc1[FC_HS], FI);
         S.fg[0][cc] = FI[0];
-        S.fg[1][cc] = FI[2] - Vt;
+        S.fg[1][cc] = FI[2] - Vt * fc1[FC_SC];
         S.fg[2][cc] = FI[1];
-        S.fg[3][cc] = FI[3] - VE;
+        S.fg[3][cc] = FI[3] - VE * fc1[FC_SC];
       } else {
+        const Real* fc = S.fc[1][kd >= n1];
         Real lr, lmn, lmt, lE, rr_, rmn, rmt, rE, FI[4], FV[4];
-        load_side(f + 1, f, lr, lmn, lmt, lE, Real(1));
-        load_side(f + 2, f + 1, rr_, rmn, rmt, rE, Real(-1));
-        lf_face(lr, lmn, lmt, lE, rr_, rmn, rmt, rE, gamma, gm1, FI);
-        const int k = kd;
-        const Real mu = k < n1 ? mu1 : mu2, kap = k < n1 ? kap1 : kap2;
-        const Real inv_dn = (Real)(k < n1 ? g.inv_dz1 : g.inv_dz2);
-        visc_face(S.v[1][f][cc + 1], S.v[0][f][cc + 1], S.v[2][f][cc + 1], S.tx[1][f][cc], S.tx[0][f][cc],
-                  S.v[1][f + 1][cc + 1], S.v[0][f + 1][cc + 1], S.v[2][f + 1][cc + 1], S.tx[1][f + 1][cc],
-                  S.tx[0][f + 1][cc], inv_dn, mu, kap, FV);
+        load_side(f + 1, f, lr, lmn, lmt, lE, quarter);
+        load_side(f + 2, f + 1, rr_, rmn, rmt, rE, -quarter);
+        lf_face(lr, lmn, lmt, lE, rr_, rmn, rmt, rE, gamma, gm1, fc[FC_HS], FI);
+        visc_face_fc(S.v[1][f][cc + 1], S.v[0][f][cc + 1], S.v[2][f][cc + 1], S.tx[1][f][cc], S.tx[0][f][cc],
+                     S.v[1][f + 1][cc + 1], S.v[0][f + 1][cc + 1], S.v[2][f + 1][cc + 1], S.tx[1][f + 1][cc],
+                     S.tx[0][f + 1][cc], fc, FV);
         S.fz[0][f][cc] = FI[0] - FV[0];
         S.fz[1][f][cc] = FI[2] - FV[2];
         S.fz[2][f][cc] = FI[1] - FV[1];
@@ -389,20 +439,22 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
       const int k = k0 + rr;
       if (k >= row_hi) continue;
       // face between columns i0+f-1 (L, ring col f) and i0+f (R, ring col f+1)
-      const Real lr = S.q[0][rr + 2][f + 1] + S.hx[0][rr][f];
-      const Real lmn = S.q[1][rr + 2][f + 1] + S.hx[1][rr][f];
-      const Real lmt = S.q[2][rr + 2][f + 1] + S.hx[2][rr][f];
-      const Real lE = S.q[3][rr + 2][f + 1] + S.hx[3][rr][f];
-      const Real rr_ = S.q[0][rr + 2][f + 2] - S.hx[0][rr][f + 1];
-      const Real rmn = S.q[1][rr + 2][f + 2] - S.hx[1][rr][f + 1];
-      const Real rmt = S.q[2][rr + 2][f + 2] - S.hx[2][rr][f + 1];
-      const Real rE = S.q[3][rr + 2][f + 2] - S.hx[3][rr][f + 1];
+      // q +- 1/4 (central difference); the products are exact, so each sum
+      // rounds once
+      const Real lr = S.q[0][rr + 2][f + 1] + quarter * S.hx[0][rr][f];
+      const Real lmn = S.q[1][rr + 2][f + 1] + quarter * S.hx[1][rr][f];
+      const Real lmt = S.q[2][rr + 2][f + 1] + quarter * S.hx[2][rr][f];
+      const Real lE = S.q[3][rr + 2][f + 1] + quarter * S.hx[3][rr][f];
+      const Real rr_ = S.q[0][rr + 2][f + 2] - quarter * S.hx[0][rr][f + 1];
+      const Real rmn = S.q[1][rr + 2][f + 2] - quarter * S.hx[1][rr][f + 1];
+      const Real rmt = S.q[2][rr + 2][f + 2] - quarter * S.hx[2][rr][f + 1];
+      const Real rE = S.q[3][rr + 2][f + 2] - quarter * S.hx[3][rr][f + 1];
+      const Real* fc = S.fc[0][k >= n1];
       Real FI[4], FV[4];
-      lf_face(lr, lmn, lmt, lE, rr_, rmn, rmt, rE, gamma, gm1, FI);
-      const Real mu = k < n1 ? mu1 : mu2, kap = k < n1 ? kap1 : kap2;
-      visc_face(S.v[0][rr + 1][f], S.v[1][rr + 1][f], S.v[2][rr + 1][f], S.tz[0][rr][f], S.tz[1][rr][f],
-                S.v[0][rr + 1][f + 1], S.v[1][rr + 1][f + 1], S.v[2][rr + 1][f + 1], S.tz[0][rr][f + 1],
-                S.tz[1][rr][f + 1], (Real)g.inv_dx, mu, kap, FV);
+      lf_face(lr, lmn, lmt, lE, rr_, rmn, rmt, rE, gamma, gm1, fc[FC_HS], FI);
+      visc_face_fc(S.v[0][rr + 1][f], S.v[1][rr + 1][f], S.v[2][rr + 1][f], S.tz[0][rr][f], S.tz[1][rr][f],
+                   S.v[0][rr + 1][f + 1], S.v[1][rr + 1][f + 1], S.v[2][rr + 1][f + 1], S.tz[0][rr][f + 1],
+                   S.tz[1][rr][f + 1], fc, FV);
       S.fx[0][rr][f] = FI[0] - FV[0];
       S.fx[1][rr][f] = FI[1] - FV[1];
       S.fx[2][rr][f] = FI[2] - FV[2];
@@ -416,14 +468,13 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
     const int rr = tid / TX, cc = tid - rr * TX;
     const int k = k0 + rr, i = i0 + cc;
     if (rr >= TZ || k >= row_hi || i >= nx) return;
-    const Real inv_dx = (Real)g.inv_dx;
-    const Real inv_dz = (Real)(k < n1 ? g.inv_dz1 : g.inv_dz2);
     const bool under_gamma = (k == n1 - 1);
     Real R[4];
 #pragma unroll
     for (int c = 0; c < 4; c++) {
+      // the face fluxes carry 1/dx and 1/dz already
       const Real up = under_gamma ? S.fg[c][cc] : S.fz[c][rr + 1][cc];
-      R[c] = (S.fx[c][rr][cc] - S.fx[c][rr][cc + 1]) * inv_dx + (S.fz[c][rr][cc] - up) * inv_dz;
+      R[c] = (S.fx[c][rr][cc] - S.fx[c][rr][cc + 1]) + (S.fz[c][rr][cc] - up);
     }
     const Real Gr = (Real)g.G;
     R[2] -= S.q[0][rr + 2][cc + 2] * Gr;
