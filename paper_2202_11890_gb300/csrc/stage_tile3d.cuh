@@ -5,7 +5,7 @@
 //
 // A stage is two launches over the active rows:
 //  * yface3: one CTA per TX x TZ tile of an x–z plane j computes the y-face
-//    fluxes G* between planes j and j+1 of its cells and stores them (face
+//    fluxes G* between planes j and j+1 of its cells and stores G*/dy (face
 //    j+1/2 at index j) in a state-sized buffer;
 //  * stage3: one CTA per TX x TZ tile of plane j computes its x and z faces
 //    as the 2-D tile does, takes the y divergence from the stored y faces,
@@ -14,6 +14,10 @@
 // of App. B: mean velocity, two-point normal derivatives, tangential
 // derivatives averaged from the two cells' central differences, sigma =
 // mu (grad u + grad u^T - 2/3 div u I), heat flux -kappa grad T.
+// Central differences are stored unscaled; their factors (1/4 for the
+// reconstruction, 1/(2 d) for a derivative), the viscosity and the
+// divergence's 1/dx, 1/dy, 1/dz are folded into per-face constants, so each
+// face flux comes out multiplied by 1/d of its normal direction.
 #pragma once
 
 #include "mprk_internal.h"
@@ -22,10 +26,43 @@ namespace mprk {
 
 constexpr int NC3 = 5;
 
-// Lax–Friedrichs flux (Sec. 2.1) in a face frame: a state is (rho, m_n,
-// m_t1, m_t2, rho E); lambda is the largest |u_n| + a over the left, right
-// and Roe-averaged states.
-__device__ __forceinline__ void lf_face5(const double l[5], const double r[5], double gamma, double gm1,
+// Face constants of one face direction in one fluid: sc = 1/d_n is the
+// divergence factor, d_n, d_t1, d_t2 the spacings normal to the face and
+// along its two tangents.
+enum {
+  F3_HS,  // sc / 2
+  F3_A,   // (4/3) mu sc / d_n
+  F3_B1,  // mu sc / (6 d_t1)
+  F3_B2,  // mu sc / (6 d_t2)
+  F3_C,   // mu sc / d_n
+  F3_D1,  // mu sc / (4 d_t1)
+  F3_D2,  // mu sc / (4 d_t2)
+  F3_K,   // kappa sc / d_n
+  F3_SC,  // sc
+  F3_N
+};
+
+// The constants of a face with normal spacing inv_dn (= sc) and tangential
+// spacings inv_dt1, inv_dt2 (reciprocals) into fc[F3_N].
+__device__ __forceinline__ void face_consts3(double inv_dn, double inv_dt1, double inv_dt2, double mu, double kap,
+                                             double* fc) {
+  const double sc = inv_dn;
+  fc[F3_HS] = 0.5 * sc;
+  fc[F3_A] = 4.0 / 3.0 * mu * inv_dn * sc;
+  fc[F3_B1] = mu * inv_dt1 * sc / 6.0;
+  fc[F3_B2] = mu * inv_dt2 * sc / 6.0;
+  fc[F3_C] = mu * inv_dn * sc;
+  fc[F3_D1] = 0.25 * mu * inv_dt1 * sc;
+  fc[F3_D2] = 0.25 * mu * inv_dt2 * sc;
+  fc[F3_K] = kap * inv_dn * sc;
+  fc[F3_SC] = sc;
+}
+
+// Lax–Friedrichs flux (Sec. 2.1) in a face frame, times sc = 2 hs: a state
+// is (rho, m_n, m_t1, m_t2, rho E); lambda is the largest |u_n| + a over the
+// left, right and Roe-averaged states. The Roe weights times the enthalpy
+// (rho E + p)/rho are formed as (rho E + p)/sqrt(rho).
+__device__ __forceinline__ void lf_face5(const double l[5], const double r[5], double gamma, double gm1, double hs,
                                          double out[5]) {
   const double rsL = rsqrt(l[0]), rsR = rsqrt(r[0]);
   const double invL = rsL * rsL, invR = rsR * rsR;
@@ -36,50 +73,45 @@ __device__ __forceinline__ void lf_face5(const double l[5], const double r[5], d
   const double pR = gm1 * (r[4] - 0.5 * (r[1] * unR + r[2] * t1R + r[3] * t2R));
   const double XL = gamma * pL * invL, XR = gamma * pR * invR;
   const double cL = XL * rsqrt(XL), cR = XR * rsqrt(XR);
-  const double HL = (l[4] + pL) * invL, HR = (r[4] + pR) * invR;
+  const double eL = l[4] + pL, eR = r[4] + pR;
   const double den = 1.0 / (sL + sR);
   const double un = (sL * unL + sR * unR) * den;
   const double t1 = (sL * t1L + sR * t1R) * den;
   const double t2 = (sL * t2L + sR * t2R) * den;
-  const double H = (sL * HL + sR * HR) * den;
+  const double H = (eL * rsL + eR * rsR) * den;
   const double X = gm1 * (H - 0.5 * (un * un + t1 * t1 + t2 * t2));
   const double c = X * rsqrt(X);
   const double lam = fmax(fmax(fabs(unL) + cL, fabs(unR) + cR), fabs(un) + c);
-  const double hl = 0.5 * lam;
-  out[0] = 0.5 * (l[1] + r[1]) + hl * (l[0] - r[0]);
-  out[1] = 0.5 * ((l[1] * unL + pL) + (r[1] * unR + pR)) + hl * (l[1] - r[1]);
-  out[2] = 0.5 * (l[2] * unL + r[2] * unR) + hl * (l[2] - r[2]);
-  out[3] = 0.5 * (l[3] * unL + r[3] * unR) + hl * (l[3] - r[3]);
-  out[4] = 0.5 * (unL * (l[4] + pL) + unR * (r[4] + pR)) + hl * (l[4] - r[4]);
+  const double hl = hs * lam;
+  out[0] = hs * (l[1] + r[1]) + hl * (l[0] - r[0]);
+  out[1] = hs * ((l[1] * unL + pL) + (r[1] * unR + pR)) + hl * (l[1] - r[1]);
+  out[2] = hs * (l[2] * unL + r[2] * unR) + hl * (l[2] - r[2]);
+  out[3] = hs * (l[3] * unL + r[3] * unR) + hl * (l[3] - r[3]);
+  out[4] = hs * (unL * eL + unR * eR) + hl * (l[4] - r[4]);
 }
 
 // One side of a face in its frame: velocity (u_n, u_t1, u_t2), T, and the
-// cell's derivatives of the velocity along t1 (d1) and t2 (d2).
+// cell's central differences (unscaled) of the velocity along t1 (d1) and
+// t2 (d2).
 struct VSide {
   double u[3], T, d1[3], d2[3];
 };
 
-// Viscous flux in the face frame: (0, sigma_nn, sigma_nt1, sigma_nt2,
-// u^.sigma_n + kappa dT/dn).
-__device__ __forceinline__ void visc_face5(const VSide& L, const VSide& R, double inv_dn, double mu, double kap,
-                                           double out[5]) {
-  double G[3][3];  // G[a][b] = d u_a / d x_b, b = normal, t1, t2
-#pragma unroll
-  for (int a = 0; a < 3; a++) {
-    G[a][0] = (R.u[a] - L.u[a]) * inv_dn;
-    G[a][1] = 0.5 * (L.d1[a] + R.d1[a]);
-    G[a][2] = 0.5 * (L.d2[a] + R.d2[a]);
-  }
-  const double div = G[0][0] + G[1][1] + G[2][2];
-  const double snn = mu * (G[0][0] + G[0][0]) - (2.0 / 3.0) * mu * div;
-  const double snt1 = mu * (G[1][0] + G[0][1]);
-  const double snt2 = mu * (G[2][0] + G[0][2]);
-  const double u0 = 0.5 * (L.u[0] + R.u[0]), u1 = 0.5 * (L.u[1] + R.u[1]), u2 = 0.5 * (L.u[2] + R.u[2]);
+// Viscous flux in the face frame, times sc: (0, sigma_nn, sigma_nt1,
+// sigma_nt2, u^.sigma_n + kappa dT/dn). With G[a][b] = d u_a / d x_b
+// (b = normal, t1, t2): sigma_nn = mu (4/3 G00 - 2/3 (G11 + G22)),
+// sigma_nt = mu (G_t0 + G_0t); the derivative factors sit in fc.
+__device__ __forceinline__ void visc_face5(const VSide& L, const VSide& R, const double* fc, double out[5]) {
+  const double snn = fc[F3_A] * (R.u[0] - L.u[0]) - fc[F3_B1] * (L.d1[1] + R.d1[1]) -
+                     fc[F3_B2] * (L.d2[2] + R.d2[2]);
+  const double snt1 = fc[F3_C] * (R.u[1] - L.u[1]) + fc[F3_D1] * (L.d1[0] + R.d1[0]);
+  const double snt2 = fc[F3_C] * (R.u[2] - L.u[2]) + fc[F3_D2] * (L.d2[0] + R.d2[0]);
   out[0] = 0.0;
   out[1] = snn;
   out[2] = snt1;
   out[3] = snt2;
-  out[4] = u0 * snn + u1 * snt1 + u2 * snt2 + kap * (R.T - L.T) * inv_dn;
+  out[4] = 0.5 * ((L.u[0] + R.u[0]) * snn + (L.u[1] + R.u[1]) * snt1 + (L.u[2] + R.u[2]) * snt2) +
+           fc[F3_K] * (R.T - L.T);
 }
 
 // ---- shared helpers --------------------------------------------------------
@@ -122,14 +154,13 @@ __device__ __forceinline__ double stage_val3(const StageArgs& a, const Geo3& G, 
   return base[o];
 }
 
-// (u, v, w, T) from a conserved state
-__device__ __forceinline__ void prim5(const double q[5], double gamma, double gm1, double v[4]) {
+// (u, v, w, T) from a conserved state; gg = gamma (gamma - 1), T = gamma p / rho
+__device__ __forceinline__ void prim5(const double q[5], double gg, double v[4]) {
   const double inv = 1.0 / q[0];
   v[0] = q[1] * inv;
   v[1] = q[2] * inv;
   v[2] = q[3] * inv;
-  const double p = gm1 * (q[4] - 0.5 * (q[1] * v[0] + q[2] * v[1] + q[3] * v[2]));
-  v[3] = gamma * p * inv;
+  v[3] = gg * (q[4] - 0.5 * (q[1] * v[0] + q[2] * v[1] + q[3] * v[2])) * inv;
 }
 
 // Interface state of column (i, j) (App. B, Eq. bulk-flux and the wall
@@ -140,10 +171,10 @@ __device__ __forceinline__ void interface3(const StageArgs& a, const Geo3& G, in
   double v1[4], v2[4], q[5];
 #pragma unroll
   for (int c = 0; c < 5; c++) q[c] = stage_val3(a, G, c, G.n1 - 1, j, i);
-  prim5(q, g.gamma, g.gm1, v1);
+  prim5(q, g.gamma * g.gm1, v1);
 #pragma unroll
   for (int c = 0; c < 5; c++) q[c] = stage_val3(a, G, c, G.n1, j, i);
-  prim5(q, g.gamma, g.gm1, v2);
+  prim5(q, g.gamma * g.gm1, v2);
   const double sxz = g.bu * (v2[0] - v1[0]);
   const double syz = g.bu * (v2[1] - v1[1]);  // b_v = b_u
   const double Pi = -g.bT * (v2[3] - v1[3]);
@@ -158,11 +189,12 @@ __device__ __forceinline__ void interface3(const StageArgs& a, const Geo3& G, in
   out[8] = v2[3] + Pi * g.cT2;
 }
 
-// d/dz of (u, v, w) at row k from the cell (c) and its neighbours above (up)
-// and below (dn), with the ghost 2*(wall state) - interior beyond a wall or
-// Gamma; gam holds the column's interface state.
+// Central z difference (unscaled) of (u, v, w) at row k from the cell (c)
+// and its neighbours above (up) and below (dn), with the ghost
+// 2*(wall state) - interior beyond a wall or Gamma; gam holds the column's
+// interface state.
 __device__ __forceinline__ void dz_uvw(const Geom& g, int k, const double* c, const double* up, const double* dn,
-                                       const double* gam, double hinv_dz, double out[3]) {
+                                       const double* gam, double out[3]) {
   double U[3], D[3];
   const int nz = g.nz, n1 = g.n1;
   const double st = g.wall ? 1.0 : -1.0;  // tangential ghost sign at a slip / no-slip wall
@@ -181,7 +213,7 @@ __device__ __forceinline__ void dz_uvw(const Geom& g, int k, const double* c, co
     D[0] = dn[0]; D[1] = dn[1]; D[2] = dn[2];
   }
 #pragma unroll
-  for (int a = 0; a < 3; a++) out[a] = (U[a] - D[a]) * hinv_dz;
+  for (int a = 0; a < 3; a++) out[a] = U[a] - D[a];
 }
 
 // ---- y faces ------------------------------------------------------------------
@@ -195,10 +227,12 @@ struct YfaceSmem {
   double v1[4][TZ + 2][TX + 2];
   double gam0[9][TX];            // interface state of the tile columns, planes j and j+1
   double gam1[9][TX];
+  double fc[2][F3_N];            // y-face constants per fluid
+  double gg;                     // gamma (gamma - 1)
 };
 
 // The y faces between planes j and j+1 of the TX x TZ tile from row k0,
-// column i0, written to a.gy at index j.
+// column i0, times 1/dy, written to a.gy at index j.
 __device__ __forceinline__ void yface_tile(const StageArgs& a, int k0, int i0, int j, YfaceSmem& S) {
   const Geom& g = a.g;
   const Geo3 G = geo3(g);
@@ -207,6 +241,12 @@ __device__ __forceinline__ void yface_tile(const StageArgs& a, int k0, int i0, i
   const int row_hi = a.rhs_only ? a.rhs_hi : nz;
   const int jm = wrap3(j - 1, ny), j1 = wrap3(j + 1, ny), jp = wrap3(j + 2, ny);
 
+  if (tid < 2) {
+    // y faces: t1 = x, t2 = z
+    face_consts3(g.inv_dy, g.inv_dx, tid ? g.inv_dz2 : g.inv_dz1, tid ? g.mu2 : g.mu1, tid ? g.kap2 : g.kap1,
+                 S.fc[tid]);
+    if (tid == 0) S.gg = g.gamma * g.gm1;
+  }
   for (int e = tid; e < 5 * (TZ + 2) * (TX + 2); e += NTHREADS) {
     const int c = e / ((TZ + 2) * (TX + 2)), rem = e - c * (TZ + 2) * (TX + 2);
     const int rr = rem / (TX + 2), cc = rem - rr * (TX + 2);
@@ -248,7 +288,7 @@ __device__ __forceinline__ void yface_tile(const StageArgs& a, int k0, int i0, i
     double q[5], v[4];
 #pragma unroll
     for (int c = 0; c < 5; c++) q[c] = side ? S.q1[c][rr][cc] : S.q0[c][rr][cc];
-    prim5(q, g.gamma, g.gm1, v);
+    prim5(q, S.gg, v);
 #pragma unroll
     for (int c = 0; c < 4; c++) (side ? S.v1 : S.v0)[c][rr][cc] = v[c];
   }
@@ -267,10 +307,9 @@ __device__ __forceinline__ void yface_tile(const StageArgs& a, int k0, int i0, i
   }
   // face frame: normal rho v, tangential rho u, rho w
   const double lf[5] = {L[0], L[2], L[1], L[3], L[4]}, rf[5] = {R[0], R[2], R[1], R[3], R[4]};
+  const double* fc = S.fc[k >= n1];
   double FI[5], FV[5];
-  lf_face5(lf, rf, g.gamma, g.gm1, FI);
-  const double hinv_dx = 0.5 * g.inv_dx;
-  const double hinv_dz = 0.5 * (k < n1 ? g.inv_dz1 : g.inv_dz2);
+  lf_face5(lf, rf, g.gamma, g.gm1, fc[F3_HS], FI);
   VSide s[2];
 #pragma unroll
   for (int side = 0; side < 2; side++) {
@@ -281,11 +320,11 @@ __device__ __forceinline__ void yface_tile(const StageArgs& a, int k0, int i0, i
     s[side].u[1] = V[0][rr + 1][cc + 1];
     s[side].u[2] = V[2][rr + 1][cc + 1];
     s[side].T = V[3][rr + 1][cc + 1];
-    // d/dx (t1) of (v, u, w)
-    s[side].d1[0] = (V[1][rr + 1][cc + 2] - V[1][rr + 1][cc]) * hinv_dx;
-    s[side].d1[1] = (V[0][rr + 1][cc + 2] - V[0][rr + 1][cc]) * hinv_dx;
-    s[side].d1[2] = (V[2][rr + 1][cc + 2] - V[2][rr + 1][cc]) * hinv_dx;
-    // d/dz (t2) of (v, u, w), ghosts beyond a wall or Gamma
+    // x (t1) differences of (v, u, w)
+    s[side].d1[0] = V[1][rr + 1][cc + 2] - V[1][rr + 1][cc];
+    s[side].d1[1] = V[0][rr + 1][cc + 2] - V[0][rr + 1][cc];
+    s[side].d1[2] = V[2][rr + 1][cc + 2] - V[2][rr + 1][cc];
+    // z (t2) differences of (v, u, w), ghosts beyond a wall or Gamma
     const double cv[3] = {V[0][rr + 1][cc + 1], V[1][rr + 1][cc + 1], V[2][rr + 1][cc + 1]};
     const double uv[3] = {V[0][rr + 2][cc + 1], V[1][rr + 2][cc + 1], V[2][rr + 2][cc + 1]};
     const double dv[3] = {V[0][rr][cc + 1], V[1][rr][cc + 1], V[2][rr][cc + 1]};
@@ -293,13 +332,12 @@ __device__ __forceinline__ void yface_tile(const StageArgs& a, int k0, int i0, i
 #pragma unroll
     for (int q = 0; q < 9; q++) gz[q] = has_gamma ? gam[q][cc] : 0.0;
     double dz[3];
-    dz_uvw(g, k, cv, uv, dv, gz, hinv_dz, dz);
+    dz_uvw(g, k, cv, uv, dv, gz, dz);
     s[side].d2[0] = dz[1];
     s[side].d2[1] = dz[0];
     s[side].d2[2] = dz[2];
   }
-  const double mu = k < n1 ? g.mu1 : g.mu2, kap = k < n1 ? g.kap1 : g.kap2;
-  visc_face5(s[0], s[1], g.inv_dy, mu, kap, FV);
+  visc_face5(s[0], s[1], fc, FV);
   const double F[5] = {FI[0] - FV[0], FI[2] - FV[2], FI[1] - FV[1], FI[3] - FV[3], FI[4] - FV[4]};
 #pragma unroll
   for (int c = 0; c < 5; c++) a.gy[G.at(c, k, j, i)] = F[c];
@@ -310,15 +348,17 @@ __device__ __forceinline__ void yface_tile(const StageArgs& a, int k0, int i0, i
 struct Tile3Smem {
   double q[5][TZ + 4][TX + 4];   // plane j, rows k0-2.., cols i0-2..
   double v[4][TZ + 2][TX + 2];   // u, v, w, T on the ring
-  double vy[3][TZ + 2][TX + 2];  // d/dy of u, v, w on the ring
-  double hx[5][TZ][TX + 2];      // quarter x differences, tile rows, cols i0-1..
-  double hz[5][TZ + 2][TX];      // quarter z differences, rows k0-1.., tile cols
-  double tz[3][TZ][TX + 2];      // d/dz of u, v, w at x-face cells
-  double tx[3][TZ + 2][TX];      // d/dx of u, v, w at z-face cells
-  double fx[5][TZ][TX + 1];      // x face fluxes, face f between cols f-1, f
-  double fz[5][TZ + 1][TX];      // z face fluxes seen from above
+  double vy[3][TZ + 2][TX + 2];  // central y differences of u, v, w on the ring
+  double hx[5][TZ][TX + 2];      // central x differences of q, tile rows, cols i0-1..
+  double hz[5][TZ + 2][TX];      // central z differences of q, rows k0-1.., tile cols
+  double tz[3][TZ][TX + 2];      // central z differences of u, v, w at x-face cells
+  double tx[3][TZ + 2][TX];      // central x differences of u, v, w at z-face cells
+  double fx[5][TZ][TX + 1];      // x face fluxes / dx, face f between cols f-1, f
+  double fz[5][TZ + 1][TX];      // z face fluxes / dz seen from above
   double fg[5][TX];              // interface flux seen from fluid 1
   double gam[9][TX + 2];         // interface state per ring column
+  double fc[2][2][F3_N];         // face constants per direction (x, z) and fluid
+  double gg;                     // gamma (gamma - 1)
 };
 
 __device__ __forceinline__ void stage_tile3(const StageArgs& a, int k0, int i0, int j, Tile3Smem& S) {
@@ -330,15 +370,23 @@ __device__ __forceinline__ void stage_tile3(const StageArgs& a, int k0, int i0, 
   const double gamma = g.gamma, gm1 = g.gm1;
   const int jm = wrap3(j - 1, ny), jp = wrap3(j + 1, ny);
 
-  // ---- 1. stage state with a two-cell halo; d/dy of the velocity on the
-  // ring from planes j-1 and j+1; the interface state
+  // ---- 1. stage state with a two-cell halo; y differences of the velocity
+  // on the ring from planes j-1 and j+1; the interface state
+  if (tid < 4) {
+    // x faces: t1 = y, t2 = z; z faces: t1 = x, t2 = y
+    const int dir = tid >> 1, fl = tid & 1;
+    const double inv_dz = fl ? g.inv_dz2 : g.inv_dz1;
+    const double mu = fl ? g.mu2 : g.mu1, kap = fl ? g.kap2 : g.kap1;
+    if (dir == 0) face_consts3(g.inv_dx, g.inv_dy, inv_dz, mu, kap, S.fc[0][fl]);
+    else face_consts3(inv_dz, g.inv_dx, g.inv_dy, mu, kap, S.fc[1][fl]);
+    if (tid == 0) S.gg = g.gamma * g.gm1;
+  }
   for (int e = tid; e < 5 * (TZ + 4) * (TX + 4); e += NTHREADS) {
     const int c = e / ((TZ + 4) * (TX + 4)), rem = e - c * (TZ + 4) * (TX + 4);
     const int rr = rem / (TX + 4), cc = rem - rr * (TX + 4);
     const int k = k0 - 2 + rr;
     S.q[c][rr][cc] = (k >= 0 && k < nz) ? stage_val3(a, G, c, k, j, wrap3(i0 - 2 + cc, nx)) : 0.0;
   }
-  const double hinv_dy = 0.5 * g.inv_dy;
   for (int e = tid; e < (TZ + 2) * (TX + 2); e += NTHREADS) {
     const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
     const int k = k0 - 1 + rr;
@@ -346,19 +394,19 @@ __device__ __forceinline__ void stage_tile3(const StageArgs& a, int k0, int i0, 
     const int i = wrap3(i0 - 1 + cc, nx);
     double up[3], dn[3];
     {
-      const double r = stage_val3(a, G, 0, k, jp, i);
-      up[0] = stage_val3(a, G, 1, k, jp, i) / r;
-      up[1] = stage_val3(a, G, 2, k, jp, i) / r;
-      up[2] = stage_val3(a, G, 3, k, jp, i) / r;
+      const double inv = 1.0 / stage_val3(a, G, 0, k, jp, i);
+      up[0] = stage_val3(a, G, 1, k, jp, i) * inv;
+      up[1] = stage_val3(a, G, 2, k, jp, i) * inv;
+      up[2] = stage_val3(a, G, 3, k, jp, i) * inv;
     }
     {
-      const double r = stage_val3(a, G, 0, k, jm, i);
-      dn[0] = stage_val3(a, G, 1, k, jm, i) / r;
-      dn[1] = stage_val3(a, G, 2, k, jm, i) / r;
-      dn[2] = stage_val3(a, G, 3, k, jm, i) / r;
+      const double inv = 1.0 / stage_val3(a, G, 0, k, jm, i);
+      dn[0] = stage_val3(a, G, 1, k, jm, i) * inv;
+      dn[1] = stage_val3(a, G, 2, k, jm, i) * inv;
+      dn[2] = stage_val3(a, G, 3, k, jm, i) * inv;
     }
 #pragma unroll
-    for (int q = 0; q < 3; q++) S.vy[q][rr][cc] = (up[q] - dn[q]) * hinv_dy;
+    for (int q = 0; q < 3; q++) S.vy[q][rr][cc] = up[q] - dn[q];
   }
   const bool has_gamma = (n1 >= k0 && n1 <= k0 + TZ);
   if (has_gamma && tid < TX + 2) {
@@ -377,20 +425,19 @@ __device__ __forceinline__ void stage_tile3(const StageArgs& a, int k0, int i0, 
     double q[5], v[4];
 #pragma unroll
     for (int c = 0; c < 5; c++) q[c] = S.q[c][rr + 1][cc + 1];
-    prim5(q, gamma, gm1, v);
+    prim5(q, S.gg, v);
 #pragma unroll
     for (int c = 0; c < 4; c++) S.v[c][rr][cc] = v[c];
   }
   __syncthreads();
 
-  // ---- 3. slopes and tangential derivatives ---------------------------------
-  const double hinv_dx = 0.5 * g.inv_dx;
+  // ---- 3. slopes and tangential differences --------------------------------
   for (int e = tid; e < TZ * (TX + 2); e += NTHREADS) {
     const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
     const int k = k0 + rr;
     if (k >= row_hi) continue;
 #pragma unroll
-    for (int c = 0; c < 5; c++) S.hx[c][rr][cc] = 0.25 * (S.q[c][rr + 2][cc + 2] - S.q[c][rr + 2][cc]);
+    for (int c = 0; c < 5; c++) S.hx[c][rr][cc] = S.q[c][rr + 2][cc + 2] - S.q[c][rr + 2][cc];
     const double cv[3] = {S.v[0][rr + 1][cc], S.v[1][rr + 1][cc], S.v[2][rr + 1][cc]};
     const double uv[3] = {S.v[0][rr + 2][cc], S.v[1][rr + 2][cc], S.v[2][rr + 2][cc]};
     const double dv[3] = {S.v[0][rr][cc], S.v[1][rr][cc], S.v[2][rr][cc]};
@@ -398,7 +445,7 @@ __device__ __forceinline__ void stage_tile3(const StageArgs& a, int k0, int i0, 
 #pragma unroll
     for (int q = 0; q < 9; q++) gz[q] = has_gamma ? S.gam[q][cc] : 0.0;
     double dz[3];
-    dz_uvw(g, k, cv, uv, dv, gz, 0.5 * (k < n1 ? g.inv_dz1 : g.inv_dz2), dz);
+    dz_uvw(g, k, cv, uv, dv, gz, dz);
 #pragma unroll
     for (int q = 0; q < 3; q++) S.tz[q][rr][cc] = dz[q];
   }
@@ -414,10 +461,10 @@ __device__ __forceinline__ void stage_tile3(const StageArgs& a, int k0, int i0, 
       const double mir = (c == 3) ? -own : own;  // mirror ghost: rho w odd
       const double up = up_in ? S.q[c][rr + 2][cc + 2] : mir;
       const double dn = dn_in ? S.q[c][rr][cc + 2] : mir;
-      S.hz[c][rr][cc] = 0.25 * (up - dn);
+      S.hz[c][rr][cc] = up - dn;
     }
 #pragma unroll
-    for (int q = 0; q < 3; q++) S.tx[q][rr][cc] = (S.v[q][rr][cc + 2] - S.v[q][rr][cc]) * hinv_dx;
+    for (int q = 0; q < 3; q++) S.tx[q][rr][cc] = S.v[q][rr][cc + 2] - S.v[q][rr][cc];
   }
   __syncthreads();
 
@@ -442,13 +489,14 @@ __device__ __forceinline__ void stage_tile3(const StageArgs& a, int k0, int i0, 
         s.d2[1] = S.vy[0][rh][cc + 1];
         s.d2[2] = S.vy[1][rh][cc + 1];
       };
-      // reconstructed state of ring row rh in the z frame, q + sgn * slope
-      auto zstate = [&](int rh, double sgn, double o[5]) {
-        const double x[5] = {S.q[0][rh + 1][cc + 2] + sgn * S.hz[0][rh][cc],
-                             S.q[1][rh + 1][cc + 2] + sgn * S.hz[1][rh][cc],
-                             S.q[2][rh + 1][cc + 2] + sgn * S.hz[2][rh][cc],
-                             S.q[3][rh + 1][cc + 2] + sgn * S.hz[3][rh][cc],
-                             S.q[4][rh + 1][cc + 2] + sgn * S.hz[4][rh][cc]};
+      // reconstructed state of ring row rh in the z frame,
+      // q + sq * (central difference), sq = +-1/4
+      auto zstate = [&](int rh, double sq, double o[5]) {
+        const double x[5] = {S.q[0][rh + 1][cc + 2] + sq * S.hz[0][rh][cc],
+                             S.q[1][rh + 1][cc + 2] + sq * S.hz[1][rh][cc],
+                             S.q[2][rh + 1][cc + 2] + sq * S.hz[2][rh][cc],
+                             S.q[3][rh + 1][cc + 2] + sq * S.hz[3][rh][cc],
+                             S.q[4][rh + 1][cc + 2] + sq * S.hz[4][rh][cc]};
         o[0] = x[0];
         o[1] = x[3];
         o[2] = x[1];
@@ -462,13 +510,14 @@ __device__ __forceinline__ void stage_tile3(const StageArgs& a, int k0, int i0, 
         const bool below = (ku == 0);
         const int rh = below ? f + 1 : f;
         const int k = below ? ku : kd;
+        const double* fc = S.fc[1][k >= n1];
         double b[5], m[5];
-        zstate(rh, below ? -1.0 : 1.0, b);
+        zstate(rh, below ? -0.25 : 0.25, b);
 #pragma unroll
         for (int c = 0; c < 5; c++) m[c] = b[c];
         m[1] = -b[1];
-        if (below) lf_face5(m, b, gamma, gm1, FI);
-        else lf_face5(b, m, gamma, gm1, FI);
+        if (below) lf_face5(m, b, gamma, gm1, fc[F3_HS], FI);
+        else lf_face5(b, m, gamma, gm1, fc[F3_HS], FI);
         VSide C, Gh;
         zside(rh, C);
         Gh = C;
@@ -481,10 +530,8 @@ __device__ __forceinline__ void stage_tile3(const StageArgs& a, int k0, int i0, 
           Gh.d1[q] = st * C.d1[q];
           Gh.d2[q] = st * C.d2[q];
         }
-        const double mu = k < n1 ? g.mu1 : g.mu2, kap = k < n1 ? g.kap1 : g.kap2;
-        const double inv_dn = k < n1 ? g.inv_dz1 : g.inv_dz2;
-        if (below) visc_face5(Gh, C, inv_dn, mu, kap, FV);
-        else visc_face5(C, Gh, inv_dn, mu, kap, FV);
+        if (below) visc_face5(Gh, C, fc, FV);
+        else visc_face5(C, Gh, fc, FV);
 #pragma unroll
         for (int c = 0; c < 5; c++) Ff[c] = FI[c] - FV[c];
         // frame (rho, w, u, v, E) -> (rho, u, v, w, E)
@@ -497,37 +544,38 @@ __device__ __forceinline__ void stage_tile3(const StageArgs& a, int k0, int i0, 
         // Gamma: a rigid lid from each side (inviscid) and the bulk fluxes
         // (viscous) with each side's wall state
         const double sxz = S.gam[0][cc + 1], syz = S.gam[1][cc + 1], Pi = S.gam[2][cc + 1];
+        const double *fc2 = S.fc[1][1], *fc1 = S.fc[1][0];
         double b[5], m[5];
-        zstate(f + 1, -1.0, b);  // fluid 2, above
+        zstate(f + 1, -0.25, b);  // fluid 2, above
 #pragma unroll
         for (int c = 0; c < 5; c++) m[c] = b[c];
         m[1] = -b[1];
-        lf_face5(m, b, gamma, gm1, FI);
+        lf_face5(m, b, gamma, gm1, fc2[F3_HS], FI);
         S.fz[0][f][cc] = FI[0];
-        S.fz[1][f][cc] = FI[2] - sxz;
-        S.fz[2][f][cc] = FI[3] - syz;
+        S.fz[1][f][cc] = FI[2] - sxz * fc2[F3_SC];
+        S.fz[2][f][cc] = FI[3] - syz * fc2[F3_SC];
         S.fz[3][f][cc] = FI[1];
-        S.fz[4][f][cc] = FI[4] - (S.gam[6][cc + 1] * sxz + S.gam[7][cc + 1] * syz - Pi);
-        zstate(f, 1.0, b);  // fluid 1, below
+        S.fz[4][f][cc] = FI[4] - (S.gam[6][cc + 1] * sxz + S.gam[7][cc + 1] * syz - Pi) * fc2[F3_SC];
+        zstate(f, 0.25, b);  // fluid 1, below
 #pragma unroll
         for (int c = 0; c < 5; c++) m[c] = b[c];
         m[1] = -b[1];
-        lf_face5(b, m, gamma, gm1, FI);
+        lf_face5(b, m, gamma, gm1, fc1[F3_HS], FI);
         S.fg[0][cc] = FI[0];
-        S.fg[1][cc] = FI[2] - sxz;
-        S.fg[2][cc] = FI[3] - syz;
+        S.fg[1][cc] = FI[2] - sxz * fc1[F3_SC];
+        S.fg[2][cc] = FI[3] - syz * fc1[F3_SC];
         S.fg[3][cc] = FI[1];
-        S.fg[4][cc] = FI[4] - (S.gam[3][cc + 1] * sxz + S.gam[4][cc + 1] * syz - Pi);
+        S.fg[4][cc] = FI[4] - (S.gam[3][cc + 1] * sxz + S.gam[4][cc + 1] * syz - Pi) * fc1[F3_SC];
       } else {
+        const double* fc = S.fc[1][kd >= n1];
         double l[5], r[5];
-        zstate(f, 1.0, l);
-        zstate(f + 1, -1.0, r);
-        lf_face5(l, r, gamma, gm1, FI);
+        zstate(f, 0.25, l);
+        zstate(f + 1, -0.25, r);
+        lf_face5(l, r, gamma, gm1, fc[F3_HS], FI);
         VSide sL, sR;
         zside(f, sL);
         zside(f + 1, sR);
-        const double mu = kd < n1 ? g.mu1 : g.mu2, kap = kd < n1 ? g.kap1 : g.kap2;
-        visc_face5(sL, sR, kd < n1 ? g.inv_dz1 : g.inv_dz2, mu, kap, FV);
+        visc_face5(sL, sR, fc, FV);
         S.fz[0][f][cc] = FI[0] - FV[0];
         S.fz[1][f][cc] = FI[2] - FV[2];
         S.fz[2][f][cc] = FI[3] - FV[3];
@@ -543,10 +591,11 @@ __device__ __forceinline__ void stage_tile3(const StageArgs& a, int k0, int i0, 
       double l[5], r[5], FI[5], FV[5];
 #pragma unroll
       for (int c = 0; c < 5; c++) {
-        l[c] = S.q[c][rr + 2][f + 1] + S.hx[c][rr][f];
-        r[c] = S.q[c][rr + 2][f + 2] - S.hx[c][rr][f + 1];
+        l[c] = S.q[c][rr + 2][f + 1] + 0.25 * S.hx[c][rr][f];
+        r[c] = S.q[c][rr + 2][f + 2] - 0.25 * S.hx[c][rr][f + 1];
       }
-      lf_face5(l, r, gamma, gm1, FI);
+      const double* fc = S.fc[0][k >= n1];
+      lf_face5(l, r, gamma, gm1, fc[F3_HS], FI);
       VSide s[2];
 #pragma unroll
       for (int side = 0; side < 2; side++) {
@@ -559,8 +608,7 @@ __device__ __forceinline__ void stage_tile3(const StageArgs& a, int k0, int i0, 
         }
         s[side].T = S.v[3][rr + 1][col];
       }
-      const double mu = k < n1 ? g.mu1 : g.mu2, kap = k < n1 ? g.kap1 : g.kap2;
-      visc_face5(s[0], s[1], g.inv_dx, mu, kap, FV);
+      visc_face5(s[0], s[1], fc, FV);
 #pragma unroll
       for (int c = 0; c < 5; c++) S.fx[c][rr][f] = FI[c] - FV[c];
     }
@@ -571,14 +619,14 @@ __device__ __forceinline__ void stage_tile3(const StageArgs& a, int k0, int i0, 
   const int rr = tid / TX, cc = tid - rr * TX;
   const int k = k0 + rr, i = i0 + cc;
   if (k >= row_hi || i >= nx) return;
-  const double inv_dz = k < n1 ? g.inv_dz1 : g.inv_dz2;
   const bool under_gamma = (k == n1 - 1);
   double R[5];
 #pragma unroll
   for (int c = 0; c < 5; c++) {
+    // every face flux carries the 1/d of its direction already
     const double up = under_gamma ? S.fg[c][cc] : S.fz[c][rr + 1][cc];
-    R[c] = (S.fx[c][rr][cc] - S.fx[c][rr][cc + 1]) * g.inv_dx + (S.fz[c][rr][cc] - up) * inv_dz +
-           (a.gy[G.at(c, k, jm, i)] - a.gy[G.at(c, k, j, i)]) * g.inv_dy;
+    R[c] = (S.fx[c][rr][cc] - S.fx[c][rr][cc + 1]) + (S.fz[c][rr][cc] - up) +
+           (a.gy[G.at(c, k, jm, i)] - a.gy[G.at(c, k, j, i)]);
   }
   R[3] -= S.q[0][rr + 2][cc + 2] * g.G;
   R[4] -= S.q[3][rr + 2][cc + 2] * g.G;
