@@ -424,7 +424,7 @@ def run_batched(args):
                              "speedup": value / plain_value, "bitwise_equal": same,
                              "max_rel_diff": maxrel, "plain_ms_per_step": t_plain / args.steps,
                              "default_launch": cs * args.steps / (t_default * 1e-3)},
-        "tuned_launch": {**tune, "defaults": "2 FP64 or 4 FP32-flux tiles per item, all CTAs that fit"},
+        "tuned_launch": {**tune, "defaults": "2 tiles per item, all CTAs that fit"},
         "roofline": roof,
         "gpu_launches": args.steps,
         "clocks": sampler.summary(),

@@ -154,9 +154,8 @@ int mprk_step_batch(mprk_instance* const* insts, int count, int n_slow_steps);
  * stage tiles per work item (1, 2, 4, 8 or 16) and the CTAs per SM (1 to 3).
  * A process-wide table keeps, per precision and size bucket (floor(log2) of
  * the mean cells per instance), the fastest pair measured; batches without
- * an entry use 2 (FP64) or 4 (FP32 flux) tiles per item and every CTA that
- * fits. mprk_step_batch and the server read the table when they build a
- * work list. */
+ * an entry use 2 tiles per item and every CTA that fits. mprk_step_batch
+ * and the server read the table when they build a work list. */
 
 /* Time every choice on these instances (reps batched slow steps each after
  * one warm-up step), record the fastest in the table and return it in out:

@@ -40,8 +40,14 @@ struct BatchInst {
   Bufs b;
   unsigned* status;  // the instance's status word
   int counter_base;  // first counter of this instance: one per stage, then completion
+  int args_base;     // first entry of this instance in BatchArgs::args: one per stage
   int precision;
 };
+
+// The work items copy their stage's arguments from a table built on the
+// host (stage_args of every instance and stage) in 16-byte words.
+static_assert(sizeof(StageArgs) % 16 == 0, "StageArgs is copied in 16-byte words");
+constexpr int ARGS_WORDS = (int)(sizeof(StageArgs) / 16);
 
 struct BatchItem {
   int inst;
@@ -51,15 +57,16 @@ struct BatchItem {
   int need;   // items of the previous stage this one waits for (0: none)
 };
 
-// Default tiles per work item. An FP32-flux tile takes a few microseconds,
-// about what an item's scheduling costs (counter, wait, barriers, argument
-// copy), so four tiles share one item (the tuner's pick on mixed batches);
-// FP64 tiles go two to an item. mprk_batch_tune may pick others per size
-// bucket.
-constexpr int batch_group(int prec) { return prec == 0 ? 2 : 4; }
+// Default tiles per work item: two in both precisions. An FP32-flux tile
+// takes a few microseconds; an item's scheduling (claim, wait, argument
+// copy, barriers) is mostly hidden behind the previous item, so two tiles
+// per item beat four on mixed batches. mprk_batch_tune may pick others per
+// size bucket.
+constexpr int batch_group(int /*precision*/) { return 2; }
 
 struct BatchArgs {
   const BatchInst* insts;
+  const StageArgs* args;  // [sum over instances of 2m], 16-byte aligned
   const BatchItem* items;
   int n_items;
   int* next;           // work counter
@@ -114,42 +121,60 @@ __device__ __forceinline__ void finalize_chunk(const Geom& g, const Bufs& b, int
   }
 }
 
+// The FP32-flux tile of a work item, compiled as a function of its own: the
+// tile reads its arguments from shared memory (not from the constant bank
+// as the single-instance kernel does), and allocated apart from the
+// persistent loop it spills less than inlined there.
+template <int PAR>
+__device__ __noinline__ void batch_tile_mixed(const StageArgs& a, int tile, MixedTileSmem& S) {
+  stage_tile_mixed<PAR>(a, tile, S);
+}
+
 // three CTAs per SM in both precisions (80 and 72 registers; the FP32-flux
 // form spills some, and still runs faster than at two CTAs)
 template <int PREC>
 __global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_item;
+  // the current and the next claimed item: thread 0 claims the next one
+  // while the CTA works on the current, so the atomic's latency is hidden.
+  // Items depend only on items before them in the list, and each CTA runs
+  // its claims in order, so claiming ahead cannot deadlock.
+  __shared__ int s_item[2];
   __shared__ int s_ok;
   // the item's stage arguments, one copy for the CTA: the tile reads its
   // launch constants from shared memory instead of a per-thread local copy
-  __shared__ StageArgs s_a;
+  __shared__ __align__(16) StageArgs s_a;
   cuda::atomic_ref<int, cuda::thread_scope_device> nxt(*A.next);
-  for (;;) {
-    if (threadIdx.x == 0) s_item = nxt.fetch_add(1, cuda::memory_order_relaxed);
-    __syncthreads();
-    const int it = s_item;
+  if (threadIdx.x == 0) s_item[0] = nxt.fetch_add(1, cuda::memory_order_relaxed);
+  __syncthreads();
+  for (int cur = 0;; cur ^= 1) {
+    const int it = s_item[cur];
     if (it >= A.n_items) break;
     const BatchItem item = A.items[it];
     const BatchInst& I = A.insts[item.inst];
+    const bool stage_item = item.stage < 2 * I.g.m;
     if (threadIdx.x == 0) {
+      s_item[cur ^ 1] = nxt.fetch_add(1, cuda::memory_order_relaxed);
       s_ok = 1;
       if (item.need > 0) s_ok = wait_for(A, I.counter_base + item.stage - 1, item.need) ? 1 : 0;
       else if (*(volatile int*)A.abort_flag) s_ok = 0;
       if (!s_ok) atomicOr(I.status, ST_TIMEOUT);  // this instance's step is incomplete
-      else if (item.stage < 2 * I.g.m) s_a = stage_args(I.g, I.b, item.stage);
+    } else if (stage_item && (int)threadIdx.x <= ARGS_WORDS) {
+      // meanwhile the next threads copy the stage's arguments
+      const int w = threadIdx.x - 1;
+      reinterpret_cast<int4*>(&s_a)[w] = reinterpret_cast<const int4*>(A.args + I.args_base + item.stage)[w];
     }
     __syncthreads();
     if (s_ok) {
-      if (item.stage < 2 * I.g.m) {
+      if (stage_item) {
         for (int t = 0; t < item.count; t++) {
           if (t > 0) __syncthreads();  // the previous tile is done with shared memory
           if (PREC == 0)
             stage_tile<double, double>(s_a, item.tile + t, *reinterpret_cast<TileSmem<double>*>(smem_raw));
           else if (s_a.stage & 1)  // the FP32-flux tile compiled per stage parity
-            stage_tile_mixed<1>(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
+            batch_tile_mixed<1>(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
           else
-            stage_tile_mixed<0>(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
+            batch_tile_mixed<0>(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
         }
       } else {
         for (int t = 0; t < item.count; t++) finalize_chunk(I.g, I.b, item.tile + t);
@@ -185,6 +210,7 @@ struct Plan {
   int grid = 0;
   long long cell_stages = 0;
   BatchInst* d_insts = nullptr;
+  StageArgs* d_args = nullptr;
   BatchItem* d_items = nullptr;
   int* d_ctr = nullptr;  // [0] next, [1] abort, [2..] counters
   cudaGraphExec_t exec = nullptr;
@@ -250,6 +276,7 @@ void free_plan(Plan* p) {
   if (!p) return;
   if (p->exec) cudaGraphExecDestroy(p->exec);
   cudaFree(p->d_insts);
+  cudaFree(p->d_args);
   cudaFree(p->d_items);
   cudaFree(p->d_ctr);
   delete p;
@@ -259,6 +286,16 @@ void free_plan(Plan* p) {
 
 
 namespace {
+
+// The stage arguments of every instance and stage, in instance order; sets
+// each instance's args_base.
+void args_table(std::vector<BatchInst>& hinst, std::vector<StageArgs>& out) {
+  out.clear();
+  for (BatchInst& bi : hinst) {
+    bi.args_base = (int)out.size();
+    for (int st = 0; st < 2 * bi.g.m; st++) out.push_back(stage_args(bi.g, bi.b, st));
+  }
+}
 
 // The stage-major work list: all first-stage items of all instances, then
 // all second-stage items, ...; each instance's completion items follow its
@@ -322,6 +359,8 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
     p->n_counters += 2 * hinst[j].g.m + 1;
     p->key.push_back(insts[j]);
   }
+  std::vector<StageArgs> hargs;
+  args_table(hinst, hargs);
   p->bucket = size_bucket(hinst);
   if (group <= 0) tuned_choice(p->precision, p->bucket, &group, &per_sm_want);
   p->group = group;
@@ -330,12 +369,18 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
   p->n_items = (int)items.size();
   cudaError_t e;
   if ((e = cudaMalloc(&p->d_insts, sizeof(BatchInst) * count)) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_args, sizeof(StageArgs) * hargs.size())) != cudaSuccess ||
       (e = cudaMalloc(&p->d_items, sizeof(BatchItem) * items.size())) != cudaSuccess ||
       (e = cudaMalloc(&p->d_ctr, sizeof(int) * (2 + p->n_counters))) != cudaSuccess) {
     free_plan(p);
     return bfail(MPRK_ENOMEM, std::string("batch plan allocation: ") + cudaGetErrorString(e));
   }
+  if (reinterpret_cast<uintptr_t>(p->d_args) % 16 != 0) {
+    free_plan(p);
+    return bfail(MPRK_ECUDA, "batch plan: argument table not 16-byte aligned");
+  }
   cudaMemcpy(p->d_insts, hinst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_args, hargs.data(), sizeof(StageArgs) * hargs.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
   // grid: every CTA resident (persistent kernel)
   const size_t smem = stage_smem_bytes(p->precision);
@@ -364,6 +409,7 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
   // capture: reset the counters, then the persistent launch
   BatchArgs A;
   A.insts = p->d_insts;
+  A.args = p->d_args;
   A.items = p->d_items;
   A.n_items = p->n_items;
   A.next = p->d_ctr;
@@ -480,9 +526,10 @@ struct BatchRunner {
   cudaStream_t stream = nullptr;
   std::vector<const void*> key;
   BatchInst* d_insts = nullptr;
+  StageArgs* d_args = nullptr;
   BatchItem* d_items = nullptr;
   int* d_ctr = nullptr;
-  size_t cap_insts = 0, cap_items = 0, cap_ctr = 0;
+  size_t cap_insts = 0, cap_args = 0, cap_items = 0, cap_ctr = 0;
   int n_items = 0, n_counters = 0, grid = 0, per_sm = 0, sms = 0;
   long long cell_stages = 0;
   unsigned* status = nullptr;
@@ -498,6 +545,7 @@ BatchRunner* runner_create(int precision, cudaStream_t stream) {
 void runner_destroy(BatchRunner* r) {
   if (!r) return;
   if (r->d_insts) cudaFreeAsync(r->d_insts, r->stream);
+  if (r->d_args) cudaFreeAsync(r->d_args, r->stream);
   if (r->d_items) cudaFreeAsync(r->d_items, r->stream);
   if (r->d_ctr) cudaFreeAsync(r->d_ctr, r->stream);
   delete r;
@@ -543,15 +591,23 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
     }
     int group, per_sm_want;
     tuned_choice(r->precision, size_bucket(hinst), &group, &per_sm_want);
+    std::vector<StageArgs> hargs;
+    args_table(hinst, hargs);
     std::vector<BatchItem> items;
     long long cs = 0;
     build_items(hinst, group, items, &cs);
     cudaError_t e = grow(&r->d_insts, &r->cap_insts, (size_t)count, r->stream);
+    if (e == cudaSuccess) e = grow(&r->d_args, &r->cap_args, hargs.size(), r->stream);
     if (e == cudaSuccess) e = grow(&r->d_items, &r->cap_items, items.size(), r->stream);
     if (e == cudaSuccess) e = grow(&r->d_ctr, &r->cap_ctr, (size_t)(2 + n_counters), r->stream);
     if (e != cudaSuccess) return bfail(MPRK_ENOMEM, std::string("batch runner: ") + cudaGetErrorString(e));
     // pageable sources: the copies are staged before the calls return
+    if (reinterpret_cast<uintptr_t>(r->d_args) % 16 != 0)
+      return bfail(MPRK_ECUDA, "batch runner: argument table not 16-byte aligned");
     e = cudaMemcpyAsync(r->d_insts, hinst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, r->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(r->d_args, hargs.data(), sizeof(StageArgs) * hargs.size(), cudaMemcpyHostToDevice,
+                          r->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(r->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
                           r->stream);
@@ -578,6 +634,7 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
   }
   BatchArgs A;
   A.insts = r->d_insts;
+  A.args = r->d_args;
   A.items = r->d_items;
   A.n_items = r->n_items;
   A.next = r->d_ctr;

@@ -97,7 +97,7 @@ def test_tuning_table_round_trip_without_a_device(lib, tmp_path):
     rejects out-of-range values; none of it needs a GPU."""
     from paper_2202_11890_gb300 import mprk as M
     M.mprk_tune_clear()
-    assert M.mprk_tune_lookup(1, 5000.0) == {"tiles_per_item": 4, "ctas_per_sm": 0, "tuned": False}
+    assert M.mprk_tune_lookup(1, 5000.0) == {"tiles_per_item": 2, "ctas_per_sm": 0, "tuned": False}
     assert M.mprk_tune_lookup(0, 5000.0)["tiles_per_item"] == 2
     src = tmp_path / "t.json"
     src.write_text('{"gpu": "", "entries": [\n'
