@@ -192,6 +192,22 @@ int mprk_get_state(mprk_instance* inst, double* q_out, int location);
  * caller). Synchronises. */
 int mprk_set_state(mprk_instance* inst, const double* q, int location);
 
+/* Run `count` independent solves of one slow step each through host
+ * memory: for j = 0 .. count-1, set the state from q_in[j], advance one slow
+ * step, and copy the result to q_out[j]. All buffers are host memory in the
+ * layout of mprk_get_state ([4][nz][nx] doubles; [5][nz][ny][nx] in 3-D),
+ * owned by the caller; q_out[j] may alias q_in[j'] only for j' <= j. The
+ * results are bitwise those of mprk_set_state, mprk_step(inst, 1) and
+ * mprk_get_state in turn. The host copies run on two copy streams of the
+ * instance: q_in[j+1] is uploaded while step j runs, and q_out[j]
+ * downloads while step j+1 runs. Page-locked host buffers are needed for the overlap; pageable ones
+ * give the same results without it. The first call allocates two
+ * state-sized device staging buffers, kept until mprk_destroy. The state
+ * left in the instance is the last result. Returns after q_out[count-1] is
+ * written; MPRK_EINVAL for a NULL pointer or count < 0. The paper has no
+ * counterpart: this is host plumbing around the slow step of Algorithm 1. */
+int mprk_step_io(mprk_instance* inst, const double* const* q_in, double* const* q_out, int count);
+
 /* Monitoring quantities of the current state (Sec. 5.1), computed on the
  * device in a fixed order: out[0..3] sums of rho, rho u, rho w, rho E times
  * the cell area over fluid 1, out[4..7] over fluid 2, out[8..10] Courant

@@ -79,6 +79,12 @@ struct mprk_instance {
   bool stream_ordered;  // buffers from cudaMallocAsync on `stream` (server instances)
   StageMaps maps;       // FP32-flux mode: tensor maps of the float planes
   double* gy;           // 3-D: y-face fluxes of the current stage
+  // mprk_step_io (allocated on its first call): staging copies of one
+  // state in the caller's layout, two copy streams and their events
+  double* io_in;
+  double* io_out;
+  cudaStream_t s_up, s_down;
+  cudaEvent_t ev_up, ev_in_free, ev_out_ready, ev_out_free;
 };
 
 namespace {
@@ -133,6 +139,15 @@ void fill_geom(mprk_instance* I) { geom_from_config(I->cfg, (I->cfg.nx + 31) / 3
 void free_instance(mprk_instance* I) {
   if (!I) return;
   if (I->stream && !I->stream_ordered) cudaStreamSynchronize(I->stream);
+  for (cudaStream_t s : {I->s_up, I->s_down})
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  for (cudaEvent_t ev : {I->ev_up, I->ev_in_free, I->ev_out_ready, I->ev_out_free})
+    if (ev) cudaEventDestroy(ev);
+  if (I->io_in) cudaFree(I->io_in);
+  if (I->io_out) cudaFree(I->io_out);
   if (I->exec) cudaGraphExecDestroy(I->exec);
   if (I->exec_diag) cudaGraphExecDestroy(I->exec_diag);
   void* bufs[] = {I->b.qA,     I->b.qB,     I->b.Ra,     I->b.accB, I->b.accS, I->partials, I->diag_dev,
@@ -532,6 +547,57 @@ int mprk_get_state(mprk_instance* I, double* q_out, int location) {
   cudaMemcpyKind kind = location == MPRK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   CU(cudaMemcpy2DAsync(q_out, (size_t)g.nx * 8, I->b.qA, (size_t)g.pitch * 8, (size_t)g.nx * 8,
                        (size_t)g.nc * g.nz * g.ny, kind, I->stream));
+  CU(cudaStreamSynchronize(I->stream));
+  return MPRK_OK;
+}
+
+int mprk_step_io(mprk_instance* I, const double* const* q_in, double* const* q_out, int count) {
+  if (!I || !q_in || !q_out) return fail(MPRK_EINVAL, "NULL argument");
+  if (count < 0) return fail(MPRK_EINVAL, "negative count");
+  if (!I->exec) return fail(MPRK_EINVAL, "this instance advances only in batches");
+  for (int j = 0; j < count; j++)
+    if (!q_in[j] || !q_out[j]) return fail(MPRK_EINVAL, "q_in[%d] or q_out[%d] is NULL", j, j);
+  if (count == 0) return MPRK_OK;
+  const Geom& g = I->g;
+  const size_t row = (size_t)g.nx * 8, rows = (size_t)g.nc * g.nz * g.ny, bytes = row * rows;
+  if (!I->io_in) {
+    CU(cudaMalloc(&I->io_in, bytes));
+    CU(cudaMalloc(&I->io_out, bytes));
+    CU(cudaStreamCreateWithFlags(&I->s_up, cudaStreamNonBlocking));
+    CU(cudaStreamCreateWithFlags(&I->s_down, cudaStreamNonBlocking));
+    for (cudaEvent_t* ev : {&I->ev_up, &I->ev_in_free, &I->ev_out_ready, &I->ev_out_free})
+      CU(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+  }
+  // everything queued on the instance stream so far comes first
+  CU(cudaEventRecord(I->ev_in_free, I->stream));
+  CU(cudaStreamWaitEvent(I->s_up, I->ev_in_free, 0));
+  CU(cudaStreamWaitEvent(I->s_down, I->ev_in_free, 0));
+  CU(cudaMemcpyAsync(I->io_in, q_in[0], bytes, cudaMemcpyHostToDevice, I->s_up));
+  CU(cudaEventRecord(I->ev_up, I->s_up));
+  for (int j = 0; j < count; j++) {
+    // state j from the staging copy (and the float shadow in FP32-flux mode)
+    CU(cudaStreamWaitEvent(I->stream, I->ev_up, 0));
+    int rc = copy_state_in(I, I->io_in, MPRK_DEVICE);
+    if (rc) return rc;
+    CU(cudaEventRecord(I->ev_in_free, I->stream));
+    // input j+1 uploads while step j runs
+    if (j + 1 < count) {
+      CU(cudaStreamWaitEvent(I->s_up, I->ev_in_free, 0));
+      CU(cudaMemcpyAsync(I->io_in, q_in[j + 1], bytes, cudaMemcpyHostToDevice, I->s_up));
+      CU(cudaEventRecord(I->ev_up, I->s_up));
+    }
+    if ((rc = mprk_step(I, 1))) return rc;
+    // result j to the output staging copy once result j-1 has left it, then
+    // down to the host while step j+1 runs
+    if (j > 0) CU(cudaStreamWaitEvent(I->stream, I->ev_out_free, 0));
+    CU(cudaMemcpy2DAsync(I->io_out, row, I->b.qA, (size_t)g.pitch * 8, row, rows, cudaMemcpyDeviceToDevice,
+                         I->stream));
+    CU(cudaEventRecord(I->ev_out_ready, I->stream));
+    CU(cudaStreamWaitEvent(I->s_down, I->ev_out_ready, 0));
+    CU(cudaMemcpyAsync(q_out[j], I->io_out, bytes, cudaMemcpyDeviceToHost, I->s_down));
+    CU(cudaEventRecord(I->ev_out_free, I->s_down));
+  }
+  CU(cudaStreamSynchronize(I->s_down));
   CU(cudaStreamSynchronize(I->stream));
   return MPRK_OK;
 }

@@ -111,6 +111,7 @@ def lib():
         "mprk_step": (ip, [vp, ip]),
         "mprk_get_state": (ip, [vp, vp, ip]),
         "mprk_set_state": (ip, [vp, vp, ip]),
+        "mprk_step_io": (ip, [vp, C.POINTER(vp), C.POINTER(vp), ip]),
         "mprk_diagnostics": (ip, [vp, dp]),
         "mprk_sync": (ip, [vp]),
         "mprk_status": (ip, [vp]),
@@ -194,6 +195,24 @@ def mprk_get_state(h: int, out) -> None:
 def mprk_set_state(h: int, q) -> None:
     addr, loc = _ptr(q)
     _check(lib().mprk_set_state(C.c_void_p(h), C.c_void_p(addr), loc))
+
+
+def mprk_step_io(h: int, q_in, q_out) -> None:
+    """One slow step per input, end to end through host buffers (lists of
+    numpy arrays or CPU tensors, pinned for the copy/compute overlap)."""
+    if len(q_in) != len(q_out):
+        raise ValueError("q_in and q_out differ in length")
+    ins, outs = [], []
+    for a, b in zip(q_in, q_out):
+        (ai, li), (bo, lo) = _ptr(a), _ptr(b)
+        if li != MPRK_HOST or lo != MPRK_HOST:
+            raise ValueError("mprk_step_io takes host buffers")
+        ins.append(ai)
+        outs.append(bo)
+    n = len(ins)
+    arr_in = (C.c_void_p * max(n, 1))(*ins)
+    arr_out = (C.c_void_p * max(n, 1))(*outs)
+    _check(lib().mprk_step_io(C.c_void_p(h), arr_in, arr_out, n))
 
 
 def mprk_diagnostics(h: int) -> np.ndarray:
