@@ -1,6 +1,7 @@
 // mprk_runtime.cu — host runtime behind the C ABI of include/mprk.h: instance
-// buffers, the slow step captured as a CUDA graph, state I/O, monitoring and
-// the right-hand-side test hook. No code path computes on the CPU.
+// buffers, the slow step captured as a CUDA graph, state I/O (with a row-copy
+// kernel for device-to-device copies), monitoring and the right-hand-side
+// test hook. No code path computes on the CPU.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -23,6 +24,25 @@ thread_local std::string g_err;
 void mprk::set_last_error(const std::string& msg) { g_err = msg; }
 
 namespace {
+
+// rows x width doubles from src (row stride spitch) to dst (row stride
+// dpitch), on the SMs: a copy-engine 2-D copy between device buffers runs
+// well below HBM bandwidth. x over columns, y over rows (grid-stride).
+__global__ void copy_rows_kernel(double* __restrict__ dst, size_t dpitch, const double* __restrict__ src,
+                                 size_t spitch, int width, long long rows) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= width) return;
+  for (long long r = blockIdx.y; r < rows; r += gridDim.y) dst[r * dpitch + c] = src[r * spitch + c];
+}
+
+cudaError_t copy_rows(double* dst, size_t dpitch, const double* src, size_t spitch, int width, long long rows,
+                      cudaStream_t s) {
+  if (width <= 0 || rows <= 0) return cudaSuccess;
+  const dim3 block(256);
+  const dim3 grid((unsigned)((width + 255) / 256), (unsigned)(rows < 32768 ? rows : 32768));
+  copy_rows_kernel<<<grid, block, 0, s>>>(dst, dpitch, src, spitch, width, rows);
+  return cudaGetLastError();
+}
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -203,9 +223,12 @@ int capture(mprk_instance* I, bool with_diag, cudaGraphExec_t* out) {
 
 int copy_state_in(mprk_instance* I, const double* q, int loc) {
   const Geom& g = I->g;
-  cudaMemcpyKind kind = loc == MPRK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  CU(cudaMemcpy2DAsync(I->b.qA, (size_t)g.pitch * 8, q, (size_t)g.nx * 8, (size_t)g.nx * 8,
-                       (size_t)g.nc * g.nz * g.ny, kind, I->stream));
+  const long long rows = (long long)g.nc * g.nz * g.ny;
+  if (loc == MPRK_DEVICE)
+    CU(copy_rows(I->b.qA, (size_t)g.pitch, q, (size_t)g.nx, g.nx, rows, I->stream));
+  else
+    CU(cudaMemcpy2DAsync(I->b.qA, (size_t)g.pitch * 8, q, (size_t)g.nx * 8, (size_t)g.nx * 8, (size_t)rows,
+                         cudaMemcpyHostToDevice, I->stream));
   if (I->b.dA && I->b.rowc) CU(launch_shadow(g, I->b.qA, I->b.rowc, I->b.dA, I->stream));
   return MPRK_OK;
 }
@@ -544,9 +567,12 @@ int mprk_get_state(mprk_instance* I, double* q_out, int location) {
   if (!I || !q_out) return fail(MPRK_EINVAL, "NULL argument");
   if (location != MPRK_HOST && location != MPRK_DEVICE) return fail(MPRK_EINVAL, "bad location");
   const Geom& g = I->g;
-  cudaMemcpyKind kind = location == MPRK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  CU(cudaMemcpy2DAsync(q_out, (size_t)g.nx * 8, I->b.qA, (size_t)g.pitch * 8, (size_t)g.nx * 8,
-                       (size_t)g.nc * g.nz * g.ny, kind, I->stream));
+  const long long rows = (long long)g.nc * g.nz * g.ny;
+  if (location == MPRK_DEVICE)
+    CU(copy_rows(q_out, (size_t)g.nx, I->b.qA, (size_t)g.pitch, g.nx, rows, I->stream));
+  else
+    CU(cudaMemcpy2DAsync(q_out, (size_t)g.nx * 8, I->b.qA, (size_t)g.pitch * 8, (size_t)g.nx * 8, (size_t)rows,
+                         cudaMemcpyDeviceToHost, I->stream));
   CU(cudaStreamSynchronize(I->stream));
   return MPRK_OK;
 }
@@ -590,8 +616,7 @@ int mprk_step_io(mprk_instance* I, const double* const* q_in, double* const* q_o
     // result j to the output staging copy once result j-1 has left it, then
     // down to the host while step j+1 runs
     if (j > 0) CU(cudaStreamWaitEvent(I->stream, I->ev_out_free, 0));
-    CU(cudaMemcpy2DAsync(I->io_out, row, I->b.qA, (size_t)g.pitch * 8, row, rows, cudaMemcpyDeviceToDevice,
-                         I->stream));
+    CU(copy_rows(I->io_out, (size_t)g.nx, I->b.qA, (size_t)g.pitch, g.nx, (long long)rows, I->stream));
     CU(cudaEventRecord(I->ev_out_ready, I->stream));
     CU(cudaStreamWaitEvent(I->s_down, I->ev_out_ready, 0));
     CU(cudaMemcpyAsync(q_out[j], I->io_out, bytes, cudaMemcpyDeviceToHost, I->s_down));
