@@ -151,7 +151,9 @@ int mprk_step_batch(mprk_instance* const* insts, int count, int n_slow_steps);
 
 /* ---- launch tuning ------------------------------------------------------
  * Two choices of the batched launch change no result, only its speed: the
- * stage tiles per work item (1, 2, 4, 8 or 16) and the CTAs per SM (1 to 3).
+ * stage tiles per work item (1, 2, 4, 8 or 16; G consecutive tiles along x,
+ * so a work block of 32G x 8 cells in FP64 and 32G x 16 in FP32 flux) and
+ * the CTAs per SM (1 to 3).
  * A process-wide table keeps, per precision and size bucket (floor(log2) of
  * the mean cells per instance), the fastest pair measured; batches without
  * an entry use 2 tiles per item and every CTA that fits. mprk_step_batch
