@@ -214,6 +214,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def fp32_accuracy(M, cfg, q0, steps: int) -> dict:
+    """The FP32-flux mode against the FP64 path after `steps` slow steps from
+    the same state and dt, and the relative change of each fluid's mass over
+    the run in both. The FP64 path matches the oracle to 1e-12 per slow step
+    (tests/test_gpu_parity.py); the FP32-flux step matches the oracle to
+    1e-5 at this size (tests/test_gpu_full_size.py)."""
+    import ctypes as C
+    c64 = M.mprk_config()
+    C.memmove(C.byref(c64), C.byref(cfg), C.sizeof(cfg))
+    c64.precision = M.MPRK_FP64
+    with M.Instance(cfg, q0) as a:
+        c64.dt = a.info()["dt"]
+        with M.Instance(c64, q0) as b:
+            d0a, d0b = a.diagnostics(), b.diagnostics()
+            a.step(steps)
+            b.step(steps)
+            d1a, d1b = a.diagnostics(), b.diagnostics()
+            qa, qb = a.state(), b.state()
+    scale = np.abs(qb).max(axis=(1, 2))
+    err = np.abs(qa - qb).max(axis=(1, 2)) / np.where(scale > 0, scale, 1.0)
+    drift = lambda d0, d1: [float((d1[0] - d0[0]) / d0[0]), float((d1[4] - d0[4]) / d0[4])]
+    return {"steps": steps, "against": "FP64 path from the same state and dt",
+            "max_rel_err": float(err.max()), "rel_err_rho_rhou_rhow_rhoE": [float(x) for x in err],
+            "mass_drift_fluid1_fluid2": {"fp32flux": drift(d0a, d1a), "fp64": drift(d0b, d1b)}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -290,6 +316,7 @@ def run_ours(args):
     nbytes = q0.nbytes
     e2e_value = replica_value(cs * e2e_steps, ws, e2e_s)
     inst.close()
+    accuracy = fp32_accuracy(M, cfg, q0, wl.steps) if (not fp64 and rank == 0) else None
 
     if rank == 0:
         out = {
@@ -321,6 +348,8 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": sampler.summary(),
         }
+        if accuracy is not None:
+            out["accuracy"] = accuracy
         if not args.no_cpu_baseline and ws == 1:
             out["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(out))
