@@ -156,18 +156,31 @@ namespace {
 
 void fill_geom(mprk_instance* I) { geom_from_config(I->cfg, (I->cfg.nx + 31) / 32 * 32, &I->g); }
 
+// mprk_step_io's staging buffers, copy streams and events: released
+// together (after their queued work) and reset, so a later call starts over.
+void release_io(mprk_instance* I) {
+  for (cudaStream_t* s : {&I->s_up, &I->s_down})
+    if (*s) {
+      cudaStreamSynchronize(*s);
+      cudaStreamDestroy(*s);
+      *s = nullptr;
+    }
+  for (cudaEvent_t* ev : {&I->ev_up, &I->ev_in_free, &I->ev_out_ready, &I->ev_out_free})
+    if (*ev) {
+      cudaEventDestroy(*ev);
+      *ev = nullptr;
+    }
+  for (double** b : {&I->io_in, &I->io_out})
+    if (*b) {
+      cudaFree(*b);
+      *b = nullptr;
+    }
+}
+
 void free_instance(mprk_instance* I) {
   if (!I) return;
   if (I->stream && !I->stream_ordered) cudaStreamSynchronize(I->stream);
-  for (cudaStream_t s : {I->s_up, I->s_down})
-    if (s) {
-      cudaStreamSynchronize(s);
-      cudaStreamDestroy(s);
-    }
-  for (cudaEvent_t ev : {I->ev_up, I->ev_in_free, I->ev_out_ready, I->ev_out_free})
-    if (ev) cudaEventDestroy(ev);
-  if (I->io_in) cudaFree(I->io_in);
-  if (I->io_out) cudaFree(I->io_out);
+  release_io(I);
   if (I->exec) cudaGraphExecDestroy(I->exec);
   if (I->exec_diag) cudaGraphExecDestroy(I->exec_diag);
   void* bufs[] = {I->b.qA,     I->b.qB,     I->b.Ra,     I->b.accB, I->b.accS, I->partials, I->diag_dev,
@@ -577,23 +590,30 @@ int mprk_get_state(mprk_instance* I, double* q_out, int location) {
   return MPRK_OK;
 }
 
-int mprk_step_io(mprk_instance* I, const double* const* q_in, double* const* q_out, int count) {
-  if (!I || !q_in || !q_out) return fail(MPRK_EINVAL, "NULL argument");
-  if (count < 0) return fail(MPRK_EINVAL, "negative count");
-  if (!I->exec) return fail(MPRK_EINVAL, "this instance advances only in batches");
-  for (int j = 0; j < count; j++)
-    if (!q_in[j] || !q_out[j]) return fail(MPRK_EINVAL, "q_in[%d] or q_out[%d] is NULL", j, j);
-  if (count == 0) return MPRK_OK;
-  const Geom& g = I->g;
-  const size_t row = (size_t)g.nx * 8, rows = (size_t)g.nc * g.nz * g.ny, bytes = row * rows;
-  if (!I->io_in) {
-    CU(cudaMalloc(&I->io_in, bytes));
-    CU(cudaMalloc(&I->io_out, bytes));
-    CU(cudaStreamCreateWithFlags(&I->s_up, cudaStreamNonBlocking));
-    CU(cudaStreamCreateWithFlags(&I->s_down, cudaStreamNonBlocking));
-    for (cudaEvent_t* ev : {&I->ev_up, &I->ev_in_free, &I->ev_out_ready, &I->ev_out_free})
-      CU(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+namespace {
+
+// Allocates mprk_step_io's staging buffers, streams and events on first use:
+// all of them or none.
+int io_setup(mprk_instance* I, size_t bytes) {
+  if (I->io_in) return MPRK_OK;
+  cudaError_t e = cudaMalloc(&I->io_in, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&I->io_out, bytes);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&I->s_up, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&I->s_down, cudaStreamNonBlocking);
+  for (cudaEvent_t* ev : {&I->ev_up, &I->ev_in_free, &I->ev_out_ready, &I->ev_out_free})
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    release_io(I);
+    return fail(MPRK_ECUDA, "mprk_step_io set-up: %s", cudaGetErrorString(e));
   }
+  return MPRK_OK;
+}
+
+// Enqueues the pipelined copies and steps of mprk_step_io; returns at the
+// first failure (the caller drains the streams either way).
+int io_enqueue(mprk_instance* I, const double* const* q_in, double* const* q_out, int count) {
+  const Geom& g = I->g;
+  const size_t rows = (size_t)g.nc * g.nz * g.ny, bytes = (size_t)g.nx * 8 * rows;
   // everything queued on the instance stream so far comes first
   CU(cudaEventRecord(I->ev_in_free, I->stream));
   CU(cudaStreamWaitEvent(I->s_up, I->ev_in_free, 0));
@@ -622,8 +642,29 @@ int mprk_step_io(mprk_instance* I, const double* const* q_in, double* const* q_o
     CU(cudaMemcpyAsync(q_out[j], I->io_out, bytes, cudaMemcpyDeviceToHost, I->s_down));
     CU(cudaEventRecord(I->ev_out_free, I->s_down));
   }
-  CU(cudaStreamSynchronize(I->s_down));
-  CU(cudaStreamSynchronize(I->stream));
+  return MPRK_OK;
+}
+
+}  // namespace
+
+int mprk_step_io(mprk_instance* I, const double* const* q_in, double* const* q_out, int count) {
+  if (!I || !q_in || !q_out) return fail(MPRK_EINVAL, "NULL argument");
+  if (count < 0) return fail(MPRK_EINVAL, "negative count");
+  if (!I->exec) return fail(MPRK_EINVAL, "this instance advances only in batches");
+  for (int j = 0; j < count; j++)
+    if (!q_in[j] || !q_out[j]) return fail(MPRK_EINVAL, "q_in[%d] or q_out[%d] is NULL", j, j);
+  if (count == 0) return MPRK_OK;
+  const Geom& g = I->g;
+  int rc = io_setup(I, (size_t)g.nx * 8 * g.nc * g.nz * g.ny);
+  if (rc) return rc;
+  rc = io_enqueue(I, q_in, q_out, count);
+  // whatever was queued finishes before the caller's buffers are released,
+  // also after a failure part way
+  const cudaError_t e_up = cudaStreamSynchronize(I->s_up), e_down = cudaStreamSynchronize(I->s_down),
+                    e_st = cudaStreamSynchronize(I->stream);
+  if (rc) return rc;
+  for (cudaError_t e : {e_up, e_down, e_st})
+    if (e != cudaSuccess) return fail(MPRK_ECUDA, "mprk_step_io: %s", cudaGetErrorString(e));
   return MPRK_OK;
 }
 
