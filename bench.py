@@ -336,7 +336,8 @@ def run_ours(args):
                 if fp64 else
                 {"bound": "hbm", "achieved": ach_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                  "frac": ach_gbs / peaks["hbm_gbs"], "traffic": traffic, "peak_source": src,
-                 "alu_achieved_gflops": ach_gflops, "alu_peak_gflops": peak_alu}),
+                 "alu_achieved_gflops": ach_gflops, "alu_peak_gflops": peak_alu,
+                 "alu_frac": ach_gflops / peak_alu, "alu_peak_source": "FP32 unit count x max clock"}),
             "kernel": {"name": kname,
                        "ms_per_step": stage_ms, "cell_stages_per_step": stage_cells,
                        "launches_per_step": 2 * wl.m,
@@ -428,17 +429,23 @@ def run_batched(args):
     # roofline of the whole batched launch (stage tiles and completions)
     fp64 = args.precision != "fp32flux"
     peaks, src = measured_peaks()
+    # both fractions: the FP64 (or FP32) units and HBM, from the algorithmic
+    # flops and bytes of every instance's stages and completion
+    nbytes = sum(sum(algorithmic_bytes(wl.grid, wl.m, fp64)) for wl in wls)
+    gbs = nbytes * args.steps / (t_batch * 1e-3) / 1e9
+    gflops = cs * FLOPS_PER_CELL_STAGE[fp64] * args.steps / (t_batch * 1e-3) / 1e9
     if fp64:
-        ach = cs * FLOPS_PER_CELL_STAGE[True] * args.steps / (t_batch * 1e-3) / 1e9
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": ach / FP64_PEAK_GFLOPS, "traffic": None,
-                "peak_source": "FP64 unit count x max clock (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
+        roof = {"bound": "alu", "achieved": gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": gflops / FP64_PEAK_GFLOPS, "traffic": None,
+                "peak_source": "FP64 unit count x max clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "hbm_achieved_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_frac": gbs / peaks["hbm_gbs"],
+                "hbm_peak_source": src, "algorithmic_bytes_per_step": nbytes}
     else:
-        nbytes = sum(sum(algorithmic_bytes(wl.grid, wl.m, False)) for wl in wls)
-        ach = nbytes * args.steps / (t_batch * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
-                "algorithmic_bytes_per_step": nbytes}
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                "algorithmic_bytes_per_step": nbytes, "alu_achieved_gflops": gflops,
+                "alu_peak_gflops": FP32_PEAK_GFLOPS, "alu_frac": gflops / FP32_PEAK_GFLOPS,
+                "alu_peak_source": "FP32 unit count x max clock"}
     for i in insts:
         i.close()
     out = {
@@ -516,6 +523,7 @@ def run_served(args):
     offered = sum(r[3] for r in reqs) / arrivals[-1]
     peaks, src = measured_peaks()
     gbs = sum(reqs[j][4] for j in range(n_warm, len(reqs))) / (t_last - t_first) / 1e9
+    gflops = value * FLOPS_PER_CELL_STAGE[False] / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": "cell-stages/s", "n_gpus": ws,
         "steps": n_meas, "warmup": n_warm, "ms_per_step": None, "higher_is_better": True,
@@ -528,7 +536,9 @@ def run_served(args):
                    "batched_steps": sstats[2], "wall_s": wall},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
-                     "note": "algorithmic bytes of the measured requests over their first submit to last finish"},
+                     "note": "algorithmic bytes of the measured requests over their first submit to last finish",
+                     "alu_achieved_gflops": gflops, "alu_peak_gflops": FP32_PEAK_GFLOPS,
+                     "alu_frac": gflops / FP32_PEAK_GFLOPS, "alu_peak_source": "FP32 unit count x max clock"},
         "gpu_launches": int(sstats[2]),
         "clocks": sampler.summary(),
     }
@@ -658,7 +668,9 @@ def run_cube(args):
                         "frac": ach / FP64_PEAK_GFLOPS, "traffic": None,
                         "peak_source": "FP64 unit count x max clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
                         "hbm_achieved_gbs": stage_bytes / (stage_ms * 1e-3) / 1e9,
-                        "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": src},
+                        "hbm_peak_gbs": peaks["hbm_gbs"],
+                        "hbm_frac": stage_bytes / (stage_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                        "hbm_peak_source": src},
            "kernel": {"name": "yface3_kernel + stage3_kernel", "ms_per_step": stage_ms,
                       "cell_stages_per_step": stage_cells, "launches_per_step": 4 * wl.m,
                       "algorithmic_bytes_per_step": stage_bytes, "completion_bytes_per_step": fin_bytes},
