@@ -379,14 +379,23 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
     free_plan(p);
     return bfail(MPRK_ECUDA, "batch plan: argument table not 16-byte aligned");
   }
-  cudaMemcpy(p->d_insts, hinst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice);
-  cudaMemcpy(p->d_args, hargs.data(), sizeof(StageArgs) * hargs.size(), cudaMemcpyHostToDevice);
-  cudaMemcpy(p->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
+  if ((e = cudaMemcpy(p->d_insts, hinst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(p->d_args, hargs.data(), sizeof(StageArgs) * hargs.size(), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(p->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice)) !=
+          cudaSuccess) {
+    free_plan(p);
+    return bfail(MPRK_ECUDA, std::string("batch plan upload: ") + cudaGetErrorString(e));
+  }
   // grid: every CTA resident (persistent kernel)
   const size_t smem = stage_smem_bytes(p->precision);
   int per_sm = 0, dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
+    free_plan(p);
+    return bfail(MPRK_ECUDA, std::string("batch plan device query: ") + cudaGetErrorString(e));
+  }
   // dynamic shared memory above 48 KB needs the kernel attribute first
   if (p->precision == 0) {
     e = cudaFuncSetAttribute(batch_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -572,6 +581,9 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
   bool same = (int)r->key.size() == count;
   for (int j = 0; j < count && same; j++) same = r->key[j] == insts[j];
   if (!same) {
+    // forget the previous set first: a failure below may already have
+    // replaced its device buffers, and must make the next call rebuild
+    r->key.clear();
     std::vector<BatchInst> hinst(count);
     int n_counters = 0;
     for (int j = 0; j < count; j++) {
@@ -619,8 +631,11 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
     if (r->per_sm == 0) {
       const size_t smem = stage_smem_bytes(r->precision);
       int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&r->sms, cudaDevAttrMultiProcessorCount, dev);
+      if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+          (e = cudaDeviceGetAttribute(&r->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
+        r->key.clear();  // rebuild on the next call
+        return bfail(MPRK_ECUDA, std::string("batch runner device query: ") + cudaGetErrorString(e));
+      }
       if (r->precision == 0) {
         e = cudaFuncSetAttribute(batch_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r->per_sm, batch_kernel<0>, batch_threads(0), smem);
@@ -628,7 +643,11 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
         e = cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r->per_sm, batch_kernel<1>, batch_threads(1), smem);
       }
-      if (e != cudaSuccess || r->per_sm < 1) return bfail(MPRK_ECUDA, "batch runner: occupancy query failed");
+      if (e != cudaSuccess || r->per_sm < 1) {
+        r->key.clear();
+        r->per_sm = 0;
+        return bfail(MPRK_ECUDA, "batch runner: occupancy query failed");
+      }
     }
     r->grid = (per_sm_want > 0 ? std::min(per_sm_want, r->per_sm) : r->per_sm) * r->sms;
   }
