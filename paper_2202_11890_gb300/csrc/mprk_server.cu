@@ -136,9 +136,16 @@ void server_loop(mprk_server* S) {
     S->thread_msg = "server: device or stream set-up failed";
     return;
   }
-  cudaEvent_t step_ev[2];
-  cudaEventCreateWithFlags(&step_ev[0], cudaEventDisableTiming);
-  cudaEventCreateWithFlags(&step_ev[1], cudaEventDisableTiming);
+  cudaEvent_t step_ev[2] = {nullptr, nullptr};
+  if (cudaEventCreateWithFlags(&step_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&step_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    for (cudaEvent_t e : step_ev)
+      if (e) cudaEventDestroy(e);
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->thread_error = MPRK_ECUDA;
+    S->thread_msg = "server: event set-up failed";
+    return;
+  }
   bool step_ev_used[2] = {false, false};
   int it = 0;
   for (;;) {
@@ -178,11 +185,11 @@ void server_loop(mprk_server* S) {
     if (!admit.empty()) {
       runner_invalidate(S->runner[0]);
       runner_invalidate(S->runner[1]);
-      cudaEvent_t ev;
-      cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-      cudaEventRecord(ev, S->copy);
-      cudaStreamWaitEvent(S->compute, ev, 0);
-      cudaEventDestroy(ev);
+      cudaEvent_t ev = nullptr;
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventRecord(ev, S->copy) != cudaSuccess || cudaStreamWaitEvent(S->compute, ev, 0) != cudaSuccess)
+        cudaStreamSynchronize(S->copy);  // the uploads land before the step either way
+      if (ev) cudaEventDestroy(ev);
     }
 
     // ---- 2. one batched slow step for every resident instance ------------
@@ -234,8 +241,14 @@ void server_loop(mprk_server* S) {
             cudaMemcpyAsync(reinterpret_cast<char*>(r->pinned) + nbytes, status, sizeof(unsigned),
                             cudaMemcpyDeviceToHost, S->copy);
           }
-          cudaEventCreateWithFlags(&r->copied, cudaEventDisableTiming);
-          cudaEventRecord(r->copied, S->copy);
+          r->copied = nullptr;
+          if (cudaEventCreateWithFlags(&r->copied, cudaEventDisableTiming) != cudaSuccess ||
+              cudaEventRecord(r->copied, S->copy) != cudaSuccess) {
+            // no event to poll: wait for the copy here
+            if (r->copied) cudaEventDestroy(r->copied);
+            r->copied = nullptr;
+            cudaStreamSynchronize(S->copy);
+          }
           r->error = err;
           S->retiring.push_back(r);
         } else {
@@ -254,11 +267,12 @@ void server_loop(mprk_server* S) {
     // ---- 4. complete retirements whose copies are done --------------------
     std::vector<Request*> still;
     for (Request* r : S->retiring) {
-      if (cudaEventQuery(r->copied) != cudaSuccess) {
+      const cudaError_t q = r->copied ? cudaEventQuery(r->copied) : cudaSuccess;
+      if (q == cudaErrorNotReady) {
         still.push_back(r);
         continue;
       }
-      cudaEventDestroy(r->copied);
+      if (r->copied) cudaEventDestroy(r->copied);
       r->copied = nullptr;
       Geom g;
       Bufs b;
@@ -268,6 +282,7 @@ void server_loop(mprk_server* S) {
       instance_view(r->inst, &g, &b, &prec, &st, &status);
       const size_t n = (size_t)4 * g.nz * g.nx;
       int error = r->error;
+      if (!error && q != cudaSuccess) error = MPRK_ECUDA;  // the copy did not complete
       if (r->pinned) {
         r->result.assign(r->pinned, r->pinned + n);
         unsigned sw;
