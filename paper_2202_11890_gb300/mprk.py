@@ -154,12 +154,15 @@ def _check(rc: int) -> int:
 
 
 def _ptr(a):
-    """(address, location) of a numpy array or a torch tensor."""
+    """(address, location) of a C-contiguous float64 numpy array or torch
+    tensor; anything else raises TypeError (the library takes raw pointers)."""
     if isinstance(a, np.ndarray):
-        assert a.dtype == np.float64 and a.flags.c_contiguous
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("state buffers are C-contiguous float64 arrays")
         return a.ctypes.data, MPRK_HOST
     import torch  # device memory comes from torch
-    assert isinstance(a, torch.Tensor) and a.dtype == torch.float64 and a.is_contiguous()
+    if not (isinstance(a, torch.Tensor) and a.dtype == torch.float64 and a.is_contiguous()):
+        raise TypeError("state buffers are contiguous float64 tensors or numpy arrays")
     return a.data_ptr(), (MPRK_DEVICE if a.is_cuda else MPRK_HOST)
 
 

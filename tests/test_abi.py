@@ -117,3 +117,21 @@ def test_tuning_table_round_trip_without_a_device(lib, tmp_path):
     with pytest.raises(M.MprkError):
         M.mprk_tune_load(str(bad))
     M.mprk_tune_clear()
+
+
+def test_binding_rejects_buffers_it_cannot_pass_as_pointers():
+    """The binding hands raw pointers to the library, so it takes only
+    C-contiguous float64 arrays and tensors and raises TypeError otherwise
+    (also under python -O)."""
+    from paper_2202_11890_gb300 import mprk as M
+    a = np.zeros((4, 3, 5))
+    assert M._ptr(a) == (a.ctypes.data, M.MPRK_HOST)
+    for bad in (np.zeros((4, 3, 5), dtype=np.float32), np.zeros((4, 3, 10))[:, :, ::2], [0.0] * 4):
+        with pytest.raises(TypeError):
+            M._ptr(bad)
+    torch = pytest.importorskip("torch")
+    t = torch.zeros(4, 3, 5, dtype=torch.float64)
+    assert M._ptr(t) == (t.data_ptr(), M.MPRK_HOST)
+    for bad in (torch.zeros(4, 3, 5), torch.zeros(4, 5, 3, dtype=torch.float64).transpose(1, 2)):
+        with pytest.raises(TypeError):
+            M._ptr(bad)
