@@ -471,19 +471,33 @@ Plan* find_plan(mprk_instance* const* insts, int count, long long wait_cycles, i
   return nullptr;
 }
 
+// Every member non-null and listed once: two work items on one instance's
+// buffers in the same launch would race.
+int check_members(mprk_instance* const* insts, int count) {
+  std::vector<const void*> v(insts, insts + count);
+  for (const void* p : v)
+    if (!p) return bfail(MPRK_EINVAL, "NULL instance in batch");
+  std::sort(v.begin(), v.end());
+  if (std::adjacent_find(v.begin(), v.end()) != v.end())
+    return bfail(MPRK_EINVAL, "an instance appears twice in the batch");
+  return MPRK_OK;
+}
+
 int step_batch(mprk_instance* const* insts, int count, int n, long long wait_cycles, int wi, int ws,
                cudaStream_t stream, long long* cell_stages) {
   if (!insts || count <= 0) return bfail(MPRK_EINVAL, "empty batch");
   if (n < 0) return bfail(MPRK_EINVAL, "negative step count");
-  for (int j = 0; j < count; j++)
-    if (!insts[j]) return bfail(MPRK_EINVAL, "NULL instance in batch");
+  if (int rc = check_members(insts, count)) return rc;
   std::lock_guard<std::mutex> lk(g_batch_mu);
   Plan* p = find_plan(insts, count, wait_cycles, wi, ws, stream);
   if (!p) {
     int rc = build_plan(insts, count, wait_cycles, wi, ws, stream, 0, 0, &p);
     if (rc) return rc;
     if (g_plans.size() >= 64) {
-      free_plan(g_plans.front());
+      // the oldest plan's launches may still be running on its stream
+      Plan* old = g_plans.front();
+      if (old->stream) cudaStreamSynchronize(old->stream);
+      free_plan(old);
       g_plans.erase(g_plans.begin());
     }
     g_plans.push_back(p);
@@ -705,6 +719,7 @@ int mprk_step_batch(mprk_instance* const* insts, int count, int n_slow_steps) {
 
 int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out[3]) {
   if (!insts || count <= 0 || reps < 1 || !out) return bfail(MPRK_EINVAL, "bad tuning arguments");
+  if (int rc = check_members(insts, count)) return rc;
   // the runs advance the states: keep them (and the step counts) to restore
   std::vector<std::vector<double>> saved(count);
   std::vector<long long> steps(count);

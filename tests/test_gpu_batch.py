@@ -119,6 +119,22 @@ def test_batch_rejects_mixed_precisions():
         ib.close()
 
 
+def test_batch_rejects_an_instance_listed_twice():
+    """Two work items on one instance's buffers in one launch would race:
+    the batch and the tuner refuse the list, and the instance still steps."""
+    from paper_2202_11890_gb300 import mprk as M
+    cfg, P, q = uneven(1, 33, 0)[0]
+    with M.Instance(cfg, q) as inst:
+        for call in (lambda: M.mprk_step_batch([inst.h, inst.h], 1),
+                     lambda: M.mprk_batch_tune([inst.h, inst.h], reps=1)):
+            with pytest.raises(M.MprkError) as ei:
+                call()
+            assert ei.value.code == M.MPRK_EINVAL
+        M.mprk_step_batch([inst.h], 1)
+        q_or, _ = O.mprk_step(P, q)
+        assert np.all(rel_err(inst.state(), q_or) < 1e-12)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_tuned_launch_leaves_states_and_results_unchanged(precision, tmp_path):
     """mprk_batch_tune restores every state and step count it advanced, its
