@@ -53,13 +53,13 @@ CSRC = os.path.join(ROOT, "paper_2202_11890_gb300", "csrc")
 TRAFFIC = {
     "stage_kernel": {
         "files": ("stage_tile.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "ea26998041765ff8bec403170af5538b73882691bf90e1be84400f6370963e9a",
-        "bytes_per_step": 1179626496,
+        "sha256": "d230c66b3ee168acc3b58409c0177deb1ce215f71a6b1023c49cb800aae5e17f",
+        "bytes_per_step": 1180983296,
     },
     "stage_kernel_mixed": {
         "files": ("stage_tile_mixed.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "6ec23e9fe334fec5d02ccc34981df2fda2de32b4dbfa5d430da8c98096d4d711",
-        "bytes_per_step": 5197735680,
+        "sha256": "bb6a132d30b142f26d1ff8b5160a136755b81dcb67d958badb9a3d115baf66b0",
+        "bytes_per_step": 5197622528,
     },
 }
 

@@ -22,15 +22,16 @@
 namespace mprk {
 
 // GEN: the general s-stage base (RK3, RK4) in place of Heun's low-storage
-// combination. Three CTAs per SM: 80 registers, a few spilled in the tile.
-// NT = 2 NTHREADS: two threads per cell for launches of few tiles (one CTA
-// per SM).
-template <typename Real, typename Store, bool GEN = false, int NT = NTHREADS>
-__global__ void __launch_bounds__(NT, NT == NTHREADS ? 3 : 1)
+// combination. TZR: tile rows (TZ; 4 or 2 for launches of few tiles). One
+// thread per cell: 80 registers, a few spilled in the tile (three 32 x 8
+// CTAs per SM). NT = 2 TX TZR: two threads per cell for launches with no
+// more tiles than SMs.
+template <typename Real, typename Store, bool GEN = false, int NT = NTHREADS, int TZR = TZ>
+__global__ void __launch_bounds__(NT, NT == TX * TZR ? 3 * NTHREADS / NT : 1)
     stage_kernel(const StageArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  TileSmem<Real>& S = *reinterpret_cast<TileSmem<Real>*>(smem_raw);
-  stage_tile<Real, Store, GEN, NT>(a, blockIdx.x, S);
+  TileSmem<Real, TZR>& S = *reinterpret_cast<TileSmem<Real, TZR>*>(smem_raw);
+  stage_tile<Real, Store, GEN, NT, TZR>(a, blockIdx.x, S);
 }
 
 // FP32-flux stage kernel: one CTA per tile, blockIdx = (tile column, tile
@@ -169,20 +170,45 @@ int sm_count() {
 }
 }  // namespace
 
+namespace {
+// One FP64 stage launch with TZR-row tiles; wide: two threads per cell.
+template <int TZR>
+void launch_fp64(const StageArgs& a, int n_tiles, bool wide, cudaStream_t stream) {
+  constexpr int NT1 = TX * TZR, NT2 = 2 * TX * TZR;
+  const size_t smem = sizeof(TileSmem<double, TZR>);
+  if (wide && a.g.gen)
+    stage_kernel<double, double, true, NT2, TZR><<<n_tiles, NT2, smem, stream>>>(a);
+  else if (wide)
+    stage_kernel<double, double, false, NT2, TZR><<<n_tiles, NT2, smem, stream>>>(a);
+  else if (a.g.gen)
+    stage_kernel<double, double, true, NT1, TZR><<<n_tiles, NT1, smem, stream>>>(a);
+  else
+    stage_kernel<double, double, false, NT1, TZR><<<n_tiles, NT1, smem, stream>>>(a);
+}
+}  // namespace
+
 cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStream_t stream,
                          const StageMaps* maps) {
   if (n_tiles <= 0) return cudaSuccess;
-  // a launch of no more tiles than SMs runs two threads per cell
-  constexpr int WIDE = 2 * NTHREADS;
-  const bool wide = precision == 0 && n_tiles <= sm_count();
-  if (wide && a.g.gen) {
-    stage_kernel<double, double, true, WIDE><<<n_tiles, WIDE, sizeof(TileSmem<double>), stream>>>(a);
-  } else if (wide) {
-    stage_kernel<double, double, false, WIDE><<<n_tiles, WIDE, sizeof(TileSmem<double>), stream>>>(a);
-  } else if (precision == 0 && a.g.gen) {
-    stage_kernel<double, double, true><<<n_tiles, NTHREADS, sizeof(TileSmem<double>), stream>>>(a);
-  } else if (precision == 0) {
-    stage_kernel<double, double><<<n_tiles, NTHREADS, sizeof(TileSmem<double>), stream>>>(a);
+  if (precision == 0) {
+    // FP64: one SM completes two FP64 operations per clock, so a launch of
+    // fewer tiles than SMs is bound by the FP64 work of one tile. Take the
+    // shortest tile (TZ/4, TZ/2 or TZ rows) whose launch still fits in one
+    // wave, with two threads per cell; a launch that does not fit even with
+    // TZ rows keeps them, one thread per cell. (Two shorter tiles on an SM
+    // ran slower than one TZ-row tile with two threads per cell.)
+    const int sms = sm_count();
+    StageArgs s = a;
+    int n = n_tiles;
+    for (const int t : {TZ / 4, TZ / 2, TZ}) {
+      s.tz = t;
+      n = stage_tiles(s);
+      if (n <= sms) break;
+    }
+    const bool wide = n <= sms;
+    if (s.tz == TZ) launch_fp64<TZ>(s, n, wide, stream);
+    else if (s.tz == TZ / 2) launch_fp64<TZ / 2>(s, n, wide, stream);
+    else launch_fp64<TZ / 4>(s, n, wide, stream);
   } else {
     StageArgs s = a;
     CUtensorMap none;

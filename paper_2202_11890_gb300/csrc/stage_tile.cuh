@@ -40,16 +40,16 @@ enum {
   FC_N
 };
 
-template <typename Real>
+template <typename Real, int TZR = TZ>
 struct TileSmem {
-  Real q[4][TZ + 4][TX + 4];   // stage state, rows k0-2.., cols i0-2..
-  Real v[3][TZ + 2][TX + 2];   // u, w, T, rows k0-1.., cols i0-1..
-  Real hx[4][TZ][TX + 2];      // central x differences of q, cols i0-1..
-  Real hz[4][TZ + 2][TX];      // central z differences of q, rows k0-1..
-  Real tz[2][TZ][TX + 2];      // central z differences of u, w (tangential at x faces)
-  Real tx[2][TZ + 2][TX];      // central x differences of u, w (tangential at z faces)
-  Real fx[4][TZ][TX + 1];      // x face fluxes / dx, face f between cols f-1, f
-  Real fz[4][TZ + 1][TX];      // z face fluxes / dz seen from above
+  Real q[4][TZR + 4][TX + 4];   // stage state, rows k0-2.., cols i0-2..
+  Real v[3][TZR + 2][TX + 2];   // u, w, T, rows k0-1.., cols i0-1..
+  Real hx[4][TZR][TX + 2];      // central x differences of q, cols i0-1..
+  Real hz[4][TZR + 2][TX];      // central z differences of q, rows k0-1..
+  Real tz[2][TZR][TX + 2];      // central z differences of u, w (tangential at x faces)
+  Real tx[2][TZR + 2][TX];      // central x differences of u, w (tangential at z faces)
+  Real fx[4][TZR][TX + 1];      // x face fluxes / dx, face f between cols f-1, f
+  Real fz[4][TZR + 1][TX];      // z face fluxes / dz seen from above
   Real fg[4][TX];              // interface flux / dz1 seen from fluid 1 (below)
   double gam[4][TX + 2];       // sigma_xz, Pi_z, u_w, T_w per column i0-1..
   Real fc[2][2][FC_N];         // face constants per direction (x, z) and fluid (1, 2)
@@ -188,16 +188,16 @@ __device__ __forceinline__ double gen_stage_value(const Geom& g, const double* b
 // more warps of the few tiles there are: every phase but the last spreads
 // its work over all threads, and the last (one cell per thread) uses the
 // first NTHREADS.
-template <typename Real, typename Store, bool GEN = false, int NT = NTHREADS>
+template <typename Real, typename Store, bool GEN = false, int NT = NTHREADS, int TZR = TZ>
 __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int tile,
-                                       TileSmem<Real>& __restrict__ S) {
+                                       TileSmem<Real, TZR>& __restrict__ S) {
   // __restrict__: the argument block and shared memory never alias, so its
   // fields need not be reloaded after shared-memory stores
   const Geom& g = a.g;
   const int tid = threadIdx.x;
   const int tzi = tile / a.tiles_x;
   const int txi = tile - tzi * a.tiles_x;
-  const int k0 = a.row0 + tzi * TZ;
+  const int k0 = a.row0 + tzi * TZR;
   const int i0 = txi * TX;
   const int nz = g.nz, nx = g.nx, n1 = g.n1;
   const int row_hi = a.rhs_only ? a.rhs_hi : nz;
@@ -224,9 +224,9 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
     fc[FC_SC] = (Real)sc;
     if (tid == 0) S.gg = (Real)(g.gamma * g.gm1);
   }
-  for (int e = tid; e < 4 * (TZ + 4) * (TX + 4); e += NT) {
-    const int c = e / ((TZ + 4) * (TX + 4));
-    const int rem = e - c * ((TZ + 4) * (TX + 4));
+  for (int e = tid; e < 4 * (TZR + 4) * (TX + 4); e += NT) {
+    const int c = e / ((TZR + 4) * (TX + 4));
+    const int rem = e - c * ((TZR + 4) * (TX + 4));
     const int rr = rem / (TX + 4), cc = rem - rr * (TX + 4);
     const int k = k0 - 2 + rr;
     Real val = Real(0);
@@ -252,12 +252,12 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
     }
     S.q[c][rr][cc] = val;
   }
-  const bool has_gamma = (n1 >= k0 && n1 <= k0 + TZ);
+  const bool has_gamma = (n1 >= k0 && n1 <= k0 + TZR);
   __syncthreads();
 
   // ---- 2. u, w, T on the one-cell ring; interface state -----------------
   const Real gamma = (Real)g.gamma, gm1 = (Real)g.gm1, gg = S.gg;
-  for (int e = tid; e < (TZ + 2) * (TX + 2); e += NT) {
+  for (int e = tid; e < (TZR + 2) * (TX + 2); e += NT) {
     const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
     const int k = k0 - 1 + rr;
     if (k < 0 || k >= nz) continue;
@@ -315,7 +315,7 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
 
   // ---- 3. slopes ---------------------------------------------------------
   // (a) central x differences of q on tile rows, cols i0-1 .. i0+TX
-  for (int e = tid; e < TZ * (TX + 2); e += NT) {
+  for (int e = tid; e < TZR * (TX + 2); e += NT) {
     const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
     if (k0 + rr >= row_hi) continue;
 #pragma unroll
@@ -335,8 +335,8 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
     S.tz[0][rr][cc] = uu - ud;
     S.tz[1][rr][cc] = wu - wd;
   }
-  // (b) central z differences of q on ring rows k0-1 .. k0+TZ, tile cols
-  for (int e = tid; e < (TZ + 2) * TX; e += NT) {
+  // (b) central z differences of q on ring rows k0-1 .. k0+TZR, tile cols
+  for (int e = tid; e < (TZR + 2) * TX; e += NT) {
     const int rr = e / TX, cc = e - rr * TX;
     const int k = k0 - 1 + rr;
     if (k < 0 || k >= nz) continue;
@@ -356,10 +356,10 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
   __syncthreads();
 
   // ---- 4. face fluxes ----------------------------------------------------
-  // z faces first: (TZ+1) rows of TX faces, one warp per face row; then x
+  // z faces first: (TZR+1) rows of TX faces, one warp per face row; then x
   // faces. Every warp sees one face kind.
   const Real quarter = Real(0.25);
-  constexpr int NZF = (TZ + 1) * TX, NXF = TZ * (TX + 1);
+  constexpr int NZF = (TZR + 1) * TX, NXF = TZR * (TX + 1);
   for (int e = tid; e < NZF + NXF; e += NT) {
     Real F[4];
     if (e < NZF) {
@@ -467,7 +467,7 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
   {
     const int rr = tid / TX, cc = tid - rr * TX;
     const int k = k0 + rr, i = i0 + cc;
-    if (rr >= TZ || k >= row_hi || i >= nx) return;
+    if (rr >= TZR || k >= row_hi || i >= nx) return;
     const bool under_gamma = (k == n1 - 1);
     Real R[4];
 #pragma unroll
