@@ -1,7 +1,8 @@
 // stage_tile.cuh — the fused right-hand-side + stage-combination tile of one
 // MPRK2 stage (device code; included by the kernel translation units).
 //
-// One CTA of TX x TZ threads owns a TX x TZ tile of cells. It
+// One CTA of TX x TZR threads owns a TX x TZR tile of cells (TZR = TZ rows,
+// or TZ/2 or TZ/4 for launches of few tiles). It
 //   1. stages the stage state of the tile plus a two-cell halo in shared
 //      memory (x periodic; stage values q + h R_a rebuilt on the fly),
 //   2. computes u, w, T on the tile plus a one-cell ring, and the interface
@@ -183,11 +184,11 @@ __device__ __forceinline__ double gen_stage_value(const Geom& g, const double* b
 // GEN selects the general s-stage base method (Sec. 3 remark) in place of
 // Heun's low-storage path: s R_a slots, the stage values of the region
 // tableaus built from the base, and its weights b in the combinations.
-// NT: threads of the CTA. NTHREADS gives one thread per cell; launches with
-// fewer tiles than the GPU has SMs take 2 NTHREADS, so that each SM holds
+// NT: threads of the CTA. TX x TZR gives one thread per cell; launches with
+// fewer tiles than the GPU has SMs take twice that, so that each SM holds
 // more warps of the few tiles there are: every phase but the last spreads
 // its work over all threads, and the last (one cell per thread) uses the
-// first NTHREADS.
+// first TX x TZR. TZR: tile rows.
 template <typename Real, typename Store, bool GEN = false, int NT = NTHREADS, int TZR = TZ>
 __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int tile,
                                        TileSmem<Real, TZR>& __restrict__ S) {
