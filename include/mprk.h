@@ -70,7 +70,8 @@ extern "C" {
 /* Base Runge-Kutta method of the MPRK framework. Sec. 3 builds the coupled
  * method from any base; the coupling keeps it second order at most, so the
  * higher-order bases serve accuracy experiments. RK3 and RK4 run in FP64 on
- * the 2-D model through mprk_create/mprk_step only. */
+ * the 2-D model: through mprk_create/mprk_step, mprk_step_batch and the
+ * server (not mprk_step_static). */
 #define MPRK_BASE_RK2 0 /* Heun's method: the Table 1 tableaus           */
 #define MPRK_BASE_RK3 1 /* the three-stage third-order SSP method        */
 #define MPRK_BASE_RK4 2 /* the classical four-stage fourth-order method  */
@@ -139,11 +140,13 @@ int mprk_step(mprk_instance* inst, int n_slow_steps);
  * graph-captured launch per slow step that covers every instance's stage
  * tiles and step completions. Items run in stage order; a tile of stage s of
  * an instance waits (bounded, about one second) for all stage s-1 tiles of
- * that instance. Instances may differ in size, m, buffer width and dt, but
- * must share the device and the precision. The batch runs on the first
+ * that instance. Instances may differ in size, m, buffer width, dt and base
+ * method, but must share the device and the precision, and each may appear
+ * only once. The batch runs on the first
  * instance's stream, ordered after and before the other instances' streams
- * with events. Each instance's result equals what mprk_step gives it alone
- * (same tile code, same arithmetic). Asynchronous. A wait that gives up sets
+ * with events. Each instance's result equals what mprk_step gives it alone:
+ * bitwise with the Heun base (same tile code, same arithmetic), and to
+ * rounding (within 1e-12) with the RK3 and RK4 bases. Asynchronous. A wait that gives up sets
  * MPRK_ETIMEOUT in the affected instances' status words (mprk_status); their
  * states are then undefined. In-graph monitoring (diag_every) does not run
  * in batched steps. Errors: MPRK_EINVAL, MPRK_ENOMEM, MPRK_ECUDA. */

@@ -51,7 +51,7 @@ constexpr int ARGS_WORDS = (int)(sizeof(StageArgs) / 16);
 
 struct BatchItem {
   int inst;
-  int stage;  // 0 .. 2m-1, or 2m for a completion item
+  int stage;  // 0 .. s m - 1 (s base stages per fast substep), or s m for a completion item
   int tile;   // first tile of the stage, or first chunk of the completion
   int count;  // consecutive tiles (chunks) the item covers
   int need;   // items of the previous stage this one waits for (0: none)
@@ -66,7 +66,7 @@ constexpr int batch_group(int /*precision*/) { return 2; }
 
 struct BatchArgs {
   const BatchInst* insts;
-  const StageArgs* args;  // [sum over instances of 2m], 16-byte aligned
+  const StageArgs* args;  // [sum over instances of s m], 16-byte aligned
   const BatchItem* items;
   int n_items;
   int* next;           // work counter
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const Bat
     if (it >= A.n_items) break;
     const BatchItem item = A.items[it];
     const BatchInst& I = A.insts[item.inst];
-    const bool stage_item = item.stage < 2 * I.g.m;
+    const bool stage_item = item.stage < I.g.s * I.g.m;
     if (threadIdx.x == 0) {
       s_item[cur ^ 1] = nxt.fetch_add(1, cuda::memory_order_relaxed);
       s_ok = 1;
@@ -169,7 +169,9 @@ __global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const Bat
       if (stage_item) {
         for (int t = 0; t < item.count; t++) {
           if (t > 0) __syncthreads();  // the previous tile is done with shared memory
-          if (PREC == 0)
+          if (PREC == 0 && s_a.g.gen)  // a general s-stage base (RK3, RK4)
+            stage_tile<double, double, true>(s_a, item.tile + t, *reinterpret_cast<TileSmem<double>*>(smem_raw));
+          else if (PREC == 0)
             stage_tile<double, double>(s_a, item.tile + t, *reinterpret_cast<TileSmem<double>*>(smem_raw));
           else if (s_a.stage & 1)  // the FP32-flux tile compiled per stage parity
             batch_tile_mixed<1>(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
@@ -293,7 +295,7 @@ void args_table(std::vector<BatchInst>& hinst, std::vector<StageArgs>& out) {
   out.clear();
   for (BatchInst& bi : hinst) {
     bi.args_base = (int)out.size();
-    for (int st = 0; st < 2 * bi.g.m; st++) out.push_back(stage_args(bi.g, bi.b, st));
+    for (int st = 0; st < bi.g.s * bi.g.m; st++) out.push_back(stage_args(bi.g, bi.b, st));
   }
 }
 
@@ -303,13 +305,13 @@ void args_table(std::vector<BatchInst>& hinst, std::vector<StageArgs>& out) {
 void build_items(const std::vector<BatchInst>& hinst, int G, std::vector<BatchItem>& items,
                  long long* cell_stages) {
   int max_stages = 0;
-  for (const BatchInst& bi : hinst) max_stages = std::max(max_stages, 2 * bi.g.m);
+  for (const BatchInst& bi : hinst) max_stages = std::max(max_stages, bi.g.s * bi.g.m);
   long long cs = 0;
   items.clear();
   for (int st = 0; st <= max_stages; st++) {
     for (int j = 0; j < (int)hinst.size(); j++) {
       const Geom& g = hinst[j].g;
-      const int ms = 2 * g.m;
+      const int ms = g.s * g.m;  // s stages per fast substep
       if (st > ms) continue;
       auto ntiles = [&](int s) {
         if (s < ms) return stage_tiles(stage_args(g, hinst[j].b, s));
@@ -341,9 +343,9 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
     int prec;
     int rc = instance_view(insts[j], &hinst[j].g, &hinst[j].b, &prec, &s, &st);
     if (rc) { free_plan(p); return rc; }
-    if (hinst[j].g.ny > 1 || hinst[j].g.gen) {
+    if (hinst[j].g.ny > 1) {
       free_plan(p);
-      return bfail(MPRK_EINVAL, "batches take 2-D instances with the Heun base only");
+      return bfail(MPRK_EINVAL, "batches take 2-D instances");
     }
     hinst[j].status = st;
     if (j == 0) {
@@ -356,7 +358,7 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
     }
     hinst[j].precision = prec;
     hinst[j].counter_base = p->n_counters;
-    p->n_counters += 2 * hinst[j].g.m + 1;
+    p->n_counters += hinst[j].g.s * hinst[j].g.m + 1;
     p->key.push_back(insts[j]);
   }
   std::vector<StageArgs> hargs;
@@ -607,12 +609,11 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
       int rc = instance_view(insts[j], &hinst[j].g, &hinst[j].b, &prec, &s, &st);
       if (rc) return rc;
       if (prec != r->precision) return bfail(MPRK_EINVAL, "batch runner: precision mismatch");
-      if (hinst[j].g.ny > 1 || hinst[j].g.gen)
-        return bfail(MPRK_EINVAL, "batch runner: 2-D instances with the Heun base only");
+      if (hinst[j].g.ny > 1) return bfail(MPRK_EINVAL, "batch runner: 2-D instances only");
       hinst[j].status = st;
       hinst[j].precision = prec;
       hinst[j].counter_base = n_counters;
-      n_counters += 2 * hinst[j].g.m + 1;
+      n_counters += hinst[j].g.s * hinst[j].g.m + 1;
       if (j == 0) r->status = st;
     }
     int group, per_sm_want;

@@ -296,7 +296,8 @@ void server_loop(mprk_server* S) {
       }
       long long cs_per_step = 0;
       const mprk_config& c = r->cfg;
-      cs_per_step = (long long)c.nx * (2LL * c.nz_S + 2LL * c.m * (c.nz_B + c.nz_F));
+      const long long s = c.base == MPRK_BASE_RK4 ? 4 : (c.base == MPRK_BASE_RK3 ? 3 : 2);  // base stages
+      cs_per_step = (long long)c.nx * (s * c.nz_S + s * c.m * (c.nz_B + c.nz_F));
       r->cell_stages = cs_per_step * r->steps_done;
       destroy_instance(r->inst);  // stream-ordered frees on the copy stream
       r->inst = nullptr;
@@ -351,7 +352,6 @@ int mprk_submit(mprk_server* S, const mprk_config* cfg, const double* q0_host, i
   int rc = validate_config(cfg);
   if (rc) return rc;
   if (cfg->ny > 1) return sfail(MPRK_EINVAL, "the server takes 2-D requests only");
-  if (cfg->base != MPRK_BASE_RK2) return sfail(MPRK_EINVAL, "the server takes the Heun base only");
   const long long bytes = instance_bytes(*cfg);
   if (bytes > S->cfg.hbm_budget_bytes)
     return sfail(MPRK_EBUDGET, "request needs " + std::to_string(bytes) + " device bytes, budget is " +

@@ -89,6 +89,39 @@ def test_served_results_equal_solo_results(precision):
         M.mprk_server_destroy(srv)
 
 
+def test_served_general_base_requests_equal_solo_results():
+    """FP64 requests with the Heun, RK3 and RK4 bases mixed in one server:
+    each result equal to the solve alone (bitwise for Heun, to 1e-12 for the
+    general bases), and the cell-stage count of each reports its s stages
+    per substep."""
+    from paper_2202_11890_gb300 import mprk as M
+    reqs = requests(9, 17, precision=0)
+    bases = [M.MPRK_BASE_RK2, M.MPRK_BASE_RK3, M.MPRK_BASE_RK4]
+    for j, (cfg, q, n) in enumerate(reqs):
+        cfg.base = bases[j % 3]
+    refs = [alone(cfg, q, n) for cfg, q, n in reqs]
+    srv = M.mprk_server_create(hbm_budget_bytes=1 << 30, max_slots=4)
+    try:
+        tickets, order = {}, {}
+        for j, (cfg, q, n) in enumerate(reqs):
+            t = M.mprk_submit(srv, cfg, q, n)
+            tickets[t] = q.shape
+            order[t] = j
+        outs = drain(M, srv, tickets)
+        for t, (buf, err, stats) in outs.items():
+            j = order[t]
+            cfg, q, n = reqs[j]
+            assert err == 0
+            if j % 3 == 0:
+                assert np.array_equal(buf, refs[j]), j
+            else:
+                assert np.all(rel_err(buf, refs[j]) < 1e-12), (j, rel_err(buf, refs[j]))
+            s = 2 + (j % 3)
+            assert stats["cell_stages"] == cfg.nx * (s * cfg.nz_S + s * cfg.m * (cfg.nz_B + cfg.nz_F)) * n
+    finally:
+        M.mprk_server_destroy(srv)
+
+
 def test_admission_order_does_not_change_results():
     from paper_2202_11890_gb300 import mprk as M
     reqs = requests(10, 11)
