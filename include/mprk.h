@@ -281,7 +281,14 @@ int mprk_selftest_convert(const double* in_dev, int n, float* narrow_dev, float*
  * overwritten; the caller owns it. cfg: as for mprk_create, but dt must be
  * given (> 0); diag_every is ignored. cuda_stream: the cudaStream_t to run
  * on (NULL = the default stream). Asynchronous: the result is in q_dev once
- * the stream reaches this work. It matches mprk_step on the same input.
+ * the stream reaches this work. In FP64 it matches mprk_step on the same
+ * input to rounding (the parity bound 1e-12 per component; in practice
+ * bitwise). In the FP32-flux mode it agrees with mprk_step within that
+ * mode's 1e-5: each call rebuilds the mode's per-row reference state and
+ * float shadow from the q_dev it is given, while an instance keeps the
+ * reference of its initial state. The FP32-flux mode also needs nx to be a
+ * multiple of 32 and q_dev to be 256-byte aligned (its tiles move whole
+ * 256-byte row segments); other layouts get MPRK_EINVAL.
  *
  * Scratch comes from one fixed array of MPRK_STATIC_SCRATCH_BYTES that every
  * GPU loading the library holds until the process exits. A configuration
@@ -289,7 +296,9 @@ int mprk_selftest_convert(const double* in_dev, int n, float* narrow_dev, float*
  * The function never calls cudaMalloc, cudaFree or any allocating routine.
  * Its first call on a device (with that device current) looks up the
  * array's device address and sets the kernels' shared-memory limits; make
- * that first call before any stream capture on the device. All calls on a
+ * that first call before any stream capture on the device. The address is
+ * kept per device and CUDA context, so a call after cudaDeviceReset (a new
+ * context) looks it up again, and is then also a first call. All calls on a
  * device share the array, which keeps the last call's contents, so calls
  * whose work overlaps on the GPU race and give undefined results: serialise
  * them (one stream, or events). No scratch entry is read before the call

@@ -30,27 +30,53 @@ constexpr size_t kStaticScratchBytes = MPRK_STATIC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
 
 std::mutex g_mu;
-void* g_scratch_ptr[64] = {nullptr};  // device address of g_scratch, per device
+// Device address of g_scratch per device, valid for the CUDA context it was
+// looked up in: a cudaDeviceReset makes a new primary context, which loads
+// the module again at another address.
+void* g_scratch_ptr[64] = {nullptr};
+CUcontext g_scratch_ctx[64] = {nullptr};
 
 int sfail(int code, const std::string& msg) {
   set_last_error(msg);
   return code;
 }
 
-// Once per device, with that device current: look up the array's device
-// address and set the kernels' shared-memory limits.
+// cuCtxGetCurrent, looked up once through the runtime (no link-time
+// dependency on the driver library).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(p);
+  }();
+  return fn;
+}
+
+// Once per device and context, with that device current: look up the
+// array's device address and set the kernels' shared-memory limits.
 int setup_device(int dev, void** out) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (dev < 0 || dev >= 64) return sfail(MPRK_ECUDA, "device ordinal out of range");
-  if (!g_scratch_ptr[dev]) {
+  const CtxGetCurrentFn get = ctx_get_current();
+  if (!get) return sfail(MPRK_ECUDA, "cuCtxGetCurrent not found in the driver");
+  // null until the runtime has made its context current on this thread
+  CUcontext ctx = nullptr;
+  if (get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+  if (!g_scratch_ptr[dev] || !ctx || g_scratch_ctx[dev] != ctx) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);  // makes the context current if needed
     if (e != cudaSuccess || !p)
       return sfail(MPRK_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     e = prepare_kernels();
     if (e != cudaSuccess)
       return sfail(MPRK_ECUDA, std::string("kernel setup: ") + cudaGetErrorString(e));
+    if (get(&ctx) != CUDA_SUCCESS || !ctx) return sfail(MPRK_ECUDA, "no current CUDA context");
     g_scratch_ptr[dev] = p;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_ptr[dev];
   return MPRK_OK;
@@ -94,6 +120,13 @@ int mprk_step_static(const mprk_config* cfg, double* q_dev, int n_slow_steps, vo
     return sfail(MPRK_EINVAL, "unknown wall type");
   if (!(cfg->dt > 0.0))
     return sfail(MPRK_EINVAL, "mprk_step_static needs an explicit dt > 0");
+  // The FP32-flux tiles prefetch whole 256-byte segments of the double rows
+  // and tensor-copy the float rows, which needs every row of the caller's
+  // unpadded layout to start on a 256-byte boundary: nx a multiple of 32
+  // (a double row is then whole segments) and q_dev itself 256-byte aligned.
+  if (cfg->precision == MPRK_FP32FLUX && (cfg->nx % 32 != 0 || (reinterpret_cast<uintptr_t>(q_dev) & 255u) != 0))
+    return sfail(MPRK_EINVAL,
+                 "the FP32-flux mode of mprk_step_static needs nx a multiple of 32 and q_dev 256-byte aligned");
   if (!(cfg->dx > 0) || !(cfg->dz1 > 0) || !(cfg->dz2 > 0) || !(cfg->gamma > 1.0) ||
       !(cfg->Pr > 0.0) || !(cfg->mu1 > 0.0) || !(cfg->mu2 > 0.0) || !(cfg->G >= 0.0))
     return sfail(MPRK_EINVAL, "invalid physical parameters");

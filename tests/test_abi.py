@@ -135,3 +135,18 @@ def test_binding_rejects_buffers_it_cannot_pass_as_pointers():
     for bad in (torch.zeros(4, 3, 5), torch.zeros(4, 5, 3, dtype=torch.float64).transpose(1, 2)):
         with pytest.raises(TypeError):
             M._ptr(bad)
+
+
+def test_static_entry_point_checks_the_fp32flux_layout_without_a_device(lib):
+    """mprk_step_static's FP32-flux mode moves whole 256-byte row segments
+    of the caller's unpadded state, so it takes only nx a multiple of 32 and
+    a 256-byte aligned state; it says so before any CUDA call. (The pointer
+    values are never dereferenced: the call returns first.)"""
+    from paper_2202_11890_gb300 import mprk as M
+    cases = [(45, 4096), (64, 4096 + 8), (96, 4096 + 128)]
+    for nx, addr in cases:
+        cfg = M.mprk_config_default(nx, 8, 4, 8, 2, dt=1e-3)
+        cfg.precision = M.MPRK_FP32FLUX
+        rc = M.lib().mprk_step_static(C.byref(cfg), C.c_void_p(addr), 1, None)
+        assert rc == M.MPRK_EINVAL, (nx, addr, rc)
+        assert "multiple of 32" in M.mprk_last_error()

@@ -31,7 +31,7 @@ def built():
 
 
 @pytest.mark.parametrize("dims,m,precision", [((45, 9, 5, 11), 2, 0), ((37, 8, 6, 10), 3, 0),
-                                              ((64, 30, 4, 30), 4, 1)])
+                                              ((64, 30, 4, 30), 4, 1), ((96, 21, 6, 21), 3, 1)])
 def test_static_entry_point_matches_mprk_step(dims, m, precision):
     from paper_2202_11890_gb300 import mprk as M
     g = W.Grid(*dims)
