@@ -39,9 +39,28 @@ METRIC = "cell-stage updates/s"
 # divergence and source 24, stage combination 8. The FP32-flux form adds
 # the reference/deviation sums: 12 per face.
 FLOPS_PER_CELL_STAGE = {True: 355.7, False: 381.6}
-# FP64 unit count x clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# Nominal unit counts of the GB300 for context: 152 SMs x 2 DFMA/clk x
+# 2 flop x 2.07 GHz, and 128 FP32 lanes per SM. The FP64 roofline's peak is
+# measured on the box by the library's register-only FMA probe
+# (mprk_probe_fp64), like the HBM peak is a measured copy.
+FP64_NOMINAL_GFLOPS = 152 * 2 * 2 * 2.07
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
+_FP64_PROBE = None
+
+
+def fp64_peak():
+    """(peak GFLOP/s, source) of the FP64 units: the probe's measured FMA
+    rate on this device (run once per process), with the SM count, clock
+    and FMAs per SM clock it saw."""
+    global _FP64_PROBE
+    if _FP64_PROBE is None:
+        from paper_2202_11890_gb300 import mprk as M
+        _FP64_PROBE = M.mprk_probe_fp64()
+    p = _FP64_PROBE
+    src = (f"measured: mprk_probe_fp64, {p['sms']} SMs x {p['dfma_per_clk_per_sm']:.3f} DFMA/clk x 2 flop "
+           f"at {p['sm_mhz']:.0f} MHz = {p['gflops']:.1f} GFLOP/s (nominal 2 DFMA/clk/SM at 2070 MHz: "
+           f"{FP64_NOMINAL_GFLOPS:.1f})")
+    return p["gflops"], src
 
 # DRAM traffic of the stage kernel (dram__bytes_read.sum + dram__bytes_write.sum)
 # summed over the 2m stage launches of one slow step of the bench workload,
@@ -240,6 +259,94 @@ def fp32_accuracy(M, cfg, q0, steps: int) -> dict:
             "mass_drift_fluid1_fluid2": {"fp32flux": drift(d0a, d1a), "fp64": drift(d0b, d1b)}}
 
 
+def roofline_of(fp64: bool, stage_cells: int, stage_ms: float, stage_bytes: float, traffic):
+    """Both fractions of the stage kernel: the binding one first (FP64 units
+    in the FP64 mode, HBM in the FP32-flux mode), the other beside it."""
+    peaks, src = measured_peaks()
+    ach_gflops = stage_cells * FLOPS_PER_CELL_STAGE[fp64] / (stage_ms * 1e-3) / 1e9
+    ach_gbs = stage_bytes / (stage_ms * 1e-3) / 1e9
+    if fp64:
+        peak, psrc = fp64_peak()
+        return {"bound": "alu", "achieved": ach_gflops, "peak": peak, "unit": "GFLOP/s",
+                "frac": ach_gflops / peak, "traffic": traffic, "peak_source": psrc,
+                "hbm_achieved_gbs": ach_gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
+                "hbm_frac": ach_gbs / peaks["hbm_gbs"], "hbm_peak_source": src}
+    return {"bound": "hbm", "achieved": ach_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach_gbs / peaks["hbm_gbs"], "traffic": traffic, "peak_source": src,
+            "alu_achieved_gflops": ach_gflops, "alu_peak_gflops": FP32_PEAK_GFLOPS,
+            "alu_frac": ach_gflops / FP32_PEAK_GFLOPS, "alu_peak_source": "FP32 unit count x max clock (nominal)"}
+
+
+def measure_single(M, T, wl: W.Workload, steps: int, warmup: int, ws: int = 1, e2e: bool = True,
+                   traffic_key: bool = True):
+    """One instance of workload wl: K slow steps timed by CUDA events on the
+    instance stream (max over ranks), the stage kernel's own time inside the
+    step graph, the roofline, clocks and (e2e) the same metric through the C
+    ABI with host buffers. Returns (record, instance config, q0, dt)."""
+    import torch
+    g = wl.grid
+    q0 = wl.initial_state()
+    cfg = M.mprk_config_default(g.nx, g.nS, g.nB, g.nF, wl.m)
+    cfg.precision = M.MPRK_FP32FLUX if wl.precision == "fp32flux" else M.MPRK_FP64
+    fp64 = cfg.precision == M.MPRK_FP64
+    inst = M.Instance(cfg, q0)
+    info = inst.info()
+    cs = info["cell_stages_per_step"]
+    stream = info["stream"]
+    inst.step(warmup)
+    inst.sync()
+    sampler = ClockSampler(torch.cuda.current_device())
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with sampler:
+        t_ms = T.time_steps(inst.h, stream, steps)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_ms = max_over_ranks(t_ms, "cuda")
+    value = replica_value(cs * steps, ws, t_ms * 1e-3)
+    # dominant kernel: the stage launches of one slow step, each timed by
+    # event nodes inside a graph of the step (median of 3 steps)
+    stage_ms, stage_cells = T.stage_kernel_times(inst.h, stream, reps=3)
+    stage_bytes, fin_bytes = algorithmic_bytes(g, wl.m, fp64)
+    kname = "stage_kernel" if fp64 else "stage_kernel_mixed"
+    traffic = measured_traffic(kname, 2 * wl.m) if traffic_key else None
+    rec = {"value": value, "unit": "cell-stages/s", "steps": steps, "warmup": warmup,
+           "ms_per_step": t_ms / steps,
+           "dtype": "f64" if fp64 else "f32 flux / f64 accumulate",
+           "config": {"workload": wl.name, "nx": g.nx, "nz": g.nz, "rows_S_B_F": [g.nS, g.nB, g.nF],
+                      "m": wl.m, "cell_stages_per_step": cs, "dt": info["dt"]},
+           "roofline": roofline_of(fp64, stage_cells, stage_ms, stage_bytes, traffic),
+           "kernel": {"name": kname, "ms_per_step": stage_ms, "cell_stages_per_step": stage_cells,
+                      "launches_per_step": 2 * wl.m, "timed": "event nodes inside a graph of one slow step",
+                      "algorithmic_bytes_per_step": stage_bytes,
+                      "algorithmic_bytes_per_launch": stage_bytes / (2 * wl.m),
+                      "completion_bytes_per_step": fin_bytes},
+           "gpu_launches": (2 * wl.m + 1) * steps,
+           "clocks": sampler.summary()}
+    if e2e:
+        # every step uploads its input state from pinned host memory,
+        # advances one slow step and downloads the result (mprk_step_io
+        # overlaps step j's copies with the neighbouring steps' compute)
+        pin_in = torch.from_numpy(q0).pin_memory()
+        pin_out = torch.empty_like(pin_in).pin_memory()
+        e2e_steps = max(3, min(steps, 20))
+        M.mprk_step_io(inst.h, [pin_in], [pin_out])  # allocates the staging buffers
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        M.mprk_step_io(inst.h, [pin_in] * e2e_steps, [pin_out] * e2e_steps)
+        e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
+        rec["e2e"] = {"value": replica_value(cs * e2e_steps, ws, e2e_s), "unit": "cell-stages/s",
+                      "h2d_bytes_per_step": q0.nbytes, "d2h_bytes_per_step": q0.nbytes, "steps": e2e_steps}
+    dt = info["dt"]
+    inst.close()
+    return rec, cfg, q0, dt
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -255,130 +362,85 @@ def run_ours(args):
     wl = workload(args.workload)
     if args.precision:
         wl.precision = args.precision
-    g = wl.grid
-    q0 = wl.initial_state()
-    cfg = M.mprk_config_default(g.nx, g.nS, g.nB, g.nF, wl.m)
-    cfg.precision = M.MPRK_FP32FLUX if wl.precision == "fp32flux" else M.MPRK_FP64
-    inst = M.Instance(cfg, q0)
-    info = inst.info()
-    cs = info["cell_stages_per_step"]
-    stream = info["stream"]
-    launches_per_step = 2 * wl.m + 1
-
-    # warm-up
-    inst.step(args.warmup)
-    inst.sync()
-
-    # timed region: K slow steps, CUDA events on the instance stream, plus the
-    # stage kernel's own launches bracketed by events inside the graph-free
-    # stage timer (T.stage_kernel_times) run afterwards on the same state
-    sampler = ClockSampler(torch.cuda.current_device())
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with sampler:
-        t_ms = T.time_steps(inst.h, stream, args.steps)
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t_ms = max_over_ranks(t_ms, "cuda")
-    value = replica_value(cs * args.steps, ws, t_ms * 1e-3)
-
-    # dominant kernel: average duration of one stage launch (events on the
-    # instance stream around each launch of one un-captured slow step)
-    stage_ms, stage_cells = T.stage_kernel_times(inst.h, stream, reps=3)
+    traffic_key = args.workload in ("large_2048", "mixed_4096") and not args.precision
+    rec, cfg, q0, dt = measure_single(M, T, wl, args.steps, args.warmup, ws, True, traffic_key)
     fp64 = cfg.precision == M.MPRK_FP64
-    peak_alu = FP64_PEAK_GFLOPS if fp64 else FP32_PEAK_GFLOPS
-    # achieved over all stage launches of a step: algorithmic work / kernel time
-    ach_gflops = stage_cells * FLOPS_PER_CELL_STAGE[fp64] / (stage_ms * 1e-3) / 1e9
-    peaks, src = measured_peaks()
-    stage_bytes, fin_bytes = algorithmic_bytes(g, wl.m, fp64)
-    ach_gbs = stage_bytes / (stage_ms * 1e-3) / 1e9
-    kname = "stage_kernel" if fp64 else "stage_kernel_mixed"
-    # traffic is per launch like achieved: the mean over the 2m stage launches
-    traffic = measured_traffic(kname, 2 * wl.m) if args.workload in ("large_2048", "mixed_4096") \
-        and not args.precision else None
-
-    # end to end through the C ABI with host buffers: every step uploads its
-    # input state from pinned host memory, advances one slow step and
-    # downloads the result (mprk_step_io overlaps step j's copies with the
-    # neighbouring steps' compute)
-    pin_in = torch.from_numpy(q0).pin_memory()
-    pin_out = torch.empty_like(pin_in).pin_memory()
-    e2e_steps = max(3, min(args.steps, 20))
-    M.mprk_step_io(inst.h, [pin_in], [pin_out])  # allocates the staging buffers
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    t0 = time.perf_counter()
-    M.mprk_step_io(inst.h, [pin_in] * e2e_steps, [pin_out] * e2e_steps)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
-    nbytes = q0.nbytes
-    e2e_value = replica_value(cs * e2e_steps, ws, e2e_s)
-    inst.close()
-    accuracy = fp32_accuracy(M, cfg, q0, wl.steps) if (not fp64 and rank == 0) else None
-
     if rank == 0:
-        out = {
-            "metric": METRIC, "value": value, "unit": "cell-stages/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if fp64 else "f32 flux / f64 accumulate", "data": "synthetic",
-            "config": {"workload": wl.name, "nx": g.nx, "nz": g.nz, "rows_S_B_F": [g.nS, g.nB, g.nF],
-                       "m": wl.m, "cell_stages_per_step": cs, "parallelism": f"replicas x{ws}",
-                       "l2": "working set > L2 (about 4 states of 67 MB); no flush"},
-            "roofline": (
-                {"bound": "alu", "achieved": ach_gflops, "peak": peak_alu, "unit": "GFLOP/s",
-                 "frac": ach_gflops / peak_alu, "traffic": traffic,
-                 "peak_source": "FP64 unit count x max clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-                 "hbm_achieved_gbs": ach_gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
-                 "hbm_frac": ach_gbs / peaks["hbm_gbs"], "hbm_peak_source": src}
-                if fp64 else
-                {"bound": "hbm", "achieved": ach_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                 "frac": ach_gbs / peaks["hbm_gbs"], "traffic": traffic, "peak_source": src,
-                 "alu_achieved_gflops": ach_gflops, "alu_peak_gflops": peak_alu,
-                 "alu_frac": ach_gflops / peak_alu, "alu_peak_source": "FP32 unit count x max clock"}),
-            "kernel": {"name": kname,
-                       "ms_per_step": stage_ms, "cell_stages_per_step": stage_cells,
-                       "launches_per_step": 2 * wl.m,
-                       "algorithmic_bytes_per_step": stage_bytes,
-                       "algorithmic_bytes_per_launch": stage_bytes / (2 * wl.m),
-                       "completion_bytes_per_step": fin_bytes},
-            "e2e": {"value": e2e_value, "unit": "cell-stages/s", "h2d_bytes_per_step": nbytes,
-                    "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
-            "gpu_launches": launches_per_step * args.steps,
-            "clocks": sampler.summary(),
-        }
-        if accuracy is not None:
-            out["accuracy"] = accuracy
+        out = {"metric": METRIC, "value": rec["value"], "unit": "cell-stages/s", "n_gpus": ws,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"],
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": rec["dtype"], "data": "synthetic",
+               "config": {**rec["config"], "parallelism": f"replicas x{ws}",
+                          "l2": "working set > L2 (about 4 states of 67 MB); no flush"},
+               "roofline": rec["roofline"], "kernel": rec["kernel"], "e2e": rec["e2e"],
+               "gpu_launches": rec["gpu_launches"], "clocks": rec["clocks"]}
+        if not fp64:
+            out["accuracy"] = mixed_accuracy(M, cfg, q0, wl, dt, args)
         if not args.no_cpu_baseline and ws == 1:
             out["cpu_baseline"] = cpu_baseline(wl)
+        if ws == 1 and args.workload == "large_2048" and not args.precision and not args.no_sub:
+            out["workloads"] = sub_records(args)
         print(json.dumps(out))
     if ws > 1:
         dist.destroy_process_group()
 
 
-def run_batched(args):
-    """256 uneven instances (sides log-uniform in [64, 512], m in {2, 4, 8},
-    buffer 4-16 rows, FP64, or FP32 flux with --precision fp32flux): one
-    persistent launch per slow step (mprk_step_batch) against the same
-    instances stepped one after another with mprk_step on the same stream."""
-    import torch
-    from paper_2202_11890_gb300 import build as B
-    from paper_2202_11890_gb300 import mprk as M
-    from paper_2202_11890_gb300 import timing as T
+def mixed_accuracy(M, cfg, q0, wl, dt, args) -> dict:
+    """The FP32-flux result's error: against the FP64 path over the whole
+    run, and against the oracle at full size over the slow steps of the
+    oracle's timed sample (the CPU-baseline leg)."""
+    acc = {"fp64_path": fp32_accuracy(M, cfg, q0, wl.steps),
+           "tests": ["tests/test_gpu_full_size.py::test_mixed_4096_20_steps_against_oracle (<= 1e-5 after 20 "
+                     "slow steps at full size)",
+                     "tests/test_gpu_full_size.py::test_mixed_strip_whole_run_against_oracle (<= 1e-5 after the "
+                     "500 slow steps on a 64-column strip of the same rows, m and dx)"]}
+    if not args.no_cpu_baseline:
+        acc["oracle"] = oracle_full_size(M, cfg, q0, wl, dt, args.oracle_steps)
+    return acc
 
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    B.build()
-    wls = W.batched_256(count=args.batch_count)
+
+def oracle_full_size(M, cfg, q0, wl, dt, steps: int) -> dict:
+    """CPU-baseline leg of the FP32-flux workload: the oracle as it stands,
+    all host cores, `steps` slow steps of the full-size workload from its
+    initial state with the GPU's dt (timed), and the GPU's FP32-flux state
+    after the same steps compared with it per component."""
+    from oracle import oracle as O
+    g = wl.grid
+    with M.Instance(cfg, q0) as inst:
+        inst.step(steps)
+        q_gpu = inst.state()
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    P = O.make_problem(g.nx, g.nS, g.nB, g.nF, wl.m, dt, g.dx, dz1=g.dz1, dz2=g.dz2)
+    t0 = time.perf_counter()
+    q_or, cnt = O.mprk_step(P, q0, steps)
+    el = time.perf_counter() - t0
+    cnt *= steps  # the oracle counts one step's RHS evaluations
+    scale = np.abs(q_or).max(axis=(1, 2))
+    err = np.abs(q_gpu - q_or).max(axis=(1, 2)) / np.where(scale > 0, scale, 1.0)
+    return {"steps": steps, "against": "the FP64 CPU oracle from the same state and dt (full size)",
+            "max_rel_err": float(err.max()), "rel_err_rho_rhou_rhow_rhoE": [float(x) for x in err],
+            "tolerance": 1e-5,
+            "cpu_baseline": {"value": cnt / el, "unit": "cell-stages/s", "cores": O.get_threads(),
+                             "kind": "oracle",
+                             "sample": f"{steps} full-size slow steps of {wl.name} ({cnt} cell-stages, {el:.1f} s)"}}
+
+
+def measure_batched(M, T, precision: str, steps: int, warmup: int, count: int = 256, tune: bool = False):
+    """256 uneven instances (sides log-uniform in [64, 512], m in {2, 4, 8},
+    buffer 4-16 rows; FP64 or FP32 flux): one persistent launch per slow step
+    (mprk_step_batch) against the same instances stepped one after another
+    with mprk_step on the same stream, and the two paths' results from the
+    same start compared bitwise on 8 instances."""
+    import torch
+    wls = W.batched_256(count=count)
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
     insts, q0s = [], []
     for wl in wls:
         g = wl.grid
         cfg = M.mprk_config_default(g.nx, g.nS, g.nB, g.nF, wl.m)
-        if args.precision == "fp32flux":
+        if precision == "fp32flux":
             cfg.precision = M.MPRK_FP32FLUX
         q0 = wl.initial_state()
         q0s.append(q0)
@@ -395,20 +457,22 @@ def run_batched(args):
     def batched(n):
         M.mprk_step_batch(hs, n)
 
-    # warm-up both paths (graphs, plan), the default launch, then the tuned
-    # one (mprk_batch_tune restores the states it advances)
-    M.mprk_tune_clear()
-    plain(args.warmup)
-    batched(args.warmup)
+    # warm-up both paths (graphs, plan), then the launch the tuning table
+    # gives (defaults when it has no entry; tune=True fills it first)
+    plain(warmup)
+    batched(warmup)
     torch.cuda.synchronize()
-    t_default = T.time_region(sp, lambda: batched(args.steps))
-    tune = M.mprk_batch_tune(hs, reps=3)
-    batched(args.warmup)
-    torch.cuda.synchronize()
+    tuned = None
+    if tune:
+        t_default = T.time_region(sp, lambda: batched(steps))
+        tuned = M.mprk_batch_tune(hs, reps=3)
+        tuned["default_launch_cell_stages_per_s"] = cs * steps / (t_default * 1e-3)
+        batched(warmup)
+        torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device())
     with sampler:
-        t_batch = T.time_region(sp, lambda: batched(args.steps))
-    t_plain = T.time_region(sp, lambda: plain(args.steps))
+        t_batch = T.time_region(sp, lambda: batched(steps))
+        t_plain = T.time_region(sp, lambda: plain(steps))
     # equal accuracy: same start, same steps, both paths, bitwise
     same = True
     for i, q0 in zip(insts[:8], q0s[:8]):
@@ -424,65 +488,76 @@ def run_batched(args):
         same = same and bool(np.array_equal(op, ob))
         scale = np.abs(ob).max(axis=(1, 2))
         maxrel = max(maxrel, float((np.abs(op - ob).max(axis=(1, 2)) / scale).max()))
-    value = cs * args.steps / (t_batch * 1e-3)
-    plain_value = cs * args.steps / (t_plain * 1e-3)
-    # roofline of the whole batched launch (stage tiles and completions)
-    fp64 = args.precision != "fp32flux"
+    value = cs * steps / (t_batch * 1e-3)
+    plain_value = cs * steps / (t_plain * 1e-3)
+    # both fractions of the whole batched launch (stage tiles and
+    # completions), from the algorithmic flops and bytes of every instance
+    fp64 = precision != "fp32flux"
     peaks, src = measured_peaks()
-    # both fractions: the FP64 (or FP32) units and HBM, from the algorithmic
-    # flops and bytes of every instance's stages and completion
     nbytes = sum(sum(algorithmic_bytes(wl.grid, wl.m, fp64)) for wl in wls)
-    gbs = nbytes * args.steps / (t_batch * 1e-3) / 1e9
-    gflops = cs * FLOPS_PER_CELL_STAGE[fp64] * args.steps / (t_batch * 1e-3) / 1e9
+    gbs = nbytes * steps / (t_batch * 1e-3) / 1e9
+    gflops = cs * FLOPS_PER_CELL_STAGE[fp64] * steps / (t_batch * 1e-3) / 1e9
     if fp64:
-        roof = {"bound": "alu", "achieved": gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": gflops / FP64_PEAK_GFLOPS, "traffic": None,
-                "peak_source": "FP64 unit count x max clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-                "hbm_achieved_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_frac": gbs / peaks["hbm_gbs"],
-                "hbm_peak_source": src, "algorithmic_bytes_per_step": nbytes}
+        peak, psrc = fp64_peak()
+        roof = {"bound": "alu", "achieved": gflops, "peak": peak, "unit": "GFLOP/s", "frac": gflops / peak,
+                "traffic": None, "peak_source": psrc, "hbm_achieved_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
+                "hbm_frac": gbs / peaks["hbm_gbs"], "hbm_peak_source": src, "algorithmic_bytes_per_step": nbytes}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
                 "algorithmic_bytes_per_step": nbytes, "alu_achieved_gflops": gflops,
                 "alu_peak_gflops": FP32_PEAK_GFLOPS, "alu_frac": gflops / FP32_PEAK_GFLOPS,
-                "alu_peak_source": "FP32 unit count x max clock"}
+                "alu_peak_source": "FP32 unit count x max clock (nominal)"}
     for i in insts:
         i.close()
-    out = {
-        "metric": METRIC, "value": value, "unit": "cell-stages/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 flux / f64 accumulate" if args.precision == "fp32flux" else "f64", "data": "synthetic",
-        "config": {"workload": f"batched_{len(wls)}_uneven_{args.precision or 'fp64'}", "instances": len(wls),
-                   "cells": cells,
-                   "cell_stages_per_step": cs, "parallelism": "replicas x1"},
-        "batched_vs_plain": {"batched": value, "plain_sequential": plain_value,
-                             "speedup": value / plain_value, "bitwise_equal": same,
-                             "max_rel_diff": maxrel, "plain_ms_per_step": t_plain / args.steps,
-                             "default_launch": cs * args.steps / (t_default * 1e-3)},
-        "tuned_launch": {**tune, "defaults": "2 tiles per item, all CTAs that fit"},
-        "roofline": roof,
-        "gpu_launches": args.steps,
-        "clocks": sampler.summary(),
-    }
-    print(json.dumps(out))
+    rec = {"value": value, "unit": "cell-stages/s", "steps": steps, "warmup": warmup,
+           "ms_per_step": t_batch / steps,
+           "dtype": "f32 flux / f64 accumulate" if precision == "fp32flux" else "f64",
+           "config": {"workload": f"batched_{len(wls)}_uneven_{precision}", "instances": len(wls), "cells": cells,
+                      "cell_stages_per_step": cs},
+           "batched_vs_plain": {"batched": value, "plain_sequential": plain_value, "speedup": value / plain_value,
+                                "bitwise_equal": same, "max_rel_diff": maxrel,
+                                "plain_ms_per_step": t_plain / steps,
+                                "plain": "each instance's own captured step graph (mprk_step), one after another"},
+           "launch": M.mprk_tune_lookup(0 if fp64 else 1, cells / len(wls)),
+           "roofline": roof, "gpu_launches": steps, "clocks": sampler.summary()}
+    if tuned is not None:
+        rec["tuned_launch"] = tuned
+    return rec
 
 
-def run_served(args):
-    """Poisson arrivals (mean 200 requests/s) of FP32-flux solves with sides
-    log-uniform in [32, 1024], m in {2, 4, 8}, buffer 4-16 rows and slow steps
-    log-uniform in [10, 1000], admitted under a 150 GB HBM budget. Reports the
-    aggregate cell-stage rate and p50/p99 latency (finish - submit on the
-    server's clock) of the requests after the warm-up ones."""
+def run_batched(args):
+    """The batched workload on its own line (--workload batched_256)."""
     import torch
     from paper_2202_11890_gb300 import build as B
     from paper_2202_11890_gb300 import mprk as M
+    from paper_2202_11890_gb300 import timing as T
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     B.build()
-    n_warm, n_meas = args.served_warmup, args.served_requests
-    arrivals, wls = W.served_stream(n_warm + n_meas, rate_hz=args.rate)
+    M.mprk_tune_clear()
+    rec = measure_batched(M, T, args.precision or "fp64", args.steps, args.warmup, args.batch_count, tune=True)
+    out = {"metric": METRIC, "value": rec["value"], "unit": "cell-stages/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": rec["dtype"], "data": "synthetic",
+           "config": {**rec["config"], "parallelism": "replicas x1"}}
+    out.update({k: v for k, v in rec.items() if k not in out})
+    print(json.dumps(out))
+
+
+def measure_served(M, rate: float, n_warm: int, n_meas: int, budget_gb: float, slots: int,
+                   sequential: bool = True):
+    """Poisson arrivals (mean `rate` requests/s) of FP32-flux solves with
+    sides log-uniform in [32, 1024], m in {2, 4, 8}, buffer 4-16 rows and slow
+    steps log-uniform in [10, 1000], admitted under an HBM budget. Reports
+    the aggregate cell-stage rate and p50/p99 latency (finish - submit on the
+    server's clock) of the requests after the warm-up ones; with sequential,
+    the same measured requests solved one after another through mprk_create,
+    mprk_step and mprk_get_state, each result checked against the served
+    one."""
+    import torch
+    arrivals, wls = W.served_stream(n_warm + n_meas, rate_hz=rate)
     reqs = []
     for wl in wls:
         g = wl.grid
@@ -490,10 +565,11 @@ def run_served(args):
         cfg.precision = M.MPRK_FP32FLUX
         reqs.append((cfg, wl.initial_state(), wl.steps, wl.cell_stages_per_step() * wl.steps,
                      sum(algorithmic_bytes(g, wl.m, False)) * wl.steps))
-    srv = M.mprk_server_create(hbm_budget_bytes=int(args.budget_gb * 1e9), max_slots=args.slots)
+    srv = M.mprk_server_create(hbm_budget_bytes=int(budget_gb * 1e9), max_slots=slots)
     sampler = ClockSampler(torch.cuda.current_device())
     tickets = {}
     done = {}
+    results = {}
     t0 = time.perf_counter()
     nxt = 0
     with sampler:
@@ -506,8 +582,11 @@ def run_served(args):
             for t, j in list(tickets.items()):
                 st, err, stats = M.mprk_poll(srv, t)
                 if st == M.MPRK_REQ_DONE:
-                    M.mprk_poll(srv, t, np.empty(reqs[j][1].shape))  # read and release
+                    res = np.empty(reqs[j][1].shape)
+                    M.mprk_poll(srv, t, res)  # read and release
                     done[j] = (err, stats)
+                    if sequential and j >= n_warm:
+                        results[j] = res
                     del tickets[t]
             time.sleep(0.0005)
     wall = time.perf_counter() - t0
@@ -518,31 +597,83 @@ def run_served(args):
     errors = sum(1 for e, _ in meas if e)
     t_first = min(s["t_submit"] for _, s in meas)
     t_last = max(s["t_finish"] for _, s in meas)
-    cells = sum(reqs[j][3] for j in range(n_warm, len(reqs)))
-    value = cells / (t_last - t_first)
-    offered = sum(r[3] for r in reqs) / arrivals[-1]
+    work = sum(reqs[j][3] for j in range(n_warm, len(reqs)))
+    value = work / (t_last - t_first)
+    offered = sum(r[3] for r in reqs[n_warm:]) / (arrivals[-1] - arrivals[n_warm])
     peaks, src = measured_peaks()
     gbs = sum(reqs[j][4] for j in range(n_warm, len(reqs))) / (t_last - t_first) / 1e9
-    gflops = value * FLOPS_PER_CELL_STAGE[False] / 1e9
-    out = {
-        "metric": METRIC, "value": value, "unit": "cell-stages/s", "n_gpus": ws,
-        "steps": n_meas, "warmup": n_warm, "ms_per_step": None, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 flux / f64 accumulate",
-        "data": "synthetic",
-        "config": {"workload": "served_poisson_fp32flux", "rate_hz": args.rate, "requests": n_meas,
-                   "budget_gb": args.budget_gb, "max_slots": args.slots, "parallelism": "replicas x1"},
-        "served": {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-                   "mean_latency_s": float(lat.mean()), "errors": errors, "offered_cell_stages_per_s": offered,
-                   "batched_steps": sstats[2], "wall_s": wall},
-        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
-                     "note": "algorithmic bytes of the measured requests over their first submit to last finish",
-                     "alu_achieved_gflops": gflops, "alu_peak_gflops": FP32_PEAK_GFLOPS,
-                     "alu_frac": gflops / FP32_PEAK_GFLOPS, "alu_peak_source": "FP32 unit count x max clock"},
-        "gpu_launches": int(sstats[2]),
-        "clocks": sampler.summary(),
-    }
+    rec = {"value": value, "unit": "cell-stages/s", "requests": n_meas, "warmup_requests": n_warm,
+           "dtype": "f32 flux / f64 accumulate",
+           "config": {"workload": "served_poisson_fp32flux", "rate_hz": rate, "requests": n_meas,
+                      "budget_gb": budget_gb, "max_slots": slots},
+           "served": {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                      "mean_latency_s": float(lat.mean()), "errors": errors,
+                      "offered_cell_stages_per_s": offered, "achieved_over_offered": value / offered,
+                      "batched_steps": int(sstats[2]), "wall_s": wall},
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                        "note": "algorithmic bytes of the measured requests over their first submit to last finish"},
+           "gpu_launches": int(sstats[2]), "clocks": sampler.summary()}
+    if sequential:
+        # the same measured requests without the server: each alone, one
+        # after another, through the plain C ABI calls
+        maxrel = 0.0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j in range(n_warm, len(reqs)):
+            cfg, q, n, _, _ = reqs[j]
+            with M.Instance(cfg, q) as inst:
+                inst.step(n)
+                out = inst.state()
+            r = results[j]
+            scale = np.abs(out).max(axis=(1, 2))
+            maxrel = max(maxrel, float((np.abs(out - r).max(axis=(1, 2)) / scale).max()))
+        seq_s = time.perf_counter() - t0
+        rec["sequential"] = {"value": work / seq_s, "wall_s": seq_s,
+                             "served_over_sequential": value / (work / seq_s),
+                             "max_rel_diff_vs_served": maxrel, "tolerance": 1e-5,
+                             "how": "each measured request alone: mprk_create (upload, graph capture), "
+                                    "mprk_step(n), mprk_get_state, mprk_destroy, one after another"}
+    return rec
+
+
+def run_served(args):
+    """The served workload on its own line (--workload served)."""
+    import torch
+    from paper_2202_11890_gb300 import build as B
+    from paper_2202_11890_gb300 import mprk as M
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    rec = measure_served(M, args.rate, args.served_warmup, args.served_requests, args.budget_gb, args.slots,
+                         sequential=args.served_sequential)
+    out = {"metric": METRIC, "value": rec["value"], "unit": "cell-stages/s", "n_gpus": ws,
+           "steps": args.served_requests, "warmup": args.served_warmup, "ms_per_step": None,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": rec["dtype"],
+           "data": "synthetic", "config": {**rec["config"], "parallelism": "replicas x1"}}
+    out.update({k: v for k, v in rec.items() if k not in out})
     print(json.dumps(out))
+
+
+def sub_records(args) -> dict:
+    """The metric's other parts on the same line as the headline: the
+    FP32-flux workload (HBM roofline, accuracy), the 256-instance batch in
+    both precisions (batched vs plain), and the served Poisson stream
+    (p50/p99 latency, served vs sequential). Each carries its own step
+    counts and clocks."""
+    from paper_2202_11890_gb300 import mprk as M
+    from paper_2202_11890_gb300 import timing as T
+    out = {}
+    wl = W.mixed_4096()
+    rec, cfg, q0, dt = measure_single(M, T, wl, args.sub_steps, args.warmup, 1, True, True)
+    rec["accuracy"] = mixed_accuracy(M, cfg, q0, wl, dt, args)
+    out["mixed_4096"] = rec
+    for prec in ("fp64", "fp32flux"):
+        out[f"batched_256_{prec}"] = measure_batched(M, T, prec, args.sub_steps, args.warmup)
+    out["served"] = measure_served(M, args.rate, args.sub_served_warmup, args.sub_served_requests, args.budget_gb,
+                                   args.slots, sequential=True)
+    return out
 
 
 def run_speedup(args):
@@ -977,6 +1108,13 @@ def main():
     ap.add_argument("--precision", default="", choices=["", "fp64", "fp32flux"])
     ap.add_argument("--ref-cols", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="headline line only, without the other workloads")
+    ap.add_argument("--sub-steps", type=int, default=20, help="slow steps timed per sub-record")
+    ap.add_argument("--sub-served-requests", type=int, default=500)
+    ap.add_argument("--sub-served-warmup", type=int, default=100)
+    ap.add_argument("--served-sequential", action="store_true")
+    ap.add_argument("--oracle-steps", type=int, default=2,
+                    help="full-size oracle slow steps of the FP32-flux CPU-baseline leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

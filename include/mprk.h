@@ -244,8 +244,9 @@ int mprk_info(const mprk_instance* inst, double* dt, long long* cell_stages_per_
  * rows of R outside [k_lo, k_hi) are left untouched. Asynchronous. */
 int mprk_rhs(mprk_instance* inst, const double* W_dev, double* R_dev, int k_lo, int k_hi);
 
-/* Timing hook: run one slow step (it advances the state) with every launch
- * enqueued on its own, bracketed by CUDA events on the instance stream.
+/* Timing hook: run one slow step (it advances the state) as a CUDA graph
+ * captured like the one mprk_step replays, with an event record node before
+ * the first launch and after every launch, on the instance stream.
  * launch_ms[j] receives the duration of launch j and launch_cells[j] the
  * cell right-hand-side evaluations it made (0 for the step completion); the
  * launches are the s*m stages in order (s = 2 for the Heun base), then the
@@ -253,6 +254,17 @@ int mprk_rhs(mprk_instance* inst, const double* W_dev, double* R_dev, int k_lo, 
  * number of launches (at most cap are written) or a negative error code.
  * Synchronises. */
 int mprk_profile_step(mprk_instance* inst, double* launch_ms, long long* launch_cells, int cap);
+
+/* Measurement hook: the FP64 fused multiply-add throughput of the current
+ * device, the denominator of the FP64 path's arithmetic roofline (the RHS
+ * of Sec. 2.1 and App. B is FP64-arithmetic-bound in the FP64 mode). A
+ * register-only kernel runs 8 independent FMA chains of `iters` steps per
+ * thread on eight 256-thread CTAs per SM. Outputs: gflops (2 flop per FMA,
+ * CUDA-event time), dfma_per_clk_per_sm (FMAs per SM clock, with the clock
+ * taken from CTA 0's clock64 count over the launch), sm_mhz (that clock)
+ * and sms (the SM count). Allocates and frees two small device buffers;
+ * synchronises. Errors: MPRK_EINVAL, MPRK_ECUDA. */
+int mprk_probe_fp64(long long iters, double* gflops, double* dfma_per_clk_per_sm, double* sm_mhz, int* sms);
 
 /* Test hook for the FP32-flux mode's conversions, which use integer bit
  * operations because this GPU converts between float and double at the FP64

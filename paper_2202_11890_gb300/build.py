@@ -1,6 +1,6 @@
 """Build the CUDA library libmprk.so for sm_103a with nvcc (in-tree, no cmake).
 
-The two translation units compile in parallel and link into
+The translation units compile in parallel and link into
 paper_2202_11890_gb300/_build/libmprk.so. A rebuild happens only when a source
 or header is newer than the library.
 """
@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmprk.so")
-SOURCES = ["mprk_kernels.cu", "mprk_runtime.cu", "mprk_static.cu", "mprk_batch.cu", "mprk_server.cu"]
+SOURCES = ["mprk_kernels.cu", "mprk_runtime.cu", "mprk_static.cu", "mprk_batch.cu", "mprk_server.cu",
+           "mprk_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

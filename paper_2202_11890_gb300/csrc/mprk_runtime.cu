@@ -754,28 +754,45 @@ int mprk_profile_step(mprk_instance* I, double* launch_ms, long long* launch_cel
   if (!I) return fail(MPRK_EINVAL, "instance is NULL");
   const Geom& g = I->g;
   const int n = g.s * g.m + 1;
+  // The step is captured like the one mprk_step replays, with an event
+  // record node before the first launch and after each launch, and runs as
+  // a graph: each duration is then the kernel as the step graph runs it.
   cudaEvent_t ev[4 * 64 + 2];
-  for (int j = 0; j <= n; j++) CU(cudaEventCreate(&ev[j]));
+  int made = 0;
   int rc = MPRK_OK;
-  CU(cudaEventRecord(ev[0], I->stream));
-  for (int st = 0; st < g.s * g.m && rc == MPRK_OK; st++) {
-    StageArgs a = stage_args(g, I->b, st);
-    a.status = I->status_dev;
-    a.gy = I->gy;
-    cudaError_t e = g.ny > 1 ? launch_stage3(a, I->stream)
-                             : launch_stage(a, I->precision, stage_tiles(a), I->stream, &I->maps);
-    if (e != cudaSuccess) rc = fail(MPRK_ECUDA, "stage launch: %s", cudaGetErrorString(e));
-    cudaEventRecord(ev[st + 1], I->stream);
-    if (st < cap && launch_cells) launch_cells[st] = (long long)(g.nz - a.row0) * g.ny * g.nx;
+  for (; made <= n; made++)
+    if (cudaEventCreate(&ev[made]) != cudaSuccess) {
+      rc = fail(MPRK_ECUDA, "event create failed");
+      break;
+    }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (rc == MPRK_OK) {
+    cudaError_t e = cudaStreamBeginCapture(I->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) rc = fail(MPRK_ECUDA, "profile capture: %s", cudaGetErrorString(e));
   }
   if (rc == MPRK_OK) {
-    cudaError_t e = launch_finalize(g, I->b, g.m & 1, I->stream);
-    if (e != cudaSuccess) rc = fail(MPRK_ECUDA, "completion launch: %s", cudaGetErrorString(e));
-    cudaEventRecord(ev[n], I->stream);
+    cudaError_t e = cudaEventRecordWithFlags(ev[0], I->stream, cudaEventRecordExternal);
+    for (int st = 0; st < g.s * g.m && e == cudaSuccess; st++) {
+      StageArgs a = stage_args(g, I->b, st);
+      a.status = I->status_dev;
+      a.gy = I->gy;
+      e = g.ny > 1 ? launch_stage3(a, I->stream)
+                   : launch_stage(a, I->precision, stage_tiles(a), I->stream, &I->maps);
+      if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[st + 1], I->stream, cudaEventRecordExternal);
+      if (st < cap && launch_cells) launch_cells[st] = (long long)(g.nz - a.row0) * g.ny * g.nx;
+    }
+    if (e == cudaSuccess) e = launch_finalize(g, I->b, g.m & 1, I->stream);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[n], I->stream, cudaEventRecordExternal);
     if (n - 1 < cap && launch_cells) launch_cells[n - 1] = 0;
+    const cudaError_t e2 = cudaStreamEndCapture(I->stream, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphUpload(exec, I->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, I->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
+    if (e != cudaSuccess) rc = fail(MPRK_ECUDA, "profile: %s", cudaGetErrorString(e));
   }
-  cudaError_t e = cudaStreamSynchronize(I->stream);
-  if (rc == MPRK_OK && e != cudaSuccess) rc = fail(MPRK_ECUDA, "profile: %s", cudaGetErrorString(e));
   if (rc == MPRK_OK) {
     for (int j = 0; j < n && j < cap; j++) {
       float ms = 0.f;
@@ -784,7 +801,9 @@ int mprk_profile_step(mprk_instance* I, double* launch_ms, long long* launch_cel
     }
     I->steps_done++;
   }
-  for (int j = 0; j <= n; j++) cudaEventDestroy(ev[j]);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  for (int j = 0; j < made; j++) cudaEventDestroy(ev[j]);
   return rc == MPRK_OK ? n : rc;
 }
 

@@ -119,6 +119,7 @@ def lib():
                            C.POINTER(vp)]),
         "mprk_rhs": (ip, [vp, vp, vp, ip, ip]),
         "mprk_profile_step": (ip, [vp, dp, C.POINTER(C.c_longlong), ip]),
+        "mprk_probe_fp64": (ip, [C.c_longlong, dp, dp, dp, C.POINTER(C.c_int)]),
         "mprk_step_static": (ip, [cfgp, vp, ip, vp]),
         "mprk_step_batch": (ip, [C.POINTER(vp), ip, ip]),
         "mprk_batch_test_withhold": (ip, [C.POINTER(vp), ip, ip, ip, C.c_longlong]),
@@ -251,7 +252,8 @@ def mprk_rhs(h: int, W, R, k_lo: int, k_hi: int) -> None:
 
 
 def mprk_profile_step(h: int):
-    """Per-launch durations (ms) and cell-stages of one un-captured slow step."""
+    """Per-launch durations (ms) and cell-stages of one slow step, run as a
+    graph with an event node after every launch."""
     cap = 4 * 64 + 1
     ms = np.zeros(cap)
     cells = np.zeros(cap, dtype=np.int64)
@@ -260,6 +262,13 @@ def mprk_profile_step(h: int):
     if n < 0:
         raise MprkError(n, mprk_last_error())
     return ms[:n].copy(), cells[:n].copy()
+
+
+def mprk_probe_fp64(iters: int = 24000) -> dict:
+    """FP64 FMA throughput of the current device (register-only probe)."""
+    g, r, mhz, sms = C.c_double(), C.c_double(), C.c_double(), C.c_int()
+    _check(lib().mprk_probe_fp64(int(iters), C.byref(g), C.byref(r), C.byref(mhz), C.byref(sms)))
+    return {"gflops": g.value, "dfma_per_clk_per_sm": r.value, "sm_mhz": mhz.value, "sms": sms.value}
 
 
 def _handles(hs):

@@ -225,10 +225,16 @@ def _modes(rng, xi, zeta, n_modes, amp):
 
 
 def fourier_modes(grid: Grid, seed: int, n_modes: int = 10, amp: float = 1e-2,
-                  gamma=GAMMA, g=G_SIGNED) -> np.ndarray:
+                  gamma=GAMMA, g=G_SIGNED, periodic_on_grid: bool = False) -> np.ndarray:
+    """periodic_on_grid: the x phase runs over the grid's own nx columns,
+    (i + 1/2)/nx, so that a strip narrower than (-5, 5) is periodic too;
+    otherwise over x in (-5, 5)."""
     rng = np.random.default_rng(seed)
     rho0, p0 = rest_primitives(grid, gamma, g)
-    xi = ((grid.x_centres() + 5.0) / 10.0)[None, :]
+    if periodic_on_grid:
+        xi = ((np.arange(grid.nx) + 0.5) / grid.nx)[None, :]
+    else:
+        xi = ((grid.x_centres() + 5.0) / 10.0)[None, :]
     z = grid.z_centres()
     zlo = -grid.n1 * grid.dz1
     zhi = (grid.nz - grid.n1) * grid.dz2
