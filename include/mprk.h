@@ -258,12 +258,13 @@ int mprk_profile_step(mprk_instance* inst, double* launch_ms, long long* launch_
 /* Measurement hook: the FP64 fused multiply-add throughput of the current
  * device, the denominator of the FP64 path's arithmetic roofline (the RHS
  * of Sec. 2.1 and App. B is FP64-arithmetic-bound in the FP64 mode). A
- * register-only kernel runs 8 independent FMA chains of `iters` steps per
- * thread on eight 256-thread CTAs per SM. Outputs: gflops (2 flop per FMA,
- * CUDA-event time), dfma_per_clk_per_sm (FMAs per SM clock, with the clock
- * taken from CTA 0's clock64 count over the launch), sm_mhz (that clock)
- * and sms (the SM count). Allocates and frees two small device buffers;
- * synchronises. Errors: MPRK_EINVAL, MPRK_ECUDA. */
+ * register-only kernel runs 16 independent FMA chains of `iters` steps per
+ * thread (1 <= iters <= 2^30) on one full wave of 256-thread CTAs (as many
+ * as fit on each SM). Each CTA times its loop in SM clocks and in
+ * nanoseconds. Outputs (medians over the CTAs): gflops (2 flop per FMA),
+ * dfma_per_clk_per_sm, sm_mhz (the SM clock during the loop) and sms (the
+ * SM count). Allocates and frees three small device buffers; synchronises.
+ * Errors: MPRK_EINVAL, MPRK_ECUDA. */
 int mprk_probe_fp64(long long iters, double* gflops, double* dfma_per_clk_per_sm, double* sm_mhz, int* sms);
 
 /* Test hook for the FP32-flux mode's conversions, which use integer bit

@@ -264,7 +264,7 @@ def mprk_profile_step(h: int):
     return ms[:n].copy(), cells[:n].copy()
 
 
-def mprk_probe_fp64(iters: int = 24000) -> dict:
+def mprk_probe_fp64(iters: int = 12000) -> dict:
     """FP64 FMA throughput of the current device (register-only probe)."""
     g, r, mhz, sms = C.c_double(), C.c_double(), C.c_double(), C.c_int()
     _check(lib().mprk_probe_fp64(int(iters), C.byref(g), C.byref(r), C.byref(mhz), C.byref(sms)))

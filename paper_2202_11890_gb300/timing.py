@@ -37,12 +37,26 @@ def time_region(stream_ptr: int, fn) -> float:
 
 
 def stage_kernel_times(h: int, stream_ptr: int, reps: int = 3):
-    """Summed duration (ms) of the stage-kernel launches of one slow step and
-    the cell-stages they computed, median over `reps` profiled steps."""
-    tot, cells = [], None
+    """(ms, cell-stages, share): the summed duration of the stage-kernel
+    launches of one slow step, the cell-stages they computed, and their
+    share of the step's launches, medians over `reps` slow steps run as a
+    graph with an event node after every launch. The event nodes add a gap
+    before each launch, so the durations run a little long; their share
+    scaled by the plain graph's step time bounds the kernel's own time
+    (see kernel_ms_per_step)."""
+    tot, share, cells = [], [], None
     for _ in range(reps):
         ms, c = M.mprk_profile_step(h)
         stage = c > 0
         tot.append(float(ms[stage].sum()))
+        share.append(float(ms[stage].sum() / ms.sum()))
         cells = int(c[stage].sum())
-    return float(np.median(tot)), cells
+    return float(np.median(tot)), cells, float(np.median(share))
+
+
+def kernel_ms_per_step(step_ms: float, share: float) -> float:
+    """The stage kernel's time per slow step inside the step graph: its share
+    of the launches (event-timed) times the plain graph's step time. It
+    counts the gaps between launches to the kernels in proportion, so it is
+    an upper bound of their busy time, and never exceeds the step."""
+    return step_ms * share
