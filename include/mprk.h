@@ -152,27 +152,57 @@ int mprk_step(mprk_instance* inst, int n_slow_steps);
  * in batched steps. Errors: MPRK_EINVAL, MPRK_ENOMEM, MPRK_ECUDA. */
 int mprk_step_batch(mprk_instance* const* insts, int count, int n_slow_steps);
 
-/* ---- launch tuning ------------------------------------------------------
- * Two choices of the batched launch change no result, only its speed: the
- * stage tiles per work item (1, 2, 4, 8 or 16; G consecutive tiles along x,
- * so a work block of 32G x 8 cells in FP64 and 32G x 16 in FP32 flux) and
- * the CTAs per SM (1 to 3).
- * A process-wide table keeps, per precision and size bucket (floor(log2) of
- * the mean cells per instance), the fastest pair measured; batches without
- * an entry use 2 tiles per item and every CTA that fits. mprk_step_batch
- * and the server read the table when they build a work list. */
+/* ---- launch and tile-shape tuning ---------------------------------------
+ * Three choices of the batched launch change no result, only its speed:
+ * the stage tiles per work item (1, 2, 4, 8 or 16; G consecutive tiles
+ * along x), the CTAs per SM (1 to 3), and in FP64 the shape of the stage
+ * tile of the 256-thread CTA: 32 x 8 cells with one thread per cell or
+ * 32 x 4 with two (the FP32-flux tile is 32 x 16). Single-instance FP64
+ * stage launches (mprk_step) choose among six tile shapes: 32 x 8, 32 x 4
+ * or 32 x 2 cells, with one or two threads per cell. Every shape evaluates
+ * the same arithmetic in the same order (Sec. 2.1, App. B), so results are
+ * bitwise the same whatever is chosen.
+ * A process-wide table keeps the fastest choices measured:
+ *  - batches: per precision and size bucket (floor(log2) of the mean cells
+ *    per instance); without an entry, 2 tiles per item, every CTA that
+ *    fits and 32 x 8 tiles;
+ *  - single-instance FP64 stage launches: per size bucket (floor(log2) of
+ *    the cells of the launch); without an entry, the shortest tile whose
+ *    launch fits in one wave of the GPU's SMs, with two threads per cell,
+ *    or 32 x 8 with one thread per cell when none fits.
+ * mprk_step_batch, the server and the FP64 stage launches (including graphs
+ * captured afterwards by mprk_create) read the table. */
 
-/* Time every choice on these instances (reps batched slow steps each after
- * one warm-up step), record the fastest in the table and return it in out:
- * {tiles per item, CTAs per SM, ms per slow step}. The instances' states and
- * step counts are restored afterwards. Synchronises. Errors: MPRK_EINVAL,
- * MPRK_ENOMEM, MPRK_ECUDA. */
-int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out[3]);
+/* Time every batch choice on these instances (reps batched slow steps each
+ * after one warm-up step), record the fastest in the table and return it
+ * in out: {tiles per item, CTAs per SM, ms per slow step, FP64 tile rows}.
+ * The instances' states and step counts are restored afterwards.
+ * Synchronises. Errors: MPRK_EINVAL, MPRK_ENOMEM, MPRK_ECUDA. */
+int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out[4]);
 
-/* The table's choice for a precision and a mean instance size in cells:
- * writes it and returns 1, or writes the defaults (ctas_per_sm 0: every CTA
- * that fits) and returns 0. Needs no device. */
-int mprk_tune_lookup(int precision, double mean_cells, int* group, int* ctas_per_sm);
+/* The table's batch choice for a precision and a mean instance size in
+ * cells: writes it and returns 1, or writes the defaults (ctas_per_sm 0:
+ * every CTA that fits) and returns 0. tile_rows: 8 or 4 in FP64 (one or two
+ * threads per cell), 16 in FP32 flux. Needs no device. */
+int mprk_tune_lookup(int precision, double mean_cells, int* group, int* ctas_per_sm, int* tile_rows);
+
+/* Time the six tile shapes of single-instance FP64 stage launches on these
+ * 2-D FP64 instances: for each instance the first stage (every row) and the
+ * first stage of the second fast substep (B and F rows), reps launches of
+ * each shape after a warm-up launch. Both stages read the state and write
+ * only stage scratch, so the states are unchanged. Records, per size bucket
+ * of a launch's cells, the shape with the smallest summed time over the
+ * launches in that bucket, and writes the number of buckets to *entries.
+ * Instances created or graphs captured before the call keep their shapes;
+ * mprk_create captures with the table's. Synchronises. Errors: MPRK_EINVAL,
+ * MPRK_ECUDA. */
+int mprk_tile_tune(mprk_instance* const* insts, int count, int reps, int* entries);
+
+/* The table's tile shape for a single-instance FP64 stage launch of `cells`
+ * cells: writes it (tile rows 8, 4 or 2; threads per cell 1 or 2) and
+ * returns 1, or returns 0 when the table has none (the default rule
+ * applies). Needs no device. */
+int mprk_tile_lookup(double cells, int* tile_rows, int* threads_per_cell);
 
 /* Save the table to a JSON file, {"gpu": <device name>, "entries": [...]}, or
  * replace it from one. Loading a table measured on a GPU of another name
@@ -260,11 +290,13 @@ int mprk_profile_step(mprk_instance* inst, double* launch_ms, long long* launch_
  * of Sec. 2.1 and App. B is FP64-arithmetic-bound in the FP64 mode). A
  * register-only kernel runs 16 independent FMA chains of `iters` steps per
  * thread (1 <= iters <= 2^30) on one full wave of 256-thread CTAs (as many
- * as fit on each SM). Each CTA times its loop in SM clocks and in
- * nanoseconds. Outputs (medians over the CTAs): gflops (2 flop per FMA),
- * dfma_per_clk_per_sm, sm_mhz (the SM clock during the loop) and sms (the
- * SM count). Allocates and frees three small device buffers; synchronises.
- * Errors: MPRK_EINVAL, MPRK_ECUDA. */
+ * as fit on each SM). Each CTA times its loop in SM clocks and on the
+ * global nanosecond timer. Outputs: gflops (2 flop per FMA, every FMA over
+ * the span from the first CTA's start to the last CTA's end),
+ * dfma_per_clk_per_sm (that rate per SM clock), sm_mhz (the median over the
+ * CTAs of their clocks per nanosecond) and sms (the SM count). Allocates and
+ * frees three small device buffers; synchronises. Errors: MPRK_EINVAL,
+ * MPRK_ECUDA. */
 int mprk_probe_fp64(long long iters, double* gflops, double* dfma_per_clk_per_sm, double* sm_mhz, int* sms);
 
 /* Test hook for the FP32-flux mode's conversions, which use integer bit

@@ -131,8 +131,10 @@ __device__ __noinline__ void batch_tile_mixed(const StageArgs& a, int tile, Mixe
 }
 
 // three CTAs per SM in both precisions (80 and 72 registers; the FP32-flux
-// form spills some, and still runs faster than at two CTAs)
-template <int PREC>
+// form spills some, and still runs faster than at two CTAs). ROWS: rows of
+// the FP64 tile, TZ (one thread per cell) or TZ / 2 (two threads per cell);
+// the block size stays the same.
+template <int PREC, int ROWS = TZ>
 __global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // the current and the next claimed item: thread 0 claims the next one
@@ -170,9 +172,11 @@ __global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const Bat
         for (int t = 0; t < item.count; t++) {
           if (t > 0) __syncthreads();  // the previous tile is done with shared memory
           if (PREC == 0 && s_a.g.gen)  // a general s-stage base (RK3, RK4)
-            stage_tile<double, double, true>(s_a, item.tile + t, *reinterpret_cast<TileSmem<double>*>(smem_raw));
+            stage_tile<double, double, true, NTHREADS, ROWS>(s_a, item.tile + t,
+                                                             *reinterpret_cast<TileSmem<double, ROWS>*>(smem_raw));
           else if (PREC == 0)
-            stage_tile<double, double>(s_a, item.tile + t, *reinterpret_cast<TileSmem<double>*>(smem_raw));
+            stage_tile<double, double, false, NTHREADS, ROWS>(s_a, item.tile + t,
+                                                              *reinterpret_cast<TileSmem<double, ROWS>*>(smem_raw));
           else if (s_a.stage & 1)  // the FP32-flux tile compiled per stage parity
             batch_tile_mixed<1>(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
           else
@@ -205,6 +209,7 @@ struct Plan {
   int precision = 0;
   int bucket = 0;      // size bucket of the instance set (tuning key)
   int group = 0;       // tiles per work item
+  int rows = TZ;       // FP64 tile rows (TZ, or TZ / 2 with two threads per cell)
   int per_sm = 0;      // CTAs per SM of the persistent launch
   int per_sm_req = 0;  // CTAs per SM asked for (0: as many as fit)
   int n_items = 0;
@@ -233,10 +238,18 @@ std::vector<Plan*> g_plans;
 struct TuneVal {
   int group, per_sm;
   double ms;
+  int rows;  // FP64 tile rows of the batch kernel (the FP32-flux tile is fixed)
 };
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, TuneVal> g_tune;
 std::string g_tune_gpu;
+// Tile shapes of single-instance FP64 stage launches per size bucket (floor
+// log2 of the launch's cells), measured by mprk_tile_tune.
+struct ShapeVal {
+  TileShape shape;
+  double ms;
+};
+std::map<int, ShapeVal> g_shape;
 
 int size_bucket(const std::vector<BatchInst>& hinst) {
   double cells = 0;
@@ -245,19 +258,23 @@ int size_bucket(const std::vector<BatchInst>& hinst) {
   return std::max(0, std::min(40, (int)std::floor(std::log2(std::max(mean, 1.0)))));
 }
 
-// The tuned (group, per_sm) of a precision and bucket, or the defaults
-// (per_sm 0: as many as fit).
-void tuned_choice(int prec, int bucket, int* group, int* per_sm) {
+// The tuned (group, per_sm, FP64 tile rows) of a precision and bucket, or
+// the defaults (per_sm 0: as many as fit; TZ rows).
+void tuned_choice(int prec, int bucket, int* group, int* per_sm, int* rows) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tune.find({prec, bucket});
   if (it != g_tune.end()) {
     *group = it->second.group;
     *per_sm = it->second.per_sm;
+    *rows = prec == 0 ? it->second.rows : MTZ;
   } else {
     *group = batch_group(prec);
     *per_sm = 0;
+    *rows = prec == 0 ? TZ : MTZ;
   }
 }
+
+int cells_bucket(double cells) { return std::max(0, std::min(40, (int)std::floor(std::log2(std::max(cells, 1.0))))); }
 
 std::string device_name() {
   int dev = 0;
@@ -289,20 +306,50 @@ void free_plan(Plan* p) {
 
 namespace {
 
+// Stage arguments of an instance of the batch: FP64 tiles of `rows` rows.
+StageArgs batch_stage_args(const BatchInst& bi, int st, int rows) {
+  StageArgs a = stage_args(bi.g, bi.b, st);
+  if (bi.precision == 0) a.tz = rows;
+  return a;
+}
+
 // The stage arguments of every instance and stage, in instance order; sets
 // each instance's args_base.
-void args_table(std::vector<BatchInst>& hinst, std::vector<StageArgs>& out) {
+void args_table(std::vector<BatchInst>& hinst, int rows, std::vector<StageArgs>& out) {
   out.clear();
   for (BatchInst& bi : hinst) {
     bi.args_base = (int)out.size();
-    for (int st = 0; st < bi.g.s * bi.g.m; st++) out.push_back(stage_args(bi.g, bi.b, st));
+    for (int st = 0; st < bi.g.s * bi.g.m; st++) out.push_back(batch_stage_args(bi, st, rows));
   }
+}
+
+// The persistent kernel of a precision and FP64 tile rows: its shared-memory
+// limit, its CTAs per SM and its launch.
+cudaError_t batch_prepare(int prec, int rows, size_t smem, int* per_sm) {
+  cudaError_t e;
+  if (prec == 1) {
+    e = cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<1>, batch_threads(1), smem);
+  } else if (rows == TZ / 2) {
+    e = cudaFuncSetAttribute(batch_kernel<0, TZ / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<0, TZ / 2>, batch_threads(0), smem);
+  } else {
+    e = cudaFuncSetAttribute(batch_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<0>, batch_threads(0), smem);
+  }
+  return e;
+}
+void batch_launch(int prec, int rows, int grid, size_t smem, cudaStream_t s, const BatchArgs& A) {
+  if (prec == 1) batch_kernel<1><<<grid, batch_threads(1), smem, s>>>(A);
+  else if (rows == TZ / 2) batch_kernel<0, TZ / 2><<<grid, batch_threads(0), smem, s>>>(A);
+  else batch_kernel<0><<<grid, batch_threads(0), smem, s>>>(A);
 }
 
 // The stage-major work list: all first-stage items of all instances, then
 // all second-stage items, ...; each instance's completion items follow its
 // last stage. Items group G consecutive tiles.
-void build_items(const std::vector<BatchInst>& hinst, int G, std::vector<BatchItem>& items,
+void build_items(const std::vector<BatchInst>& hinst, int G, int rows, std::vector<BatchItem>& items,
                  long long* cell_stages) {
   int max_stages = 0;
   for (const BatchInst& bi : hinst) max_stages = std::max(max_stages, bi.g.s * bi.g.m);
@@ -314,7 +361,7 @@ void build_items(const std::vector<BatchInst>& hinst, int G, std::vector<BatchIt
       const int ms = g.s * g.m;  // s stages per fast substep
       if (st > ms) continue;
       auto ntiles = [&](int s) {
-        if (s < ms) return stage_tiles(stage_args(g, hinst[j].b, s));
+        if (s < ms) return stage_tiles(batch_stage_args(hinst[j], s, rows));
         const int rows = ((g.m & 1) || hinst[j].b.dA) ? g.nz : g.n1_r;
         const long long total = 4LL * rows * g.nx;
         return (int)((total + FIN_CHUNK - 1) / FIN_CHUNK);
@@ -328,9 +375,10 @@ void build_items(const std::vector<BatchInst>& hinst, int G, std::vector<BatchIt
   *cell_stages = cs;
 }
 
-// group / per_sm: the launch choices, or 0 for the tuned (else default) ones.
+// group / per_sm / rows: the launch choices, or 0 for the tuned (else
+// default) ones.
 int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, int wi, int ws,
-               cudaStream_t stream, int group, int per_sm_want, Plan** out) {
+               cudaStream_t stream, int group, int per_sm_want, int rows, Plan** out) {
   Plan* p = new Plan();
   p->wait_cycles = wait_cycles;
   p->withhold_inst = wi;
@@ -361,13 +409,16 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
     p->n_counters += hinst[j].g.s * hinst[j].g.m + 1;
     p->key.push_back(insts[j]);
   }
-  std::vector<StageArgs> hargs;
-  args_table(hinst, hargs);
   p->bucket = size_bucket(hinst);
-  if (group <= 0) tuned_choice(p->precision, p->bucket, &group, &per_sm_want);
+  if (group <= 0) tuned_choice(p->precision, p->bucket, &group, &per_sm_want, &rows);
+  if (p->precision != 0) rows = MTZ;
+  else if (rows != TZ && rows != TZ / 2) rows = TZ;
   p->group = group;
+  p->rows = rows;
+  std::vector<StageArgs> hargs;
+  args_table(hinst, rows, hargs);
   std::vector<BatchItem> items;
-  build_items(hinst, group, items, &p->cell_stages);
+  build_items(hinst, group, rows, items, &p->cell_stages);
   p->n_items = (int)items.size();
   cudaError_t e;
   if ((e = cudaMalloc(&p->d_insts, sizeof(BatchInst) * count)) != cudaSuccess ||
@@ -399,15 +450,7 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
     return bfail(MPRK_ECUDA, std::string("batch plan device query: ") + cudaGetErrorString(e));
   }
   // dynamic shared memory above 48 KB needs the kernel attribute first
-  if (p->precision == 0) {
-    e = cudaFuncSetAttribute(batch_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<0>, batch_threads(0), smem);
-  } else {
-    e = cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<1>, batch_threads(1), smem);
-  }
+  e = batch_prepare(p->precision, p->rows, smem, &per_sm);
   if (e != cudaSuccess || per_sm < 1) {
     free_plan(p);
     return bfail(MPRK_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e) + ", " +
@@ -434,8 +477,7 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
   e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaMemsetAsync(p->d_ctr, 0, sizeof(int) * (2 + p->n_counters), p->stream);
-    if (p->precision == 0) batch_kernel<0><<<p->grid, batch_threads(0), smem, p->stream>>>(A);
-    else batch_kernel<1><<<p->grid, batch_threads(1), smem, p->stream>>>(A);
+    batch_launch(p->precision, p->rows, p->grid, smem, p->stream, A);
     cudaError_t el = cudaGetLastError();
     e = cudaStreamEndCapture(p->stream, &graph);
     if (el != cudaSuccess) e = el;
@@ -462,9 +504,9 @@ Plan* find_plan(mprk_instance* const* insts, int count, long long wait_cycles, i
     bool same = true;
     for (int j = 0; j < count && same; j++) same = p->key[j] == insts[j];
     if (!same) continue;
-    int group, per_sm;
-    tuned_choice(p->precision, p->bucket, &group, &per_sm);
-    if (group == p->group && per_sm == p->per_sm_req) return p;
+    int group, per_sm, rows;
+    tuned_choice(p->precision, p->bucket, &group, &per_sm, &rows);
+    if (group == p->group && per_sm == p->per_sm_req && rows == p->rows) return p;
     if (p->stream) cudaStreamSynchronize(p->stream);
     free_plan(p);
     g_plans.erase(g_plans.begin() + k);
@@ -493,7 +535,7 @@ int step_batch(mprk_instance* const* insts, int count, int n, long long wait_cyc
   std::lock_guard<std::mutex> lk(g_batch_mu);
   Plan* p = find_plan(insts, count, wait_cycles, wi, ws, stream);
   if (!p) {
-    int rc = build_plan(insts, count, wait_cycles, wi, ws, stream, 0, 0, &p);
+    int rc = build_plan(insts, count, wait_cycles, wi, ws, stream, 0, 0, 0, &p);
     if (rc) return rc;
     if (g_plans.size() >= 64) {
       // the oldest plan's launches may still be running on its stream
@@ -556,6 +598,7 @@ struct BatchRunner {
   int* d_ctr = nullptr;
   size_t cap_insts = 0, cap_args = 0, cap_items = 0, cap_ctr = 0;
   int n_items = 0, n_counters = 0, grid = 0, per_sm = 0, sms = 0;
+  int rows = TZ;  // FP64 tile rows of the current work list
   long long cell_stages = 0;
   unsigned* status = nullptr;
 };
@@ -616,13 +659,15 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
       n_counters += hinst[j].g.s * hinst[j].g.m + 1;
       if (j == 0) r->status = st;
     }
-    int group, per_sm_want;
-    tuned_choice(r->precision, size_bucket(hinst), &group, &per_sm_want);
+    int group, per_sm_want, rows;
+    tuned_choice(r->precision, size_bucket(hinst), &group, &per_sm_want, &rows);
+    if (r->precision == 0 && rows != r->rows) r->per_sm = 0;  // another kernel: query its occupancy
+    r->rows = rows;
     std::vector<StageArgs> hargs;
-    args_table(hinst, hargs);
+    args_table(hinst, rows, hargs);
     std::vector<BatchItem> items;
     long long cs = 0;
-    build_items(hinst, group, items, &cs);
+    build_items(hinst, group, rows, items, &cs);
     cudaError_t e = grow(&r->d_insts, &r->cap_insts, (size_t)count, r->stream);
     if (e == cudaSuccess) e = grow(&r->d_args, &r->cap_args, hargs.size(), r->stream);
     if (e == cudaSuccess) e = grow(&r->d_items, &r->cap_items, items.size(), r->stream);
@@ -651,13 +696,7 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
         r->key.clear();  // rebuild on the next call
         return bfail(MPRK_ECUDA, std::string("batch runner device query: ") + cudaGetErrorString(e));
       }
-      if (r->precision == 0) {
-        e = cudaFuncSetAttribute(batch_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r->per_sm, batch_kernel<0>, batch_threads(0), smem);
-      } else {
-        e = cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r->per_sm, batch_kernel<1>, batch_threads(1), smem);
-      }
+      e = batch_prepare(r->precision, r->rows, smem, &r->per_sm);
       if (e != cudaSuccess || r->per_sm < 1) {
         r->key.clear();
         r->per_sm = 0;
@@ -682,13 +721,21 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
   if (e != cudaSuccess) return bfail(MPRK_ECUDA, std::string("batch runner: ") + cudaGetErrorString(e));
   const size_t smem = stage_smem_bytes(r->precision);
   const int grid = std::min(r->grid, r->n_items);
-  if (r->precision == 0) batch_kernel<0><<<grid, batch_threads(0), smem, r->stream>>>(A);
-  else batch_kernel<1><<<grid, batch_threads(1), smem, r->stream>>>(A);
+  batch_launch(r->precision, r->rows, grid, smem, r->stream, A);
   e = cudaGetLastError();
   if (e != cudaSuccess) return bfail(MPRK_ECUDA, std::string("batch runner launch: ") + cudaGetErrorString(e));
   for (int j = 0; j < count; j++) instance_count_steps(insts[j], 1);
   if (cell_stages) *cell_stages = r->cell_stages;
   return MPRK_OK;
+}
+
+bool tuned_tile_shape(long long cells, TileShape* out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_shape.empty()) return false;
+  auto it = g_shape.find(cells_bucket((double)cells));
+  if (it == g_shape.end()) return false;
+  *out = it->second.shape;
+  return true;
 }
 
 int batch_step_on(mprk_instance* const* insts, int count, int n, cudaStream_t stream, long long* cell_stages) {
@@ -718,7 +765,7 @@ int mprk_step_batch(mprk_instance* const* insts, int count, int n_slow_steps) {
   return step_batch(insts, count, n_slow_steps, 2000000000LL, -1, -1, nullptr, nullptr);
 }
 
-int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out[3]) {
+int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out[4]) {
   if (!insts || count <= 0 || reps < 1 || !out) return bfail(MPRK_EINVAL, "bad tuning arguments");
   if (int rc = check_members(insts, count)) return rc;
   // the runs advance the states: keep them (and the step counts) to restore
@@ -738,35 +785,50 @@ int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out
     steps[j] = instance_steps(insts[j]);
   }
   std::lock_guard<std::mutex> lk(g_batch_mu);
-  int best_g = 0, best_c = 0, prec = 0, bucket = 0;
+  int best_g = 0, best_c = 0, best_r = TZ, prec = 0, bucket = 0;
   double best_ms = 1e300;
   int rc = MPRK_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = bfail(MPRK_ECUDA, "event create");
-  for (int G : {1, 2, 4, 8, 16}) {
-    for (int c = 1; c <= 3 && rc == MPRK_OK; c++) {
-      Plan* p = nullptr;
-      rc = build_plan(insts, count, 2000000000LL, -1, -1, nullptr, G, c, &p);
-      if (rc) break;
-      prec = p->precision;
-      bucket = p->bucket;
-      if (p->per_sm < c) {  // more CTAs than fit
+  // FP64 tile shapes of the 256-thread CTA: TZ rows with one thread per
+  // cell, TZ / 2 rows with two; the FP32-flux tile has one shape
+  int prec0 = 0;
+  {
+    Geom g;
+    Bufs b;
+    cudaStream_t st;
+    unsigned* sw;
+    if ((rc = instance_view(insts[0], &g, &b, &prec0, &st, &sw))) prec0 = 0;
+  }
+  const std::vector<int> row_choices = prec0 == 0 ? std::vector<int>{TZ, TZ / 2} : std::vector<int>{MTZ};
+  for (int R : row_choices) {
+    for (int G : {1, 2, 4, 8, 16}) {
+      for (int c = 1; c <= 3 && rc == MPRK_OK; c++) {
+        Plan* p = nullptr;
+        rc = build_plan(insts, count, 2000000000LL, -1, -1, nullptr, G, c, R, &p);
+        if (rc) break;
+        prec = p->precision;
+        bucket = p->bucket;
+        if (p->per_sm < c) {  // more CTAs than fit
+          free_plan(p);
+          continue;
+        }
+        cudaGraphLaunch(p->exec, p->stream);  // warm-up
+        cudaEventRecord(e0, p->stream);
+        for (int k = 0; k < reps; k++) cudaGraphLaunch(p->exec, p->stream);
+        cudaEventRecord(e1, p->stream);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+          rc = bfail(MPRK_ECUDA, "tuning run failed");
         free_plan(p);
-        continue;
+        if (rc == MPRK_OK && ms / reps < best_ms) {
+          best_ms = ms / reps;
+          best_g = G;
+          best_c = c;
+          best_r = R;
+        }
       }
-      cudaGraphLaunch(p->exec, p->stream);  // warm-up
-      cudaEventRecord(e0, p->stream);
-      for (int k = 0; k < reps; k++) cudaGraphLaunch(p->exec, p->stream);
-      cudaEventRecord(e1, p->stream);
-      float ms = 0.f;
-      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
-        rc = bfail(MPRK_ECUDA, "tuning run failed");
-      free_plan(p);
-      if (rc == MPRK_OK && ms / reps < best_ms) {
-        best_ms = ms / reps;
-        best_g = G;
-        best_c = c;
-      }
+      if (rc) break;
     }
     if (rc) break;
   }
@@ -780,34 +842,105 @@ int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out
   if (rc) return rc;
   {
     std::lock_guard<std::mutex> tl(g_tune_mu);
-    g_tune[{prec, bucket}] = TuneVal{best_g, best_c, best_ms};
+    g_tune[{prec, bucket}] = TuneVal{best_g, best_c, best_ms, best_r};
     g_tune_gpu = device_name();
   }
   out[0] = best_g;
   out[1] = best_c;
   out[2] = best_ms;
+  out[3] = best_r;
   return MPRK_OK;
 }
 
-int mprk_tune_lookup(int precision, double mean_cells, int* group, int* ctas_per_sm) {
-  if (!group || !ctas_per_sm || precision < 0 || precision > 1 || !(mean_cells >= 1.0))
+int mprk_tune_lookup(int precision, double mean_cells, int* group, int* ctas_per_sm, int* tile_rows) {
+  if (!group || !ctas_per_sm || !tile_rows || precision < 0 || precision > 1 || !(mean_cells >= 1.0))
     return bfail(MPRK_EINVAL, "bad tuning lookup");
-  const int bucket = std::max(0, std::min(40, (int)std::floor(std::log2(mean_cells))));
+  const int bucket = cells_bucket(mean_cells);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tune.find({precision, bucket});
   if (it == g_tune.end()) {
     *group = batch_group(precision);
     *ctas_per_sm = 0;
+    *tile_rows = precision == 0 ? TZ : MTZ;
     return 0;
   }
   *group = it->second.group;
   *ctas_per_sm = it->second.per_sm;
+  *tile_rows = precision == 0 ? it->second.rows : MTZ;
   return 1;
+}
+
+int mprk_tile_lookup(double cells, int* tile_rows, int* threads_per_cell) {
+  if (!tile_rows || !threads_per_cell || !(cells >= 1.0)) return bfail(MPRK_EINVAL, "bad tile lookup");
+  TileShape t;
+  if (!tuned_tile_shape((long long)cells, &t)) return 0;
+  *tile_rows = t.rows;
+  *threads_per_cell = t.tpc;
+  return 1;
+}
+
+int mprk_tile_tune(mprk_instance* const* insts, int count, int reps, int* entries) {
+  if (!insts || count <= 0 || reps < 1 || !entries) return bfail(MPRK_EINVAL, "bad tile tuning arguments");
+  // Per size bucket of a launch's cells: the summed time of each shape over
+  // the instances' launches of that bucket. The launches timed are the first
+  // stage (every row) and the first stage of the second fast substep (the B
+  // and F rows): both read the state and write only the stage scratch, so
+  // the instances' states are untouched.
+  const TileShape shapes[6] = {{TZ, 1}, {TZ, 2}, {TZ / 2, 1}, {TZ / 2, 2}, {TZ / 4, 1}, {TZ / 4, 2}};
+  std::map<int, std::vector<double>> tsum;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = MPRK_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    rc = bfail(MPRK_ECUDA, "event create");
+  for (int j = 0; j < count && rc == MPRK_OK; j++) {
+    Geom g;
+    Bufs b;
+    int prec;
+    cudaStream_t st;
+    unsigned* sw;
+    if (!insts[j]) { rc = bfail(MPRK_EINVAL, "NULL instance"); break; }
+    if ((rc = instance_view(insts[j], &g, &b, &prec, &st, &sw))) break;
+    if (prec != MPRK_FP64 || g.ny > 1) { rc = bfail(MPRK_EINVAL, "tile tuning takes 2-D FP64 instances"); break; }
+    std::vector<int> stages{0};
+    if (g.m > 1) stages.push_back(g.s);
+    for (int stg : stages) {
+      StageArgs a = stage_args(g, b, stg);
+      a.status = sw;
+      const int bucket = cells_bucket((double)(g.nz - a.row0) * g.nx);
+      std::vector<double>& acc = tsum[bucket];
+      acc.resize(6, 0.0);
+      for (int k = 0; k < 6 && rc == MPRK_OK; k++) {
+        cudaError_t e = launch_stage(a, 0, stage_tiles(a), st, nullptr, &shapes[k]);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && e == cudaSuccess; r++) e = launch_stage(a, 0, stage_tiles(a), st, nullptr, &shapes[k]);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) rc = bfail(MPRK_ECUDA, std::string("tile tuning: ") + cudaGetErrorString(e));
+        acc[k] += ms / reps;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> tl(g_tune_mu);
+  for (const auto& kv : tsum) {
+    int best = 0;
+    for (int k = 1; k < 6; k++)
+      if (kv.second[k] < kv.second[best]) best = k;
+    g_shape[kv.first] = ShapeVal{shapes[best], kv.second[best]};
+  }
+  g_tune_gpu = device_name();
+  *entries = (int)tsum.size();
+  return MPRK_OK;
 }
 
 int mprk_tune_clear(void) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune.clear();
+  g_shape.clear();
   g_tune_gpu.clear();
   return MPRK_OK;
 }
@@ -826,8 +959,18 @@ int mprk_tune_save(const char* path) {
   bool first = true;
   char buf[256];
   for (const auto& kv : g_tune) {
-    snprintf(buf, sizeof buf, "%s\n  {\"precision\": %d, \"bucket\": %d, \"group\": %d, \"ctas_per_sm\": %d, \"ms\": %.6g}",
-             first ? "" : ",", kv.first.first, kv.first.second, kv.second.group, kv.second.per_sm, kv.second.ms);
+    snprintf(buf, sizeof buf,
+             "%s\n  {\"precision\": %d, \"bucket\": %d, \"group\": %d, \"ctas_per_sm\": %d, \"tile_rows\": %d, "
+             "\"ms\": %.6g}",
+             first ? "" : ",", kv.first.first, kv.first.second, kv.second.group, kv.second.per_sm,
+             kv.first.first == 0 ? kv.second.rows : MTZ, kv.second.ms);
+    f << buf;
+    first = false;
+  }
+  for (const auto& kv : g_shape) {
+    snprintf(buf, sizeof buf,
+             "%s\n  {\"stage_launch\": 1, \"bucket\": %d, \"tile_rows\": %d, \"threads_per_cell\": %d, \"ms\": %.6g}",
+             first ? "" : ",", kv.first, kv.second.shape.rows, kv.second.shape.tpc, kv.second.ms);
     f << buf;
     first = false;
   }
@@ -864,24 +1007,39 @@ int mprk_tune_load(const char* path) {
     return end != obj.c_str() + c + 1;
   };
   std::map<std::pair<int, int>, TuneVal> table;
+  std::map<int, ShapeVal> shapes;
   size_t pos = t.find("\"entries\"");
   if (pos == std::string::npos) return bfail(MPRK_EINVAL, "tuning file: no entries");
   for (;;) {
     const size_t a = t.find('{', pos), b = a == std::string::npos ? a : t.find('}', a);
     if (a == std::string::npos || b == std::string::npos) break;
     const std::string obj = t.substr(a, b - a + 1);
-    double pr, bu, gr, ct, ms = 0.0;
+    double pr, bu, gr, ct, rows = TZ, tpc, sl = 0.0, ms = 0.0;
+    num(obj, "ms", &ms);
+    if (num(obj, "stage_launch", &sl) && sl != 0.0) {
+      // a tile shape of single-instance FP64 stage launches
+      if (!num(obj, "bucket", &bu) || !num(obj, "tile_rows", &rows) || !num(obj, "threads_per_cell", &tpc))
+        return bfail(MPRK_EINVAL, "tuning file: incomplete tile-shape entry");
+      const TileShape ts{(int)rows, (int)tpc};
+      if (bu < 0 || bu > 40 || !tile_shape_valid(ts) || rows != (int)rows || tpc != (int)tpc)
+        return bfail(MPRK_EINVAL, "tuning file: tile shape out of range");
+      shapes[(int)bu] = ShapeVal{ts, ms};
+      pos = b + 1;
+      continue;
+    }
     if (!num(obj, "precision", &pr) || !num(obj, "bucket", &bu) || !num(obj, "group", &gr) ||
         !num(obj, "ctas_per_sm", &ct))
       return bfail(MPRK_EINVAL, "tuning file: incomplete entry");
-    num(obj, "ms", &ms);
-    if ((pr != 0 && pr != 1) || bu < 0 || bu > 40 || gr < 1 || gr > 64 || ct < 0 || ct > 8)
+    num(obj, "tile_rows", &rows);
+    if ((pr != 0 && pr != 1) || bu < 0 || bu > 40 || gr < 1 || gr > 64 || ct < 0 || ct > 8 ||
+        (pr == 0 && rows != TZ && rows != TZ / 2))
       return bfail(MPRK_EINVAL, "tuning file: value out of range");
-    table[{(int)pr, (int)bu}] = TuneVal{(int)gr, (int)ct, ms};
+    table[{(int)pr, (int)bu}] = TuneVal{(int)gr, (int)ct, ms, pr == 0 ? (int)rows : MTZ};
     pos = b + 1;
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune.swap(table);
+  g_shape.swap(shapes);
   g_tune_gpu = gpu;
   return MPRK_OK;
 }

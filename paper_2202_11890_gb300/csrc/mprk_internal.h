@@ -144,10 +144,28 @@ struct StageMaps {
 // directly.
 cudaError_t make_stage_maps(const Geom& g, const Bufs& b, StageMaps* out);
 
+// Shape of the FP64 stage tile: rows per tile (TZ, TZ/2 or TZ/4, with TX
+// columns) and threads per cell (1 or 2). Every shape computes the same
+// arithmetic in the same order, so results do not depend on it.
+struct TileShape {
+  int rows, tpc;
+};
+inline bool tile_shape_valid(const TileShape& t) {
+  return (t.rows == TZ || t.rows == TZ / 2 || t.rows == TZ / 4) && (t.tpc == 1 || t.tpc == 2);
+}
+// The tuned shape of single-instance FP64 stage launches of `cells` cells,
+// when the tuning table has one for their size bucket (mprk_batch.cu).
+bool tuned_tile_shape(long long cells, TileShape* out);
+// The shape launch_stage takes without a tuned one: the shortest tile whose
+// launch fits in one wave (n tiles <= SMs), with two threads per cell; a
+// launch that does not fit even with TZ rows keeps them, one thread per cell.
+TileShape default_tile_shape(const StageArgs& a);
+
 // Launchers (mprk_kernels.cu). All enqueue on `stream` and return the launch error.
-// maps (FP32-flux only, may be null) enables the staged tiles.
+// maps (FP32-flux only, may be null) enables the staged tiles. shape (FP64
+// only, may be null) overrides the tuned and the default tile shape.
 cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStream_t stream,
-                         const StageMaps* maps = nullptr);
+                         const StageMaps* maps = nullptr, const TileShape* shape = nullptr);
 cudaError_t launch_finalize(const Geom& g, const Bufs& b, int m_odd, cudaStream_t stream);
 // 3-D (g.ny > 1): the y-face launch and the stage launch of one stage; a.gy
 // must point at a state-sized buffer.

@@ -10,7 +10,6 @@
 //                       and energy; Courant numbers; non-finite count)
 #include <cudaTypedefs.h>
 
-#include <cstdlib>
 #include <cstring>
 
 #include <algorithm>
@@ -57,71 +56,6 @@ __global__ void __launch_bounds__(MIXED_THREADS, 3)
     // copies one more bounded wait, and leave
     if (threadIdx.x == 0 && a.status) atomicOr(a.status, ST_TIMEOUT);
     (void)mbar_wait(&S.bar, 0);
-  }
-}
-
-// Persistent FP32-flux stage kernel. CTA c takes the tiles c, c + G, c + 2G,
-// ... (G CTAs; tiles numbered row-major over (tile row, tile column)), so
-// the tiles in flight at any time form a band of neighbouring rows. Before
-// a CTA computes a tile it issues the tensor copies of its next tile into
-// the other staging buffer: every CTA keeps one tile's float planes in
-// flight while it computes. The copies of buffer b complete successive
-// phases of bar[b]; bit b of `phase` holds the parity to wait for next.
-// Odd stages stage twice the bytes (the shadow and R_a boxes), which leaves
-// room for two CTAs per SM; even stages run three.
-template <int PAR, int MINB>
-__global__ void __launch_bounds__(MIXED_THREADS, MINB)
-    stage_kernel_mixed_pipe(const StageArgs a, const __grid_constant__ CUtensorMap tm_sb,
-                            const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_ra,
-                            const int n_tiles) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  PipeSmemHead& H = *reinterpret_cast<PipeSmemHead*>(smem_raw);
-  // staging buffer b at smem_raw + pipe_stage_offset() + b * stride (computed,
-  // not a local array, so that it stays out of local memory)
-  unsigned char* const stg0 = smem_raw + pipe_stage_offset();
-  constexpr size_t STRIDE = pipe_buffer_stride(PAR == 1);
-  constexpr int ISSUER = MIXED_THREADS - 32;
-  const int tiles_x = a.tiles_x;
-  if (threadIdx.x == ISSUER) {
-    mbar_init(&H.bar[0]);
-    mbar_init(&H.bar[1]);
-  }
-  __syncthreads();  // the mbarriers are initialised before anyone uses them
-  int t = blockIdx.x;
-  if (t < n_tiles && threadIdx.x == ISSUER) {
-    const int k0 = a.row0 + (t / tiles_x) * MTZ, i0 = (t % tiles_x) * TX;
-    if (tile_bulk_ok(a, k0, i0))
-      stage_issue(a, k0, i0, *reinterpret_cast<Stage*>(stg0), &H.bar[0], &tm_sb, &tm_f, &tm_ra);
-  }
-  unsigned phase = 0u;
-  bool ok = true;
-  for (int j = 0; t < n_tiles; j++, t += gridDim.x) {
-    const int b = j & 1;
-    const int tn = t + gridDim.x;
-    if (tn < n_tiles && threadIdx.x == ISSUER) {
-      // buffer b^1 was last read by the previous tile, which every thread
-      // finished before the barrier that ended it
-      const int k0n = a.row0 + (tn / tiles_x) * MTZ, i0n = (tn % tiles_x) * TX;
-      if (tile_bulk_ok(a, k0n, i0n)) {
-        fence_proxy_async();
-        stage_issue(a, k0n, i0n, *reinterpret_cast<Stage*>(stg0 + (b ^ 1) * STRIDE), &H.bar[b ^ 1], &tm_sb, &tm_f,
-                    &tm_ra);
-      }
-    }
-    const int k0 = a.row0 + (t / tiles_x) * MTZ, i0 = (t % tiles_x) * TX;
-    const bool staged = tile_bulk_ok(a, k0, i0);
-    const Stage* sb = staged ? reinterpret_cast<const Stage*>(stg0 + b * STRIDE) : nullptr;
-    ok = stage_tile_mixed<PAR>(a, k0, i0, H.work, sb, &H.bar[b], (phase >> b) & 1u);
-    if (!ok) break;  // uniform: the tile's wait result is shared by a barrier
-    if (staged) phase ^= 1u << b;
-    __syncthreads();  // the tile's working set and buffer b are free again
-  }
-  if (!ok) {
-    // a tensor copy never completed within the bound: flag it, and give
-    // both buffers' copies one more bounded wait before the CTA leaves
-    if (threadIdx.x == 0 && a.status) atomicOr(a.status, ST_TIMEOUT);
-    (void)mbar_wait(&H.bar[0], phase & 1u);
-    (void)mbar_wait(&H.bar[1], (phase >> 1) & 1u);
   }
 }
 
@@ -178,13 +112,6 @@ cudaError_t prepare_kernels() {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MixedKernelSmem));
     if (e != cudaSuccess) return e;
   }
-  for (auto k : {stage_kernel_mixed_pipe<0, 3>, stage_kernel_mixed_pipe<0, 2>}) {
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pipe_kernel_smem(false));
-    if (e != cudaSuccess) return e;
-  }
-  e = cudaFuncSetAttribute(stage_kernel_mixed_pipe<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)pipe_kernel_smem(true));
-  if (e != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -244,34 +171,6 @@ int sm_count() {
 }  // namespace
 
 namespace {
-// CTAs of the persistent FP32-flux kernel that fit on one SM (per parity;
-// queried once per process: every device here is the same kind of GPU).
-int pipe_ctas_per_sm(int which) {
-  static int n[3] = {0, 0, 0};
-  int& v = n[which];
-  if (v == 0) {
-    int c = 0;
-    const cudaError_t e =
-        which == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, stage_kernel_mixed_pipe<1, 2>, MIXED_THREADS,
-                                                                   pipe_kernel_smem(true))
-        : which == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, stage_kernel_mixed_pipe<0, 2>,
-                                                                     MIXED_THREADS, pipe_kernel_smem(false))
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, stage_kernel_mixed_pipe<0, 3>,
-                                                                     MIXED_THREADS, pipe_kernel_smem(false));
-    v = (e == cudaSuccess && c > 0) ? c : 1;
-  }
-  return v;
-}
-// Whether staged FP32-flux launches use the persistent kernel: on unless
-// the environment sets MPRK_MIXED_PIPE=0 (the one-CTA-per-tile kernel).
-int pipe_mode() {
-  static int m = [] {
-    const char* e = getenv("MPRK_MIXED_PIPE");
-    return e ? atoi(e) : 1;
-  }();
-  return m;
-}
-
 // One FP64 stage launch with TZR-row tiles; wide: two threads per cell.
 template <int TZR>
 void launch_fp64(const StageArgs& a, int n_tiles, bool wide, cudaStream_t stream) {
@@ -288,25 +187,37 @@ void launch_fp64(const StageArgs& a, int n_tiles, bool wide, cudaStream_t stream
 }
 }  // namespace
 
+TileShape default_tile_shape(const StageArgs& a) {
+  // One SM completes two FP64 operations per clock, so a launch of fewer
+  // tiles than SMs is bound by the FP64 work of one tile.
+  const int sms = sm_count();
+  StageArgs s = a;
+  int n = 0;
+  for (const int t : {TZ / 4, TZ / 2, TZ}) {
+    s.tz = t;
+    n = stage_tiles(s);
+    if (n <= sms) break;
+  }
+  return TileShape{s.tz, n <= sms ? 2 : 1};
+}
+
 cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStream_t stream,
-                         const StageMaps* maps) {
+                         const StageMaps* maps, const TileShape* shape) {
   if (n_tiles <= 0) return cudaSuccess;
   if (precision == 0) {
-    // FP64: one SM completes two FP64 operations per clock, so a launch of
-    // fewer tiles than SMs is bound by the FP64 work of one tile. Take the
-    // shortest tile (TZ/4, TZ/2 or TZ rows) whose launch still fits in one
-    // wave, with two threads per cell; a launch that does not fit even with
-    // TZ rows keeps them, one thread per cell. (Two shorter tiles on an SM
-    // ran slower than one TZ-row tile with two threads per cell.)
-    const int sms = sm_count();
-    StageArgs s = a;
-    int n = n_tiles;
-    for (const int t : {TZ / 4, TZ / 2, TZ}) {
-      s.tz = t;
-      n = stage_tiles(s);
-      if (n <= sms) break;
+    // FP64: the shape given, else the tuned one for the launch's size
+    // bucket (mprk_tile_tune), else the default rule
+    TileShape ts;
+    if (shape && tile_shape_valid(*shape)) {
+      ts = *shape;
+    } else {
+      const int hi = a.rhs_only ? a.rhs_hi : a.g.nz;
+      if (!tuned_tile_shape((long long)(hi - a.row0) * a.g.nx, &ts)) ts = default_tile_shape(a);
     }
-    const bool wide = n <= sms;
+    StageArgs s = a;
+    s.tz = ts.rows;
+    const int n = stage_tiles(s);
+    const bool wide = ts.tpc == 2;
     if (s.tz == TZ) launch_fp64<TZ>(s, n, wide, stream);
     else if (s.tz == TZ / 2) launch_fp64<TZ / 2>(s, n, wide, stream);
     else launch_fp64<TZ / 4>(s, n, wide, stream);
@@ -323,21 +234,6 @@ cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStr
     const size_t smem = mixed_kernel_smem(a.stage & 1);
     if (a.rhs_only) {
       stage_kernel_mixed<PAR_RT><<<grid, MIXED_THREADS, smem, stream>>>(s, sb, f, ra);
-    } else if (staged && pipe_mode() != 0) {
-      // persistent: as many CTAs as fit on the GPU at once, at most one per tile
-      const bool odd = a.stage & 1;
-      const int which = odd ? 2 : (pipe_mode() == 2 ? 1 : 0);
-      const int per_sm = pipe_ctas_per_sm(which);
-      const int ctas = std::max(1, std::min(n_tiles, sm_count() * per_sm));
-      if (which == 2)
-        stage_kernel_mixed_pipe<1, 2><<<ctas, MIXED_THREADS, pipe_kernel_smem(true), stream>>>(s, sb, f, ra,
-                                                                                               n_tiles);
-      else if (which == 1)
-        stage_kernel_mixed_pipe<0, 2><<<ctas, MIXED_THREADS, pipe_kernel_smem(false), stream>>>(s, sb, f, ra,
-                                                                                                n_tiles);
-      else
-        stage_kernel_mixed_pipe<0, 3><<<ctas, MIXED_THREADS, pipe_kernel_smem(false), stream>>>(s, sb, f, ra,
-                                                                                                n_tiles);
     } else if (a.stage & 1) {
       stage_kernel_mixed<1><<<grid, MIXED_THREADS, smem, stream>>>(s, sb, f, ra);
     } else {

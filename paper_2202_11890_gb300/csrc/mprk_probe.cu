@@ -4,9 +4,13 @@
 // Every thread runs NCHAIN independent dependency chains of double FMAs on
 // registers only (no memory traffic inside the timed loop). The grid is one
 // full wave: as many CTAs as fit on every SM at once, all running the same
-// number of FMAs. Each CTA records its own SM-clock cycles (clock64) and
-// nanoseconds (globaltimer) between two block-wide barriers, which gives
-// the SM clock and the FMAs per SM clock independent of launch overhead.
+// number of FMAs. Each CTA records its SM-clock cycles (clock64) and its
+// start and end on the global nanosecond timer, between two block-wide
+// barriers. The cycles over the nanoseconds of each CTA give
+// the SM clock. The FMA rate is all FMAs over the span from the first CTA's
+// start to the last CTA's end on the global timer: CTAs sharing an SM do
+// not progress at the same pace (the oldest warps tend to win issue), so a
+// single CTA's duration would not do.
 // The result is stored only where it cannot be predicted, so the compiler
 // keeps every FMA.
 #include <cuda_runtime.h>
@@ -51,7 +55,8 @@ __global__ void __launch_bounds__(PROBE_THREADS) fp64_fma_probe(int iters, doubl
   if (s == -1.0) sink[blockIdx.x * PROBE_THREADS + threadIdx.x] = s;  // never true for b, c > 0
   if (threadIdx.x == 0) {
     cycles[blockIdx.x] = c1 - c0;
-    nanos[blockIdx.x] = (long long)(n1 - n0);
+    nanos[2 * blockIdx.x] = (long long)n0;  // the global timer is one clock for all SMs
+    nanos[2 * blockIdx.x + 1] = (long long)n1;
   }
 }
 
@@ -77,10 +82,10 @@ extern "C" int mprk_probe_fp64(long long iters, double* gflops, double* dfma_per
   long long* ns = nullptr;
   cudaStream_t s = nullptr;
   int rc = MPRK_OK;
-  std::vector<long long> hc(blocks), hn(blocks);
+  std::vector<long long> hc(blocks), hn(2 * blocks);
   e = cudaMalloc(&sink, sizeof(double) * blocks * PROBE_THREADS);
   if (e == cudaSuccess) e = cudaMalloc(&cyc, sizeof(long long) * blocks);
-  if (e == cudaSuccess) e = cudaMalloc(&ns, sizeof(long long) * blocks);
+  if (e == cudaSuccess) e = cudaMalloc(&ns, sizeof(long long) * 2 * blocks);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   if (e == cudaSuccess) {
     // a short warm-up launch, then the measured one
@@ -89,23 +94,27 @@ extern "C" int mprk_probe_fp64(long long iters, double* gflops, double* dfma_per
     e = cudaStreamSynchronize(s);
   }
   if (e == cudaSuccess) e = cudaMemcpy(hc.data(), cyc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemcpy(hn.data(), ns, sizeof(long long) * blocks, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(hn.data(), ns, sizeof(long long) * 2 * blocks, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) {
     mprk::set_last_error(std::string("mprk_probe_fp64: ") + cudaGetErrorString(e));
     rc = MPRK_ECUDA;
   } else {
-    // medians over the CTAs: cycles and nanoseconds of one CTA's loop; all
-    // CTAs of the wave share their SM's FP64 units the whole time
+    // the SM clock: the median over the CTAs of cycles per nanosecond; the
+    // FMA rate: every FMA over first start to last end
     std::vector<double> clk(blocks);
-    for (int j = 0; j < blocks; j++) clk[j] = hn[j] > 0 ? (double)hc[j] / (double)hn[j] : 0.0;  // cycles per ns
+    long long t_start = hn[0], t_end = hn[1];
+    for (int j = 0; j < blocks; j++) {
+      const long long d = hn[2 * j + 1] - hn[2 * j];
+      clk[j] = d > 0 ? (double)hc[j] / (double)d : 0.0;
+      t_start = std::min(t_start, hn[2 * j]);
+      t_end = std::max(t_end, hn[2 * j + 1]);
+    }
     std::sort(clk.begin(), clk.end());
-    std::sort(hc.begin(), hc.end());
-    std::sort(hn.begin(), hn.end());
-    const double cyc_med = (double)hc[blocks / 2], ns_med = (double)hn[blocks / 2];
-    const double fmas_per_sm = (double)per_sm * PROBE_THREADS * NCHAIN * (double)iters;
-    *dfma_per_clk_per_sm = fmas_per_sm / cyc_med;
+    const double fmas = (double)blocks * PROBE_THREADS * NCHAIN * (double)iters;
+    const double sec = (double)std::max(1ll, t_end - t_start) * 1e-9;
     *sm_mhz = clk[blocks / 2] * 1e3;
-    *gflops = 2.0 * fmas_per_sm * nsm / (ns_med * 1e-9) / 1e9;
+    *gflops = 2.0 * fmas / sec / 1e9;
+    *dfma_per_clk_per_sm = fmas / sec / (*sm_mhz * 1e6) / nsm;
     *sms = nsm;
   }
   if (s) cudaStreamDestroy(s);

@@ -125,7 +125,9 @@ def lib():
         "mprk_batch_test_withhold": (ip, [C.POINTER(vp), ip, ip, ip, C.c_longlong]),
         "mprk_selftest_convert": (ip, [vp, ip, vp, vp, vp, vp]),
         "mprk_batch_tune": (ip, [C.POINTER(vp), ip, ip, dp]),
-        "mprk_tune_lookup": (ip, [ip, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "mprk_tune_lookup": (ip, [ip, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "mprk_tile_tune": (ip, [C.POINTER(vp), ip, ip, C.POINTER(C.c_int)]),
+        "mprk_tile_lookup": (ip, [C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "mprk_tune_save": (ip, [C.c_char_p]),
         "mprk_tune_load": (ip, [C.c_char_p]),
         "mprk_tune_clear": (ip, []),
@@ -294,19 +296,39 @@ def mprk_selftest_convert(x_dev, narrow, narrow_hw, widen, widen_hw) -> None:
 
 
 def mprk_batch_tune(handles, reps: int = 3) -> dict:
-    """Time the batched launch choices on these instances; the fastest goes
-    to the table and is returned."""
-    out = (C.c_double * 3)()
+    """Time the batched launch choices (tiles per item, CTAs per SM, FP64
+    tile shape) on these instances; the fastest goes to the table and is
+    returned."""
+    out = (C.c_double * 4)()
     _check(lib().mprk_batch_tune(_handles(handles), len(handles), int(reps), out))
-    return {"tiles_per_item": int(out[0]), "ctas_per_sm": int(out[1]), "ms_per_step": float(out[2])}
+    return {"tiles_per_item": int(out[0]), "ctas_per_sm": int(out[1]), "ms_per_step": float(out[2]),
+            "tile_rows": int(out[3])}
 
 
 def mprk_tune_lookup(precision: int, mean_cells: float):
-    g, c = C.c_int(), C.c_int()
-    rc = lib().mprk_tune_lookup(int(precision), float(mean_cells), C.byref(g), C.byref(c))
+    g, c, r = C.c_int(), C.c_int(), C.c_int()
+    rc = lib().mprk_tune_lookup(int(precision), float(mean_cells), C.byref(g), C.byref(c), C.byref(r))
     if rc < 0:
         raise MprkError(rc, mprk_last_error())
-    return {"tiles_per_item": g.value, "ctas_per_sm": c.value, "tuned": bool(rc)}
+    return {"tiles_per_item": g.value, "ctas_per_sm": c.value, "tile_rows": r.value, "tuned": bool(rc)}
+
+
+def mprk_tile_tune(handles, reps: int = 3) -> int:
+    """Time the six FP64 stage-tile shapes on these instances' launches; the
+    fastest per size bucket goes to the table. Returns the buckets written."""
+    n = C.c_int()
+    _check(lib().mprk_tile_tune(_handles(handles), len(handles), int(reps), C.byref(n)))
+    return n.value
+
+
+def mprk_tile_lookup(cells: float):
+    """The table's tile shape for a single-instance FP64 stage launch of
+    `cells` cells, or None when the default rule applies."""
+    r, t = C.c_int(), C.c_int()
+    rc = lib().mprk_tile_lookup(float(cells), C.byref(r), C.byref(t))
+    if rc < 0:
+        raise MprkError(rc, mprk_last_error())
+    return {"tile_rows": r.value, "threads_per_cell": t.value} if rc else None
 
 
 def mprk_tune_save(path: str) -> None:
