@@ -287,11 +287,12 @@ int mprk_profile_step(mprk_instance* inst, double* launch_ms, long long* launch_
 
 /* Measurement hook: the FP64 fused multiply-add throughput of the current
  * device, the denominator of the FP64 path's arithmetic roofline (the RHS
- * of Sec. 2.1 and App. B is FP64-arithmetic-bound in the FP64 mode). A
- * register-only kernel runs 16 independent FMA chains of `iters` steps per
- * thread (1 <= iters <= 2^30) on one full wave of 256-thread CTAs (as many
- * as fit on each SM). Each CTA times its loop in SM clocks and on the
- * global nanosecond timer. Outputs: gflops (2 flop per FMA, every FMA over
+ * of Sec. 2.1 and App. B is FP64-arithmetic-bound in the FP64 mode).
+ * Register-only kernels run independent FMA chains per thread (16 chains
+ * of `iters` steps, or 8 of 2 iters; multiplier and addend in registers or
+ * literals; 1 <= iters <= 2^30) on one full wave of 256-thread CTAs (as
+ * many as fit on each SM), and the fastest of the four is reported. Each
+ * CTA times its loop in SM clocks and on the global nanosecond timer. Outputs: gflops (2 flop per FMA, every FMA over
  * the span from the first CTA's start to the last CTA's end),
  * dfma_per_clk_per_sm (that rate per SM clock), sm_mhz (the median over the
  * CTAs of their clocks per nanosecond) and sms (the SM count). Allocates and
