@@ -594,6 +594,7 @@ def measure_served(M, rate: float, n_warm: int, n_meas: int, budget_gb: float, s
             time.sleep(0.0005)
     wall = time.perf_counter() - t0
     sstats = M.mprk_server_stats(srv)
+    sprof = M.mprk_server_profile(srv)
     M.mprk_server_destroy(srv)
     meas = [done[j] for j in range(n_warm, len(reqs))]
     lat = np.array([s["t_finish"] - s["t_submit"] for _, s in meas])
@@ -612,7 +613,8 @@ def measure_served(M, rate: float, n_warm: int, n_meas: int, budget_gb: float, s
            "served": {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                       "mean_latency_s": float(lat.mean()), "errors": errors,
                       "offered_cell_stages_per_s": offered, "achieved_over_offered": value / offered,
-                      "batched_steps": int(sstats[2]), "wall_s": wall},
+                      "batched_steps": int(sstats[2]), "wall_s": wall,
+                      "loop": {**sprof, "gpu_busy_over_step_span": sprof["gpu_busy_s"] / max(sprof["step_span_s"], 1e-9)}},
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
                         "note": "algorithmic bytes of the measured requests over their first submit to last finish"},

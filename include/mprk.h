@@ -409,6 +409,19 @@ int mprk_poll(mprk_server* srv, uint64_t ticket, int* status, double* q_out_host
  * out[5] ledger bytes now, out[6] seconds since start, out[7] failed requests. */
 int mprk_server_stats(mprk_server* srv, double out[8]);
 
+/* Where the server thread's time goes, accumulated since the server started:
+ * out[0] loop iterations that launched a batched step, out[1] seconds
+ * admitting requests (instance creation: allocation, upload, reference
+ * set-up, initial check), out[2] seconds enqueueing the batched steps
+ * (including work-list rebuilds when the resident set changed), out[3]
+ * seconds retiring finished requests, out[4] seconds waiting for the step
+ * two iterations back (the in-flight limit), out[5] GPU seconds of the
+ * batched steps (CUDA events around each iteration's launches), out[6]
+ * seconds from the first batched step to the last one's end, out[7]
+ * requests admitted. The paper has no counterpart; this is instrumentation
+ * of the request loop. */
+int mprk_server_profile(mprk_server* srv, double out[8]);
+
 /* Stop the server thread (queued and resident requests are dropped) and free
  * its resources. */
 int mprk_server_destroy(mprk_server* srv);

@@ -124,20 +124,30 @@ __device__ __forceinline__ void finalize_chunk(const Geom& g, const Bufs& b, int
   }
 }
 
+// Whether the FP32-flux tile `tile` of a work item has its float planes
+// tensor-copied: an interior tile away from the x wrap of an instance with
+// tensor maps. A tensor copy writes shared memory at a 128-byte boundary
+// only; the kernel aligns the buffer, and a misaligned one would load
+// directly instead.
+__device__ __forceinline__ bool batch_tile_staged(const StageArgs& a, int tile, const CUtensorMap* maps,
+                                                  const Stage* stg) {
+  const int tzi = tile / a.tiles_x;
+  return maps != nullptr && (smem_u32(stg) & 127u) == 0u &&
+         tile_bulk_ok(a, a.row0 + tzi * MTZ, (tile - tzi * a.tiles_x) * TX);
+}
+
 // The FP32-flux tile of a work item, compiled as a function of its own: the
 // tile reads its arguments from shared memory (not from the constant bank
 // as the single-instance kernel does), and allocated apart from the
-// persistent loop it spills less than inlined there. An interior tile of an
-// instance with tensor maps (away from the x wrap) has its float planes
-// tensor-copied into stg first: one thread issues the copies, which
-// complete the next phase of bar, of parity `parity`. Returns false if the
-// wait for them gave up.
+// persistent loop it spills less than inlined there. A staged tile
+// (batch_tile_staged) has its float planes tensor-copied into stg first:
+// one thread issues the copies, which complete the next phase of bar, of
+// parity `parity`. Returns false if the wait for them gave up.
 template <int PAR>
 __device__ __noinline__ bool batch_tile_mixed(const StageArgs& a, int tile, MixedTileSmem& S, const CUtensorMap* maps,
-                                              Stage* stg, unsigned long long* bar, unsigned parity) {
+                                              Stage* stg, unsigned long long* bar, unsigned parity, bool staged) {
   const int tzi = tile / a.tiles_x;
   const int k0 = a.row0 + tzi * MTZ, i0 = (tile - tzi * a.tiles_x) * TX;
-  const bool staged = maps != nullptr && tile_bulk_ok(a, k0, i0);
   if (staged && threadIdx.x == MIXED_THREADS - 32) {
     // the previous tile's reads of stg ended at the barrier before this call
     fence_proxy_async();
@@ -147,12 +157,20 @@ __device__ __noinline__ bool batch_tile_mixed(const StageArgs& a, int tile, Mixe
 }
 
 // Shared memory of the FP32-flux batch kernel: the tile's working set, the
-// staging buffer's mbarrier and the staging buffer.
+// staging buffer's mbarrier and the staging buffer. The kernel's static
+// shared variables come first in the CTA's shared memory, so the dynamic
+// part starts at no particular 128-byte boundary: the kernel places this
+// struct at the first 128-byte boundary of it (the staging buffer, which
+// tensor copies write, then starts on one) and the launch allots 128 bytes
+// more for that.
 struct BatchMixedSmem {
   MixedTileSmem work;
   unsigned long long bar;
   Stage stg;
 };
+__device__ __forceinline__ unsigned char* align128_shared(unsigned char* p) {
+  return p + ((128u - (smem_u32(p) & 127u)) & 127u);
+}
 
 // three CTAs per SM in both precisions (80 and 72 registers; the FP32-flux
 // form spills some, and still runs faster than at two CTAs). ROWS: rows of
@@ -175,7 +193,7 @@ __global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const Bat
   // FP32 flux: the staging buffer's mbarrier, initialised once; every
   // staged tile completes one phase of it, so the parity to wait for is the
   // count of staged tiles so far (the same in every thread)
-  BatchMixedSmem& MS = *reinterpret_cast<BatchMixedSmem*>(smem_raw);
+  BatchMixedSmem& MS = *reinterpret_cast<BatchMixedSmem*>(align128_shared(smem_raw));
   unsigned staged_tiles = 0;
   if (PREC == 1 && threadIdx.x == MIXED_THREADS - 32) mbar_init(&MS.bar);
   __syncthreads();
@@ -210,12 +228,11 @@ __global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const Bat
           else {
             // the FP32-flux tile compiled per stage parity
             const int tile = item.tile + t;
-            const int tzi = tile / s_a.tiles_x;
-            const bool staged = I.maps != nullptr &&
-                                tile_bulk_ok(s_a, s_a.row0 + tzi * MTZ, (tile - tzi * s_a.tiles_x) * TX);
-            const bool ok = (s_a.stage & 1)
-                                ? batch_tile_mixed<1>(s_a, tile, MS.work, I.maps, &MS.stg, &MS.bar, staged_tiles & 1u)
-                                : batch_tile_mixed<0>(s_a, tile, MS.work, I.maps, &MS.stg, &MS.bar, staged_tiles & 1u);
+            const bool staged = batch_tile_staged(s_a, tile, I.maps, &MS.stg);
+            const bool ok = (s_a.stage & 1) ? batch_tile_mixed<1>(s_a, tile, MS.work, I.maps, &MS.stg, &MS.bar,
+                                                                  staged_tiles & 1u, staged)
+                                            : batch_tile_mixed<0>(s_a, tile, MS.work, I.maps, &MS.stg, &MS.bar,
+                                                                  staged_tiles & 1u, staged);
             if (staged) staged_tiles++;
             if (!ok) {
               // a tensor copy never completed within the bound: this
@@ -364,8 +381,9 @@ StageArgs batch_stage_args(const BatchInst& bi, int st, int rows) {
   return a;
 }
 
-// Shared memory of the batch kernel per precision.
-size_t batch_smem(int prec) { return prec == 1 ? sizeof(BatchMixedSmem) : stage_smem_bytes(0); }
+// Shared memory of the batch kernel per precision (FP32 flux: with the
+// slack for the 128-byte alignment of its struct).
+size_t batch_smem(int prec) { return prec == 1 ? sizeof(BatchMixedSmem) + 128 : stage_smem_bytes(0); }
 
 // The tensor maps of the instances (three per instance, valid FP32-flux
 // maps only) for upload to `d_maps`; sets each instance's maps pointer

@@ -111,6 +111,12 @@ struct mprk_server {
   // counters (read under mu)
   long long n_done = 0, n_failed = 0, cells_done = 0, batched_steps = 0;
   int n_resident = 0;
+  // time accounting of the loop (written by the server thread under mu):
+  // iterations, host seconds in admission, step launch, retirement and the
+  // in-flight wait, GPU seconds of the steps, first step start and last
+  // step end (server clock), admissions
+  double prof[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double first_step = -1.0;
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
@@ -136,10 +142,12 @@ void server_loop(mprk_server* S) {
     S->thread_msg = "server: device or stream set-up failed";
     return;
   }
-  cudaEvent_t step_ev[2] = {nullptr, nullptr};
-  if (cudaEventCreateWithFlags(&step_ev[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&step_ev[1], cudaEventDisableTiming) != cudaSuccess) {
-    for (cudaEvent_t e : step_ev)
+  // step_ev[slot] ends iteration slot's launches; beg_ev[slot] starts them
+  // (both timed, for the GPU-seconds account)
+  cudaEvent_t step_ev[2] = {nullptr, nullptr}, beg_ev[2] = {nullptr, nullptr};
+  if (cudaEventCreate(&step_ev[0]) != cudaSuccess || cudaEventCreate(&step_ev[1]) != cudaSuccess ||
+      cudaEventCreate(&beg_ev[0]) != cudaSuccess || cudaEventCreate(&beg_ev[1]) != cudaSuccess) {
+    for (cudaEvent_t e : {step_ev[0], step_ev[1], beg_ev[0], beg_ev[1]})
       if (e) cudaEventDestroy(e);
     std::lock_guard<std::mutex> lk(S->mu);
     S->thread_error = MPRK_ECUDA;
@@ -148,6 +156,15 @@ void server_loop(mprk_server* S) {
   }
   bool step_ev_used[2] = {false, false};
   int it = 0;
+  // adds the GPU time of the iteration in slot (its events have completed)
+  auto account = [&](int slot) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, beg_ev[slot], step_ev[slot]) == cudaSuccess) {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->prof[5] += ms * 1e-3;
+      S->prof[6] = S->now();
+    }
+  };
   for (;;) {
     // ---- 1. admission --------------------------------------------------
     std::vector<Request*> admit;
@@ -165,6 +182,7 @@ void server_loop(mprk_server* S) {
         admit.push_back(r);
       }
     }
+    const double t_admit0 = S->now();
     for (Request* r : admit) {
       mprk_instance* inst = nullptr;
       const int rc = create_instance(&r->cfg, r->q0.data(), MPRK_HOST, S->copy, true, &inst);
@@ -192,11 +210,23 @@ void server_loop(mprk_server* S) {
       if (ev) cudaEventDestroy(ev);
     }
 
+    if (!admit.empty()) {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->prof[1] += S->now() - t_admit0;
+      S->prof[7] += (double)admit.size();
+    }
+
     // ---- 2. one batched slow step for every resident instance ------------
     if (!S->resident.empty()) {
       // keep at most two iterations in flight
       const int slot = it & 1;
-      if (step_ev_used[slot]) cudaEventSynchronize(step_ev[slot]);
+      const double t_wait0 = S->now();
+      if (step_ev_used[slot]) {
+        cudaEventSynchronize(step_ev[slot]);
+        account(slot);
+      }
+      const double t_step0 = S->now();
+      cudaEventRecord(beg_ev[slot], S->compute);
       std::vector<mprk_instance*> group[2];
       for (Request* r : S->resident) group[r->cfg.precision == MPRK_FP64 ? 0 : 1].push_back(r->inst);
       int err = 0;
@@ -212,10 +242,15 @@ void server_loop(mprk_server* S) {
       cudaEventRecord(step_ev[slot], S->compute);
       step_ev_used[slot] = true;
       it++;
+      const double t_ret0 = S->now();
       {
         std::lock_guard<std::mutex> lk(S->mu);
         S->batched_steps++;
         S->cells_done += cells;
+        S->prof[0] += 1.0;
+        S->prof[2] += t_ret0 - t_step0;
+        S->prof[4] += t_step0 - t_wait0;
+        if (S->first_step < 0) S->first_step = t_step0;
       }
       // ---- 3. retire instances that reached their step count -------------
       std::vector<Request*> keep;
@@ -262,6 +297,7 @@ void server_loop(mprk_server* S) {
       S->resident.swap(keep);
       std::lock_guard<std::mutex> lk(S->mu);
       S->n_resident = (int)S->resident.size();
+      S->prof[3] += S->now() - t_ret0;
     }
 
     // ---- 4. complete retirements whose copies are done --------------------
@@ -307,6 +343,8 @@ void server_loop(mprk_server* S) {
   }
   // shutdown: drop everything the thread still owns
   cudaStreamSynchronize(S->compute);
+  for (int slot = 0; slot < 2; slot++)
+    if (step_ev_used[slot]) account(slot);
   cudaStreamSynchronize(S->copy);
   for (Request* r : S->resident)
     if (r->inst) destroy_instance(r->inst), r->inst = nullptr;
@@ -319,8 +357,7 @@ void server_loop(mprk_server* S) {
   cudaStreamSynchronize(S->copy);
   for (int p = 0; p < 2; p++) runner_destroy(S->runner[p]);
   cudaStreamSynchronize(S->compute);
-  cudaEventDestroy(step_ev[0]);
-  cudaEventDestroy(step_ev[1]);
+  for (cudaEvent_t e : {step_ev[0], step_ev[1], beg_ev[0], beg_ev[1]}) cudaEventDestroy(e);
   cudaStreamDestroy(S->compute);
   cudaStreamDestroy(S->copy);
 }
@@ -419,6 +456,14 @@ int mprk_server_stats(mprk_server* S, double out[8]) {
   out[5] = (double)S->ledger;
   out[6] = S->now();
   out[7] = (double)S->n_failed;
+  return MPRK_OK;
+}
+
+int mprk_server_profile(mprk_server* S, double out[8]) {
+  if (!S || !out) return sfail(MPRK_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  for (int j = 0; j < 8; j++) out[j] = S->prof[j];
+  out[6] = S->first_step >= 0 ? S->prof[6] - S->first_step : 0.0;
   return MPRK_OK;
 }
 

@@ -135,6 +135,7 @@ def lib():
         "mprk_submit": (ip, [vp, cfgp, vp, ip, C.POINTER(C.c_uint64)]),
         "mprk_poll": (ip, [vp, C.c_uint64, C.POINTER(C.c_int), vp, C.POINTER(mprk_stats)]),
         "mprk_server_stats": (ip, [vp, dp]),
+        "mprk_server_profile": (ip, [vp, dp]),
         "mprk_server_destroy": (ip, [vp]),
         "mprk_last_error": (C.c_char_p, []),
     }
@@ -390,6 +391,16 @@ def mprk_server_stats(srv: int) -> np.ndarray:
     out = np.zeros(8)
     _check(lib().mprk_server_stats(C.c_void_p(srv), out.ctypes.data_as(C.POINTER(C.c_double))))
     return out
+
+
+def mprk_server_profile(srv: int) -> dict:
+    """Where the server thread's time went (seconds) and the GPU seconds of
+    its batched steps."""
+    out = np.zeros(8)
+    _check(lib().mprk_server_profile(C.c_void_p(srv), out.ctypes.data_as(C.POINTER(C.c_double))))
+    keys = ("iterations", "admit_s", "step_enqueue_s", "retire_s", "inflight_wait_s", "gpu_busy_s",
+            "step_span_s", "admitted")
+    return {k: float(v) for k, v in zip(keys, out)}
 
 
 def mprk_server_destroy(srv: int) -> None:
