@@ -295,10 +295,11 @@ int mprk_profile_step(mprk_instance* inst, double* launch_ms, long long* launch_
  * CTA times its loop in SM clocks and on the global nanosecond timer. Outputs: gflops (2 flop per FMA, every FMA over
  * the span from the first CTA's start to the last CTA's end),
  * dfma_per_clk_per_sm (that rate per SM clock), sm_mhz (the median over the
- * CTAs of their clocks per nanosecond) and sms (the SM count). Allocates and
- * frees three small device buffers; synchronises. Errors: MPRK_EINVAL,
- * MPRK_ECUDA. */
-int mprk_probe_fp64(long long iters, double* gflops, double* dfma_per_clk_per_sm, double* sm_mhz, int* sms);
+ * CTAs of their clocks per nanosecond), sms (the SM count) and max_mhz (the
+ * device's peak SM clock, cudaDevAttrClockRate). Allocates and frees three
+ * small device buffers; synchronises. Errors: MPRK_EINVAL, MPRK_ECUDA. */
+int mprk_probe_fp64(long long iters, double* gflops, double* dfma_per_clk_per_sm, double* sm_mhz, int* sms,
+                    double* max_mhz);
 
 /* Test hook for the FP32-flux mode's conversions, which use integer bit
  * operations because this GPU converts between float and double at the FP64

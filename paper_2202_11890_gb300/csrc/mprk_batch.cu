@@ -42,9 +42,6 @@ struct BatchInst {
   int counter_base;  // first counter of this instance: one per stage, then completion
   int args_base;     // first entry of this instance in BatchArgs::args: one per stage
   int precision;
-  // FP32 flux: the tensor maps of the instance's float planes in device
-  // memory (shadow A, shadow B, R_a), or null when its tiles load directly
-  const CUtensorMap* maps;
 };
 
 // The work items copy their stage's arguments from a table built on the
@@ -124,52 +121,13 @@ __device__ __forceinline__ void finalize_chunk(const Geom& g, const Bufs& b, int
   }
 }
 
-// Whether the FP32-flux tile `tile` of a work item has its float planes
-// tensor-copied: an interior tile away from the x wrap of an instance with
-// tensor maps. A tensor copy writes shared memory at a 128-byte boundary
-// only; the kernel aligns the buffer, and a misaligned one would load
-// directly instead.
-__device__ __forceinline__ bool batch_tile_staged(const StageArgs& a, int tile, const CUtensorMap* maps,
-                                                  const Stage* stg) {
-  const int tzi = tile / a.tiles_x;
-  return maps != nullptr && (smem_u32(stg) & 127u) == 0u &&
-         tile_bulk_ok(a, a.row0 + tzi * MTZ, (tile - tzi * a.tiles_x) * TX);
-}
-
 // The FP32-flux tile of a work item, compiled as a function of its own: the
 // tile reads its arguments from shared memory (not from the constant bank
 // as the single-instance kernel does), and allocated apart from the
-// persistent loop it spills less than inlined there. A staged tile
-// (batch_tile_staged) has its float planes tensor-copied into stg first:
-// one thread issues the copies, which complete the next phase of bar, of
-// parity `parity`. Returns false if the wait for them gave up.
+// persistent loop it spills less than inlined there.
 template <int PAR>
-__device__ __noinline__ bool batch_tile_mixed(const StageArgs& a, int tile, MixedTileSmem& S, const CUtensorMap* maps,
-                                              Stage* stg, unsigned long long* bar, unsigned parity, bool staged) {
-  const int tzi = tile / a.tiles_x;
-  const int k0 = a.row0 + tzi * MTZ, i0 = (tile - tzi * a.tiles_x) * TX;
-  if (staged && threadIdx.x == MIXED_THREADS - 32) {
-    // the previous tile's reads of stg ended at the barrier before this call
-    fence_proxy_async();
-    stage_issue(a, k0, i0, *stg, bar, &maps[0], a.dF == a.b.dA ? &maps[0] : &maps[1], &maps[2]);
-  }
-  return stage_tile_mixed<PAR>(a, k0, i0, S, staged ? stg : nullptr, bar, parity);
-}
-
-// Shared memory of the FP32-flux batch kernel: the tile's working set, the
-// staging buffer's mbarrier and the staging buffer. The kernel's static
-// shared variables come first in the CTA's shared memory, so the dynamic
-// part starts at no particular 128-byte boundary: the kernel places this
-// struct at the first 128-byte boundary of it (the staging buffer, which
-// tensor copies write, then starts on one) and the launch allots 128 bytes
-// more for that.
-struct BatchMixedSmem {
-  MixedTileSmem work;
-  unsigned long long bar;
-  Stage stg;
-};
-__device__ __forceinline__ unsigned char* align128_shared(unsigned char* p) {
-  return p + ((128u - (smem_u32(p) & 127u)) & 127u);
+__device__ __noinline__ void batch_tile_mixed(const StageArgs& a, int tile, MixedTileSmem& S) {
+  stage_tile_mixed<PAR>(a, tile, S);
 }
 
 // three CTAs per SM in both precisions (80 and 72 registers; the FP32-flux
@@ -190,12 +148,6 @@ __global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const Bat
   __shared__ __align__(16) StageArgs s_a;
   cuda::atomic_ref<int, cuda::thread_scope_device> nxt(*A.next);
   if (threadIdx.x == 0) s_item[0] = nxt.fetch_add(1, cuda::memory_order_relaxed);
-  // FP32 flux: the staging buffer's mbarrier, initialised once; every
-  // staged tile completes one phase of it, so the parity to wait for is the
-  // count of staged tiles so far (the same in every thread)
-  BatchMixedSmem& MS = *reinterpret_cast<BatchMixedSmem*>(align128_shared(smem_raw));
-  unsigned staged_tiles = 0;
-  if (PREC == 1 && threadIdx.x == MIXED_THREADS - 32) mbar_init(&MS.bar);
   __syncthreads();
   for (int cur = 0;; cur ^= 1) {
     const int it = s_item[cur];
@@ -225,26 +177,10 @@ __global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const Bat
           else if (PREC == 0)
             stage_tile<double, double, false, NTHREADS, ROWS>(s_a, item.tile + t,
                                                               *reinterpret_cast<TileSmem<double, ROWS>*>(smem_raw));
-          else {
-            // the FP32-flux tile compiled per stage parity
-            const int tile = item.tile + t;
-            const bool staged = batch_tile_staged(s_a, tile, I.maps, &MS.stg);
-            const bool ok = (s_a.stage & 1) ? batch_tile_mixed<1>(s_a, tile, MS.work, I.maps, &MS.stg, &MS.bar,
-                                                                  staged_tiles & 1u, staged)
-                                            : batch_tile_mixed<0>(s_a, tile, MS.work, I.maps, &MS.stg, &MS.bar,
-                                                                  staged_tiles & 1u, staged);
-            if (staged) staged_tiles++;
-            if (!ok) {
-              // a tensor copy never completed within the bound: this
-              // instance's step is incomplete; drain like a timed-out wait
-              if (threadIdx.x == 0) {
-                atomicOr(I.status, ST_TIMEOUT);
-                atomicExch(A.abort_flag, 1);
-              }
-              (void)mbar_wait(&MS.bar, (staged_tiles - 1u) & 1u);
-              break;
-            }
-          }
+          else if (s_a.stage & 1)  // the FP32-flux tile compiled per stage parity
+            batch_tile_mixed<1>(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
+          else
+            batch_tile_mixed<0>(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
         }
       } else {
         for (int t = 0; t < item.count; t++) finalize_chunk(I.g, I.b, item.tile + t);
@@ -283,7 +219,6 @@ struct Plan {
   BatchInst* d_insts = nullptr;
   StageArgs* d_args = nullptr;
   BatchItem* d_items = nullptr;
-  CUtensorMap* d_maps = nullptr;  // FP32 flux: three tensor maps per instance
   int* d_ctr = nullptr;  // [0] next, [1] abort, [2..] counters
   cudaGraphExec_t exec = nullptr;
   cudaStream_t stream = nullptr;
@@ -362,7 +297,6 @@ void free_plan(Plan* p) {
   cudaFree(p->d_insts);
   cudaFree(p->d_args);
   cudaFree(p->d_items);
-  cudaFree(p->d_maps);
   cudaFree(p->d_ctr);
   delete p;
 }
@@ -372,36 +306,11 @@ void free_plan(Plan* p) {
 
 namespace {
 
-// Stage arguments of an instance of the batch: FP64 tiles of `rows` rows;
-// FP32-flux instances with tensor maps stage their interior tiles.
+// Stage arguments of an instance of the batch: FP64 tiles of `rows` rows.
 StageArgs batch_stage_args(const BatchInst& bi, int st, int rows) {
   StageArgs a = stage_args(bi.g, bi.b, st);
   if (bi.precision == 0) a.tz = rows;
-  a.bulk = bi.maps != nullptr ? 1 : 0;
   return a;
-}
-
-// Shared memory of the batch kernel per precision (FP32 flux: with the
-// slack for the 128-byte alignment of its struct).
-size_t batch_smem(int prec) { return prec == 1 ? sizeof(BatchMixedSmem) + 128 : stage_smem_bytes(0); }
-
-// The tensor maps of the instances (three per instance, valid FP32-flux
-// maps only) for upload to `d_maps`; sets each instance's maps pointer
-// into it (null where an instance has none).
-void maps_table(mprk_instance* const* insts, std::vector<BatchInst>& hinst, CUtensorMap* d_maps,
-                std::vector<CUtensorMap>& out) {
-  out.assign(3 * hinst.size(), CUtensorMap{});
-  for (size_t j = 0; j < hinst.size(); j++) {
-    const StageMaps m = instance_maps(insts[j]);
-    if (hinst[j].precision == 1 && m.valid && d_maps) {
-      out[3 * j] = m.dA;
-      out[3 * j + 1] = m.dB;
-      out[3 * j + 2] = m.Ra;
-      hinst[j].maps = d_maps + 3 * j;
-    } else {
-      hinst[j].maps = nullptr;
-    }
-  }
 }
 
 // The stage arguments of every instance and stage, in instance order; sets
@@ -506,18 +415,12 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
   else if (rows != TZ && rows != TZ / 2) rows = TZ;
   p->group = group;
   p->rows = rows;
-  cudaError_t e;
-  std::vector<CUtensorMap> hmaps;
-  if (p->precision == 1 && (e = cudaMalloc(&p->d_maps, sizeof(CUtensorMap) * 3 * count)) != cudaSuccess) {
-    free_plan(p);
-    return bfail(MPRK_ENOMEM, std::string("batch plan allocation: ") + cudaGetErrorString(e));
-  }
-  maps_table(insts, hinst, p->d_maps, hmaps);
   std::vector<StageArgs> hargs;
   args_table(hinst, rows, hargs);
   std::vector<BatchItem> items;
   build_items(hinst, group, rows, items, &p->cell_stages);
   p->n_items = (int)items.size();
+  cudaError_t e;
   if ((e = cudaMalloc(&p->d_insts, sizeof(BatchInst) * count)) != cudaSuccess ||
       (e = cudaMalloc(&p->d_args, sizeof(StageArgs) * hargs.size())) != cudaSuccess ||
       (e = cudaMalloc(&p->d_items, sizeof(BatchItem) * items.size())) != cudaSuccess ||
@@ -534,14 +437,12 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
       (e = cudaMemcpy(p->d_args, hargs.data(), sizeof(StageArgs) * hargs.size(), cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
       (e = cudaMemcpy(p->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice)) !=
-          cudaSuccess ||
-      (p->d_maps && (e = cudaMemcpy(p->d_maps, hmaps.data(), sizeof(CUtensorMap) * hmaps.size(),
-                                    cudaMemcpyHostToDevice)) != cudaSuccess)) {
+          cudaSuccess) {
     free_plan(p);
     return bfail(MPRK_ECUDA, std::string("batch plan upload: ") + cudaGetErrorString(e));
   }
   // grid: every CTA resident (persistent kernel)
-  const size_t smem = batch_smem(p->precision);
+  const size_t smem = stage_smem_bytes(p->precision);
   int per_sm = 0, dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
       (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
@@ -694,9 +595,8 @@ struct BatchRunner {
   BatchInst* d_insts = nullptr;
   StageArgs* d_args = nullptr;
   BatchItem* d_items = nullptr;
-  CUtensorMap* d_maps = nullptr;
   int* d_ctr = nullptr;
-  size_t cap_insts = 0, cap_args = 0, cap_items = 0, cap_ctr = 0, cap_maps = 0;
+  size_t cap_insts = 0, cap_args = 0, cap_items = 0, cap_ctr = 0;
   int n_items = 0, n_counters = 0, grid = 0, per_sm = 0, sms = 0;
   int rows = TZ;  // FP64 tile rows of the current work list
   long long cell_stages = 0;
@@ -715,7 +615,6 @@ void runner_destroy(BatchRunner* r) {
   if (r->d_insts) cudaFreeAsync(r->d_insts, r->stream);
   if (r->d_args) cudaFreeAsync(r->d_args, r->stream);
   if (r->d_items) cudaFreeAsync(r->d_items, r->stream);
-  if (r->d_maps) cudaFreeAsync(r->d_maps, r->stream);
   if (r->d_ctr) cudaFreeAsync(r->d_ctr, r->stream);
   delete r;
 }
@@ -764,17 +663,12 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
     tuned_choice(r->precision, size_bucket(hinst), &group, &per_sm_want, &rows);
     if (r->precision == 0 && rows != r->rows) r->per_sm = 0;  // another kernel: query its occupancy
     r->rows = rows;
-    cudaError_t e = cudaSuccess;
-    if (r->precision == 1) e = grow(&r->d_maps, &r->cap_maps, (size_t)3 * count, r->stream);
-    if (e != cudaSuccess) return bfail(MPRK_ENOMEM, std::string("batch runner: ") + cudaGetErrorString(e));
-    std::vector<CUtensorMap> hmaps;
-    maps_table(insts, hinst, r->d_maps, hmaps);
     std::vector<StageArgs> hargs;
     args_table(hinst, rows, hargs);
     std::vector<BatchItem> items;
     long long cs = 0;
     build_items(hinst, group, rows, items, &cs);
-    e = grow(&r->d_insts, &r->cap_insts, (size_t)count, r->stream);
+    cudaError_t e = grow(&r->d_insts, &r->cap_insts, (size_t)count, r->stream);
     if (e == cudaSuccess) e = grow(&r->d_args, &r->cap_args, hargs.size(), r->stream);
     if (e == cudaSuccess) e = grow(&r->d_items, &r->cap_items, items.size(), r->stream);
     if (e == cudaSuccess) e = grow(&r->d_ctr, &r->cap_ctr, (size_t)(2 + n_counters), r->stream);
@@ -789,16 +683,13 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(r->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
                           r->stream);
-    if (e == cudaSuccess && r->precision == 1)
-      e = cudaMemcpyAsync(r->d_maps, hmaps.data(), sizeof(CUtensorMap) * hmaps.size(), cudaMemcpyHostToDevice,
-                          r->stream);
     if (e != cudaSuccess) return bfail(MPRK_ECUDA, std::string("batch runner upload: ") + cudaGetErrorString(e));
     r->key.assign(insts, insts + count);
     r->n_items = (int)items.size();
     r->n_counters = n_counters;
     r->cell_stages = cs;
     if (r->per_sm == 0) {
-      const size_t smem = batch_smem(r->precision);
+      const size_t smem = stage_smem_bytes(r->precision);
       int dev = 0;
       if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
           (e = cudaDeviceGetAttribute(&r->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
@@ -828,7 +719,7 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
   A.withhold_stage = -1;
   cudaError_t e = cudaMemsetAsync(r->d_ctr, 0, sizeof(int) * (2 + r->n_counters), r->stream);
   if (e != cudaSuccess) return bfail(MPRK_ECUDA, std::string("batch runner: ") + cudaGetErrorString(e));
-  const size_t smem = batch_smem(r->precision);
+  const size_t smem = stage_smem_bytes(r->precision);
   const int grid = std::min(r->grid, r->n_items);
   batch_launch(r->precision, r->rows, grid, smem, r->stream, A);
   e = cudaGetLastError();

@@ -199,9 +199,6 @@ namespace mprk {
 // Instance internals the batch path uses (mprk_runtime.cu).
 int instance_view(const mprk_instance* inst, Geom* g, Bufs* b, int* precision, cudaStream_t* stream,
                   unsigned** status);
-// The tensor maps of an FP32-flux instance's float planes (valid = false
-// when the planes cannot be tensor-copied, and in FP64).
-StageMaps instance_maps(const mprk_instance* inst);
 cudaStream_t instance_stream(const mprk_instance* inst);
 void instance_count_steps(mprk_instance* inst, int n);
 // Drops cached batch plans that mention inst (mprk_batch.cu).

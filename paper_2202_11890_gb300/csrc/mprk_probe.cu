@@ -121,14 +121,15 @@ cudaError_t run_probe(long long iters, int nsm, cudaStream_t s, ProbeResult* out
 }  // namespace
 
 extern "C" int mprk_probe_fp64(long long iters, double* gflops, double* dfma_per_clk_per_sm, double* sm_mhz,
-                               int* sms) {
-  if (iters < 1 || iters > (1ll << 30) || !gflops || !dfma_per_clk_per_sm || !sm_mhz || !sms) {
+                               int* sms, double* max_mhz) {
+  if (iters < 1 || iters > (1ll << 30) || !gflops || !dfma_per_clk_per_sm || !sm_mhz || !sms || !max_mhz) {
     mprk::set_last_error("mprk_probe_fp64: bad argument");
     return MPRK_EINVAL;
   }
-  int dev = 0, nsm = 0;
+  int dev = 0, nsm = 0, khz = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
   cudaStream_t s = nullptr;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   // the fastest of four kernels: 8 or 16 chains per thread, FMA operands in
@@ -152,5 +153,6 @@ extern "C" int mprk_probe_fp64(long long iters, double* gflops, double* dfma_per
   *dfma_per_clk_per_sm = best.dfma_per_clk;
   *sm_mhz = best.mhz;
   *sms = nsm;
+  *max_mhz = khz * 1e-3;
   return MPRK_OK;
 }

@@ -269,17 +269,6 @@ int mprk::instance_view(const mprk_instance* I, Geom* g, Bufs* b, int* precision
   return MPRK_OK;
 }
 
-StageMaps mprk::instance_maps(const mprk_instance* I) {
-  StageMaps m;
-  if (I) {
-    m = I->maps;
-  } else {
-    memset(&m, 0, sizeof(m));
-    m.valid = false;
-  }
-  return m;
-}
-
 cudaStream_t mprk::instance_stream(const mprk_instance* I) { return I->stream; }
 
 long long mprk::instance_steps(const mprk_instance* I) { return I->steps_done; }

@@ -855,11 +855,10 @@ __device__ __forceinline__ void prefetch_combination(const StageArgs& a, int k0,
 
 // The pair path on the TX x MTZ interior tile from row k0, column i0. stg,
 // when not null, receives the tile's float planes by tensor copies that
-// complete the phase of parity `parity` of bar. Returns false if the wait
-// for them gave up.
+// complete on bar (phase 0). Returns false if the wait for them gave up.
 template <int PAR>
 __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, PairSmem& S, const Stage* stg,
-                                          unsigned long long* bar, unsigned parity = 0) {
+                                          unsigned long long* bar) {
   const Geom& g = a.g;
   const int tid = threadIdx.x;
   prefetch_combination<PAR>(a, k0, i0);
@@ -913,7 +912,7 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
       const int j = t2 / PHR, r = t2 - j * PHR;
       S.rc[j][r] = rowp[j * nz + k0 - 2 + r];
     }
-    if (stg) ok = mbar_wait(bar, parity);  // the row constants above are in flight meanwhile
+    if (stg) ok = mbar_wait(bar, 0);  // the row constants above are in flight meanwhile
 #pragma unroll
     for (int e = 0; e < 2; e++) {
       if (e == 1 && !two) break;
@@ -1094,9 +1093,8 @@ union MixedTileSmem {
 
 template <int PAR>
 __device__ __forceinline__ bool stage_tile_mixed(const StageArgs& a, int k0, int i0, MixedTileSmem& S,
-                                                 const Stage* stg, unsigned long long* bar,
-                                                 unsigned parity = 0) {
-  if (pair_interior(a, k0, i0)) return pair_tile<PAR>(a, k0, i0, S.pair, stg, bar, parity);
+                                                 const Stage* stg, unsigned long long* bar) {
+  if (pair_interior(a, k0, i0)) return pair_tile<PAR>(a, k0, i0, S.pair, stg, bar);
   mixed_subtile<PAR>(a, k0, i0, S.gen);
   const int hi = rhs_mode<PAR>(a) ? a.rhs_hi : a.g.nz;
   if (k0 + TZ < hi) {

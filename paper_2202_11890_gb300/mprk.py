@@ -119,7 +119,7 @@ def lib():
                            C.POINTER(vp)]),
         "mprk_rhs": (ip, [vp, vp, vp, ip, ip]),
         "mprk_profile_step": (ip, [vp, dp, C.POINTER(C.c_longlong), ip]),
-        "mprk_probe_fp64": (ip, [C.c_longlong, dp, dp, dp, C.POINTER(C.c_int)]),
+        "mprk_probe_fp64": (ip, [C.c_longlong, dp, dp, dp, C.POINTER(C.c_int), dp]),
         "mprk_step_static": (ip, [cfgp, vp, ip, vp]),
         "mprk_step_batch": (ip, [C.POINTER(vp), ip, ip]),
         "mprk_batch_test_withhold": (ip, [C.POINTER(vp), ip, ip, ip, C.c_longlong]),
@@ -269,9 +269,10 @@ def mprk_profile_step(h: int):
 
 def mprk_probe_fp64(iters: int = 12000) -> dict:
     """FP64 FMA throughput of the current device (register-only probe)."""
-    g, r, mhz, sms = C.c_double(), C.c_double(), C.c_double(), C.c_int()
-    _check(lib().mprk_probe_fp64(int(iters), C.byref(g), C.byref(r), C.byref(mhz), C.byref(sms)))
-    return {"gflops": g.value, "dfma_per_clk_per_sm": r.value, "sm_mhz": mhz.value, "sms": sms.value}
+    g, r, mhz, sms, mx = C.c_double(), C.c_double(), C.c_double(), C.c_int(), C.c_double()
+    _check(lib().mprk_probe_fp64(int(iters), C.byref(g), C.byref(r), C.byref(mhz), C.byref(sms), C.byref(mx)))
+    return {"gflops": g.value, "dfma_per_clk_per_sm": r.value, "sm_mhz": mhz.value, "sms": sms.value,
+            "max_mhz": mx.value}
 
 
 def _handles(hs):
