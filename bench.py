@@ -371,7 +371,10 @@ def run_ours(args):
     if args.precision:
         wl.precision = args.precision
     traffic_key = args.workload in ("large_2048", "mixed_4096") and not args.precision
+    tiles = tune_tiles(M, wl) if wl.precision == "fp64" and not args.no_tune else None
     rec, cfg, q0, dt = measure_single(M, T, wl, args.steps, args.warmup, ws, True, traffic_key)
+    if tiles is not None:
+        rec["kernel"]["tile_shapes"] = tiles
     fp64 = cfg.precision == M.MPRK_FP64
     if rank == 0:
         out = {"metric": METRIC, "value": rec["value"], "unit": "cell-stages/s", "n_gpus": ws,
@@ -391,6 +394,24 @@ def run_ours(args):
         print(json.dumps(out))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def tune_tiles(M, wl) -> dict:
+    """The library's tile-shape autotuner (mprk_tile_tune) on an instance of
+    the workload, before the measured instance is created (it captures its
+    step with the tuned shapes; results do not depend on them). Returns the
+    shape chosen for each of the workload's stage launches."""
+    g = wl.grid
+    cfg = M.mprk_config_default(g.nx, g.nS, g.nB, g.nF, wl.m)
+    M.mprk_tune_clear()
+    with M.Instance(cfg, wl.initial_state()) as inst:
+        M.mprk_tile_tune([inst.h], reps=3)
+    out = {}
+    for name, rows in (("first_substep_all_rows", g.nz), ("later_substeps_B_F_rows", g.nB + g.nF)):
+        sh = M.mprk_tile_lookup(float(g.nx * rows))
+        out[name] = {"cells": g.nx * rows, "tile": f"32x{sh['tile_rows']}" if sh else None,
+                     "threads_per_cell": sh["threads_per_cell"] if sh else None}
+    return out
 
 
 def mixed_accuracy(M, cfg, q0, wl, dt, args) -> dict:
@@ -680,9 +701,17 @@ def sub_records(args) -> dict:
     rec["accuracy"] = mixed_accuracy(M, cfg, q0, wl, dt, args)
     out["mixed_4096"] = rec
     for prec in ("fp64", "fp32flux"):
-        out[f"batched_256_{prec}"] = measure_batched(M, T, prec, args.sub_steps, args.warmup)
+        # the launch choices (tiles per item, CTAs per SM, FP64 tile shape)
+        # tuned on the instances first, the default launch timed beside
+        out[f"batched_256_{prec}"] = measure_batched(M, T, prec, args.sub_steps, args.warmup,
+                                                     tune=not args.no_tune)
     out["served"] = measure_served(M, args.rate, args.sub_served_warmup, args.sub_served_requests, args.budget_gb,
                                    args.slots, sequential=True)
+    # the same stream's distribution at a lower arrival rate, below the
+    # GPU's saturation, for the latency of an unsaturated server
+    out["served_below_saturation"] = measure_served(M, args.sub_served_rate_low, args.sub_served_warmup,
+                                                    args.sub_served_requests, args.budget_gb, args.slots,
+                                                    sequential=False)
     return out
 
 
@@ -1121,9 +1150,11 @@ def main():
     ap.add_argument("--ref-cols", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="headline line only, without the other workloads")
+    ap.add_argument("--no-tune", action="store_true", help="default launch choices, no autotuning")
     ap.add_argument("--sub-steps", type=int, default=20, help="slow steps timed per sub-record")
     ap.add_argument("--sub-served-requests", type=int, default=500)
     ap.add_argument("--sub-served-warmup", type=int, default=100)
+    ap.add_argument("--sub-served-rate-low", type=float, default=120.0)
     ap.add_argument("--served-sequential", action="store_true")
     ap.add_argument("--oracle-steps", type=int, default=2,
                     help="full-size oracle slow steps of the FP32-flux CPU-baseline leg")

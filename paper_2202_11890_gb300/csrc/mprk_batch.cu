@@ -9,12 +9,14 @@
 // stage s of instance I first waits until every item of stage s-1 of I has
 // finished (a per-instance counter). The tiles per item and the CTAs per SM
 // come from a tuning table (mprk_batch_tune) or defaults.
+// This file builds the work lists, plans and tuning; the kernel itself is
+// compiled with the single-instance stage kernels (batch_kernel.cuh, included
+// by mprk_kernels.cu), so that both call one compiled copy of the FP64 tile.
 // Since items are taken in list order, every item an item waits on was taken
 // earlier by a CTA that is already running, so the waits always end. Waits
 // are bounded all the same: after a fixed number of clock cycles a CTA sets
 // the status word's timeout bit and an abort flag, and every CTA then drains
 // without touching the states (no trap, no hang).
-#include <cuda/atomic>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,174 +30,10 @@
 #include <string>
 #include <vector>
 
+#include "batch_types.h"
 #include "mprk.h"
 #include "mprk_internal.h"
-#include "stage_tile.cuh"
-#include "stage_tile_mixed.cuh"
 
-namespace mprk {
-
-struct BatchInst {
-  Geom g;
-  Bufs b;
-  unsigned* status;  // the instance's status word
-  int counter_base;  // first counter of this instance: one per stage, then completion
-  int args_base;     // first entry of this instance in BatchArgs::args: one per stage
-  int precision;
-};
-
-// The work items copy their stage's arguments from a table built on the
-// host (stage_args of every instance and stage) in 16-byte words.
-static_assert(sizeof(StageArgs) % 16 == 0, "StageArgs is copied in 16-byte words");
-constexpr int ARGS_WORDS = (int)(sizeof(StageArgs) / 16);
-
-struct BatchItem {
-  int inst;
-  int stage;  // 0 .. s m - 1 (s base stages per fast substep), or s m for a completion item
-  int tile;   // first tile of the stage, or first chunk of the completion
-  int count;  // consecutive tiles (chunks) the item covers
-  int need;   // items of the previous stage this one waits for (0: none)
-};
-
-// Default tiles per work item: two in both precisions. An FP32-flux tile
-// takes a few microseconds; an item's scheduling (claim, wait, argument
-// copy, barriers) is mostly hidden behind the previous item, so two tiles
-// per item beat four on mixed batches. mprk_batch_tune may pick others per
-// size bucket.
-constexpr int batch_group(int /*precision*/) { return 2; }
-
-struct BatchArgs {
-  const BatchInst* insts;
-  const StageArgs* args;  // [sum over instances of s m], 16-byte aligned
-  const BatchItem* items;
-  int n_items;
-  int* next;           // work counter
-  int* counters;       // per-instance stage completion counters
-  int* abort_flag;
-  unsigned* status;
-  long long wait_cycles;
-  int withhold_inst;   // test hook: this instance's withhold_stage tiles never report done
-  int withhold_stage;
-};
-
-constexpr int FIN_CHUNK = NTHREADS * 8;  // cells per completion item
-
-// block size of the batch kernel per precision (the tile's own block size)
-constexpr int batch_threads(int prec) { return prec == 0 ? NTHREADS : MIXED_THREADS; }
-
-__device__ __forceinline__ bool wait_for(const BatchArgs& A, int ctr, int need) {
-  // one thread waits with acquire semantics; returns false after an abort or timeout
-  cuda::atomic_ref<int, cuda::thread_scope_device> c(A.counters[ctr]);
-  cuda::atomic_ref<int, cuda::thread_scope_device> ab(*A.abort_flag);
-  const long long t0 = clock64();
-  while (c.load(cuda::memory_order_acquire) < need) {
-    if (ab.load(cuda::memory_order_relaxed)) return false;
-    if (clock64() - t0 > A.wait_cycles) {
-      atomicOr(A.status, ST_TIMEOUT);
-      ab.store(1, cuda::memory_order_relaxed);
-      return false;
-    }
-    __nanosleep(256);
-  }
-  return true;
-}
-
-__device__ __forceinline__ void finalize_chunk(const Geom& g, const Bufs& b, int chunk) {
-  const int m_odd = g.m & 1;
-  const bool mixed = b.dA != nullptr;
-  const int rows = (m_odd || mixed) ? g.nz : g.n1_r;
-  const long long per_c = (long long)rows * g.nx;  // elements of one component (< 2^31)
-  const long long total = 4LL * per_c;
-  for (long long e = (long long)chunk * FIN_CHUNK + threadIdx.x; e < total && e < (long long)(chunk + 1) * FIN_CHUNK;
-       e += blockDim.x) {
-    const int c = (e >= per_c) + (e >= 2 * per_c) + (e >= 3 * per_c);
-    const int rem = (int)(e - c * per_c);
-    const int k = rem / g.nx, i = rem - k * g.nx;
-    const size_t o = ((size_t)c * g.nz + k) * g.pitch + i;
-    double v;
-    if (k < g.nS_r) v = b.accS[((size_t)c * g.nS_r + k) * g.pitch + i];
-    else if (k < g.n1_r) v = b.accB[((size_t)c * (g.n1_r - g.nS_r) + (k - g.nS_r)) * g.pitch + i];
-    else v = m_odd ? b.qB[o] : b.qA[o];
-    if (k < g.n1_r || m_odd) b.qA[o] = v;  // F rows after an even m hold q_{n+1} already
-    if (mixed) b.dA[o] = narrow(v - (double)b.rowc[4 * k + c]);
-  }
-}
-
-// The FP32-flux tile of a work item, compiled as a function of its own: the
-// tile reads its arguments from shared memory (not from the constant bank
-// as the single-instance kernel does), and allocated apart from the
-// persistent loop it spills less than inlined there.
-template <int PAR>
-__device__ __noinline__ void batch_tile_mixed(const StageArgs& a, int tile, MixedTileSmem& S) {
-  stage_tile_mixed<PAR>(a, tile, S);
-}
-
-// three CTAs per SM in both precisions (80 and 72 registers; the FP32-flux
-// form spills some, and still runs faster than at two CTAs). ROWS: rows of
-// the FP64 tile, TZ (one thread per cell) or TZ / 2 (two threads per cell);
-// the block size stays the same.
-template <int PREC, int ROWS = TZ>
-__global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const BatchArgs A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  // the current and the next claimed item: thread 0 claims the next one
-  // while the CTA works on the current, so the atomic's latency is hidden.
-  // Items depend only on items before them in the list, and each CTA runs
-  // its claims in order, so claiming ahead cannot deadlock.
-  __shared__ int s_item[2];
-  __shared__ int s_ok;
-  // the item's stage arguments, one copy for the CTA: the tile reads its
-  // launch constants from shared memory instead of a per-thread local copy
-  __shared__ __align__(16) StageArgs s_a;
-  cuda::atomic_ref<int, cuda::thread_scope_device> nxt(*A.next);
-  if (threadIdx.x == 0) s_item[0] = nxt.fetch_add(1, cuda::memory_order_relaxed);
-  __syncthreads();
-  for (int cur = 0;; cur ^= 1) {
-    const int it = s_item[cur];
-    if (it >= A.n_items) break;
-    const BatchItem item = A.items[it];
-    const BatchInst& I = A.insts[item.inst];
-    const bool stage_item = item.stage < I.g.s * I.g.m;
-    if (threadIdx.x == 0) {
-      s_item[cur ^ 1] = nxt.fetch_add(1, cuda::memory_order_relaxed);
-      s_ok = 1;
-      if (item.need > 0) s_ok = wait_for(A, I.counter_base + item.stage - 1, item.need) ? 1 : 0;
-      else if (*(volatile int*)A.abort_flag) s_ok = 0;
-      if (!s_ok) atomicOr(I.status, ST_TIMEOUT);  // this instance's step is incomplete
-    } else if (stage_item && (int)threadIdx.x <= ARGS_WORDS) {
-      // meanwhile the next threads copy the stage's arguments
-      const int w = threadIdx.x - 1;
-      reinterpret_cast<int4*>(&s_a)[w] = reinterpret_cast<const int4*>(A.args + I.args_base + item.stage)[w];
-    }
-    __syncthreads();
-    if (s_ok) {
-      if (stage_item) {
-        for (int t = 0; t < item.count; t++) {
-          if (t > 0) __syncthreads();  // the previous tile is done with shared memory
-          if (PREC == 0 && s_a.g.gen)  // a general s-stage base (RK3, RK4)
-            stage_tile<double, double, true, NTHREADS, ROWS>(s_a, item.tile + t,
-                                                             *reinterpret_cast<TileSmem<double, ROWS>*>(smem_raw));
-          else if (PREC == 0)
-            stage_tile<double, double, false, NTHREADS, ROWS>(s_a, item.tile + t,
-                                                              *reinterpret_cast<TileSmem<double, ROWS>*>(smem_raw));
-          else if (s_a.stage & 1)  // the FP32-flux tile compiled per stage parity
-            batch_tile_mixed<1>(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
-          else
-            batch_tile_mixed<0>(s_a, item.tile + t, *reinterpret_cast<MixedTileSmem*>(smem_raw));
-        }
-      } else {
-        for (int t = 0; t < item.count; t++) finalize_chunk(I.g, I.b, item.tile + t);
-      }
-    }
-    __syncthreads();  // the tile's writes are done; shared memory is free again
-    if (threadIdx.x == 0 && s_ok &&
-        !(item.inst == A.withhold_inst && item.stage == A.withhold_stage)) {
-      cuda::atomic_ref<int, cuda::thread_scope_device> c(A.counters[I.counter_base + item.stage]);
-      c.fetch_add(1, cuda::memory_order_release);
-    }
-  }
-}
-
-}  // namespace mprk
 
 using namespace mprk;
 
@@ -321,29 +159,6 @@ void args_table(std::vector<BatchInst>& hinst, int rows, std::vector<StageArgs>&
     bi.args_base = (int)out.size();
     for (int st = 0; st < bi.g.s * bi.g.m; st++) out.push_back(batch_stage_args(bi, st, rows));
   }
-}
-
-// The persistent kernel of a precision and FP64 tile rows: its shared-memory
-// limit, its CTAs per SM and its launch.
-cudaError_t batch_prepare(int prec, int rows, size_t smem, int* per_sm) {
-  cudaError_t e;
-  if (prec == 1) {
-    e = cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<1>, batch_threads(1), smem);
-  } else if (rows == TZ / 2) {
-    e = cudaFuncSetAttribute(batch_kernel<0, TZ / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<0, TZ / 2>, batch_threads(0), smem);
-  } else {
-    e = cudaFuncSetAttribute(batch_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<0>, batch_threads(0), smem);
-  }
-  return e;
-}
-void batch_launch(int prec, int rows, int grid, size_t smem, cudaStream_t s, const BatchArgs& A) {
-  if (prec == 1) batch_kernel<1><<<grid, batch_threads(1), smem, s>>>(A);
-  else if (rows == TZ / 2) batch_kernel<0, TZ / 2><<<grid, batch_threads(0), smem, s>>>(A);
-  else batch_kernel<0><<<grid, batch_threads(0), smem, s>>>(A);
 }
 
 // The stage-major work list: all first-stage items of all instances, then

@@ -33,6 +33,10 @@ constexpr int NTHREADS = TX * TZ;
 constexpr int MTZ = 2 * TZ;
 // Floats of per-row constants in the FP32-flux mode (layout in stage_tile_mixed.cuh).
 constexpr int NROWC = 48;
+// Threads of the FP32-flux tile: nine warps. Warps 0-7 own the TX x TZ cell
+// pairs, warp 8 computes the faces on the tile's top edge (one pass) and
+// right edge (one pass), so every warp makes two face passes.
+constexpr int MIXED_THREADS = NTHREADS + 32;
 
 // Status bits written by device code.
 constexpr unsigned ST_NONFINITE = 1u;

@@ -18,6 +18,7 @@
 #include "stage_tile.cuh"
 #include "stage_tile3d.cuh"
 #include "stage_tile_mixed.cuh"
+#include "batch_kernel.cuh"
 
 namespace mprk {
 
@@ -242,6 +243,30 @@ cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStr
   }
   return cudaGetLastError();
 }
+
+// The persistent batch kernel: shared-memory limit, occupancy and launch
+// (declared in batch_types.h).
+cudaError_t batch_prepare(int prec, int rows, size_t smem, int* per_sm) {
+  cudaError_t e;
+  if (prec == 1) {
+    e = cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<1>, batch_threads(1), smem);
+  } else if (rows == TZ / 2) {
+    e = cudaFuncSetAttribute(batch_kernel<0, TZ / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<0, TZ / 2>, batch_threads(0), smem);
+  } else {
+    e = cudaFuncSetAttribute(batch_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel<0>, batch_threads(0), smem);
+  }
+  return e;
+}
+void batch_launch(int prec, int rows, int grid, size_t smem, cudaStream_t s, const BatchArgs& A) {
+  if (prec == 1) batch_kernel<1><<<grid, batch_threads(1), smem, s>>>(A);
+  else if (rows == TZ / 2) batch_kernel<0, TZ / 2><<<grid, batch_threads(0), smem, s>>>(A);
+  else batch_kernel<0><<<grid, batch_threads(0), smem, s>>>(A);
+}
+
 
 // ---------------------------------------------------------------------------
 // FP32-flux mode set-up. Row means of q give the reference q_ref(k), rounded

@@ -171,14 +171,24 @@ __device__ __forceinline__ bool x_ghost(int i, int nx, int xwall) { return xwall
 // the same alone and in a batch.
 // The stage value of a general s-stage base (GEN): base + h sum_{q<p}
 // A_pq R_q over the R_a slots of the current substep (slot q at
-// Ra + q * slot); p = 0 gives the base value.
+// Ra + q * slot); p = 0 gives the base value. Every product-sum is an
+// explicit fused multiply-add, so no launch shape or kernel that compiles
+// this code can round it differently.
 __device__ __forceinline__ double gen_stage_value(const Geom& g, const double* base, const double* Ra, size_t slot,
                                                   size_t off, int p, double h) {
   if (p == 0) return base[off];
   double sum = 0.0;
   for (int q = 0; q < p; q++)
-    if (g.bA[p][q] != 0.0) sum += g.bA[p][q] * Ra[(size_t)q * slot + off];
-  return base[off] + h * sum;
+    if (g.bA[p][q] != 0.0) sum = __fma_rn(g.bA[p][q], Ra[(size_t)q * slot + off], sum);
+  return __fma_rn(h, sum, base[off]);
+}
+
+// sum_q b_q R_q over the first s - 1 R_a slots and the current R (slot
+// s - 1), as explicit fused multiply-adds in ascending q.
+__device__ __forceinline__ double gen_weighted_sum(const Geom& g, const double* Rs, size_t slot, size_t o, double r) {
+  double sum = 0.0;
+  for (int q = 0; q < g.s - 1; q++) sum = __fma_rn(g.bb[q], Rs[(size_t)q * slot + o], sum);
+  return __fma_rn(g.bb[g.s - 1], r, sum);
 }
 
 // GEN selects the general s-stage base method (Sec. 3 remark) in place of
@@ -504,22 +514,15 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
         const double r = (double)R[c];
         if (!sub_end) Rs[(size_t)p * slot + o] = r;
         if (k >= g.n1_r) {
-          if (sub_end) {
-            double sum = 0.0;
-            for (int q = 0; q < s - 1; q++) sum += g.bb[q] * Rs[(size_t)q * slot + o];
-            sum += g.bb[s - 1] * r;
-            a.qF_next[o] = a.qF[o] + g.hF * sum;
-          }
+          if (sub_end) a.qF_next[o] = __fma_rn(g.hF, gen_weighted_sum(g, Rs, slot, o, r), a.qF[o]);
         } else if (k >= g.nS_r) {
           const size_t pb = (size_t)(g.n1_r - g.nS_r) * g.pitch;
           double* acc = a.b.accB + (size_t)c * pb + (size_t)(k - g.nS_r) * g.pitch + i;
-          const double v = (st == 0) ? g.bb[p] * r : *acc + g.bb[p] * r;
-          *acc = (st == s * g.m - 1) ? a.b.qA[o] + g.hF * v : v;
+          const double v = (st == 0) ? __dmul_rn(g.bb[p], r) : __fma_rn(g.bb[p], r, *acc);
+          *acc = (st == s * g.m - 1) ? __fma_rn(g.hF, v, a.b.qA[o]) : v;
         } else if (sub_end) {
-          double sum = 0.0;
-          for (int q = 0; q < s - 1; q++) sum += g.bb[q] * Rs[(size_t)q * slot + o];
-          sum += g.bb[s - 1] * r;
-          a.b.accS[(size_t)c * ((size_t)g.nS_r * g.pitch) + row_off] = a.b.qA[o] + g.dt * sum;
+          a.b.accS[(size_t)c * ((size_t)g.nS_r * g.pitch) + row_off] =
+              __fma_rn(g.dt, gen_weighted_sum(g, Rs, slot, o, r), a.b.qA[o]);
         }
       }
       return;

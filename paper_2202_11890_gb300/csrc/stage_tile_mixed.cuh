@@ -83,10 +83,6 @@ __device__ __forceinline__ float narrow(double x) {
 //   j = 11     (D.y, 0): the R(rho w) constant
 constexpr int RC_PAIR = 4;  // first paired group
 
-// Nine warps: warps 0-7 own the TX x TZ cells, warp 8 computes the faces on
-// the tile's top edge (one pass) and right edge (one pass), so every warp
-// makes two face passes.
-constexpr int MIXED_THREADS = NTHREADS + 32;
 
 struct MixedSmem {
   float4 q[TZ + 4][TX + 4];  // deviation d of the stage state (rho, mu, mw, E) on the halo
