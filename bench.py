@@ -139,7 +139,8 @@ def algorithmic_bytes(g: W.Grid, m: int, fp64: bool):
     if fp64:
         fin = nx * (nS + nB) * 64 + (nx * nF * 64 if m % 2 else 0)
     else:
-        fin = nx * (nS + nB) * 80 + nx * nF * (80 if m % 2 else 48)
+        # after an even m the last stage resynchronises the F rows' shadow
+        fin = nx * (nS + nB) * 80 + (nx * nF * 80 if m % 2 else 0)
     return tot, fin
 
 

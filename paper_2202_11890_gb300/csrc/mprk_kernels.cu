@@ -378,19 +378,23 @@ cudaError_t launch_shadow(const Geom& g, const double* q, const float* rowc, flo
 
 // ---------------------------------------------------------------------------
 // Step completion: S and B rows from accS / accB; F rows from qB when the
-// fast state ended in qB (odd m). In the FP32-flux mode every row's float
-// shadow is also resynchronised to the new double state. One thread per
-// (component, row, column).
+// fast state ended in qB (odd m). In the FP32-flux mode the float shadow of
+// every row it visits is also resynchronised to the new double state (the
+// F rows of an even m are resynchronised by the last stage).
 // ---------------------------------------------------------------------------
 // An x-row r of a component is (k, j) with r = k ny + j (ny = 1 in 2-D);
 // the buffers' rows of the S and B bands are numbered the same way.
 // One row of one component per block row: blockIdx.z the component,
 // rows r = blockIdx.y + n gridDim.y (r = k ny + j, k the z row), threads
-// over x. F rows after an even m already hold q_{n+1} in qA and only
-// refresh the float shadow.
-__global__ void finalize_kernel(const Geom g, const Bufs b, int m_odd) {
+// over x, two consecutive cells per thread. vec: every row starts on a
+// 16-byte boundary (an even pitch and 16-byte aligned buffers, as
+// mprk_create's padded layout always has), so the pairs move as 16-byte
+// loads and stores; otherwise (mprk_step_static's unpadded rows) one cell
+// at a time. F rows after an even m already hold q_{n+1} in qA, and the last
+// stage has rebuilt their float shadow: they are not visited.
+__global__ void finalize_kernel(const Geom g, const Bufs b, int m_odd, int vec) {
   const bool mixed = b.dA != nullptr;
-  const int rows = (m_odd || mixed) ? g.nz : g.n1_r;
+  const int rows = m_odd ? g.nz : g.n1_r;
   const int c = blockIdx.z;
   for (int r = blockIdx.y; r < rows * g.ny; r += gridDim.y) {
     const int k = r / g.ny;
@@ -401,19 +405,32 @@ __global__ void finalize_kernel(const Geom g, const Bufs b, int m_odd) {
     else src = (m_odd ? b.qB : b.qA) + o;
     const bool store_q = k < g.n1_r || m_odd;
     const double ref = mixed ? (double)b.rowc[4 * k + c] : 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nx; i += gridDim.x * blockDim.x) {
-      const double v = src[i];
-      if (store_q) b.qA[o + i] = v;
-      if (mixed) b.dA[o + i] = narrow(v - ref);
+    for (int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x); i < g.nx; i += 2 * gridDim.x * blockDim.x) {
+      if (vec && i + 1 < g.nx) {
+        const double2 v = *reinterpret_cast<const double2*>(src + i);
+        if (store_q) *reinterpret_cast<double2*>(b.qA + o + i) = v;
+        if (mixed) *reinterpret_cast<float2*>(b.dA + o + i) = make_float2(narrow(v.x - ref), narrow(v.y - ref));
+      } else {
+        for (int j = i; j < i + 2 && j < g.nx; j++) {
+          const double v = src[j];
+          if (store_q) b.qA[o + j] = v;
+          if (mixed) b.dA[o + j] = narrow(v - ref);
+        }
+      }
     }
   }
 }
 
 cudaError_t launch_finalize(const Geom& g, const Bufs& b, int m_odd, cudaStream_t stream) {
-  const int rows = (m_odd || b.dA != nullptr) ? g.nz : g.n1_r;
+  const int rows = m_odd ? g.nz : g.n1_r;
   if (rows == 0) return cudaSuccess;
-  const dim3 grid((g.nx + 255) / 256, (unsigned)std::min(rows * g.ny, 65535), (unsigned)g.nc);
-  finalize_kernel<<<grid, 256, 0, stream>>>(g, b, m_odd);
+  auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  const int vec = (g.pitch % 2 == 0 && a16(b.qA) && a16(b.qB) && a16(b.accS) && a16(b.accB) &&
+                   (!b.dA || (reinterpret_cast<uintptr_t>(b.dA) & 7u) == 0))
+                      ? 1
+                      : 0;
+  const dim3 grid((g.nx + 511) / 512, (unsigned)std::min(rows * g.ny, 65535), (unsigned)g.nc);
+  finalize_kernel<<<grid, 256, 0, stream>>>(g, b, m_odd, vec);
   return cudaGetLastError();
 }
 
