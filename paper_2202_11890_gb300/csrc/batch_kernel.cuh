@@ -39,7 +39,7 @@ __device__ __forceinline__ bool wait_for(const BatchArgs& A, int ctr, int need) 
 __device__ __forceinline__ void finalize_chunk(const Geom& g, const Bufs& b, int chunk) {
   const int m_odd = g.m & 1;
   const bool mixed = b.dA != nullptr;
-  const int rows = m_odd ? g.nz : g.n1_r;  // F rows of an even m: done by the last stage
+  const int rows = (m_odd || mixed) ? g.nz : g.n1_r;
   const long long per_c = (long long)rows * g.nx;  // elements of one component (< 2^31)
   const long long total = 4LL * per_c;
   for (long long e = (long long)chunk * FIN_CHUNK + threadIdx.x; e < total && e < (long long)(chunk + 1) * FIN_CHUNK;

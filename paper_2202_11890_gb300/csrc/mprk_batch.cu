@@ -177,7 +177,7 @@ void build_items(const std::vector<BatchInst>& hinst, int G, int rows, std::vect
       if (st > ms) continue;
       auto ntiles = [&](int s) {
         if (s < ms) return stage_tiles(batch_stage_args(hinst[j], s, rows));
-        const int rows = (g.m & 1) ? g.nz : g.n1_r;  // as finalize_chunk
+        const int rows = ((g.m & 1) || hinst[j].b.dA) ? g.nz : g.n1_r;  // as finalize_chunk
         const long long total = 4LL * rows * g.nx;
         return (int)((total + FIN_CHUNK - 1) / FIN_CHUNK);
       };

@@ -378,9 +378,8 @@ cudaError_t launch_shadow(const Geom& g, const double* q, const float* rowc, flo
 
 // ---------------------------------------------------------------------------
 // Step completion: S and B rows from accS / accB; F rows from qB when the
-// fast state ended in qB (odd m). In the FP32-flux mode the float shadow of
-// every row it visits is also resynchronised to the new double state (the
-// F rows of an even m are resynchronised by the last stage).
+// fast state ended in qB (odd m). In the FP32-flux mode every row's float
+// shadow is also resynchronised to the new double state.
 // ---------------------------------------------------------------------------
 // An x-row r of a component is (k, j) with r = k ny + j (ny = 1 in 2-D);
 // the buffers' rows of the S and B bands are numbered the same way.
@@ -390,13 +389,13 @@ cudaError_t launch_shadow(const Geom& g, const double* q, const float* rowc, flo
 // 16-byte boundary (an even pitch and 16-byte aligned buffers, as
 // mprk_create's padded layout always has), so the pairs move as 16-byte
 // loads and stores; otherwise (mprk_step_static's unpadded rows) one cell
-// at a time. F rows after an even m already hold q_{n+1} in qA, and the last
-// stage has rebuilt their float shadow: they are not visited.
-__global__ void finalize_kernel(const Geom g, const Bufs b, int m_odd, int vec) {
+// at a time. F rows after an even m already hold q_{n+1} in qA and only
+// refresh the float shadow (which the last stage leaves to this kernel).
+// Rows k_lo <= k < k_hi of those it completes (x-rows r = k ny + j).
+__global__ void finalize_kernel(const Geom g, const Bufs b, int m_odd, int vec, int k_lo, int k_hi) {
   const bool mixed = b.dA != nullptr;
-  const int rows = m_odd ? g.nz : g.n1_r;
   const int c = blockIdx.z;
-  for (int r = blockIdx.y; r < rows * g.ny; r += gridDim.y) {
+  for (int r = k_lo * g.ny + blockIdx.y; r < k_hi * g.ny; r += gridDim.y) {
     const int k = r / g.ny;
     const size_t o = ((size_t)c * g.nz * g.ny + r) * g.pitch;
     const double* src;
@@ -421,16 +420,19 @@ __global__ void finalize_kernel(const Geom g, const Bufs b, int m_odd, int vec) 
   }
 }
 
-cudaError_t launch_finalize(const Geom& g, const Bufs& b, int m_odd, cudaStream_t stream) {
-  const int rows = m_odd ? g.nz : g.n1_r;
-  if (rows == 0) return cudaSuccess;
+cudaError_t launch_finalize(const Geom& g, const Bufs& b, int m_odd, cudaStream_t stream, int k_lo, int k_hi) {
+  const int end = (m_odd || b.dA) ? g.nz : g.n1_r;  // rows it completes
+  k_hi = k_hi < 0 ? end : std::min(k_hi, end);
+  k_lo = std::max(k_lo, 0);
+  const int rows = k_hi - k_lo;
+  if (rows <= 0) return cudaSuccess;
   auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   const int vec = (g.pitch % 2 == 0 && a16(b.qA) && a16(b.qB) && a16(b.accS) && a16(b.accB) &&
                    (!b.dA || (reinterpret_cast<uintptr_t>(b.dA) & 7u) == 0))
                       ? 1
                       : 0;
   const dim3 grid((g.nx + 511) / 512, (unsigned)std::min(rows * g.ny, 65535), (unsigned)g.nc);
-  finalize_kernel<<<grid, 256, 0, stream>>>(g, b, m_odd, vec);
+  finalize_kernel<<<grid, 256, 0, stream>>>(g, b, m_odd, vec, k_lo, k_hi);
   return cudaGetLastError();
 }
 

@@ -309,10 +309,10 @@ __device__ __forceinline__ void z_face3(MixedSmem& S, const Geom& g, int k0, int
 
 // Whether this stage writes the step's F-row result into the state buffer:
 // its last stage with an even number of fast substeps (the F rows ping-pong
-// between the two state buffers and end where they started). The float
-// shadow of those rows is then rebuilt from the double result, as the step
-// completion does for the S and B rows.
-__device__ __forceinline__ bool resync_stage(const StageArgs& a) {
+// between the two state buffers and end where they started). The step
+// completion then rebuilds the float shadow of every row from the double
+// state, so this stage does not write the F rows' shadow.
+__device__ __forceinline__ bool shadow_by_completion(const StageArgs& a) {
   return !a.rhs_only && a.stage == 2 * a.g.m - 1 && (a.g.m & 1) == 0;
 }
 
@@ -496,15 +496,12 @@ __device__ __forceinline__ void mixed_subtile(const StageArgs& a, int k0, int i0
       for (int c = 0; c < 4; c++) Ra_w[(size_t)c * plane + row_off] = R[c];
     } else {
 #pragma unroll
-      const bool resync = resync_stage(a);  // as in the pair path
-      const float4 ref = S.rcA[ty + 2];
-      const float refc[4] = {ref.x, ref.y, ref.z, ref.w};
+      const bool shadow = !shadow_by_completion(a);  // as in the pair path
       for (int c = 0; c < 4; c++) {
         const size_t o = (size_t)c * plane + row_off;
         const float s = Ra[o] + R[c];
-        const double n = fma(h2, widen(s), a.qF[o]);
-        a.qF_next[o] = n;
-        a.dF_next[o] = resync ? narrow(n - (double)refc[c]) : a.dF[o] + g.h2f * s;
+        a.qF_next[o] = fma(h2, widen(s), a.qF[o]);
+        if (shadow) a.dF_next[o] = a.dF[o] + g.h2f * s;  // float shadow
       }
     }
   } else if (k >= g.nS_r) {
@@ -1062,24 +1059,16 @@ __device__ __forceinline__ bool pair_tile(const StageArgs& a, int k0, int i0, Pa
       }
     }
     const float2 h2f = sp2(g.h2f);
-    // the step's last stage with an even m writes q_{n+1} of the F rows into
-    // the state buffer: their float shadow is then resynchronised to it here
-    // (the step completion no longer visits F rows); otherwise the shadow
-    // follows the double state in float
-    const bool resync = resync_stage(a);
-    const float4 r01 = S.rc[0][p + 2], r23 = S.rc[1][p + 2];
-    const float refA[4] = {r01.x, r01.z, r23.x, r23.z}, refB[4] = {r01.y, r01.w, r23.y, r23.w};
+    // the float shadow follows the double state in float, except where the
+    // step completion rebuilds it anyway (the last stage, even m)
+    const bool shadow = !shadow_by_completion(a);
 #pragma unroll
     for (int c = 0; c < 4; c++) {
       const size_t oA = c * plane + offA, oB = c * plane + offB;
       const float2 s = add2(ra[c], R[c]);
-      const double nA = fma(g.h2, (double)s.x, qa[c]), nB = fma(g.h2, (double)s.y, qb[c]);
-      a.qF_next[oA] = nA;
-      a.qF_next[oB] = nB;
-      if (resync) {
-        a.dF_next[oA] = narrow(nA - (double)refA[c]);
-        a.dF_next[oB] = narrow(nB - (double)refB[c]);
-      } else {
+      a.qF_next[oA] = fma(g.h2, (double)s.x, qa[c]);
+      a.qF_next[oB] = fma(g.h2, (double)s.y, qb[c]);
+      if (shadow) {
         const float2 dn = fma2(h2f, s, dfo[c]);
         a.dF_next[oA] = dn.x;
         a.dF_next[oB] = dn.y;
