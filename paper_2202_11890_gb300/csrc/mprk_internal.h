@@ -170,10 +170,7 @@ TileShape default_tile_shape(const StageArgs& a);
 // only, may be null) overrides the tuned and the default tile shape.
 cudaError_t launch_stage(const StageArgs& a, int precision, int n_tiles, cudaStream_t stream,
                          const StageMaps* maps = nullptr, const TileShape* shape = nullptr);
-// The step completion of rows k_lo <= k < k_hi (z rows; k_hi < 0: to the
-// last row it completes).
-cudaError_t launch_finalize(const Geom& g, const Bufs& b, int m_odd, cudaStream_t stream, int k_lo = 0,
-                            int k_hi = -1);
+cudaError_t launch_finalize(const Geom& g, const Bufs& b, int m_odd, cudaStream_t stream);
 // 3-D (g.ny > 1): the y-face launch and the stage launch of one stage; a.gy
 // must point at a state-sized buffer.
 cudaError_t launch_stage3(const StageArgs& a, cudaStream_t stream);

@@ -391,7 +391,7 @@ cudaError_t launch_shadow(const Geom& g, const double* q, const float* rowc, flo
 // loads and stores; otherwise (mprk_step_static's unpadded rows) one cell
 // at a time. F rows after an even m already hold q_{n+1} in qA and only
 // refresh the float shadow (which the last stage leaves to this kernel).
-// Rows k_lo <= k < k_hi of those it completes (x-rows r = k ny + j).
+// Rows k_lo <= k < k_hi (x-rows r = k ny + j).
 __global__ void finalize_kernel(const Geom g, const Bufs b, int m_odd, int vec, int k_lo, int k_hi) {
   const bool mixed = b.dA != nullptr;
   const int c = blockIdx.z;
@@ -420,10 +420,9 @@ __global__ void finalize_kernel(const Geom g, const Bufs b, int m_odd, int vec, 
   }
 }
 
-cudaError_t launch_finalize(const Geom& g, const Bufs& b, int m_odd, cudaStream_t stream, int k_lo, int k_hi) {
-  const int end = (m_odd || b.dA) ? g.nz : g.n1_r;  // rows it completes
-  k_hi = k_hi < 0 ? end : std::min(k_hi, end);
-  k_lo = std::max(k_lo, 0);
+cudaError_t launch_finalize(const Geom& g, const Bufs& b, int m_odd, cudaStream_t stream) {
+  const int k_lo = 0;
+  const int k_hi = (m_odd || b.dA) ? g.nz : g.n1_r;  // rows it completes
   const int rows = k_hi - k_lo;
   if (rows <= 0) return cudaSuccess;
   auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };

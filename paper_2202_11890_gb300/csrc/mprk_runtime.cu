@@ -104,10 +104,6 @@ struct mprk_instance {
   double* io_in;
   double* io_out;
   cudaStream_t s_up, s_down;
-  // graph instances: the side branch of the step graph that completes the
-  // S rows no later stage reads, concurrently with those stages
-  cudaStream_t side;
-  cudaEvent_t ev_fork, ev_join;
   cudaEvent_t ev_up, ev_in_free, ev_out_ready, ev_out_free;
 };
 
@@ -196,46 +192,24 @@ void free_instance(mprk_instance* I) {
     if (I->stream_ordered) cudaFreeAsync(p, I->stream);
     else cudaFree(p);
   }
-  if (I->side) cudaStreamDestroy(I->side);
-  if (I->ev_fork) cudaEventDestroy(I->ev_fork);
-  if (I->ev_join) cudaEventDestroy(I->ev_join);
   if (I->own_stream && I->stream) cudaStreamDestroy(I->stream);
   delete I;
 }
 
-// The S rows the step completion may move as soon as the S band's last
-// stage (stage s of the step) is done: all but the top two, which the later
-// stages' B tiles still read as halo (their stencil reaches two rows). 0 when
-// there is no side branch or no later stage.
-int early_rows(const mprk_instance* I) {
-  const Geom& g = I->g;
-  return (I->side && g.nS_r >= 3 && g.m > 1) ? g.nS_r - 2 : 0;
-}
-
-// Enqueue the stage launches and the completion of one slow step. With a
-// side branch, the completion of the early S rows runs on it, concurrently
-// with the stages after the S band's last one; the rest follows the last
-// stage. after_launch(j), when given, runs after launch j on s (0-based,
-// stages first, the completion last): the profiling hook records events.
+// Enqueue the stage launches and the completion of one slow step.
+// after_launch(j), when given, runs after launch j on s (0-based, stages
+// first, the completion last): the profiling hook records events there.
 template <typename F>
 int enqueue_step_with(mprk_instance* I, cudaStream_t s, F after_launch) {
   const Geom& g = I->g;
-  const int k_early = early_rows(I);
   for (int st = 0; st < g.s * g.m; st++) {
     StageArgs a = stage_args(g, I->b, st);
     a.status = I->status_dev;
     a.gy = I->gy;
     CU(g.ny > 1 ? launch_stage3(a, s) : launch_stage(a, I->precision, stage_tiles(a), s, &I->maps));
     CU(after_launch(st));
-    if (k_early > 0 && st == g.s - 1) {
-      CU(cudaEventRecord(I->ev_fork, s));
-      CU(cudaStreamWaitEvent(I->side, I->ev_fork, 0));
-      CU(launch_finalize(g, I->b, g.m & 1, I->side, 0, k_early));
-      CU(cudaEventRecord(I->ev_join, I->side));
-    }
   }
-  if (k_early > 0) CU(cudaStreamWaitEvent(s, I->ev_join, 0));
-  CU(launch_finalize(g, I->b, g.m & 1, s, k_early, -1));
+  CU(launch_finalize(g, I->b, g.m & 1, s));
   CU(after_launch(g.s * g.m));
   return MPRK_OK;
 }
@@ -572,10 +546,6 @@ int mprk::create_instance(const mprk_config* cfg, const double* q0, int q0_locat
   I->cfg.dt = dt;
   geom_from_config(I->cfg, I->g.pitch, &I->g);
   if (!stream_ordered) {  // stream-ordered (server) instances advance only in batches
-    if (cudaStreamCreateWithFlags(&I->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&I->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&I->ev_join, cudaEventDisableTiming) != cudaSuccess)
-      return fin(fail(MPRK_ECUDA, "step graph: side stream or events"));
     if ((rc = capture(I, false, &I->exec))) return fin(rc);
     if (I->cfg.diag_every > 0 && (rc = capture(I, true, &I->exec_diag))) return fin(rc);
   }
@@ -789,8 +759,8 @@ int mprk_profile_step(mprk_instance* I, double* launch_ms, long long* launch_cel
   if (!I) return fail(MPRK_EINVAL, "instance is NULL");
   const Geom& g = I->g;
   const int n = g.s * g.m + 1;
-  // The step is captured exactly as the one mprk_step replays (side branch
-  // included), with an event record node before the first launch and after
+  // The step is captured exactly as the one mprk_step replays, with an
+  // event record node before the first launch and after
   // each launch on the instance stream, and runs as a graph: each duration
   // is then the kernel as the step graph runs it.
   cudaEvent_t ev[4 * 64 + 2];
