@@ -81,8 +81,8 @@ TRAFFIC = {
     },
     "stage_kernel_mixed": {
         "files": ("stage_tile_mixed.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "bb6a132d30b142f26d1ff8b5160a136755b81dcb67d958badb9a3d115baf66b0",
-        "bytes_per_step": 5197622528,
+        "sha256": "580385d0fb3a8644572365eaa5b5d8beb447c69e085e083dfaa666eb07d3b1fa",
+        "bytes_per_step": 5149946112,
     },
 }
 
