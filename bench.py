@@ -76,8 +76,8 @@ CSRC = os.path.join(ROOT, "paper_2202_11890_gb300", "csrc")
 TRAFFIC = {
     "stage_kernel": {
         "files": ("stage_tile.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "d230c66b3ee168acc3b58409c0177deb1ce215f71a6b1023c49cb800aae5e17f",
-        "bytes_per_step": 1180983296,
+        "sha256": "d9b96663336d9f5c70724c9fa33e47e1393d41992c18a78ca64e4627a4adc318",
+        "bytes_per_step": 1172199936,
     },
     "stage_kernel_mixed": {
         "files": ("stage_tile_mixed.cuh", "mprk_internal.h", "mprk_kernels.cu"),

@@ -311,6 +311,15 @@ int mprk_probe_fp64(long long iters, double* gflops, double* dfma_per_clk_per_sm
 int mprk_selftest_convert(const double* in_dev, int n, float* narrow_dev, float* narrow_hw_dev,
                           double* widen_dev, double* widen_hw_dev);
 
+/* Test hook for the FP64 tiles' 1/x, 1/sqrt(x) and sqrt(x): the hardware's
+ * approximate reciprocal and reciprocal square root refined by one
+ * third-order Householder step, within about one unit in the last place of
+ * the exact values (not correctly rounded). For n device doubles in_dev[j]
+ * it writes those three results to recip_dev, rsqrt_dev and sqrt_dev (device
+ * buffers of n doubles each). Runs on the default stream and synchronises.
+ * Errors: MPRK_EINVAL (null buffer, n < 0), MPRK_ECUDA. */
+int mprk_selftest_recip(const double* in_dev, int n, double* recip_dev, double* rsqrt_dev, double* sqrt_dev);
+
 /* ---- allocation-free stepping ------------------------------------------ */
 /* Largest scratch mprk_step_static may use: 32 MiB. In FP64 a grid needs
  * 8 bytes x 4 components x (2 nx nz + nx (nz_S + nz_B)), each part rounded

@@ -15,12 +15,16 @@
 // single CTA's duration would not do.
 // The result is stored only where it cannot be predicted, so the compiler
 // keeps every FMA.
+//
+// It also holds the test hook of the FP64 tiles' reciprocal, reciprocal
+// square root and square root (fp64_recip.cuh).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <string>
 #include <vector>
 
+#include "fp64_recip.cuh"
 #include "mprk.h"
 #include "mprk_internal.h"
 
@@ -62,6 +66,15 @@ __global__ void __launch_bounds__(PROBE_THREADS) fp64_fma_probe(int iters, doubl
     nanos[2 * blockIdx.x] = (long long)n0;  // the global timer is one clock for all SMs
     nanos[2 * blockIdx.x + 1] = (long long)n1;
   }
+}
+
+__global__ void recip_check_kernel(const double* x, int n, double* rcp, double* rsq, double* sq) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double v = x[j];
+  rcp[j] = mprk::recip_f64(v);
+  rsq[j] = mprk::rsqrt_f64(v);
+  sq[j] = mprk::sqrt_f64(v);
 }
 
 }  // namespace
@@ -154,5 +167,21 @@ extern "C" int mprk_probe_fp64(long long iters, double* gflops, double* dfma_per
   *sm_mhz = best.mhz;
   *sms = nsm;
   *max_mhz = khz * 1e-3;
+  return MPRK_OK;
+}
+
+extern "C" int mprk_selftest_recip(const double* in_dev, int n, double* recip_dev, double* rsqrt_dev,
+                                   double* sqrt_dev) {
+  if (!in_dev || !recip_dev || !rsqrt_dev || !sqrt_dev || n < 0) {
+    mprk::set_last_error("mprk_selftest_recip: bad argument");
+    return MPRK_EINVAL;
+  }
+  if (n > 0) recip_check_kernel<<<(n + 255) / 256, 256>>>(in_dev, n, recip_dev, rsqrt_dev, sqrt_dev);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  if (e != cudaSuccess) {
+    mprk::set_last_error(std::string("mprk_selftest_recip: ") + cudaGetErrorString(e));
+    return MPRK_ECUDA;
+  }
   return MPRK_OK;
 }

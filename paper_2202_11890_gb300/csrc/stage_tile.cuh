@@ -23,6 +23,7 @@
 // FP32-flux mode); Store is the type of the saved stage-one right-hand side.
 #pragma once
 
+#include "fp64_recip.cuh"
 #include "mprk_internal.h"
 
 namespace mprk {
@@ -36,7 +37,7 @@ enum {
   FC_B,   // mu sc / (6 d_t): sigma_nn from the two cells' tangential differences of u_t
   FC_C,   // mu sc / d_n: sigma_nt from the normal difference of u_t
   FC_D,   // mu sc / (4 d_t): sigma_nt from the two cells' tangential differences of u_n
-  FC_K,   // kappa sc / d_n: heat flux from the normal difference of T
+  FC_K,   // kappa gamma (gamma - 1) sc / d_n: heat flux from the normal difference of e = T / (gamma (gamma - 1))
   FC_SC,  // sc
   FC_N
 };
@@ -44,7 +45,7 @@ enum {
 template <typename Real, int TZR = TZ>
 struct TileSmem {
   Real q[4][TZR + 4][TX + 4];   // stage state, rows k0-2.., cols i0-2..
-  Real v[3][TZR + 2][TX + 2];   // u, w, T, rows k0-1.., cols i0-1..
+  Real v[3][TZR + 2][TX + 2];   // u, w, e = T / (gamma (gamma - 1)), rows k0-1.., cols i0-1..
   Real hx[4][TZR][TX + 2];      // central x differences of q, cols i0-1..
   Real hz[4][TZR + 2][TX];      // central z differences of q, rows k0-1..
   Real tz[2][TZR][TX + 2];      // central z differences of u, w (tangential at x faces)
@@ -54,25 +55,42 @@ struct TileSmem {
   Real fg[4][TX];              // interface flux / dz1 seen from fluid 1 (below)
   double gam[4][TX + 2];       // sigma_xz, Pi_z, u_w, T_w per column i0-1..
   Real fc[2][2][FC_N];         // face constants per direction (x, z) and fluid (1, 2)
-  Real gg;                     // gamma (gamma - 1)
 };
 
 template <typename Real>
 __device__ __forceinline__ Real rsq(Real x);
 template <>
-__device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
+__device__ __forceinline__ double rsq<double>(double x) { return rsqrt_f64(x); }
 template <>
 __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
 
+template <typename Real>
+__device__ __forceinline__ Real sqr(Real x);
+template <>
+__device__ __forceinline__ double sqr<double>(double x) { return sqrt_f64(x); }
+template <>
+__device__ __forceinline__ float sqr<float>(float x) { return x * rsqrtf(x); }
+
+template <typename Real>
+__device__ __forceinline__ Real rcp(Real x);
+template <>
+__device__ __forceinline__ double rcp<double>(double x) { return recip_f64(x); }
+template <>
+__device__ __forceinline__ float rcp<float>(float x) { return 1.0f / x; }
+
 // Lax–Friedrichs flux in the face frame. A state is (rho, m_n, m_t, rho E):
 // m_n is the momentum along the face normal, m_t along the face. Output is
-// hs = sc/2 times twice the flux, i.e. sc (F_rho, F_mn, F_mt, F_E). lambda is
-// the largest |u_n| + a over the left, right and Roe-averaged states
-// (Sec. 2.1); the Roe weights sqrt(rho)/(sqrt(rho_L) + sqrt(rho_R)) times
-// the enthalpy H = (rho E + p)/rho are formed as (rho E + p)/sqrt(rho).
+// sc (F_rho, F_mn, F_mt, F_E) - sub, where hs = sc/2 and each component is
+// hs (f(q_L) + f(q_R) + lambda (q_L - q_R)) - sub: sub carries the viscous
+// or interface part of the face flux, taken off in the last fused
+// multiply-add. lambda is the largest |u_n| + a over the left, right and
+// Roe-averaged states (Sec. 2.1); the Roe weights sqrt(rho)/(sqrt(rho_L) +
+// sqrt(rho_R)) times the enthalpy H = (rho E + p)/rho are formed as
+// (rho E + p)/sqrt(rho).
 template <typename Real>
 __device__ __forceinline__ void lf_face(Real lr, Real lmn, Real lmt, Real lE, Real rr, Real rmn,
-                                        Real rmt, Real rE, Real gamma, Real gm1, Real hs, Real out[4]) {
+                                        Real rmt, Real rE, Real gamma, Real gm1, Real hs, const Real sub[4],
+                                        Real out[4]) {
   const Real half = Real(0.5);
   const Real rsL = rsq(lr), rsR = rsq(rr);
   const Real invL = rsL * rsL, invR = rsR * rsR;
@@ -81,21 +99,18 @@ __device__ __forceinline__ void lf_face(Real lr, Real lmn, Real lmt, Real lE, Re
   const Real unR = rmn * invR, utR = rmt * invR;
   const Real pL = gm1 * (lE - half * (lmn * unL + lmt * utL));
   const Real pR = gm1 * (rE - half * (rmn * unR + rmt * utR));
-  const Real XL = gamma * pL * invL, XR = gamma * pR * invR;
-  const Real cL = XL * rsq(XL), cR = XR * rsq(XR);
+  const Real cL = sqr(gamma * pL * invL), cR = sqr(gamma * pR * invR);
   const Real eL = lE + pL, eR = rE + pR;
-  const Real den = Real(1) / (sL + sR);
+  const Real den = rcp(sL + sR);
   const Real un = (sL * unL + sR * unR) * den;
   const Real ut = (sL * utL + sR * utR) * den;
   const Real H = (eL * rsL + eR * rsR) * den;
-  const Real X = gm1 * (H - half * (un * un + ut * ut));
-  const Real c = X * rsq(X);
+  const Real c = sqr(gm1 * (H - half * (un * un + ut * ut)));
   const Real lam = fmax(fmax(fabs(unL) + cL, fabs(unR) + cR), fabs(un) + c);
-  const Real hl = hs * lam;
-  out[0] = hs * (lmn + rmn) + hl * (lr - rr);
-  out[1] = hs * ((lmn * unL + pL) + (rmn * unR + pR)) + hl * (lmn - rmn);
-  out[2] = hs * (lmt * unL + rmt * unR) + hl * (lmt - rmt);
-  out[3] = hs * (unL * eL + unR * eR) + hl * (lE - rE);
+  out[0] = hs * fma(lam, lr - rr, lmn + rmn) - sub[0];
+  out[1] = fma(hs, fma(lam, lmn - rmn, (lmn * unL + pL) + (rmn * unR + pR)), -sub[1]);
+  out[2] = fma(hs, fma(lam, lmt - rmt, lmt * unL + rmt * unR), -sub[2]);
+  out[3] = fma(hs, fma(lam, lE - rE, unL * eL + unR * eR), -sub[3]);
 }
 
 // Viscous flux in the face frame from the common values of App. B: face
@@ -123,7 +138,9 @@ __device__ __forceinline__ void visc_face(Real unL, Real utL, Real TL, Real gnL,
 
 // visc_face with the spacings, viscosity and divergence factor folded into
 // the face constants fc (FC_*): the tangential inputs gn, gt are the cells'
-// unscaled central differences of u_n, u_t along the face. Output
+// unscaled central differences of u_n, u_t along the face, and TL, TR the
+// cells' temperatures in the units of fc[FC_K] (the tile passes e = T /
+// (gamma (gamma - 1)) and folds that factor into FC_K). Output
 // sc (0, sigma_nn, sigma_nt, u.sigma_n + kappa dT/dn); the same sums as
 // visc_face, regrouped.
 template <typename Real>
@@ -231,9 +248,8 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
     fc[FC_B] = (Real)(mu * inv_dt * sc / 6.0);
     fc[FC_C] = (Real)(mu * inv_dn * sc);
     fc[FC_D] = (Real)(0.25 * mu * inv_dt * sc);
-    fc[FC_K] = (Real)(kap * inv_dn * sc);
+    fc[FC_K] = (Real)(kap * inv_dn * sc * (g.gamma * g.gm1));  // times the factor T / e of S.v[2]
     fc[FC_SC] = (Real)sc;
-    if (tid == 0) S.gg = (Real)(g.gamma * g.gm1);
   }
   for (int e = tid; e < 4 * (TZR + 4) * (TX + 4); e += NT) {
     const int c = e / ((TZR + 4) * (TX + 4));
@@ -267,19 +283,21 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
   __syncthreads();
 
   // ---- 2. u, w, T on the one-cell ring; interface state -----------------
-  const Real gamma = (Real)g.gamma, gm1 = (Real)g.gm1, gg = S.gg;
+  const Real gamma = (Real)g.gamma, gm1 = (Real)g.gm1;
   for (int e = tid; e < (TZR + 2) * (TX + 2); e += NT) {
     const int rr = e / (TX + 2), cc = e - rr * (TX + 2);
     const int k = k0 - 1 + rr;
     if (k < 0 || k >= nz) continue;
     const Real r = S.q[0][rr + 1][cc + 1], mu_ = S.q[1][rr + 1][cc + 1];
     const Real mw = S.q[2][rr + 1][cc + 1], E = S.q[3][rr + 1][cc + 1];
-    const Real inv = Real(1) / r;
+    const Real inv = rcp(r);
     const Real u = mu_ * inv, w = mw * inv;
     S.v[0][rr][cc] = u;
     // the mirror state's u is already flipped; a no-slip wall flips w too
     S.v[1][rr][cc] = (x_ghost(i0 - 1 + cc, nx, g.xwall) && g.wall == 0) ? -w : w;
-    S.v[2][rr][cc] = gg * (E - Real(0.5) * (mu_ * u + mw * w)) * inv;  // T = gamma p / rho
+    // internal energy per mass e = T / (gamma (gamma - 1)) with T = gamma p / rho;
+    // the heat-flux constant carries the factor
+    S.v[2][rr][cc] = (E - Real(0.5) * (mu_ * u + mw * w)) * inv;
   }
   if (has_gamma && tid < TX + 2) {
     // Interface state of column i0-1+tid in double precision from the two
@@ -399,50 +417,52 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
         const Real* fc = S.fc[1][k >= n1];
         Real r, mn, mt, E;
         load_side(rq, rh, r, mn, mt, E, below ? -quarter : quarter);
-        Real FI[4], FV[4];
-        if (below) lf_face(r, -mn, mt, E, r, mn, mt, E, gamma, gm1, fc[FC_HS], FI);
-        else lf_face(r, mn, mt, E, r, -mn, mt, E, gamma, gm1, fc[FC_HS], FI);
+        Real F[4], FV[4];
         const Real un = S.v[1][rv][cc + 1], ut = S.v[0][rv][cc + 1], T = S.v[2][rv][cc + 1];
         const Real gn = S.tx[1][rv][cc], gt = S.tx[0][rv][cc];
         const Real utg = g.wall ? ut : -ut, gtg = g.wall ? gt : -gt;
         if (below) visc_face_fc(-un, utg, T, -gn, gtg, un, ut, T, gn, gt, fc, FV);
         else visc_face_fc(un, ut, T, gn, gt, -un, utg, T, -gn, gtg, fc, FV);
-        S.fz[0][f][cc] = FI[0] - FV[0];
-        S.fz[1][f][cc] = FI[2] - FV[2];
-        S.fz[2][f][cc] = FI[1] - FV[1];
-        S.fz[3][f][cc] = FI[3] - FV[3];
+        if (below) lf_face(r, -mn, mt, E, r, mn, mt, E, gamma, gm1, fc[FC_HS], FV, F);
+        else lf_face(r, mn, mt, E, r, -mn, mt, E, gamma, gm1, fc[FC_HS], FV, F);
+        S.fz[0][f][cc] = F[0];
+        S.fz[1][f][cc] = F[2];
+        S.fz[2][f][cc] = F[1];
+        S.fz[3][f][cc] = F[3];
       } else if (ku == n1) {
         // the interface: a rigid lid seen from each fluid (inviscid), the bulk
         // fluxes of App. B (viscous, shared by both fluids)
         const double sig = S.gam[0][cc + 1], Pi = S.gam[1][cc + 1], uw = S.gam[2][cc + 1];
         const Real Vt = (Real)sig, VE = (Real)(uw * sig - Pi);
         const Real *fc2 = S.fc[1][1], *fc1 = S.fc[1][0];
-        Real r, mn, mt, E, FI[4];
+        Real r, mn, mt, E, F[4];
         load_side(f + 2, f + 1, r, mn, mt, E, -quarter);  // fluid 2, above
-        lf_face(r, -mn, mt, E, r, mn, mt, E, gamma, gm1, fc2[FC_HS], FI);
-        S.fz[0][f][cc] = FI[0];
-        S.fz[1][f][cc] = FI[2] - Vt * fc2[FC_SC];
-        S.fz[2][f][cc] = FI[1];
-        S.fz[3][f][cc] = FI[3] - VE * fc2[FC_SC];
+        const Real sub2[4] = {Real(0), Real(0), Vt * fc2[FC_SC], VE * fc2[FC_SC]};
+        lf_face(r, -mn, mt, E, r, mn, mt, E, gamma, gm1, fc2[FC_HS], sub2, F);
+        S.fz[0][f][cc] = F[0];
+        S.fz[1][f][cc] = F[2];
+        S.fz[2][f][cc] = F[1];
+        S.fz[3][f][cc] = F[3];
         load_side(f + 1, f, r, mn, mt, E, quarter);  // fluid 1, below
-        lf_face(r, mn, mt, E, r, -mn, mt, E, gamma, gm1, fc1[FC_HS], FI);
-        S.fg[0][cc] = FI[0];
-        S.fg[1][cc] = FI[2] - Vt * fc1[FC_SC];
-        S.fg[2][cc] = FI[1];
-        S.fg[3][cc] = FI[3] - VE * fc1[FC_SC];
+        const Real sub1[4] = {Real(0), Real(0), Vt * fc1[FC_SC], VE * fc1[FC_SC]};
+        lf_face(r, mn, mt, E, r, -mn, mt, E, gamma, gm1, fc1[FC_HS], sub1, F);
+        S.fg[0][cc] = F[0];
+        S.fg[1][cc] = F[2];
+        S.fg[2][cc] = F[1];
+        S.fg[3][cc] = F[3];
       } else {
         const Real* fc = S.fc[1][kd >= n1];
-        Real lr, lmn, lmt, lE, rr_, rmn, rmt, rE, FI[4], FV[4];
+        Real lr, lmn, lmt, lE, rr_, rmn, rmt, rE, F[4], FV[4];
         load_side(f + 1, f, lr, lmn, lmt, lE, quarter);
         load_side(f + 2, f + 1, rr_, rmn, rmt, rE, -quarter);
-        lf_face(lr, lmn, lmt, lE, rr_, rmn, rmt, rE, gamma, gm1, fc[FC_HS], FI);
         visc_face_fc(S.v[1][f][cc + 1], S.v[0][f][cc + 1], S.v[2][f][cc + 1], S.tx[1][f][cc], S.tx[0][f][cc],
                      S.v[1][f + 1][cc + 1], S.v[0][f + 1][cc + 1], S.v[2][f + 1][cc + 1], S.tx[1][f + 1][cc],
                      S.tx[0][f + 1][cc], fc, FV);
-        S.fz[0][f][cc] = FI[0] - FV[0];
-        S.fz[1][f][cc] = FI[2] - FV[2];
-        S.fz[2][f][cc] = FI[1] - FV[1];
-        S.fz[3][f][cc] = FI[3] - FV[3];
+        lf_face(lr, lmn, lmt, lE, rr_, rmn, rmt, rE, gamma, gm1, fc[FC_HS], FV, F);
+        S.fz[0][f][cc] = F[0];
+        S.fz[1][f][cc] = F[2];
+        S.fz[2][f][cc] = F[1];
+        S.fz[3][f][cc] = F[3];
       }
     } else {
       const int x = e - NZF;
@@ -461,15 +481,15 @@ __device__ __noinline__ void stage_tile(const StageArgs& __restrict__ a, int til
       const Real rmt = S.q[2][rr + 2][f + 2] - quarter * S.hx[2][rr][f + 1];
       const Real rE = S.q[3][rr + 2][f + 2] - quarter * S.hx[3][rr][f + 1];
       const Real* fc = S.fc[0][k >= n1];
-      Real FI[4], FV[4];
-      lf_face(lr, lmn, lmt, lE, rr_, rmn, rmt, rE, gamma, gm1, fc[FC_HS], FI);
+      Real F[4], FV[4];
       visc_face_fc(S.v[0][rr + 1][f], S.v[1][rr + 1][f], S.v[2][rr + 1][f], S.tz[0][rr][f], S.tz[1][rr][f],
                    S.v[0][rr + 1][f + 1], S.v[1][rr + 1][f + 1], S.v[2][rr + 1][f + 1], S.tz[0][rr][f + 1],
                    S.tz[1][rr][f + 1], fc, FV);
-      S.fx[0][rr][f] = FI[0] - FV[0];
-      S.fx[1][rr][f] = FI[1] - FV[1];
-      S.fx[2][rr][f] = FI[2] - FV[2];
-      S.fx[3][rr][f] = FI[3] - FV[3];
+      lf_face(lr, lmn, lmt, lE, rr_, rmn, rmt, rE, gamma, gm1, fc[FC_HS], FV, F);
+      S.fx[0][rr][f] = F[0];
+      S.fx[1][rr][f] = F[1];
+      S.fx[2][rr][f] = F[2];
+      S.fx[3][rr][f] = F[3];
     }
   }
   __syncthreads();

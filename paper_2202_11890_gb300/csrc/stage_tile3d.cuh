@@ -20,6 +20,7 @@
 // face flux comes out multiplied by 1/d of its normal direction.
 #pragma once
 
+#include "fp64_recip.cuh"
 #include "mprk_internal.h"
 
 namespace mprk {
@@ -64,7 +65,7 @@ __device__ __forceinline__ void face_consts3(double inv_dn, double inv_dt1, doub
 // (rho E + p)/rho are formed as (rho E + p)/sqrt(rho).
 __device__ __forceinline__ void lf_face5(const double l[5], const double r[5], double gamma, double gm1, double hs,
                                          double out[5]) {
-  const double rsL = rsqrt(l[0]), rsR = rsqrt(r[0]);
+  const double rsL = rsqrt_f64(l[0]), rsR = rsqrt_f64(r[0]);
   const double invL = rsL * rsL, invR = rsR * rsR;
   const double sL = l[0] * rsL, sR = r[0] * rsR;  // sqrt(rho)
   const double unL = l[1] * invL, t1L = l[2] * invL, t2L = l[3] * invL;
@@ -72,15 +73,15 @@ __device__ __forceinline__ void lf_face5(const double l[5], const double r[5], d
   const double pL = gm1 * (l[4] - 0.5 * (l[1] * unL + l[2] * t1L + l[3] * t2L));
   const double pR = gm1 * (r[4] - 0.5 * (r[1] * unR + r[2] * t1R + r[3] * t2R));
   const double XL = gamma * pL * invL, XR = gamma * pR * invR;
-  const double cL = XL * rsqrt(XL), cR = XR * rsqrt(XR);
+  const double cL = XL * rsqrt_f64(XL), cR = XR * rsqrt_f64(XR);
   const double eL = l[4] + pL, eR = r[4] + pR;
-  const double den = 1.0 / (sL + sR);
+  const double den = recip_f64(sL + sR);
   const double un = (sL * unL + sR * unR) * den;
   const double t1 = (sL * t1L + sR * t1R) * den;
   const double t2 = (sL * t2L + sR * t2R) * den;
   const double H = (eL * rsL + eR * rsR) * den;
   const double X = gm1 * (H - 0.5 * (un * un + t1 * t1 + t2 * t2));
-  const double c = X * rsqrt(X);
+  const double c = X * rsqrt_f64(X);
   const double lam = fmax(fmax(fabs(unL) + cL, fabs(unR) + cR), fabs(un) + c);
   const double hl = hs * lam;
   out[0] = hs * (l[1] + r[1]) + hl * (l[0] - r[0]);
@@ -156,7 +157,7 @@ __device__ __forceinline__ double stage_val3(const StageArgs& a, const Geo3& G, 
 
 // (u, v, w, T) from a conserved state; gg = gamma (gamma - 1), T = gamma p / rho
 __device__ __forceinline__ void prim5(const double q[5], double gg, double v[4]) {
-  const double inv = 1.0 / q[0];
+  const double inv = recip_f64(q[0]);
   v[0] = q[1] * inv;
   v[1] = q[2] * inv;
   v[2] = q[3] * inv;
@@ -394,13 +395,13 @@ __device__ __forceinline__ void stage_tile3(const StageArgs& a, int k0, int i0, 
     const int i = wrap3(i0 - 1 + cc, nx);
     double up[3], dn[3];
     {
-      const double inv = 1.0 / stage_val3(a, G, 0, k, jp, i);
+      const double inv = recip_f64(stage_val3(a, G, 0, k, jp, i));
       up[0] = stage_val3(a, G, 1, k, jp, i) * inv;
       up[1] = stage_val3(a, G, 2, k, jp, i) * inv;
       up[2] = stage_val3(a, G, 3, k, jp, i) * inv;
     }
     {
-      const double inv = 1.0 / stage_val3(a, G, 0, k, jm, i);
+      const double inv = recip_f64(stage_val3(a, G, 0, k, jm, i));
       dn[0] = stage_val3(a, G, 1, k, jm, i) * inv;
       dn[1] = stage_val3(a, G, 2, k, jm, i) * inv;
       dn[2] = stage_val3(a, G, 3, k, jm, i) * inv;

@@ -124,6 +124,7 @@ def lib():
         "mprk_step_batch": (ip, [C.POINTER(vp), ip, ip]),
         "mprk_batch_test_withhold": (ip, [C.POINTER(vp), ip, ip, ip, C.c_longlong]),
         "mprk_selftest_convert": (ip, [vp, ip, vp, vp, vp, vp]),
+        "mprk_selftest_recip": (ip, [vp, ip, vp, vp, vp]),
         "mprk_batch_tune": (ip, [C.POINTER(vp), ip, ip, dp]),
         "mprk_tune_lookup": (ip, [ip, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "mprk_tile_tune": (ip, [C.POINTER(vp), ip, ip, C.POINTER(C.c_int)]),
@@ -295,6 +296,13 @@ def mprk_selftest_convert(x_dev, narrow, narrow_hw, widen, widen_hw) -> None:
     _check(lib().mprk_selftest_convert(C.c_void_p(x_dev.data_ptr()), int(x_dev.numel()),
                                        C.c_void_p(narrow.data_ptr()), C.c_void_p(narrow_hw.data_ptr()),
                                        C.c_void_p(widen.data_ptr()), C.c_void_p(widen_hw.data_ptr())))
+
+
+def mprk_selftest_recip(x_dev, recip, rsqrt, sqrt) -> None:
+    """The FP64 tiles' 1/x, 1/sqrt(x), sqrt(x) of a device tensor of doubles."""
+    _check(lib().mprk_selftest_recip(C.c_void_p(x_dev.data_ptr()), int(x_dev.numel()),
+                                     C.c_void_p(recip.data_ptr()), C.c_void_p(rsqrt.data_ptr()),
+                                     C.c_void_p(sqrt.data_ptr())))
 
 
 def mprk_batch_tune(handles, reps: int = 3) -> dict:
