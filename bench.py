@@ -603,11 +603,17 @@ def measure_served(M, rate: float, n_warm: int, n_meas: int, budget_gb: float, s
     results = {}
     t0 = time.perf_counter()
     nxt = 0
+    # the server's count of cell-stages done, sampled when the first and the
+    # last measured request are submitted: the work rate over the arrival
+    # window of the measured requests, without the drain after it
+    window = {}
     with sampler:
         while len(done) < len(reqs):
             now = time.perf_counter() - t0
             while nxt < len(reqs) and arrivals[nxt] <= now:
                 cfg, q, n, _, _ = reqs[nxt]
+                if nxt in (n_warm, len(reqs) - 1):
+                    window[nxt] = (time.perf_counter(), M.mprk_server_stats(srv)[1])
                 tickets[M.mprk_submit(srv, cfg, q, n)] = nxt
                 nxt += 1
             for t, j in list(tickets.items()):
@@ -632,6 +638,8 @@ def measure_served(M, rate: float, n_warm: int, n_meas: int, budget_gb: float, s
     work = sum(reqs[j][3] for j in range(n_warm, len(reqs)))
     value = work / (t_last - t_first)
     offered = sum(r[3] for r in reqs[n_warm:]) / (arrivals[-1] - arrivals[n_warm])
+    (w0, c0), (w1, c1) = window[n_warm], window[len(reqs) - 1]
+    window_rate = (c1 - c0) / max(w1 - w0, 1e-9)
     peaks, src = measured_peaks()
     gbs = sum(reqs[j][4] for j in range(n_warm, len(reqs))) / (t_last - t_first) / 1e9
     rec = {"value": value, "unit": "cell-stages/s", "requests": n_meas, "warmup_requests": n_warm,
@@ -641,6 +649,14 @@ def measure_served(M, rate: float, n_warm: int, n_meas: int, budget_gb: float, s
            "served": {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                       "mean_latency_s": float(lat.mean()), "errors": errors,
                       "offered_cell_stages_per_s": offered, "achieved_over_offered": value / offered,
+                      "arrival_window": {
+                          "cell_stages_per_s": window_rate, "over_offered": window_rate / offered,
+                          "seconds": w1 - w0,
+                          "how": "cell-stages of the server's batched steps (all resident requests; "
+                                 "counted as each step is enqueued, at most two steps ahead of the GPU) "
+                                 "between the first and the last measured submission, over that time; "
+                                 "value above divides the measured requests' work by first submit to "
+                                 "last finish, which includes the drain of the longest requests"},
                       "batched_steps": int(sstats[2]), "wall_s": wall,
                       "loop": {**sprof, "gpu_busy_over_step_span": sprof["gpu_busy_s"] / max(sprof["step_span_s"], 1e-9)}},
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",

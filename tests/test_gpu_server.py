@@ -89,6 +89,44 @@ def test_served_results_equal_solo_results(precision):
         M.mprk_server_destroy(srv)
 
 
+@pytest.mark.parametrize("precision", [1, 0])
+def test_served_requests_at_full_size_equal_solo_results(precision):
+    """Requests drawn like the served workload (sides log-uniform in
+    [32, 1024], m in {2, 4, 8}, buffer 4-16 rows) plus a 1024 x 1024 one, a
+    few slow steps each: large instances run many waves of tiles, and in
+    FP32 flux their interior tiles take the packed pair path. Each result
+    equals the solve alone: within 1e-5 in FP32 flux, bitwise in FP64."""
+    from paper_2202_11890_gb300 import mprk as M
+    _, wls = W.served_stream(7, seed=41 + precision)
+    grids = [(wl.grid, wl.m) for wl in wls] + [(W.Grid(1024, 506, 12, 506), 8)]
+    rng = np.random.default_rng(43)
+    reqs = []
+    for j, (g, m) in enumerate(grids):
+        q = W.gaussian_bumps(g, 300 + j, sigma_cells=4.0)
+        cfg, P, dt = pair(g, m, q0=q, precision=precision)
+        reqs.append((cfg, q, int(rng.integers(2, 5))))
+    assert max(cfg.nx * (cfg.nz_S + cfg.nz_B + cfg.nz_F) for cfg, _, _ in reqs) >= 1 << 20
+    refs = [alone(cfg, q, n) for cfg, q, n in reqs]
+    srv = M.mprk_server_create(hbm_budget_bytes=8 << 30, max_slots=8)
+    try:
+        tickets, order = {}, {}
+        for j, (cfg, q, n) in enumerate(reqs):
+            t = M.mprk_submit(srv, cfg, q, n)
+            tickets[t] = q.shape
+            order[t] = j
+        outs = drain(M, srv, tickets, timeout=300.0)
+        for t, (buf, err, stats) in outs.items():
+            j = order[t]
+            assert err == 0
+            assert stats["steps_done"] == reqs[j][2]
+            if precision == 0:
+                assert np.array_equal(buf, refs[j]), (j, rel_err(buf, refs[j]))
+            else:
+                assert np.all(rel_err(buf, refs[j]) < 1e-5), (j, rel_err(buf, refs[j]))
+    finally:
+        M.mprk_server_destroy(srv)
+
+
 def test_served_general_base_requests_equal_solo_results():
     """FP64 requests with the Heun, RK3 and RK4 bases mixed in one server:
     each result bitwise equal to the solve alone (every FP64 launch runs the
