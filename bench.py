@@ -81,8 +81,8 @@ TRAFFIC = {
     },
     "stage_kernel_mixed": {
         "files": ("stage_tile_mixed.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "580385d0fb3a8644572365eaa5b5d8beb447c69e085e083dfaa666eb07d3b1fa",
-        "bytes_per_step": 5149946112,
+        "sha256": "a1d3563a96699f5f65587509daaa965c18fdf9cad53c19730e0767b2c544457a",
+        "bytes_per_step": 5147348736,
     },
 }
 

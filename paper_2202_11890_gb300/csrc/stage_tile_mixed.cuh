@@ -14,8 +14,8 @@
 //
 // A tile is TX x MTZ (32 x 16) cells and takes one of two paths:
 //
-// * Interior tiles (no wall, no interface and no change of stage region
-//   within two rows) take the pair path. Each thread carries the cells of
+// * Interior tiles (no wall, no interface and no F-row bound within two
+//   rows) take the pair path. Each thread carries the cells of
 //   rows k and k + TZ of one column. Shared memory interleaves the two
 //   cells' values, so every float operation of the flux is one packed
 //   f32x2 instruction (sm_100 and later) for both. The tile has no branch on
@@ -778,8 +778,7 @@ __device__ __forceinline__ void pair_z_face(PairSmem& S, const PairConst& C, int
 // An interior tile needs none of the ghost rules: rows k0-2 .. k0+MTZ+1 lie
 // inside the grid and inside one fluid, and with x walls its halo columns
 // i0-2 .. i0+TX+1 lie between them. For a stage (not the right-hand-side
-// hook) they also lie on one side of the F-row bound, and the tile's MTZ rows
-// share one stage region.
+// hook) they also lie on one side of the F-row bound.
 __device__ __forceinline__ bool pair_interior(const StageArgs& a, int k0, int i0) {
   const Geom& g = a.g;
   const int hi = a.rhs_only ? a.rhs_hi : g.nz;
@@ -787,7 +786,10 @@ __device__ __forceinline__ bool pair_interior(const StageArgs& a, int k0, int i0
   if (lo_h < 0 || hi_h > g.nz || k0 + MTZ > hi || !(g.n1 <= lo_h || g.n1 >= hi_h)) return false;
   if (g.xwall && (i0 < 2 || i0 + TX + 2 > g.nx)) return false;  // halo columns inside the walls
   if (a.rhs_only) return true;
-  return (g.n1_r <= lo_h || g.n1_r >= hi_h) && (g.nS_r <= k0 || g.nS_r >= k0 + MTZ);
+  // S and B rows may share a tile (the combination picks per cell, and both
+  // take their stage values from q_n with dt); the F rows' state and step
+  // differ, so no F row lies within the halo of a tile with S or B rows
+  return g.n1_r <= lo_h || g.n1_r >= hi_h;
 }
 
 // Stage combination of one cell outside the F rows (B and S rows), the

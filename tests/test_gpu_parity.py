@@ -361,6 +361,27 @@ def test_fp32_flux_pair_path_in_every_band(m, wall):
     assert np.all(err < 1e-5), err
 
 
+def test_fp32_flux_pair_path_across_the_slow_buffer_bound():
+    """nS = 40: the tile of rows 32-47 holds S rows (32-39) and B rows
+    (40-47) and takes the pair path at the two full-row stages, each cell
+    combined by its own region. 20 slow steps within 1e-5 of the FP64
+    oracle, and the batch kernel (same tile paths) within float rounding
+    (1e-6) of the single-instance one."""
+    mp = M()
+    g = W.Grid(96, 40, 24, 40)
+    q0 = W.gaussian_bumps(g, 61, sigma_cells=3.0)
+    cfg, P, dt = pair(g, 4, q0=q0, precision=mp.MPRK_FP32FLUX)
+    q_or, _ = O.mprk_step(P, q0, 20)
+    with mp.Instance(cfg, q0) as a, mp.Instance(cfg, q0) as b:
+        a.step(20)
+        mp.mprk_step_batch([b.h], 20)
+        qa, qb = a.state(), b.state()
+    err = rel_err(qa, q_or)
+    print("fp32flux S/B-bound tile error per component:", err)
+    assert np.all(err < 1e-5), err
+    assert np.all(rel_err(qb, qa) < 1e-6)
+
+
 def test_both_fp64_launch_forms_in_one_step():
     """512 x 96 cells with a thin buffer and fast band: the two full-row
     stages launch 192 tiles (one thread per cell), the later B+F stages 32
