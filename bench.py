@@ -578,7 +578,7 @@ def run_batched(args):
 
 
 def measure_served(M, rate: float, n_warm: int, n_meas: int, budget_gb: float, slots: int,
-                   sequential: bool = True):
+                   sequential: bool = True, solo_cells: int = 0):
     """Poisson arrivals (mean `rate` requests/s) of FP32-flux solves with
     sides log-uniform in [32, 1024], m in {2, 4, 8}, buffer 4-16 rows and slow
     steps log-uniform in [10, 1000], admitted under an HBM budget. Reports
@@ -596,7 +596,7 @@ def measure_served(M, rate: float, n_warm: int, n_meas: int, budget_gb: float, s
         cfg.precision = M.MPRK_FP32FLUX
         reqs.append((cfg, wl.initial_state(), wl.steps, wl.cell_stages_per_step() * wl.steps,
                      sum(algorithmic_bytes(g, wl.m, False)) * wl.steps))
-    srv = M.mprk_server_create(hbm_budget_bytes=int(budget_gb * 1e9), max_slots=slots)
+    srv = M.mprk_server_create(hbm_budget_bytes=int(budget_gb * 1e9), max_slots=slots, solo_cells=solo_cells)
     sampler = ClockSampler(torch.cuda.current_device())
     tickets = {}
     done = {}
@@ -645,7 +645,8 @@ def measure_served(M, rate: float, n_warm: int, n_meas: int, budget_gb: float, s
     rec = {"value": value, "unit": "cell-stages/s", "requests": n_meas, "warmup_requests": n_warm,
            "dtype": "f32 flux / f64 accumulate",
            "config": {"workload": "served_poisson_fp32flux", "rate_hz": rate, "requests": n_meas,
-                      "budget_gb": budget_gb, "max_slots": slots},
+                      "budget_gb": budget_gb, "max_slots": slots,
+                      "solo_cells": solo_cells if solo_cells else M.MPRK_SOLO_CELLS_DEFAULT},
            "served": {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                       "mean_latency_s": float(lat.mean()), "errors": errors,
                       "offered_cell_stages_per_s": offered, "achieved_over_offered": value / offered,
@@ -696,7 +697,7 @@ def run_served(args):
     torch.cuda.set_device(local)
     B.build()
     rec = measure_served(M, args.rate, args.served_warmup, args.served_requests, args.budget_gb, args.slots,
-                         sequential=args.served_sequential)
+                         sequential=args.served_sequential, solo_cells=args.served_solo_cells)
     out = {"metric": METRIC, "value": rec["value"], "unit": "cell-stages/s", "n_gpus": ws,
            "steps": args.served_requests, "warmup": args.served_warmup, "ms_per_step": None,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": rec["dtype"],
@@ -1176,6 +1177,8 @@ def main():
     ap.add_argument("--sub-served-warmup", type=int, default=100)
     ap.add_argument("--sub-served-rate-low", type=float, default=120.0)
     ap.add_argument("--served-sequential", action="store_true")
+    ap.add_argument("--served-solo-cells", type=int, default=0,
+                    help="server's solo_cells: 0 the library default, -1 every instance batched")
     ap.add_argument("--oracle-steps", type=int, default=2,
                     help="full-size oracle slow steps of the FP32-flux CPU-baseline leg")
     args = ap.parse_args()

@@ -370,8 +370,16 @@ typedef struct {
   int max_slots;              /* most instances resident at once              */
   int device;                 /* CUDA device ordinal                         */
   int max_queue;              /* queued requests beyond which submit is EBUSY */
-  int reserved;               /* must be 0                                   */
+  int solo_cells;             /* instances of at least this many cells step by
+                                 their own stage launches on side streams, not
+                                 in the batched launch: 0 = the default
+                                 (MPRK_SOLO_CELLS_DEFAULT), -1 = never        */
 } mprk_server_config;
+
+/* 2^18 cells, e.g. 512 x 512: from there on an instance's stage launches
+ * cover the GPU's SMs about once or more, and its own kernels beat the
+ * batch kernel. */
+#define MPRK_SOLO_CELLS_DEFAULT 262144
 
 #define MPRK_REQ_PENDING 1 /* queued, not admitted          */
 #define MPRK_REQ_RUNNING 2 /* resident on the device         */
@@ -389,9 +397,13 @@ typedef struct {
 
 /* Start a server thread on a device. It admits queued requests in arrival
  * order while a slot is free and the HBM ledger has room, advances all
- * resident instances together by one batched slow step at a time (the
- * persistent kernel of mprk_step_batch, one launch per precision), and
- * retires each request when it reaches its step count. Requests join and
+ * resident instances together by one slow step at a time (the persistent
+ * kernel of mprk_step_batch, one launch per precision, for the instances
+ * below cfg->solo_cells cells; the larger ones by the same stage kernels as
+ * mprk_step, on side streams that run beside each other), and retires each
+ * request when it reaches its step count. Either way a request's result is
+ * that of the same solve alone: bitwise in FP64, within float rounding in
+ * FP32 flux (bitwise for the instances stepped alone). Requests join and
  * leave between slow steps while the others keep running (continuous
  * batching). Uploads and downloads run on a copy stream that overlaps the
  * compute stream, and instance memory is stream-ordered (cudaMallocAsync and

@@ -205,6 +205,12 @@ int instance_view(const mprk_instance* inst, Geom* g, Bufs* b, int* precision, c
                   unsigned** status);
 cudaStream_t instance_stream(const mprk_instance* inst);
 void instance_count_steps(mprk_instance* inst, int n);
+// One slow step of an instance by its own stage launches on stream s (the
+// kernels mprk_step's graph replays), counted in its steps; cell_stages gets
+// the step's cell-stages (mprk_runtime.cu).
+int instance_step_alone(mprk_instance* inst, cudaStream_t s, long long* cell_stages);
+// Cells of an instance (nx ny nz).
+long long instance_cells(const mprk_instance* inst);
 // Drops cached batch plans that mention inst (mprk_batch.cu).
 void batch_forget(const void* inst);
 // One batched launch per slow step on an explicit stream (mprk_batch.cu).

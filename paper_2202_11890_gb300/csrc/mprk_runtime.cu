@@ -431,6 +431,17 @@ int mprk_config_default(mprk_config* cfg, int nx, int nz_S, int nz_B, int nz_F, 
 
 }  // extern "C"
 
+int mprk::instance_step_alone(mprk_instance* I, cudaStream_t s, long long* cell_stages) {
+  const int rc = enqueue_step(I, s);
+  if (rc) return rc;
+  I->steps_done++;
+  return mprk_info(I, nullptr, cell_stages, nullptr, nullptr);
+}
+
+long long mprk::instance_cells(const mprk_instance* I) {
+  return (long long)I->g.nx * I->g.ny * I->g.nz;
+}
+
 int mprk::create_instance(const mprk_config* cfg, const double* q0, int q0_location, void* cuda_stream,
                           bool stream_ordered, mprk_instance** out) {
   if (!out) return fail(MPRK_EINVAL, "out is NULL");

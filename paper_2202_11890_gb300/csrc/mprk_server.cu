@@ -5,8 +5,13 @@
 //   1. admit queued requests in arrival order while a slot is free and the
 //      HBM ledger has room: the instance is created stream-ordered on the
 //      copy stream (cudaMallocAsync, upload, reference set-up);
-//   2. advance every resident instance by one slow step with one persistent
-//      batched launch per precision on the compute stream;
+//   2. advance every resident instance by one slow step: the instances below
+//      the solo size with one persistent batched launch per precision on
+//      the compute stream, the larger ones by their own stage launches on
+//      side streams forked from it and joined back (a large instance fills
+//      the GPU by itself, and the single-instance kernels run its tiles
+//      faster than the batch kernel, which reads its arguments from shared
+//      memory);
 //   3. retire instances that reached their step count: the state is copied
 //      to pinned host memory on the copy stream after the step's event, and
 //      the buffers return to the pool with cudaFreeAsync.
@@ -106,6 +111,12 @@ struct mprk_server {
   std::vector<Request*> resident;
   std::vector<Request*> retiring;
   cudaStream_t compute = nullptr, copy = nullptr;
+  // side streams of the instances stepped alone, with the events that fork
+  // them from the compute stream and join them back
+  static constexpr int NSIDE = 4;
+  cudaStream_t side[NSIDE] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[NSIDE] = {nullptr, nullptr, nullptr, nullptr};
+  long long solo_cells = 0;  // instances of at least this many cells step alone (0: none)
   BatchRunner* runner[2] = {nullptr, nullptr};
   PinnedPool pool;
   // counters (read under mu)
@@ -134,9 +145,14 @@ void finish(mprk_server* S, Request* r, int error) {
 }
 
 void server_loop(mprk_server* S) {
-  if (cudaSetDevice(S->cfg.device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&S->compute, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking) != cudaSuccess) {
+  bool ok = cudaSetDevice(S->cfg.device) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&S->compute, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < mprk_server::NSIDE && ok; k++)
+    ok = cudaStreamCreateWithFlags(&S->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&S->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
     std::lock_guard<std::mutex> lk(S->mu);
     S->thread_error = MPRK_ECUDA;
     S->thread_msg = "server: device or stream set-up failed";
@@ -227,10 +243,35 @@ void server_loop(mprk_server* S) {
       }
       const double t_step0 = S->now();
       cudaEventRecord(beg_ev[slot], S->compute);
-      std::vector<mprk_instance*> group[2];
-      for (Request* r : S->resident) group[r->cfg.precision == MPRK_FP64 ? 0 : 1].push_back(r->inst);
+      std::vector<mprk_instance*> group[2], alone;
+      for (Request* r : S->resident) {
+        if (S->solo_cells > 0 && instance_cells(r->inst) >= S->solo_cells) alone.push_back(r->inst);
+        else group[r->cfg.precision == MPRK_FP64 ? 0 : 1].push_back(r->inst);
+      }
       int err = 0;
       long long cells = 0;
+      if (!alone.empty()) {
+        // fork: each side stream starts after everything queued on the
+        // compute stream so far (uploads of new instances, the previous
+        // iteration's work and joins), so an instance's steps stay ordered
+        // whichever side stream takes it
+        const int nside = std::min((int)alone.size(), (int)mprk_server::NSIDE);
+        if (cudaEventRecord(S->ev_fork, S->compute) != cudaSuccess) err = MPRK_ECUDA;
+        for (int k = 0; k < nside && !err; k++)
+          if (cudaStreamWaitEvent(S->side[k], S->ev_fork, 0) != cudaSuccess) err = MPRK_ECUDA;
+        for (size_t j = 0; j < alone.size() && !err; j++) {
+          long long cs = 0;
+          const int rc = instance_step_alone(alone[j], S->side[j % nside], &cs);
+          if (rc) err = rc;
+          cells += cs;
+        }
+        // join: the compute stream (and the step event after it) waits for
+        // every side stream used
+        for (int k = 0; k < nside; k++)
+          if (cudaEventRecord(S->ev_join[k], S->side[k]) != cudaSuccess ||
+              cudaStreamWaitEvent(S->compute, S->ev_join[k], 0) != cudaSuccess)
+            err = MPRK_ECUDA;
+      }
       for (int p = 0; p < 2; p++) {
         if (group[p].empty()) continue;
         if (!S->runner[p]) S->runner[p] = runner_create(p, S->compute);
@@ -358,6 +399,11 @@ void server_loop(mprk_server* S) {
   for (int p = 0; p < 2; p++) runner_destroy(S->runner[p]);
   cudaStreamSynchronize(S->compute);
   for (cudaEvent_t e : {step_ev[0], step_ev[1], beg_ev[0], beg_ev[1]}) cudaEventDestroy(e);
+  for (int k = 0; k < mprk_server::NSIDE; k++) {
+    if (S->side[k]) cudaStreamDestroy(S->side[k]);
+    if (S->ev_join[k]) cudaEventDestroy(S->ev_join[k]);
+  }
+  if (S->ev_fork) cudaEventDestroy(S->ev_fork);
   cudaStreamDestroy(S->compute);
   cudaStreamDestroy(S->copy);
 }
@@ -369,13 +415,14 @@ extern "C" {
 int mprk_server_create(const mprk_server_config* cfg, mprk_server** out) {
   if (!cfg || !out) return sfail(MPRK_EINVAL, "NULL argument");
   *out = nullptr;
-  if (cfg->hbm_budget_bytes <= 0 || cfg->max_slots <= 0 || cfg->max_queue <= 0 || cfg->reserved != 0)
-    return sfail(MPRK_EINVAL, "budget, slots and queue length must be positive");
+  if (cfg->hbm_budget_bytes <= 0 || cfg->max_slots <= 0 || cfg->max_queue <= 0 || cfg->solo_cells < -1)
+    return sfail(MPRK_EINVAL, "budget, slots and queue length must be positive, solo_cells >= -1");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
     return sfail(MPRK_ECUDA, "no such CUDA device");
   mprk_server* S = new mprk_server();
   S->cfg = *cfg;
+  S->solo_cells = cfg->solo_cells == 0 ? MPRK_SOLO_CELLS_DEFAULT : (cfg->solo_cells < 0 ? 0 : cfg->solo_cells);
   S->t0 = Clock::now();
   S->th = std::thread(server_loop, S);
   *out = S;

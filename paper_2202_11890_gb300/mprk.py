@@ -42,6 +42,8 @@ MPRK_BASE_RK4 = 2
 MPRK_HOST = 0
 MPRK_DEVICE = 1
 
+MPRK_SOLO_CELLS_DEFAULT = 262144
+
 MPRK_REQ_PENDING = 1
 MPRK_REQ_RUNNING = 2
 MPRK_REQ_DONE = 3
@@ -70,7 +72,7 @@ class mprk_config(C.Structure):
 
 class mprk_server_config(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_longlong), ("max_slots", C.c_int), ("device", C.c_int),
-                ("max_queue", C.c_int), ("reserved", C.c_int)]
+                ("max_queue", C.c_int), ("solo_cells", C.c_int)]
 
 
 class mprk_stats(C.Structure):
@@ -367,9 +369,11 @@ def mprk_step_static(cfg: mprk_config, q_dev, n: int, stream=None) -> None:
 
 
 def mprk_server_create(hbm_budget_bytes: int, max_slots: int = 1024, device: int = 0,
-                       max_queue: int = 1 << 20) -> int:
+                       max_queue: int = 1 << 20, solo_cells: int = 0) -> int:
+    """solo_cells: instances of at least this many cells step alone on side
+    streams (0: MPRK_SOLO_CELLS_DEFAULT, -1: every instance in the batch)."""
     cfg = mprk_server_config(hbm_budget_bytes=int(hbm_budget_bytes), max_slots=max_slots, device=device,
-                             max_queue=max_queue, reserved=0)
+                             max_queue=max_queue, solo_cells=int(solo_cells))
     h = C.c_void_p()
     _check(lib().mprk_server_create(C.byref(cfg), C.byref(h)))
     return h.value

@@ -59,12 +59,15 @@ def drain(M, srv, tickets, timeout=120.0):
     return outs
 
 
-@pytest.mark.parametrize("precision", [1, 0])
-def test_served_results_equal_solo_results(precision):
+@pytest.mark.parametrize("precision,solo_cells", [(1, 0), (0, 0), (1, 2000), (0, 2000), (1, -1)])
+def test_served_results_equal_solo_results(precision, solo_cells):
+    """solo_cells 2000: the instances of at least 2000 cells step alone on
+    the side streams (bitwise the solve alone in both precisions), the
+    others in the batched launch, in the same iterations; -1: all batched."""
     from paper_2202_11890_gb300 import mprk as M
     reqs = requests(24, 5 + precision, precision)
     refs = [alone(cfg, q, n) for cfg, q, n in reqs]
-    srv = M.mprk_server_create(hbm_budget_bytes=1 << 30, max_slots=7)
+    srv = M.mprk_server_create(hbm_budget_bytes=1 << 30, max_slots=7, solo_cells=solo_cells)
     try:
         tickets = {}
         order = {}
@@ -79,7 +82,9 @@ def test_served_results_equal_solo_results(precision):
             j = order[t]
             assert err == 0
             assert stats["steps_done"] == reqs[j][2]
-            if precision == 0:
+            cfg = reqs[j][0]
+            solo = solo_cells > 0 and cfg.nx * (cfg.nz_S + cfg.nz_B + cfg.nz_F) >= solo_cells
+            if precision == 0 or solo:
                 assert np.array_equal(buf, refs[j]), j
             else:  # FP32 flux: batch and solo kernels agree to float rounding
                 assert np.all(rel_err(buf, refs[j]) < 1e-5), (j, rel_err(buf, refs[j]))
