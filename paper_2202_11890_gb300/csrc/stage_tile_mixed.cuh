@@ -826,38 +826,39 @@ __device__ __forceinline__ void combine_slow_cell(const StageArgs& a, int k, siz
   }
 }
 
-// One bulk L2 prefetch of bytes (a multiple of 16) from a 16-byte aligned
-// global address.
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+// L2 prefetch of the 128-byte line holding p: an ordinary load-store
+// instruction, one per thread with the thread's own address (a bulk
+// prefetch with per-thread addresses runs once per thread in turn).
+__device__ __forceinline__ void prefetch_line_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 // L2 prefetch of the double rows that the stage combination of the tile's
 // rows k0 .. k0+MTZ-1, columns i0 .. i0+TX-1 will read after the tile's
 // second barrier: q_F (F rows, odd stages), the buffer accumulator (B rows,
 // every stage but the first) and q_n (S rows at the second stage, B rows at
-// the last). The last 4 MTZ threads (which stage one pair row rather than
-// two) each issue one 256-byte segment: thread t counted from there takes
-// row t / 4, component t % 4. Every segment is 256-byte aligned and inside
-// its row's pitch. Issued as the tile starts, so that those loads find L2.
-// The run-time form (the right-hand-side hook) does not prefetch.
+// the last). The last 8 MTZ threads (which stage one pair row rather than
+// two) each prefetch one 128-byte half of a row's TX doubles: thread t
+// counted from there takes row t / 8, component (t / 2) % 4, half t % 2.
+// Every address lies inside its row's pitch. Issued as the tile starts, so
+// that those loads find L2. The run-time form (the right-hand-side hook)
+// does not prefetch.
 template <int PAR>
 __device__ __forceinline__ void prefetch_combination(const StageArgs& a, int k0, int i0) {
-  const int t = (int)threadIdx.x - (MIXED_THREADS - 4 * MTZ);
+  const int t = (int)threadIdx.x - (MIXED_THREADS - 8 * MTZ);
   if (PAR == PAR_RT || t < 0) return;
   const Geom& g = a.g;
-  const int k = k0 + t / 4, c = t % 4;
+  const int k = k0 + t / 8, c = (t / 2) % 4, col = i0 + (t % 2) * (TX / 2);
   if (k >= g.nz) return;
-  const size_t off = (size_t)c * g.nz * g.pitch + (size_t)k * g.pitch + i0;
+  const size_t off = (size_t)c * g.nz * g.pitch + (size_t)k * g.pitch + col;
   const int st = a.stage;
   if (k >= g.n1_r) {
-    if (odd_mode<PAR>(a)) prefetch_l2(a.qF + off, TX * 8);
+    if (odd_mode<PAR>(a)) prefetch_line_l2(a.qF + off);
   } else if (k >= g.nS_r) {
-    if (st > 0)
-      prefetch_l2(a.b.accB + ((size_t)c * (g.n1_r - g.nS_r) + (k - g.nS_r)) * g.pitch + i0, TX * 8);
-    if (st == 2 * g.m - 1) prefetch_l2(a.b.qA + off, TX * 8);
+    if (st > 0) prefetch_line_l2(a.b.accB + ((size_t)c * (g.n1_r - g.nS_r) + (k - g.nS_r)) * g.pitch + col);
+    if (st == 2 * g.m - 1) prefetch_line_l2(a.b.qA + off);
   } else if (st == 1) {
-    prefetch_l2(a.b.qA + off, TX * 8);
+    prefetch_line_l2(a.b.qA + off);
   }
 }
 
