@@ -136,26 +136,35 @@ int mprk_destroy(mprk_instance* inst);
  * mprk_status reads. */
 int mprk_step(mprk_instance* inst, int n_slow_steps);
 
-/* Advance `count` instances by n_slow_steps each with one persistent,
- * graph-captured launch per slow step that covers every instance's stage
- * tiles and step completions. Items run in stage order; a tile of stage s of
- * an instance waits (bounded, about one second) for all stage s-1 tiles of
- * that instance. Instances may differ in size, m, buffer width, dt and base
- * method, but must share the device and the precision, and each may appear
- * only once. The batch runs on the first
- * instance's stream, ordered after and before the other instances' streams
- * with events. Each instance's result equals what mprk_step gives it alone:
- * bitwise with the Heun base (same tile code, same arithmetic), and to
- * rounding (within 1e-12) with the RK3 and RK4 bases. Asynchronous. A wait that gives up sets
- * MPRK_ETIMEOUT in the affected instances' status words (mprk_status); their
- * states are then undefined. In-graph monitoring (diag_every) does not run
- * in batched steps. Errors: MPRK_EINVAL, MPRK_ENOMEM, MPRK_ECUDA. */
+/* Advance `count` instances by n_slow_steps each, one CUDA graph launch per
+ * slow step. The graph holds one of two forms (the tuning table below picks
+ * it per precision and size bucket):
+ *  - one persistent launch that covers every instance's stage tiles and step
+ *    completions (FP64, and FP32 flux when tuned so): items run in stage
+ *    order; a tile of stage s of an instance waits (bounded, about one
+ *    second) for all stage s-1 tiles of that instance;
+ *  - per-stage launches (FP32 flux, the default there): one launch per stage
+ *    index over every instance that has that stage, then one launch of all
+ *    step completions, ordered by the stream.
+ * Instances may differ in size, m, buffer width, dt and base method, but
+ * must share the device and the precision, and each may appear only once.
+ * The batch runs on the first instance's stream, ordered after and before
+ * the other instances' streams with events. Each instance's result equals
+ * what mprk_step gives it alone: bitwise in FP64 with the Heun base (same
+ * tile code, same arithmetic), to rounding (within 1e-12) with the RK3 and
+ * RK4 bases, and to float rounding in FP32 flux (the batch kernels compile
+ * the float tile apart from the single-instance kernel). Asynchronous. A
+ * wait of the persistent form that gives up sets MPRK_ETIMEOUT in the
+ * affected instances' status words (mprk_status); their states are then
+ * undefined. In-graph monitoring (diag_every) does not run in batched
+ * steps. Errors: MPRK_EINVAL, MPRK_ENOMEM, MPRK_ECUDA. */
 int mprk_step_batch(mprk_instance* const* insts, int count, int n_slow_steps);
 
 /* ---- launch and tile-shape tuning ---------------------------------------
  * Three choices of the batched launch change no result, only its speed:
  * the stage tiles per work item (1, 2, 4, 8 or 16; G consecutive tiles
- * along x), the CTAs per SM (1 to 3), and in FP64 the shape of the stage
+ * along x; in FP32 flux 0 stands for the per-stage form, which has no work
+ * items), the CTAs per SM (1 to 3), and in FP64 the shape of the stage
  * tile of the 256-thread CTA: 32 x 8 cells with one thread per cell or
  * 32 x 4 with two (the FP32-flux tile is 32 x 16). Single-instance FP64
  * stage launches (mprk_step) choose among six tile shapes: 32 x 8, 32 x 4
@@ -164,8 +173,8 @@ int mprk_step_batch(mprk_instance* const* insts, int count, int n_slow_steps);
  * bitwise the same whatever is chosen.
  * A process-wide table keeps the fastest choices measured:
  *  - batches: per precision and size bucket (floor(log2) of the mean cells
- *    per instance); without an entry, 2 tiles per item, every CTA that
- *    fits and 32 x 8 tiles;
+ *    per instance); without an entry, in FP64 2 tiles per item, every CTA
+ *    that fits and 32 x 8 tiles, in FP32 flux the per-stage form;
  *  - single-instance FP64 stage launches: per size bucket (floor(log2) of
  *    the cells of the launch); without an entry, the shortest tile whose
  *    launch fits in one wave of the GPU's SMs, with two threads per cell,
@@ -175,15 +184,17 @@ int mprk_step_batch(mprk_instance* const* insts, int count, int n_slow_steps);
 
 /* Time every batch choice on these instances (reps batched slow steps each
  * after one warm-up step), record the fastest in the table and return it
- * in out: {tiles per item, CTAs per SM, ms per slow step, FP64 tile rows}.
+ * in out: {tiles per item (0: the per-stage form), CTAs per SM (0 with the
+ * per-stage form), ms per slow step, tile rows}.
  * The instances' states and step counts are restored afterwards.
  * Synchronises. Errors: MPRK_EINVAL, MPRK_ENOMEM, MPRK_ECUDA. */
 int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out[4]);
 
 /* The table's batch choice for a precision and a mean instance size in
  * cells: writes it and returns 1, or writes the defaults (ctas_per_sm 0:
- * every CTA that fits) and returns 0. tile_rows: 8 or 4 in FP64 (one or two
- * threads per cell), 16 in FP32 flux. Needs no device. */
+ * every CTA that fits; group 0 in FP32 flux: the per-stage form) and
+ * returns 0. tile_rows: 8 or 4 in FP64 (one or two threads per cell), 16 in
+ * FP32 flux. Needs no device. */
 int mprk_tune_lookup(int precision, double mean_cells, int* group, int* ctas_per_sm, int* tile_rows);
 
 /* Time the six tile shapes of single-instance FP64 stage launches on these
@@ -213,9 +224,10 @@ int mprk_tune_load(const char* path);
 int mprk_tune_clear(void);
 
 /* Test hook for the bounded waits of mprk_step_batch: one batched slow step
- * in which the tiles of stage `stage` of instance inst_index never report
- * completion, and each wait gives up after wait_cycles clock cycles. The
- * waiting tiles give up, set the timeout bit and drain; nothing hangs. */
+ * of the persistent form (in either precision) in which the tiles of stage
+ * `stage` of instance inst_index never report completion, and each wait
+ * gives up after wait_cycles clock cycles. The waiting tiles give up, set
+ * the timeout bit and drain; nothing hangs. */
 int mprk_batch_test_withhold(mprk_instance* const* insts, int count, int inst_index, int stage,
                              long long wait_cycles);
 

@@ -131,4 +131,30 @@ __global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const Bat
   }
 }
 
+// ---- the per-stage form ----------------------------------------------------
+// One launch per stage index covers every instance that has that stage: one
+// CTA per (stage arguments, tile) pair of the launch's work list. Stream
+// order between the launches takes the place of the persistent kernel's
+// waits. With no persistent loop around it, the FP32-flux tile fits its
+// registers without spilling while it reads its arguments from the table in
+// global memory.
+template <int PAR>
+__global__ void __launch_bounds__(MIXED_THREADS, 3)
+    wave_stage_mixed(const StageArgs* __restrict__ tab, const StageWork* __restrict__ work) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const StageWork w = work[blockIdx.x];
+  const StageArgs& a = tab[w.args];
+  const int tzi = w.tile / a.tiles_x, txi = w.tile - tzi * a.tiles_x;
+  (void)stage_tile_mixed<PAR>(a, a.row0 + tzi * MTZ, txi * TX, *reinterpret_cast<MixedTileSmem*>(smem_raw),
+                              nullptr, nullptr);
+}
+
+// The step completions of the per-stage form: one CTA per (instance, chunk).
+__global__ void __launch_bounds__(NTHREADS) wave_finalize(const BatchInst* __restrict__ insts,
+                                                          const StageWork* __restrict__ work) {
+  const StageWork w = work[blockIdx.x];
+  const BatchInst& I = insts[w.args];
+  finalize_chunk(I.g, I.b, w.tile);
+}
+
 }  // namespace mprk

@@ -53,6 +53,14 @@ struct BatchArgs {
 
 constexpr int FIN_CHUNK = NTHREADS * 8;  // cells per completion item
 
+// A CTA of the per-stage form: its stage arguments (an index into the
+// table) and its tile of that stage, or for a completion launch the
+// instance (an index into the instance table) and its chunk.
+struct StageWork {
+  int args;
+  int tile;
+};
+
 // block size of the batch kernel per precision (the tile's own block size)
 constexpr int batch_threads(int prec) { return prec == 0 ? NTHREADS : MIXED_THREADS; }
 
@@ -62,5 +70,11 @@ constexpr int batch_threads(int prec) { return prec == 0 ? NTHREADS : MIXED_THRE
 // limit and CTAs per SM, and its launch.
 cudaError_t batch_prepare(int prec, int rows, size_t smem, int* per_sm);
 void batch_launch(int prec, int rows, int grid, size_t smem, cudaStream_t s, const BatchArgs& A);
+// The per-stage form (FP32 flux): one stage launch of `grid` CTAs of stage
+// parity `parity`, and one completion launch; cudaFuncSetAttribute first
+// (wave_prepare).
+cudaError_t wave_prepare();
+void wave_launch_stage(int parity, int grid, const StageArgs* tab, const StageWork* work, cudaStream_t s);
+void wave_launch_finalize(int grid, const BatchInst* insts, const StageWork* work, cudaStream_t s);
 
 }  // namespace mprk

@@ -9,6 +9,10 @@
 // stage s of instance I first waits until every item of stage s-1 of I has
 // finished (a per-instance counter). The tiles per item and the CTAs per SM
 // come from a tuning table (mprk_batch_tune) or defaults.
+// FP32-flux batches have a second form, the per-stage launches (tiles per
+// item 0 in the tuning table, and the default): one launch per stage index
+// over every instance that has it, and one for the step completions, in
+// stream order (captured in one graph per slow step by mprk_step_batch).
 // This file builds the work lists, plans and tuning; the kernel itself is
 // compiled with the single-instance stage kernels (batch_kernel.cuh, included
 // by mprk_kernels.cu), so that both call one compiled copy of the FP64 tile.
@@ -22,6 +26,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <map>
@@ -58,6 +63,9 @@ struct Plan {
   StageArgs* d_args = nullptr;
   BatchItem* d_items = nullptr;
   int* d_ctr = nullptr;  // [0] next, [1] abort, [2..] counters
+  int form = 0;                   // 0 persistent launch, 1 per-stage launches
+  StageWork* d_work = nullptr;    // per-stage form: the launches' work lists
+  std::vector<int> off;           // launch s lists entries off[s] .. off[s+1]
   cudaGraphExec_t exec = nullptr;
   cudaStream_t stream = nullptr;
   long long wait_cycles = 0;
@@ -73,6 +81,7 @@ std::vector<Plan*> g_plans;
 // (floor(log2) of the mean cells per instance), the fastest pair
 // mprk_batch_tune measured, with the name of the GPU it ran on. Plans
 // without an entry take the defaults (batch_group tiles, every CTA that fits).
+// Tiles per item 0 stands for the per-stage form of FP32-flux batches.
 struct TuneVal {
   int group, per_sm;
   double ms;
@@ -106,7 +115,7 @@ void tuned_choice(int prec, int bucket, int* group, int* per_sm, int* rows) {
     *per_sm = it->second.per_sm;
     *rows = prec == 0 ? it->second.rows : MTZ;
   } else {
-    *group = batch_group(prec);
+    *group = prec == 0 ? batch_group(prec) : 0;
     *per_sm = 0;
     *rows = prec == 0 ? TZ : MTZ;
   }
@@ -136,6 +145,7 @@ void free_plan(Plan* p) {
   cudaFree(p->d_args);
   cudaFree(p->d_items);
   cudaFree(p->d_ctr);
+  cudaFree(p->d_work);
   delete p;
 }
 
@@ -190,8 +200,54 @@ void build_items(const std::vector<BatchInst>& hinst, int G, int rows, std::vect
   *cell_stages = cs;
 }
 
-// group / per_sm / rows: the launch choices, or 0 for the tuned (else
-// default) ones.
+// The work lists of the per-stage form: launch s (s = 0 .. the most stages
+// of any instance, minus one) lists the (stage argument index, tile) pairs
+// of every instance that has a stage s, and a last launch the (instance,
+// chunk) pairs of every instance's step completion. Launch s takes the
+// entries off[s] .. off[s+1]. Needs the args_base of args_table.
+void build_wave(const std::vector<BatchInst>& hinst, std::vector<StageWork>& work, std::vector<int>& off,
+                long long* cell_stages) {
+  int max_stages = 0;
+  for (const BatchInst& bi : hinst) max_stages = std::max(max_stages, bi.g.s * bi.g.m);
+  long long cs = 0;
+  work.clear();
+  off.assign(1, 0);
+  for (int st = 0; st < max_stages; st++) {
+    for (const BatchInst& bi : hinst) {
+      if (st >= bi.g.s * bi.g.m) continue;
+      const StageArgs a = batch_stage_args(bi, st, MTZ);
+      const int nt = stage_tiles(a);
+      for (int t = 0; t < nt; t++) work.push_back({bi.args_base + st, t});
+      cs += (long long)(bi.g.nz - a.row0) * bi.g.nx;
+    }
+    off.push_back((int)work.size());
+  }
+  for (int j = 0; j < (int)hinst.size(); j++) {
+    const Geom& g = hinst[j].g;
+    const int rows = ((g.m & 1) || hinst[j].b.dA) ? g.nz : g.n1_r;  // as finalize_chunk
+    const long long total = 4LL * rows * g.nx;
+    const int chunks = (int)((total + FIN_CHUNK - 1) / FIN_CHUNK);
+    for (int c = 0; c < chunks; c++) work.push_back({j, c});
+  }
+  off.push_back((int)work.size());
+  *cell_stages = cs;
+}
+
+// Launches of one slow step in the per-stage form on stream s.
+void wave_step(const std::vector<int>& off, const BatchInst* d_insts, const StageArgs* d_args,
+               const StageWork* d_work, cudaStream_t s) {
+  const int launches = (int)off.size() - 1;
+  for (int st = 0; st + 1 < launches; st++)
+    wave_launch_stage(st & 1, off[st + 1] - off[st], d_args, d_work + off[st], s);
+  wave_launch_finalize(off[launches] - off[launches - 1], d_insts, d_work + off[launches - 1], s);
+}
+
+// The form of a batch: 1 (per-stage launches) for FP32-flux batches with
+// tiles per item 0, else 0 (the persistent launch).
+int batch_form(int precision, int group) { return precision == 1 && group == 0 ? 1 : 0; }
+
+// group / per_sm / rows: the launch choices (group 0: the per-stage form of
+// FP32 flux), or group < 0 for the tuned (else default) ones.
 int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, int wi, int ws,
                cudaStream_t stream, int group, int per_sm_want, int rows, Plan** out) {
   Plan* p = new Plan();
@@ -225,17 +281,58 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
     p->key.push_back(insts[j]);
   }
   p->bucket = size_bucket(hinst);
-  if (group <= 0) tuned_choice(p->precision, p->bucket, &group, &per_sm_want, &rows);
+  if (group < 0) tuned_choice(p->precision, p->bucket, &group, &per_sm_want, &rows);
+  // FP64 has no per-stage form, and the test hook withholds a persistent
+  // launch's completion reports
+  if (group == 0 && (p->precision == 0 || wi >= 0)) group = batch_group(p->precision);
   if (p->precision != 0) rows = MTZ;
   else if (rows != TZ && rows != TZ / 2) rows = TZ;
   p->group = group;
   p->rows = rows;
+  p->per_sm_req = per_sm_want;
   std::vector<StageArgs> hargs;
   args_table(hinst, rows, hargs);
+  cudaError_t e;
+  p->form = batch_form(p->precision, group);
+  if (p->form == 1) {
+    std::vector<StageWork> work;
+    build_wave(hinst, work, p->off, &p->cell_stages);
+    if ((e = cudaMalloc(&p->d_insts, sizeof(BatchInst) * count)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_args, sizeof(StageArgs) * hargs.size())) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_work, sizeof(StageWork) * work.size())) != cudaSuccess) {
+      free_plan(p);
+      return bfail(MPRK_ENOMEM, std::string("batch plan allocation: ") + cudaGetErrorString(e));
+    }
+    if ((e = cudaMemcpy(p->d_insts, hinst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(p->d_args, hargs.data(), sizeof(StageArgs) * hargs.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(p->d_work, work.data(), sizeof(StageWork) * work.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = wave_prepare()) != cudaSuccess) {
+      free_plan(p);
+      return bfail(MPRK_ECUDA, std::string("batch plan upload: ") + cudaGetErrorString(e));
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      wave_step(p->off, p->d_insts, p->d_args, p->d_work, p->stream);
+      cudaError_t el = cudaGetLastError();
+      e = cudaStreamEndCapture(p->stream, &graph);
+      if (el != cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      free_plan(p);
+      return bfail(MPRK_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    }
+    *out = p;
+    return MPRK_OK;
+  }
   std::vector<BatchItem> items;
   build_items(hinst, group, rows, items, &p->cell_stages);
   p->n_items = (int)items.size();
-  cudaError_t e;
   if ((e = cudaMalloc(&p->d_insts, sizeof(BatchInst) * count)) != cudaSuccess ||
       (e = cudaMalloc(&p->d_args, sizeof(StageArgs) * hargs.size())) != cudaSuccess ||
       (e = cudaMalloc(&p->d_items, sizeof(BatchItem) * items.size())) != cudaSuccess ||
@@ -350,7 +447,7 @@ int step_batch(mprk_instance* const* insts, int count, int n, long long wait_cyc
   std::lock_guard<std::mutex> lk(g_batch_mu);
   Plan* p = find_plan(insts, count, wait_cycles, wi, ws, stream);
   if (!p) {
-    int rc = build_plan(insts, count, wait_cycles, wi, ws, stream, 0, 0, 0, &p);
+    int rc = build_plan(insts, count, wait_cycles, wi, ws, stream, -1, 0, 0, &p);
     if (rc) return rc;
     if (g_plans.size() >= 64) {
       // the oldest plan's launches may still be running on its stream
@@ -416,6 +513,10 @@ struct BatchRunner {
   int rows = TZ;  // FP64 tile rows of the current work list
   long long cell_stages = 0;
   unsigned* status = nullptr;
+  int form = 0;  // as Plan::form
+  StageWork* d_work = nullptr;
+  size_t cap_work = 0;
+  std::vector<int> off;
 };
 
 BatchRunner* runner_create(int precision, cudaStream_t stream) {
@@ -431,6 +532,7 @@ void runner_destroy(BatchRunner* r) {
   if (r->d_args) cudaFreeAsync(r->d_args, r->stream);
   if (r->d_items) cudaFreeAsync(r->d_items, r->stream);
   if (r->d_ctr) cudaFreeAsync(r->d_ctr, r->stream);
+  if (r->d_work) cudaFreeAsync(r->d_work, r->stream);
   delete r;
 }
 
@@ -476,67 +578,100 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
     }
     int group, per_sm_want, rows;
     tuned_choice(r->precision, size_bucket(hinst), &group, &per_sm_want, &rows);
-    if (r->precision == 0 && rows != r->rows) r->per_sm = 0;  // another kernel: query its occupancy
-    r->rows = rows;
-    std::vector<StageArgs> hargs;
-    args_table(hinst, rows, hargs);
-    std::vector<BatchItem> items;
-    long long cs = 0;
-    build_items(hinst, group, rows, items, &cs);
-    cudaError_t e = grow(&r->d_insts, &r->cap_insts, (size_t)count, r->stream);
-    if (e == cudaSuccess) e = grow(&r->d_args, &r->cap_args, hargs.size(), r->stream);
-    if (e == cudaSuccess) e = grow(&r->d_items, &r->cap_items, items.size(), r->stream);
-    if (e == cudaSuccess) e = grow(&r->d_ctr, &r->cap_ctr, (size_t)(2 + n_counters), r->stream);
-    if (e != cudaSuccess) return bfail(MPRK_ENOMEM, std::string("batch runner: ") + cudaGetErrorString(e));
-    // pageable sources: the copies are staged before the calls return
-    if (reinterpret_cast<uintptr_t>(r->d_args) % 16 != 0)
-      return bfail(MPRK_ECUDA, "batch runner: argument table not 16-byte aligned");
-    e = cudaMemcpyAsync(r->d_insts, hinst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, r->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(r->d_args, hargs.data(), sizeof(StageArgs) * hargs.size(), cudaMemcpyHostToDevice,
+    r->form = batch_form(r->precision, group);
+    cudaError_t e;
+    if (r->form == 1) {
+      std::vector<StageArgs> hargs;
+      args_table(hinst, MTZ, hargs);
+      std::vector<StageWork> work;
+      long long cs = 0;
+      build_wave(hinst, work, r->off, &cs);
+      e = grow(&r->d_insts, &r->cap_insts, (size_t)count, r->stream);
+      if (e == cudaSuccess) e = grow(&r->d_args, &r->cap_args, hargs.size(), r->stream);
+      if (e == cudaSuccess) e = grow(&r->d_work, &r->cap_work, work.size(), r->stream);
+      if (e != cudaSuccess) return bfail(MPRK_ENOMEM, std::string("batch runner: ") + cudaGetErrorString(e));
+      // pageable sources: the copies are staged before the calls return
+      e = cudaMemcpyAsync(r->d_insts, hinst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice,
                           r->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(r->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r->d_args, hargs.data(), sizeof(StageArgs) * hargs.size(), cudaMemcpyHostToDevice,
+                            r->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r->d_work, work.data(), sizeof(StageWork) * work.size(), cudaMemcpyHostToDevice,
+                            r->stream);
+      if (e == cudaSuccess) e = wave_prepare();
+      if (e != cudaSuccess) return bfail(MPRK_ECUDA, std::string("batch runner upload: ") + cudaGetErrorString(e));
+      r->key.assign(insts, insts + count);
+      r->cell_stages = cs;
+    } else {
+      if (r->precision == 0 && rows != r->rows) r->per_sm = 0;  // another kernel: query its occupancy
+      r->rows = rows;
+      std::vector<StageArgs> hargs;
+      args_table(hinst, rows, hargs);
+      std::vector<BatchItem> items;
+      long long cs = 0;
+      build_items(hinst, group, rows, items, &cs);
+      e = grow(&r->d_insts, &r->cap_insts, (size_t)count, r->stream);
+      if (e == cudaSuccess) e = grow(&r->d_args, &r->cap_args, hargs.size(), r->stream);
+      if (e == cudaSuccess) e = grow(&r->d_items, &r->cap_items, items.size(), r->stream);
+      if (e == cudaSuccess) e = grow(&r->d_ctr, &r->cap_ctr, (size_t)(2 + n_counters), r->stream);
+      if (e != cudaSuccess) return bfail(MPRK_ENOMEM, std::string("batch runner: ") + cudaGetErrorString(e));
+      // pageable sources: the copies are staged before the calls return
+      if (reinterpret_cast<uintptr_t>(r->d_args) % 16 != 0)
+        return bfail(MPRK_ECUDA, "batch runner: argument table not 16-byte aligned");
+      e = cudaMemcpyAsync(r->d_insts, hinst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice,
                           r->stream);
-    if (e != cudaSuccess) return bfail(MPRK_ECUDA, std::string("batch runner upload: ") + cudaGetErrorString(e));
-    r->key.assign(insts, insts + count);
-    r->n_items = (int)items.size();
-    r->n_counters = n_counters;
-    r->cell_stages = cs;
-    if (r->per_sm == 0) {
-      const size_t smem = stage_smem_bytes(r->precision);
-      int dev = 0;
-      if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-          (e = cudaDeviceGetAttribute(&r->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
-        r->key.clear();  // rebuild on the next call
-        return bfail(MPRK_ECUDA, std::string("batch runner device query: ") + cudaGetErrorString(e));
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r->d_args, hargs.data(), sizeof(StageArgs) * hargs.size(), cudaMemcpyHostToDevice,
+                            r->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                            r->stream);
+      if (e != cudaSuccess) return bfail(MPRK_ECUDA, std::string("batch runner upload: ") + cudaGetErrorString(e));
+      r->key.assign(insts, insts + count);
+      r->n_items = (int)items.size();
+      r->n_counters = n_counters;
+      r->cell_stages = cs;
+      if (r->per_sm == 0) {
+        const size_t smem = stage_smem_bytes(r->precision);
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&r->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
+          r->key.clear();  // rebuild on the next call
+          return bfail(MPRK_ECUDA, std::string("batch runner device query: ") + cudaGetErrorString(e));
+        }
+        e = batch_prepare(r->precision, r->rows, smem, &r->per_sm);
+        if (e != cudaSuccess || r->per_sm < 1) {
+          r->key.clear();
+          r->per_sm = 0;
+          return bfail(MPRK_ECUDA, "batch runner: occupancy query failed");
+        }
       }
-      e = batch_prepare(r->precision, r->rows, smem, &r->per_sm);
-      if (e != cudaSuccess || r->per_sm < 1) {
-        r->key.clear();
-        r->per_sm = 0;
-        return bfail(MPRK_ECUDA, "batch runner: occupancy query failed");
-      }
+      r->grid = (per_sm_want > 0 ? std::min(per_sm_want, r->per_sm) : r->per_sm) * r->sms;
     }
-    r->grid = (per_sm_want > 0 ? std::min(per_sm_want, r->per_sm) : r->per_sm) * r->sms;
   }
-  BatchArgs A;
-  A.insts = r->d_insts;
-  A.args = r->d_args;
-  A.items = r->d_items;
-  A.n_items = r->n_items;
-  A.next = r->d_ctr;
-  A.abort_flag = r->d_ctr + 1;
-  A.counters = r->d_ctr + 2;
-  A.status = r->status;
-  A.wait_cycles = 2000000000LL;
-  A.withhold_inst = -1;
-  A.withhold_stage = -1;
-  cudaError_t e = cudaMemsetAsync(r->d_ctr, 0, sizeof(int) * (2 + r->n_counters), r->stream);
-  if (e != cudaSuccess) return bfail(MPRK_ECUDA, std::string("batch runner: ") + cudaGetErrorString(e));
-  const size_t smem = stage_smem_bytes(r->precision);
-  const int grid = std::min(r->grid, r->n_items);
-  batch_launch(r->precision, r->rows, grid, smem, r->stream, A);
+  cudaError_t e;
+  if (r->form == 1) {
+    wave_step(r->off, r->d_insts, r->d_args, r->d_work, r->stream);
+  } else {
+    BatchArgs A;
+    A.insts = r->d_insts;
+    A.args = r->d_args;
+    A.items = r->d_items;
+    A.n_items = r->n_items;
+    A.next = r->d_ctr;
+    A.abort_flag = r->d_ctr + 1;
+    A.counters = r->d_ctr + 2;
+    A.status = r->status;
+    A.wait_cycles = 2000000000LL;
+    A.withhold_inst = -1;
+    A.withhold_stage = -1;
+    e = cudaMemsetAsync(r->d_ctr, 0, sizeof(int) * (2 + r->n_counters), r->stream);
+    if (e != cudaSuccess) return bfail(MPRK_ECUDA, std::string("batch runner: ") + cudaGetErrorString(e));
+    const size_t smem = stage_smem_bytes(r->precision);
+    const int grid = std::min(r->grid, r->n_items);
+    batch_launch(r->precision, r->rows, grid, smem, r->stream, A);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return bfail(MPRK_ECUDA, std::string("batch runner launch: ") + cudaGetErrorString(e));
   for (int j = 0; j < count; j++) instance_count_steps(insts[j], 1);
@@ -616,15 +751,17 @@ int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out
     if ((rc = instance_view(insts[0], &g, &b, &prec0, &st, &sw))) prec0 = 0;
   }
   const std::vector<int> row_choices = prec0 == 0 ? std::vector<int>{TZ, TZ / 2} : std::vector<int>{MTZ};
+  // FP32 flux also times the per-stage form (tiles per item 0; one run)
+  const std::vector<int> groups = prec0 == 0 ? std::vector<int>{1, 2, 4, 8, 16} : std::vector<int>{0, 1, 2, 4, 8, 16};
   for (int R : row_choices) {
-    for (int G : {1, 2, 4, 8, 16}) {
-      for (int c = 1; c <= 3 && rc == MPRK_OK; c++) {
+    for (int G : groups) {
+      for (int c = 1; c <= (G == 0 ? 1 : 3) && rc == MPRK_OK; c++) {
         Plan* p = nullptr;
         rc = build_plan(insts, count, 2000000000LL, -1, -1, nullptr, G, c, R, &p);
         if (rc) break;
         prec = p->precision;
         bucket = p->bucket;
-        if (p->per_sm < c) {  // more CTAs than fit
+        if (p->form == 0 && p->per_sm < c) {  // more CTAs than fit
           free_plan(p);
           continue;
         }
@@ -639,7 +776,7 @@ int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out
         if (rc == MPRK_OK && ms / reps < best_ms) {
           best_ms = ms / reps;
           best_g = G;
-          best_c = c;
+          best_c = G == 0 ? 0 : c;
           best_r = R;
         }
       }
@@ -674,7 +811,7 @@ int mprk_tune_lookup(int precision, double mean_cells, int* group, int* ctas_per
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tune.find({precision, bucket});
   if (it == g_tune.end()) {
-    *group = batch_group(precision);
+    *group = precision == 0 ? batch_group(precision) : 0;
     *ctas_per_sm = 0;
     *tile_rows = precision == 0 ? TZ : MTZ;
     return 0;
@@ -846,7 +983,7 @@ int mprk_tune_load(const char* path) {
         !num(obj, "ctas_per_sm", &ct))
       return bfail(MPRK_EINVAL, "tuning file: incomplete entry");
     num(obj, "tile_rows", &rows);
-    if ((pr != 0 && pr != 1) || bu < 0 || bu > 40 || gr < 1 || gr > 64 || ct < 0 || ct > 8 ||
+    if ((pr != 0 && pr != 1) || bu < 0 || bu > 40 || gr < (pr == 0 ? 1 : 0) || gr > 64 || ct < 0 || ct > 8 ||
         (pr == 0 && rows != TZ && rows != TZ / 2))
       return bfail(MPRK_EINVAL, "tuning file: value out of range");
     table[{(int)pr, (int)bu}] = TuneVal{(int)gr, (int)ct, ms, pr == 0 ? (int)rows : MTZ};

@@ -261,6 +261,28 @@ cudaError_t batch_prepare(int prec, int rows, size_t smem, int* per_sm) {
   }
   return e;
 }
+cudaError_t wave_prepare() {
+  static const cudaError_t e = [] {
+    cudaError_t r = cudaFuncSetAttribute(wave_stage_mixed<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(MixedTileSmem));
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(wave_stage_mixed<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sizeof(MixedTileSmem));
+    return r;
+  }();
+  return e;
+}
+
+void wave_launch_stage(int parity, int grid, const StageArgs* tab, const StageWork* work, cudaStream_t s) {
+  if (grid <= 0) return;
+  if (parity) wave_stage_mixed<1><<<grid, MIXED_THREADS, sizeof(MixedTileSmem), s>>>(tab, work);
+  else wave_stage_mixed<0><<<grid, MIXED_THREADS, sizeof(MixedTileSmem), s>>>(tab, work);
+}
+
+void wave_launch_finalize(int grid, const BatchInst* insts, const StageWork* work, cudaStream_t s) {
+  if (grid > 0) wave_finalize<<<grid, NTHREADS, 0, s>>>(insts, work);
+}
+
 void batch_launch(int prec, int rows, int grid, size_t smem, cudaStream_t s, const BatchArgs& A) {
   if (prec == 1) batch_kernel<1><<<grid, batch_threads(1), smem, s>>>(A);
   else if (rows == TZ / 2) batch_kernel<0, TZ / 2><<<grid, batch_threads(0), smem, s>>>(A);

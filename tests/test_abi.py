@@ -97,7 +97,8 @@ def test_tuning_table_round_trip_without_a_device(lib, tmp_path):
     rejects out-of-range values; none of it needs a GPU."""
     from paper_2202_11890_gb300 import mprk as M
     M.mprk_tune_clear()
-    assert M.mprk_tune_lookup(1, 5000.0) == {"tiles_per_item": 2, "ctas_per_sm": 0, "tile_rows": 16,
+    # FP32 flux defaults to the per-stage form (tiles per item 0)
+    assert M.mprk_tune_lookup(1, 5000.0) == {"tiles_per_item": 0, "ctas_per_sm": 0, "tile_rows": 16,
                                              "tuned": False}
     assert M.mprk_tune_lookup(0, 5000.0)["tiles_per_item"] == 2
     assert M.mprk_tune_lookup(0, 5000.0)["tile_rows"] == 8
@@ -106,11 +107,14 @@ def test_tuning_table_round_trip_without_a_device(lib, tmp_path):
     src.write_text('{"gpu": "", "entries": [\n'
                    ' {"precision": 1, "bucket": 12, "group": 4, "ctas_per_sm": 2, "ms": 1.5},\n'
                    ' {"precision": 0, "bucket": 16, "group": 1, "ctas_per_sm": 3, "tile_rows": 4, "ms": 9},\n'
+                   ' {"precision": 1, "bucket": 14, "group": 0, "ctas_per_sm": 0, "ms": 2.5},\n'
                    ' {"stage_launch": 1, "bucket": 21, "tile_rows": 2, "threads_per_cell": 2, "ms": 0.1}\n]}\n')
     M.mprk_tune_load(str(src))
     assert M.mprk_tune_lookup(1, 5000.0) == {"tiles_per_item": 4, "ctas_per_sm": 2, "tile_rows": 16,
                                              "tuned": True}  # 2^12 <= 5000
     assert M.mprk_tune_lookup(1, 9000.0)["tuned"] is False                                            # bucket 13
+    assert M.mprk_tune_lookup(1, 20000.0) == {"tiles_per_item": 0, "ctas_per_sm": 0, "tile_rows": 16,
+                                              "tuned": True}  # the per-stage form, bucket 14
     assert M.mprk_tune_lookup(0, 70000.0) == {"tiles_per_item": 1, "ctas_per_sm": 3, "tile_rows": 4,
                                               "tuned": True}
     assert M.mprk_tile_lookup(2.5e6) == {"tile_rows": 2, "threads_per_cell": 2}  # 2^21 <= 2.5e6 < 2^22
@@ -123,7 +127,8 @@ def test_tuning_table_round_trip_without_a_device(lib, tmp_path):
     assert M.mprk_tune_lookup(0, 70000.0)["tiles_per_item"] == 1
     assert M.mprk_tune_lookup(0, 70000.0)["tile_rows"] == 4
     assert M.mprk_tile_lookup(2.5e6) == {"tile_rows": 2, "threads_per_cell": 2}
-    for bad_entry in ('{"precision": 1, "bucket": 12, "group": 0, "ctas_per_sm": 2}',
+    for bad_entry in ('{"precision": 1, "bucket": 12, "group": -1, "ctas_per_sm": 2}',
+                      '{"precision": 0, "bucket": 12, "group": 0, "ctas_per_sm": 2}',
                       '{"precision": 0, "bucket": 12, "group": 2, "ctas_per_sm": 2, "tile_rows": 2}',
                       '{"stage_launch": 1, "bucket": 21, "tile_rows": 3, "threads_per_cell": 1}',
                       '{"stage_launch": 1, "bucket": 21, "tile_rows": 8, "threads_per_cell": 4}',

@@ -150,7 +150,10 @@ def test_tuned_launch_leaves_states_and_results_unchanged(precision, tmp_path):
         M.mprk_step_batch([i.h for i in b], 2)  # default launch
         before = [i.state() for i in a]
         best = M.mprk_batch_tune([i.h for i in a], reps=2)
-        assert best["tiles_per_item"] in (1, 2, 4, 8, 16) and 1 <= best["ctas_per_sm"] <= 3
+        if best["tiles_per_item"] == 0:  # the per-stage form (FP32 flux only)
+            assert precision == 1 and best["ctas_per_sm"] == 0
+        else:
+            assert best["tiles_per_item"] in (1, 2, 4, 8, 16) and 1 <= best["ctas_per_sm"] <= 3
         assert best["ms_per_step"] > 0
         for i, q in zip(a, before):
             assert np.array_equal(i.state(), q) and i.info()["cell_stages_per_step"] > 0
@@ -159,7 +162,10 @@ def test_tuned_launch_leaves_states_and_results_unchanged(precision, tmp_path):
         assert look["tuned"] and look["tiles_per_item"] == best["tiles_per_item"]
         M.mprk_step_batch([i.h for i in a], 2)  # tuned launch
         for x, y in zip(a, b):
-            assert np.array_equal(x.state(), y.state())
+            if precision == 0 or best["tiles_per_item"] == 0:  # same form and tile code as the default
+                assert np.array_equal(x.state(), y.state())
+            else:  # the persistent kernel's float tile against the per-stage one's
+                assert np.all(rel_err(x.state(), y.state()) < 1e-6)
         path = tmp_path / "tune.json"
         M.mprk_tune_save(str(path))
         assert torch.cuda.get_device_name(0) in path.read_text()

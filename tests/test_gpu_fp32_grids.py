@@ -48,18 +48,32 @@ def test_fp32_flux_steps_close_to_oracle(dims, m, wall):
     assert np.all(err < 1e-5), err
 
 
+@pytest.mark.parametrize("form", ["per_stage", "persistent"])
 @pytest.mark.parametrize("scheme", [0, 1])
-def test_single_and_batch_kernels_agree(scheme):
+def test_single_and_batch_kernels_agree(scheme, form, tmp_path):
     """One instance steps with the single-instance stage kernel, its twin
-    with the persistent batch kernel: the states agree to float rounding."""
+    with a batched step in either form (the per-stage launches, the FP32-flux
+    default, or the persistent kernel, chosen here through a tuning entry for
+    the instance's size bucket): the states agree to float rounding."""
     mp = M()
     g = W.Grid(124, 20, 12, 36)
     q0 = W.gaussian_bumps(g, 7, sigma_cells=3.0)
     cfg, P, dt = pair(g, 3, q0=q0, precision=mp.MPRK_FP32FLUX, scheme=scheme)
-    with mp.Instance(cfg, q0) as a, mp.Instance(cfg, q0) as b:
-        for _ in range(3):
-            a.step(1)
-            mp.mprk_step_batch([b.h], 1)
-            err = rel_err(a.state(), b.state())
-            print("single vs batch:", err)
-            assert np.all(err < 1e-6), err
+    mp.mprk_tune_clear()
+    if form == "persistent":
+        bucket = int(np.floor(np.log2(g.nx * g.nz)))
+        path = tmp_path / "t.json"
+        path.write_text('{"gpu": "%s", "entries": [{"precision": 1, "bucket": %d, "group": 2, '
+                        '"ctas_per_sm": 0, "ms": 1}]}' % (torch.cuda.get_device_name(0), bucket))
+        mp.mprk_tune_load(str(path))
+        assert mp.mprk_tune_lookup(1, g.nx * g.nz)["tiles_per_item"] == 2
+    try:
+        with mp.Instance(cfg, q0) as a, mp.Instance(cfg, q0) as b:
+            for _ in range(3):
+                a.step(1)
+                mp.mprk_step_batch([b.h], 1)
+                err = rel_err(a.state(), b.state())
+                print(form, "single vs batch:", err)
+                assert np.all(err < 1e-6), err
+    finally:
+        mp.mprk_tune_clear()
