@@ -459,10 +459,12 @@ def oracle_full_size(M, cfg, q0, wl, dt, steps: int) -> dict:
 
 def measure_batched(M, T, precision: str, steps: int, warmup: int, count: int = 256, tune: bool = False):
     """256 uneven instances (sides log-uniform in [64, 512], m in {2, 4, 8},
-    buffer 4-16 rows; FP64 or FP32 flux): one persistent launch per slow step
-    (mprk_step_batch) against the same instances stepped one after another
-    with mprk_step on the same stream, and the two paths' results from the
-    same start compared bitwise on 8 instances."""
+    buffer 4-16 rows; FP64 or FP32 flux): one graph launch per slow step
+    (mprk_step_batch; in the form the tuning table picks: the persistent
+    kernel, or for FP32 flux the per-stage launches) against the same
+    instances stepped one after another with mprk_step on the same stream,
+    and the two paths' results from the same start compared bitwise on 8
+    instances. FP32 flux adds one 4096 x 2048 instance stepped both ways."""
     import torch
     wls = W.batched_256(count=count)
     stream = torch.cuda.Stream()
@@ -541,6 +543,14 @@ def measure_batched(M, T, precision: str, steps: int, warmup: int, count: int = 
                 "alu_peak_source": "FP32 unit count x max clock (nominal)"}
     for i in insts:
         i.close()
+    launch = M.mprk_tune_lookup(0 if fp64 else 1, cells / len(wls))
+    if launch["tiles_per_item"] == 0:
+        # per-stage form: each instance group launches its stages and its
+        # completions (at most as many stages as the largest m gives)
+        groups = min(launch["ctas_per_sm"] or 2, len(wls))
+        kernels = groups * (2 * max(wl.m for wl in wls) + 1)
+    else:
+        kernels = 1
     rec = {"value": value, "unit": "cell-stages/s", "steps": steps, "warmup": warmup,
            "ms_per_step": t_batch / steps,
            "dtype": "f32 flux / f64 accumulate" if precision == "fp32flux" else "f64",
@@ -550,11 +560,47 @@ def measure_batched(M, T, precision: str, steps: int, warmup: int, count: int = 
                                 "bitwise_equal": same, "max_rel_diff": maxrel,
                                 "plain_ms_per_step": t_plain / steps,
                                 "plain": "each instance's own captured step graph (mprk_step), one after another"},
-           "launch": M.mprk_tune_lookup(0 if fp64 else 1, cells / len(wls)),
-           "roofline": roof, "gpu_launches": steps, "clocks": sampler.summary()}
+           "launch": launch,
+           "roofline": roof, "gpu_launches": steps * kernels,
+           "gpu_launches_note": "kernels per slow step x steps (upper bound for the per-stage form)",
+           "clocks": sampler.summary()}
     if tuned is not None:
         rec["tuned_launch"] = tuned
+    if not fp64:
+        rec["one_large_instance"] = one_large_batched(M, T, steps, warmup)
     return rec
+
+
+def one_large_batched(M, T, steps: int, warmup: int) -> dict:
+    """One 4096 x 2048 FP32-flux instance (the mixed workload's grid, m = 8):
+    slow steps through mprk_step_batch (a batch of one) against mprk_step,
+    and the two results from the same start after one step compared."""
+    import torch
+    wl = W.mixed_4096()
+    g = wl.grid
+    cfg = M.mprk_config_default(g.nx, g.nS, g.nB, g.nF, wl.m)
+    cfg.precision = M.MPRK_FP32FLUX
+    q0 = wl.initial_state()
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    with M.Instance(cfg, q0, stream=sp) as inst:
+        cs = inst.info()["cell_stages_per_step"]
+        M.mprk_step_batch([inst.h], warmup)
+        inst.step(warmup)
+        t_b = T.time_region(sp, lambda: M.mprk_step_batch([inst.h], steps))
+        t_s = T.time_region(sp, lambda: inst.step(steps))
+        inst.set_state(q0)
+        M.mprk_step_batch([inst.h], 1)
+        qb = inst.state()
+        inst.set_state(q0)
+        inst.step(1)
+        qs = inst.state()
+    scale = np.abs(qs).max(axis=(1, 2))
+    rel = float((np.abs(qb - qs).max(axis=(1, 2)) / scale).max())
+    return {"workload": "mixed_4096x2048_m8_fp32flux", "steps": steps,
+            "batched": cs * steps / (t_b * 1e-3), "single_instance": cs * steps / (t_s * 1e-3),
+            "batched_over_single": t_s / t_b, "bitwise_equal": bool(np.array_equal(qb, qs)),
+            "max_rel_diff_one_step": rel, "launch": M.mprk_tune_lookup(1, g.nx * g.nz)}
 
 
 def run_batched(args):

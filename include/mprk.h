@@ -164,7 +164,10 @@ int mprk_step_batch(mprk_instance* const* insts, int count, int n_slow_steps);
  * Three choices of the batched launch change no result, only its speed:
  * the stage tiles per work item (1, 2, 4, 8 or 16; G consecutive tiles
  * along x; in FP32 flux 0 stands for the per-stage form, which has no work
- * items), the CTAs per SM (1 to 3), and in FP64 the shape of the stage
+ * items), the CTAs per SM (1 to 3; with the per-stage form, the number of
+ * instance groups, 1, 2 or 4, whose launches run on streams of their own so
+ * that one group's launch tail overlaps another's work), and in FP64 the
+ * shape of the stage
  * tile of the 256-thread CTA: 32 x 8 cells with one thread per cell or
  * 32 x 4 with two (the FP32-flux tile is 32 x 16). Single-instance FP64
  * stage launches (mprk_step) choose among six tile shapes: 32 x 8, 32 x 4
@@ -174,7 +177,8 @@ int mprk_step_batch(mprk_instance* const* insts, int count, int n_slow_steps);
  * A process-wide table keeps the fastest choices measured:
  *  - batches: per precision and size bucket (floor(log2) of the mean cells
  *    per instance); without an entry, in FP64 2 tiles per item, every CTA
- *    that fits and 32 x 8 tiles, in FP32 flux the per-stage form;
+ *    that fits and 32 x 8 tiles, in FP32 flux the per-stage form with two
+ *    instance groups;
  *  - single-instance FP64 stage launches: per size bucket (floor(log2) of
  *    the cells of the launch); without an entry, the shortest tile whose
  *    launch fits in one wave of the GPU's SMs, with two threads per cell,
@@ -184,15 +188,16 @@ int mprk_step_batch(mprk_instance* const* insts, int count, int n_slow_steps);
 
 /* Time every batch choice on these instances (reps batched slow steps each
  * after one warm-up step), record the fastest in the table and return it
- * in out: {tiles per item (0: the per-stage form), CTAs per SM (0 with the
- * per-stage form), ms per slow step, tile rows}.
+ * in out: {tiles per item (0: the per-stage form), CTAs per SM (instance
+ * groups with the per-stage form), ms per slow step, tile rows}.
  * The instances' states and step counts are restored afterwards.
  * Synchronises. Errors: MPRK_EINVAL, MPRK_ENOMEM, MPRK_ECUDA. */
 int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out[4]);
 
 /* The table's batch choice for a precision and a mean instance size in
  * cells: writes it and returns 1, or writes the defaults (ctas_per_sm 0:
- * every CTA that fits; group 0 in FP32 flux: the per-stage form) and
+ * every CTA that fits, or two instance groups; group 0 in FP32 flux: the
+ * per-stage form) and
  * returns 0. tile_rows: 8 or 4 in FP64 (one or two threads per cell), 16 in
  * FP32 flux. Needs no device. */
 int mprk_tune_lookup(int precision, double mean_cells, int* group, int* ctas_per_sm, int* tile_rows);

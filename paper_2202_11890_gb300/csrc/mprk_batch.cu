@@ -47,6 +47,37 @@ using namespace mprk;
 // ---------------------------------------------------------------------------
 namespace {
 
+// Streams and events for the groups of the per-stage form beyond the first
+// (which runs on the batch's own stream).
+struct WaveStreams {
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> ev;  // [0] the fork, [g] group g's join
+  cudaError_t ensure(int groups) {
+    while ((int)aux.size() < groups - 1) {
+      cudaStream_t st;
+      cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+      aux.push_back(st);
+    }
+    while ((int)ev.size() < groups) {
+      cudaEvent_t e0;
+      cudaError_t e = cudaEventCreateWithFlags(&e0, cudaEventDisableTiming);
+      if (e != cudaSuccess) return e;
+      ev.push_back(e0);
+    }
+    return cudaSuccess;
+  }
+  void release() {
+    for (cudaStream_t st : aux) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    aux.clear();
+    ev.clear();
+  }
+};
+
 struct Plan {
   std::vector<const void*> key;
   int precision = 0;
@@ -65,7 +96,8 @@ struct Plan {
   int* d_ctr = nullptr;  // [0] next, [1] abort, [2..] counters
   int form = 0;                   // 0 persistent launch, 1 per-stage launches
   StageWork* d_work = nullptr;    // per-stage form: the launches' work lists
-  std::vector<int> off;           // launch s lists entries off[s] .. off[s+1]
+  std::vector<std::vector<int>> off;  // per group: launch s lists entries off[g][s] .. off[g][s+1]
+  WaveStreams ws;                 // the groups' streams (per-stage form)
   cudaGraphExec_t exec = nullptr;
   cudaStream_t stream = nullptr;
   long long wait_cycles = 0;
@@ -81,7 +113,8 @@ std::vector<Plan*> g_plans;
 // (floor(log2) of the mean cells per instance), the fastest pair
 // mprk_batch_tune measured, with the name of the GPU it ran on. Plans
 // without an entry take the defaults (batch_group tiles, every CTA that fits).
-// Tiles per item 0 stands for the per-stage form of FP32-flux batches.
+// Tiles per item 0 stands for the per-stage form of FP32-flux batches; its
+// CTAs per SM field then holds the number of instance groups (0: two).
 struct TuneVal {
   int group, per_sm;
   double ms;
@@ -146,6 +179,7 @@ void free_plan(Plan* p) {
   cudaFree(p->d_items);
   cudaFree(p->d_ctr);
   cudaFree(p->d_work);
+  p->ws.release();
   delete p;
 }
 
@@ -200,47 +234,96 @@ void build_items(const std::vector<BatchInst>& hinst, int G, int rows, std::vect
   *cell_stages = cs;
 }
 
-// The work lists of the per-stage form: launch s (s = 0 .. the most stages
-// of any instance, minus one) lists the (stage argument index, tile) pairs
-// of every instance that has a stage s, and a last launch the (instance,
-// chunk) pairs of every instance's step completion. Launch s takes the
-// entries off[s] .. off[s+1]. Needs the args_base of args_table.
-void build_wave(const std::vector<BatchInst>& hinst, std::vector<StageWork>& work, std::vector<int>& off,
-                long long* cell_stages) {
-  int max_stages = 0;
-  for (const BatchInst& bi : hinst) max_stages = std::max(max_stages, bi.g.s * bi.g.m);
-  long long cs = 0;
+// The work lists of the per-stage form. The instances are split into
+// `groups` groups of about equal work (largest first, each to the least
+// loaded group); each group's launches go on a stream of their own, so that
+// one group's launch tail overlaps another group's work. Launch s of a group
+// (s = 0 .. the most stages of its instances, minus one) lists the (stage
+// argument index, tile) pairs of its instances that have a stage s, and a
+// last launch the (instance, chunk) pairs of their step completions. Launch
+// s of group g takes the entries off[g][s] .. off[g][s+1]. Needs the
+// args_base of args_table.
+void build_wave(const std::vector<BatchInst>& hinst, int groups, std::vector<StageWork>& work,
+                std::vector<std::vector<int>>& off, long long* cell_stages) {
+  const int n = (int)hinst.size();
+  groups = std::max(1, std::min(groups, n));
+  auto step_cs = [&](int j) {
+    long long cs = 0;
+    for (int st = 0; st < hinst[j].g.s * hinst[j].g.m; st++)
+      cs += (long long)(hinst[j].g.nz - batch_stage_args(hinst[j], st, MTZ).row0) * hinst[j].g.nx;
+    return cs;
+  };
+  std::vector<int> order(n);
+  std::vector<long long> cs(n);
+  for (int j = 0; j < n; j++) {
+    order[j] = j;
+    cs[j] = step_cs(j);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cs[x] > cs[y]; });
+  std::vector<std::vector<int>> members(groups);
+  std::vector<long long> load(groups, 0);
+  for (int j : order) {
+    const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    members[g].push_back(j);
+    load[g] += cs[j];
+  }
+  long long total = 0;
   work.clear();
-  off.assign(1, 0);
-  for (int st = 0; st < max_stages; st++) {
-    for (const BatchInst& bi : hinst) {
-      if (st >= bi.g.s * bi.g.m) continue;
-      const StageArgs a = batch_stage_args(bi, st, MTZ);
-      const int nt = stage_tiles(a);
-      for (int t = 0; t < nt; t++) work.push_back({bi.args_base + st, t});
-      cs += (long long)(bi.g.nz - a.row0) * bi.g.nx;
+  off.assign(groups, std::vector<int>());
+  for (int g = 0; g < groups; g++) {
+    std::sort(members[g].begin(), members[g].end());  // instance order within a launch
+    int max_stages = 0;
+    for (int j : members[g]) max_stages = std::max(max_stages, hinst[j].g.s * hinst[j].g.m);
+    off[g].push_back((int)work.size());
+    for (int st = 0; st < max_stages; st++) {
+      for (int j : members[g]) {
+        const BatchInst& bi = hinst[j];
+        if (st >= bi.g.s * bi.g.m) continue;
+        const int nt = stage_tiles(batch_stage_args(bi, st, MTZ));
+        for (int t = 0; t < nt; t++) work.push_back({bi.args_base + st, t});
+      }
+      off[g].push_back((int)work.size());
     }
-    off.push_back((int)work.size());
+    for (int j : members[g]) {
+      const Geom& gm = hinst[j].g;
+      const int rows = ((gm.m & 1) || hinst[j].b.dA) ? gm.nz : gm.n1_r;  // as finalize_chunk
+      const long long cells = 4LL * rows * gm.nx;
+      const int chunks = (int)((cells + FIN_CHUNK - 1) / FIN_CHUNK);
+      for (int c = 0; c < chunks; c++) work.push_back({j, c});
+      total += cs[j];
+    }
+    off[g].push_back((int)work.size());
   }
-  for (int j = 0; j < (int)hinst.size(); j++) {
-    const Geom& g = hinst[j].g;
-    const int rows = ((g.m & 1) || hinst[j].b.dA) ? g.nz : g.n1_r;  // as finalize_chunk
-    const long long total = 4LL * rows * g.nx;
-    const int chunks = (int)((total + FIN_CHUNK - 1) / FIN_CHUNK);
-    for (int c = 0; c < chunks; c++) work.push_back({j, c});
-  }
-  off.push_back((int)work.size());
-  *cell_stages = cs;
+  *cell_stages = total;
 }
 
-// Launches of one slow step in the per-stage form on stream s.
-void wave_step(const std::vector<int>& off, const BatchInst* d_insts, const StageArgs* d_args,
-               const StageWork* d_work, cudaStream_t s) {
-  const int launches = (int)off.size() - 1;
-  for (int st = 0; st + 1 < launches; st++)
-    wave_launch_stage(st & 1, off[st + 1] - off[st], d_args, d_work + off[st], s);
-  wave_launch_finalize(off[launches] - off[launches - 1], d_insts, d_work + off[launches - 1], s);
+// Launches of one slow step in the per-stage form: group 0 on stream s, the
+// others forked from s onto their own streams and joined back into s.
+void wave_step(const std::vector<std::vector<int>>& off, const BatchInst* d_insts, const StageArgs* d_args,
+               const StageWork* d_work, cudaStream_t s, WaveStreams& ws) {
+  const int groups = (int)off.size();
+  if (groups > 1) {
+    cudaEventRecord(ws.ev[0], s);
+    for (int g = 1; g < groups; g++) cudaStreamWaitEvent(ws.aux[g - 1], ws.ev[0], 0);
+  }
+  for (int g = 0; g < groups; g++) {
+    const cudaStream_t st = g == 0 ? s : ws.aux[g - 1];
+    const std::vector<int>& o = off[g];
+    const int launches = (int)o.size() - 1;
+    for (int k = 0; k + 1 < launches; k++)
+      wave_launch_stage(k & 1, o[k + 1] - o[k], d_args, d_work + o[k], st);
+    wave_launch_finalize(o[launches] - o[launches - 1], d_insts, d_work + o[launches - 1], st);
+  }
+  for (int g = 1; g < groups; g++) {
+    cudaEventRecord(ws.ev[g], ws.aux[g - 1]);
+    cudaStreamWaitEvent(s, ws.ev[g], 0);
+  }
 }
+
+// Instance groups of the per-stage form: the tuned count (the table's CTAs
+// per SM field holds it for this form), else two.
+constexpr int WAVE_GROUPS_DEFAULT = 2;
+int wave_groups(int want) { return want > 0 ? want : WAVE_GROUPS_DEFAULT; }
 
 // The form of a batch: 1 (per-stage launches) for FP32-flux batches with
 // tiles per item 0, else 0 (the persistent launch).
@@ -296,7 +379,7 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
   p->form = batch_form(p->precision, group);
   if (p->form == 1) {
     std::vector<StageWork> work;
-    build_wave(hinst, work, p->off, &p->cell_stages);
+    build_wave(hinst, wave_groups(per_sm_want), work, p->off, &p->cell_stages);
     if ((e = cudaMalloc(&p->d_insts, sizeof(BatchInst) * count)) != cudaSuccess ||
         (e = cudaMalloc(&p->d_args, sizeof(StageArgs) * hargs.size())) != cudaSuccess ||
         (e = cudaMalloc(&p->d_work, sizeof(StageWork) * work.size())) != cudaSuccess) {
@@ -309,14 +392,14 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
             cudaSuccess ||
         (e = cudaMemcpy(p->d_work, work.data(), sizeof(StageWork) * work.size(), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
-        (e = wave_prepare()) != cudaSuccess) {
+        (e = wave_prepare()) != cudaSuccess || (e = p->ws.ensure((int)p->off.size())) != cudaSuccess) {
       free_plan(p);
       return bfail(MPRK_ECUDA, std::string("batch plan upload: ") + cudaGetErrorString(e));
     }
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      wave_step(p->off, p->d_insts, p->d_args, p->d_work, p->stream);
+      wave_step(p->off, p->d_insts, p->d_args, p->d_work, p->stream, p->ws);
       cudaError_t el = cudaGetLastError();
       e = cudaStreamEndCapture(p->stream, &graph);
       if (el != cudaSuccess) e = el;
@@ -516,7 +599,8 @@ struct BatchRunner {
   int form = 0;  // as Plan::form
   StageWork* d_work = nullptr;
   size_t cap_work = 0;
-  std::vector<int> off;
+  std::vector<std::vector<int>> off;
+  WaveStreams ws;
 };
 
 BatchRunner* runner_create(int precision, cudaStream_t stream) {
@@ -533,6 +617,7 @@ void runner_destroy(BatchRunner* r) {
   if (r->d_items) cudaFreeAsync(r->d_items, r->stream);
   if (r->d_ctr) cudaFreeAsync(r->d_ctr, r->stream);
   if (r->d_work) cudaFreeAsync(r->d_work, r->stream);
+  r->ws.release();
   delete r;
 }
 
@@ -585,7 +670,7 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
       args_table(hinst, MTZ, hargs);
       std::vector<StageWork> work;
       long long cs = 0;
-      build_wave(hinst, work, r->off, &cs);
+      build_wave(hinst, wave_groups(per_sm_want), work, r->off, &cs);
       e = grow(&r->d_insts, &r->cap_insts, (size_t)count, r->stream);
       if (e == cudaSuccess) e = grow(&r->d_args, &r->cap_args, hargs.size(), r->stream);
       if (e == cudaSuccess) e = grow(&r->d_work, &r->cap_work, work.size(), r->stream);
@@ -600,6 +685,7 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
         e = cudaMemcpyAsync(r->d_work, work.data(), sizeof(StageWork) * work.size(), cudaMemcpyHostToDevice,
                             r->stream);
       if (e == cudaSuccess) e = wave_prepare();
+      if (e == cudaSuccess) e = r->ws.ensure((int)r->off.size());
       if (e != cudaSuccess) return bfail(MPRK_ECUDA, std::string("batch runner upload: ") + cudaGetErrorString(e));
       r->key.assign(insts, insts + count);
       r->cell_stages = cs;
@@ -652,7 +738,7 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
   }
   cudaError_t e;
   if (r->form == 1) {
-    wave_step(r->off, r->d_insts, r->d_args, r->d_work, r->stream);
+    wave_step(r->off, r->d_insts, r->d_args, r->d_work, r->stream, r->ws);
   } else {
     BatchArgs A;
     A.insts = r->d_insts;
@@ -751,11 +837,12 @@ int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out
     if ((rc = instance_view(insts[0], &g, &b, &prec0, &st, &sw))) prec0 = 0;
   }
   const std::vector<int> row_choices = prec0 == 0 ? std::vector<int>{TZ, TZ / 2} : std::vector<int>{MTZ};
-  // FP32 flux also times the per-stage form (tiles per item 0; one run)
+  // FP32 flux also times the per-stage form (tiles per item 0) with 1, 2 or
+  // 4 instance groups (held in the CTAs per SM field)
   const std::vector<int> groups = prec0 == 0 ? std::vector<int>{1, 2, 4, 8, 16} : std::vector<int>{0, 1, 2, 4, 8, 16};
   for (int R : row_choices) {
     for (int G : groups) {
-      for (int c = 1; c <= (G == 0 ? 1 : 3) && rc == MPRK_OK; c++) {
+      for (int c = 1; c <= (G == 0 ? 4 : 3) && rc == MPRK_OK; c += (G == 0 && c == 2) ? 2 : 1) {
         Plan* p = nullptr;
         rc = build_plan(insts, count, 2000000000LL, -1, -1, nullptr, G, c, R, &p);
         if (rc) break;
@@ -776,7 +863,7 @@ int mprk_batch_tune(mprk_instance* const* insts, int count, int reps, double out
         if (rc == MPRK_OK && ms / reps < best_ms) {
           best_ms = ms / reps;
           best_g = G;
-          best_c = G == 0 ? 0 : c;
+          best_c = c;
           best_r = R;
         }
       }

@@ -151,7 +151,7 @@ def test_tuned_launch_leaves_states_and_results_unchanged(precision, tmp_path):
         before = [i.state() for i in a]
         best = M.mprk_batch_tune([i.h for i in a], reps=2)
         if best["tiles_per_item"] == 0:  # the per-stage form (FP32 flux only)
-            assert precision == 1 and best["ctas_per_sm"] == 0
+            assert precision == 1 and best["ctas_per_sm"] in (1, 2, 4)  # instance groups
         else:
             assert best["tiles_per_item"] in (1, 2, 4, 8, 16) and 1 <= best["ctas_per_sm"] <= 3
         assert best["ms_per_step"] > 0
