@@ -149,12 +149,50 @@ __global__ void __launch_bounds__(MIXED_THREADS, 3)
                               nullptr, nullptr);
 }
 
-// The step completions of the per-stage form: one CTA per (instance, chunk).
+// Step completion of rows r0 .. r0 + fin_rows(nx) - 1 of component c of one
+// 2-D instance (the rows the single-instance completion covers): q_{n+1}
+// of S and B rows (and of F rows after an odd m) into the state buffer,
+// and in FP32-flux mode the float shadow of every row. The threads walk the
+// rows' cells two at a time, with 16-byte accesses where the buffers allow.
+__device__ __forceinline__ int fin_rows(int nx) { return max(1, FIN_CHUNK / nx); }
+__device__ __forceinline__ void finalize_rows(const Geom& g, const Bufs& b, int c, int r0) {
+  const bool m_odd = g.m & 1;
+  const bool mixed = b.dA != nullptr;
+  const int k_hi = min(r0 + fin_rows(g.nx), (m_odd || mixed) ? g.nz : g.n1_r);
+  auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  const bool vec = (g.pitch % 2 == 0) && a16(b.qA) && a16(b.qB) && a16(b.accS) && a16(b.accB) &&
+                   (!mixed || (reinterpret_cast<uintptr_t>(b.dA) & 7u) == 0);
+  const int hx = (g.nx + 1) / 2;  // cell pairs per row
+  for (int e = threadIdx.x; e < (k_hi - r0) * hx; e += blockDim.x) {
+    const int k = r0 + e / hx, i = 2 * (e - (k - r0) * hx);
+    const size_t o = ((size_t)c * g.nz + k) * g.pitch;
+    const double* src;
+    if (k < g.nS_r) src = b.accS + ((size_t)c * g.nS_r + k) * g.pitch;
+    else if (k < g.n1_r) src = b.accB + ((size_t)c * (g.n1_r - g.nS_r) + (k - g.nS_r)) * g.pitch;
+    else src = (m_odd ? b.qB : b.qA) + o;
+    const bool store_q = k < g.n1_r || m_odd;
+    const double ref = mixed ? (double)b.rowc[4 * k + c] : 0.0;
+    if (vec && i + 1 < g.nx) {
+      const double2 v = *reinterpret_cast<const double2*>(src + i);
+      if (store_q) *reinterpret_cast<double2*>(b.qA + o + i) = v;
+      if (mixed) *reinterpret_cast<float2*>(b.dA + o + i) = make_float2(narrow(v.x - ref), narrow(v.y - ref));
+    } else {
+      for (int j = i; j < i + 2 && j < g.nx; j++) {
+        const double v = src[j];
+        if (store_q) b.qA[o + j] = v;
+        if (mixed) b.dA[o + j] = narrow(v - ref);
+      }
+    }
+  }
+}
+
+// The step completions of the per-stage form: one CTA per (instance, band of
+// rows of one component); tile = 4 r0 + c.
 __global__ void __launch_bounds__(NTHREADS) wave_finalize(const BatchInst* __restrict__ insts,
                                                           const StageWork* __restrict__ work) {
   const StageWork w = work[blockIdx.x];
   const BatchInst& I = insts[w.args];
-  finalize_chunk(I.g, I.b, w.tile);
+  finalize_rows(I.g, I.b, w.tile & 3, w.tile >> 2);
 }
 
 }  // namespace mprk

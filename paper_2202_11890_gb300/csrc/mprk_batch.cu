@@ -241,7 +241,9 @@ void build_items(const std::vector<BatchInst>& hinst, int G, int rows, std::vect
 // (s = 0 .. the most stages of its instances, minus one) lists the (stage
 // argument index, tile) pairs of its instances that have a stage s, and a
 // last launch the (instance, chunk) pairs of their step completions. Launch
-// s of group g takes the entries off[g][s] .. off[g][s+1]. Needs the
+// s of group g takes the entries off[g][s] .. off[g][s+1] (a completion
+// entry holds the instance and 4 r0 + c: the band of rows from r0 of
+// component c). Needs the
 // args_base of args_table.
 void build_wave(const std::vector<BatchInst>& hinst, int groups, std::vector<StageWork>& work,
                 std::vector<std::vector<int>>& off, long long* cell_stages) {
@@ -285,11 +287,12 @@ void build_wave(const std::vector<BatchInst>& hinst, int groups, std::vector<Sta
       off[g].push_back((int)work.size());
     }
     for (int j : members[g]) {
+      // bands of rows of one component (finalize_rows in batch_kernel.cuh)
       const Geom& gm = hinst[j].g;
-      const int rows = ((gm.m & 1) || hinst[j].b.dA) ? gm.nz : gm.n1_r;  // as finalize_chunk
-      const long long cells = 4LL * rows * gm.nx;
-      const int chunks = (int)((cells + FIN_CHUNK - 1) / FIN_CHUNK);
-      for (int c = 0; c < chunks; c++) work.push_back({j, c});
+      const int rows = ((gm.m & 1) || hinst[j].b.dA) ? gm.nz : gm.n1_r;
+      const int band = std::max(1, FIN_CHUNK / gm.nx);
+      for (int c = 0; c < 4; c++)
+        for (int r0 = 0; r0 < rows; r0 += band) work.push_back({j, 4 * r0 + c});
       total += cs[j];
     }
     off[g].push_back((int)work.size());
