@@ -692,7 +692,8 @@ def measure_served(M, rate: float, n_warm: int, n_meas: int, budget_gb: float, s
            "dtype": "f32 flux / f64 accumulate",
            "config": {"workload": "served_poisson_fp32flux", "rate_hz": rate, "requests": n_meas,
                       "budget_gb": budget_gb, "max_slots": slots,
-                      "solo_cells": solo_cells if solo_cells else M.MPRK_SOLO_CELLS_DEFAULT},
+                      "solo_cells": solo_cells if solo_cells else
+                      f"default: {M.MPRK_SOLO_CELLS_DEFAULT} for FP64 requests, FP32-flux requests all batched"},
            "served": {"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                       "mean_latency_s": float(lat.mean()), "errors": errors,
                       "offered_cell_stages_per_s": offered, "achieved_over_offered": value / offered,

@@ -390,12 +390,15 @@ typedef struct {
   int solo_cells;             /* instances of at least this many cells step by
                                  their own stage launches on side streams, not
                                  in the batched launch: 0 = the default
-                                 (MPRK_SOLO_CELLS_DEFAULT), -1 = never        */
+                                 (MPRK_SOLO_CELLS_DEFAULT for FP64 requests;
+                                 FP32-flux requests all batched), -1 = never */
 } mprk_server_config;
 
 /* 2^18 cells, e.g. 512 x 512: from there on an instance's stage launches
  * cover the GPU's SMs about once or more, and its own kernels beat the
- * batch kernel. */
+ * persistent batch kernel. The per-stage form of FP32-flux batches runs
+ * such instances within the batch about as fast, with lower latency for
+ * the mix (measured), so the default applies to FP64 requests only. */
 #define MPRK_SOLO_CELLS_DEFAULT 262144
 
 #define MPRK_REQ_PENDING 1 /* queued, not admitted          */
@@ -414,9 +417,9 @@ typedef struct {
 
 /* Start a server thread on a device. It admits queued requests in arrival
  * order while a slot is free and the HBM ledger has room, advances all
- * resident instances together by one slow step at a time (the persistent
- * kernel of mprk_step_batch, one launch per precision, for the instances
- * below cfg->solo_cells cells; the larger ones by the same stage kernels as
+ * resident instances together by one slow step at a time (the batched step
+ * of mprk_step_batch per precision, in the form the tuning table picks, for
+ * the instances below cfg->solo_cells cells; the larger ones by the same stage kernels as
  * mprk_step, on side streams that run beside each other), and retires each
  * request when it reaches its step count. Either way a request's result is
  * that of the same solve alone: bitwise in FP64, within float rounding in

@@ -117,6 +117,7 @@ struct mprk_server {
   cudaStream_t side[NSIDE] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join[NSIDE] = {nullptr, nullptr, nullptr, nullptr};
   long long solo_cells = 0;  // instances of at least this many cells step alone (0: none)
+  bool solo_fp64_only = false;  // the default threshold: FP32-flux instances all batched
   BatchRunner* runner[2] = {nullptr, nullptr};
   PinnedPool pool;
   // counters (read under mu)
@@ -245,7 +246,9 @@ void server_loop(mprk_server* S) {
       cudaEventRecord(beg_ev[slot], S->compute);
       std::vector<mprk_instance*> group[2], alone;
       for (Request* r : S->resident) {
-        if (S->solo_cells > 0 && instance_cells(r->inst) >= S->solo_cells) alone.push_back(r->inst);
+        if (S->solo_cells > 0 && instance_cells(r->inst) >= S->solo_cells &&
+            !(S->solo_fp64_only && r->cfg.precision != MPRK_FP64))
+          alone.push_back(r->inst);
         else group[r->cfg.precision == MPRK_FP64 ? 0 : 1].push_back(r->inst);
       }
       int err = 0;
@@ -423,6 +426,7 @@ int mprk_server_create(const mprk_server_config* cfg, mprk_server** out) {
   mprk_server* S = new mprk_server();
   S->cfg = *cfg;
   S->solo_cells = cfg->solo_cells == 0 ? MPRK_SOLO_CELLS_DEFAULT : (cfg->solo_cells < 0 ? 0 : cfg->solo_cells);
+  S->solo_fp64_only = cfg->solo_cells == 0;
   S->t0 = Clock::now();
   S->th = std::thread(server_loop, S);
   *out = S;

@@ -371,7 +371,8 @@ def mprk_step_static(cfg: mprk_config, q_dev, n: int, stream=None) -> None:
 def mprk_server_create(hbm_budget_bytes: int, max_slots: int = 1024, device: int = 0,
                        max_queue: int = 1 << 20, solo_cells: int = 0) -> int:
     """solo_cells: instances of at least this many cells step alone on side
-    streams (0: MPRK_SOLO_CELLS_DEFAULT, -1: every instance in the batch)."""
+    streams (0: MPRK_SOLO_CELLS_DEFAULT for FP64 requests, FP32-flux
+    requests all batched; -1: every instance in the batch)."""
     cfg = mprk_server_config(hbm_budget_bytes=int(hbm_budget_bytes), max_slots=max_slots, device=device,
                              max_queue=max_queue, solo_cells=int(solo_cells))
     h = C.c_void_p()
