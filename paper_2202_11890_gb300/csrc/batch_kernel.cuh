@@ -138,11 +138,13 @@ __global__ void __launch_bounds__(batch_threads(PREC), 3) batch_kernel(const Bat
 // waits. With no persistent loop around it, the FP32-flux tile fits its
 // registers without spilling while it reads its arguments from the table in
 // global memory.
+// single >= 0: every CTA of the launch takes stage arguments `single` and
+// tile blockIdx.x (a launch over one instance: no work-list load).
 template <int PAR>
 __global__ void __launch_bounds__(MIXED_THREADS, 3)
-    wave_stage_mixed(const StageArgs* __restrict__ tab, const StageWork* __restrict__ work) {
+    wave_stage_mixed(const StageArgs* __restrict__ tab, const StageWork* __restrict__ work, int single) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const StageWork w = work[blockIdx.x];
+  const StageWork w = single >= 0 ? StageWork{single, (int)blockIdx.x} : work[blockIdx.x];
   const StageArgs& a = tab[w.args];
   const int tzi = w.tile / a.tiles_x, txi = w.tile - tzi * a.tiles_x;
   (void)stage_tile_mixed<PAR>(a, a.row0 + tzi * MTZ, txi * TX, *reinterpret_cast<MixedTileSmem*>(smem_raw),

@@ -74,7 +74,8 @@ void batch_launch(int prec, int rows, int grid, size_t smem, cudaStream_t s, con
 // parity `parity`, and one completion launch; cudaFuncSetAttribute first
 // (wave_prepare).
 cudaError_t wave_prepare();
-void wave_launch_stage(int parity, int grid, const StageArgs* tab, const StageWork* work, cudaStream_t s);
+void wave_launch_stage(int parity, int grid, const StageArgs* tab, const StageWork* work, int single,
+                       cudaStream_t s);
 void wave_launch_finalize(int grid, const BatchInst* insts, const StageWork* work, cudaStream_t s);
 
 }  // namespace mprk

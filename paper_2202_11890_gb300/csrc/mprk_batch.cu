@@ -47,6 +47,20 @@ using namespace mprk;
 // ---------------------------------------------------------------------------
 namespace {
 
+// What the per-stage form launches from: the work lists and their bounds,
+// and for the launches over a single instance (single[g][k] >= 0: its stage
+// argument index) the host copies of the arguments and tensor maps. Those
+// launches take the single-instance FP32-flux kernel (launch_stage):
+// arguments as kernel parameters and tensor-copied tiles, the code mprk_step
+// runs, so that an instance alone in a launch steps exactly as it would
+// alone, and as fast.
+struct WaveLaunches {
+  std::vector<std::vector<int>> off, single;
+  std::vector<StageArgs> h_args;  // the argument table (host copy)
+  std::vector<int> args_inst;     // instance of each argument entry
+  std::vector<StageMaps> h_maps;  // per instance
+};
+
 // Streams and events for the groups of the per-stage form beyond the first
 // (which runs on the batch's own stream).
 struct WaveStreams {
@@ -96,7 +110,7 @@ struct Plan {
   int* d_ctr = nullptr;  // [0] next, [1] abort, [2..] counters
   int form = 0;                   // 0 persistent launch, 1 per-stage launches
   StageWork* d_work = nullptr;    // per-stage form: the launches' work lists
-  std::vector<std::vector<int>> off;  // per group: launch s lists entries off[g][s] .. off[g][s+1]
+  WaveLaunches wl;                 // per-stage form: launch bounds and host tables
   WaveStreams ws;                 // the groups' streams (per-stage form)
   cudaGraphExec_t exec = nullptr;
   cudaStream_t stream = nullptr;
@@ -246,7 +260,8 @@ void build_items(const std::vector<BatchInst>& hinst, int G, int rows, std::vect
 // component c). Needs the
 // args_base of args_table.
 void build_wave(const std::vector<BatchInst>& hinst, int groups, std::vector<StageWork>& work,
-                std::vector<std::vector<int>>& off, long long* cell_stages) {
+                std::vector<std::vector<int>>& off, std::vector<std::vector<int>>& single,
+                long long* cell_stages) {
   const int n = (int)hinst.size();
   groups = std::max(1, std::min(groups, n));
   auto step_cs = [&](int j) {
@@ -272,19 +287,24 @@ void build_wave(const std::vector<BatchInst>& hinst, int groups, std::vector<Sta
   long long total = 0;
   work.clear();
   off.assign(groups, std::vector<int>());
+  single.assign(groups, std::vector<int>());
   for (int g = 0; g < groups; g++) {
     std::sort(members[g].begin(), members[g].end());  // instance order within a launch
     int max_stages = 0;
     for (int j : members[g]) max_stages = std::max(max_stages, hinst[j].g.s * hinst[j].g.m);
     off[g].push_back((int)work.size());
     for (int st = 0; st < max_stages; st++) {
+      int n_in = 0, only = -1;
       for (int j : members[g]) {
         const BatchInst& bi = hinst[j];
         if (st >= bi.g.s * bi.g.m) continue;
         const int nt = stage_tiles(batch_stage_args(bi, st, MTZ));
         for (int t = 0; t < nt; t++) work.push_back({bi.args_base + st, t});
+        n_in++;
+        only = bi.args_base + st;
       }
       off[g].push_back((int)work.size());
+      single[g].push_back(n_in == 1 ? only : -1);  // a launch over one instance reads no work list
     }
     for (int j : members[g]) {
       // bands of rows of one component (finalize_rows in batch_kernel.cuh)
@@ -300,10 +320,28 @@ void build_wave(const std::vector<BatchInst>& hinst, int groups, std::vector<Sta
   *cell_stages = total;
 }
 
+// The host copies of the argument table and each instance's tensor maps.
+cudaError_t wave_host_tables(const std::vector<BatchInst>& hinst, const std::vector<StageArgs>& hargs,
+                             WaveLaunches& L) {
+  L.h_args = hargs;
+  L.args_inst.assign(hargs.size(), 0);
+  L.h_maps.assign(hinst.size(), StageMaps{});
+  for (size_t j = 0; j < hinst.size(); j++) {
+    for (int st = 0; st < hinst[j].g.s * hinst[j].g.m; st++) {
+      L.args_inst[hinst[j].args_base + st] = (int)j;
+      L.h_args[hinst[j].args_base + st].status = hinst[j].status;
+    }
+    cudaError_t e = make_stage_maps(hinst[j].g, hinst[j].b, &L.h_maps[j]);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Launches of one slow step in the per-stage form: group 0 on stream s, the
 // others forked from s onto their own streams and joined back into s.
-void wave_step(const std::vector<std::vector<int>>& off, const BatchInst* d_insts, const StageArgs* d_args,
-               const StageWork* d_work, cudaStream_t s, WaveStreams& ws) {
+void wave_step(const WaveLaunches& L, const BatchInst* d_insts, const StageArgs* d_args, const StageWork* d_work,
+               cudaStream_t s, WaveStreams& ws) {
+  const std::vector<std::vector<int>>& off = L.off;
   const int groups = (int)off.size();
   if (groups > 1) {
     cudaEventRecord(ws.ev[0], s);
@@ -313,8 +351,13 @@ void wave_step(const std::vector<std::vector<int>>& off, const BatchInst* d_inst
     const cudaStream_t st = g == 0 ? s : ws.aux[g - 1];
     const std::vector<int>& o = off[g];
     const int launches = (int)o.size() - 1;
-    for (int k = 0; k + 1 < launches; k++)
-      wave_launch_stage(k & 1, o[k + 1] - o[k], d_args, d_work + o[k], st);
+    for (int k = 0; k + 1 < launches; k++) {
+      const int one = L.single[g][k];
+      if (one >= 0)
+        launch_stage(L.h_args[one], 1, o[k + 1] - o[k], st, &L.h_maps[L.args_inst[one]]);
+      else
+        wave_launch_stage(k & 1, o[k + 1] - o[k], d_args, d_work + o[k], -1, st);
+    }
     wave_launch_finalize(o[launches] - o[launches - 1], d_insts, d_work + o[launches - 1], st);
   }
   for (int g = 1; g < groups; g++) {
@@ -382,7 +425,11 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
   p->form = batch_form(p->precision, group);
   if (p->form == 1) {
     std::vector<StageWork> work;
-    build_wave(hinst, wave_groups(per_sm_want), work, p->off, &p->cell_stages);
+    build_wave(hinst, wave_groups(per_sm_want), work, p->wl.off, p->wl.single, &p->cell_stages);
+    if ((e = wave_host_tables(hinst, hargs, p->wl)) != cudaSuccess) {
+      free_plan(p);
+      return bfail(MPRK_ECUDA, std::string("batch plan tensor maps: ") + cudaGetErrorString(e));
+    }
     if ((e = cudaMalloc(&p->d_insts, sizeof(BatchInst) * count)) != cudaSuccess ||
         (e = cudaMalloc(&p->d_args, sizeof(StageArgs) * hargs.size())) != cudaSuccess ||
         (e = cudaMalloc(&p->d_work, sizeof(StageWork) * work.size())) != cudaSuccess) {
@@ -395,14 +442,14 @@ int build_plan(mprk_instance* const* insts, int count, long long wait_cycles, in
             cudaSuccess ||
         (e = cudaMemcpy(p->d_work, work.data(), sizeof(StageWork) * work.size(), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
-        (e = wave_prepare()) != cudaSuccess || (e = p->ws.ensure((int)p->off.size())) != cudaSuccess) {
+        (e = wave_prepare()) != cudaSuccess || (e = p->ws.ensure((int)p->wl.off.size())) != cudaSuccess) {
       free_plan(p);
       return bfail(MPRK_ECUDA, std::string("batch plan upload: ") + cudaGetErrorString(e));
     }
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      wave_step(p->off, p->d_insts, p->d_args, p->d_work, p->stream, p->ws);
+      wave_step(p->wl, p->d_insts, p->d_args, p->d_work, p->stream, p->ws);
       cudaError_t el = cudaGetLastError();
       e = cudaStreamEndCapture(p->stream, &graph);
       if (el != cudaSuccess) e = el;
@@ -602,7 +649,7 @@ struct BatchRunner {
   int form = 0;  // as Plan::form
   StageWork* d_work = nullptr;
   size_t cap_work = 0;
-  std::vector<std::vector<int>> off;
+  WaveLaunches wl;
   WaveStreams ws;
 };
 
@@ -673,7 +720,9 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
       args_table(hinst, MTZ, hargs);
       std::vector<StageWork> work;
       long long cs = 0;
-      build_wave(hinst, wave_groups(per_sm_want), work, r->off, &cs);
+      build_wave(hinst, wave_groups(per_sm_want), work, r->wl.off, r->wl.single, &cs);
+      if ((e = wave_host_tables(hinst, hargs, r->wl)) != cudaSuccess)
+        return bfail(MPRK_ECUDA, std::string("batch runner tensor maps: ") + cudaGetErrorString(e));
       e = grow(&r->d_insts, &r->cap_insts, (size_t)count, r->stream);
       if (e == cudaSuccess) e = grow(&r->d_args, &r->cap_args, hargs.size(), r->stream);
       if (e == cudaSuccess) e = grow(&r->d_work, &r->cap_work, work.size(), r->stream);
@@ -688,7 +737,7 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
         e = cudaMemcpyAsync(r->d_work, work.data(), sizeof(StageWork) * work.size(), cudaMemcpyHostToDevice,
                             r->stream);
       if (e == cudaSuccess) e = wave_prepare();
-      if (e == cudaSuccess) e = r->ws.ensure((int)r->off.size());
+      if (e == cudaSuccess) e = r->ws.ensure((int)r->wl.off.size());
       if (e != cudaSuccess) return bfail(MPRK_ECUDA, std::string("batch runner upload: ") + cudaGetErrorString(e));
       r->key.assign(insts, insts + count);
       r->cell_stages = cs;
@@ -741,7 +790,7 @@ int runner_step(BatchRunner* r, mprk_instance* const* insts, int count, long lon
   }
   cudaError_t e;
   if (r->form == 1) {
-    wave_step(r->off, r->d_insts, r->d_args, r->d_work, r->stream, r->ws);
+    wave_step(r->wl, r->d_insts, r->d_args, r->d_work, r->stream, r->ws);
   } else {
     BatchArgs A;
     A.insts = r->d_insts;

@@ -273,10 +273,11 @@ cudaError_t wave_prepare() {
   return e;
 }
 
-void wave_launch_stage(int parity, int grid, const StageArgs* tab, const StageWork* work, cudaStream_t s) {
+void wave_launch_stage(int parity, int grid, const StageArgs* tab, const StageWork* work, int single,
+                       cudaStream_t s) {
   if (grid <= 0) return;
-  if (parity) wave_stage_mixed<1><<<grid, MIXED_THREADS, sizeof(MixedTileSmem), s>>>(tab, work);
-  else wave_stage_mixed<0><<<grid, MIXED_THREADS, sizeof(MixedTileSmem), s>>>(tab, work);
+  if (parity) wave_stage_mixed<1><<<grid, MIXED_THREADS, sizeof(MixedTileSmem), s>>>(tab, work, single);
+  else wave_stage_mixed<0><<<grid, MIXED_THREADS, sizeof(MixedTileSmem), s>>>(tab, work, single);
 }
 
 void wave_launch_finalize(int grid, const BatchInst* insts, const StageWork* work, cudaStream_t s) {
