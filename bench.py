@@ -75,14 +75,14 @@ def fp64_peak():
 CSRC = os.path.join(ROOT, "paper_2202_11890_gb300", "csrc")
 TRAFFIC = {
     "stage_kernel": {
-        "files": ("stage_tile.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "d9b96663336d9f5c70724c9fa33e47e1393d41992c18a78ca64e4627a4adc318",
-        "bytes_per_step": 1172199936,
+        "files": ("stage_tile.cuh", "fp64_recip.cuh", "mprk_internal.h", "mprk_kernels.cu"),
+        "sha256": "eb96f71da41766e6a56fc6398d7a49b905e8575ace8b46cf96856cb259e008dd",
+        "bytes_per_step": 1171727872,
     },
     "stage_kernel_mixed": {
         "files": ("stage_tile_mixed.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "a1d3563a96699f5f65587509daaa965c18fdf9cad53c19730e0767b2c544457a",
-        "bytes_per_step": 5147348736,
+        "sha256": "70f97e7c7a75239400053bc9d8f307e748da86b7a75da26c9e9f119fa6b11ae3",
+        "bytes_per_step": 5149178880,
     },
 }
 
