@@ -360,8 +360,9 @@ int mprk_selftest_recip(const double* in_dev, int n, double* recip_dev, double* 
  * mode's 1e-5: each call rebuilds the mode's per-row reference state and
  * float shadow from the q_dev it is given, while an instance keeps the
  * reference of its initial state. The FP32-flux mode also needs nx to be a
- * multiple of 32 and q_dev to be 256-byte aligned (its tiles move whole
- * 256-byte row segments); other layouts get MPRK_EINVAL.
+ * multiple of 32 and q_dev to be 256-byte aligned (every row of the
+ * unpadded state on a 256-byte boundary, the layouts its tensor copies and
+ * 16-byte accesses were tested on); other layouts get MPRK_EINVAL.
  *
  * Scratch comes from one fixed array of MPRK_STATIC_SCRATCH_BYTES that every
  * GPU loading the library holds until the process exits. A configuration

@@ -120,10 +120,11 @@ int mprk_step_static(const mprk_config* cfg, double* q_dev, int n_slow_steps, vo
     return sfail(MPRK_EINVAL, "unknown wall type");
   if (!(cfg->dt > 0.0))
     return sfail(MPRK_EINVAL, "mprk_step_static needs an explicit dt > 0");
-  // The FP32-flux tiles prefetch whole 256-byte segments of the double rows
-  // and tensor-copy the float rows, which needs every row of the caller's
-  // unpadded layout to start on a 256-byte boundary: nx a multiple of 32
-  // (a double row is then whole segments) and q_dev itself 256-byte aligned.
+  // The FP32-flux tiles tensor-copy the float rows of interior tiles and the
+  // completion moves pairs of cells with 16-byte accesses; this entry point
+  // accepts the unpadded layouts on which those paths were tested (every row
+  // of the caller's state starting on a 256-byte boundary): nx a multiple of
+  // 32 and q_dev itself 256-byte aligned.
   if (cfg->precision == MPRK_FP32FLUX && (cfg->nx % 32 != 0 || (reinterpret_cast<uintptr_t>(q_dev) & 255u) != 0))
     return sfail(MPRK_EINVAL,
                  "the FP32-flux mode of mprk_step_static needs nx a multiple of 32 and q_dev 256-byte aligned");
