@@ -76,8 +76,8 @@ CSRC = os.path.join(ROOT, "paper_2202_11890_gb300", "csrc")
 TRAFFIC = {
     "stage_kernel": {
         "files": ("stage_tile.cuh", "fp64_recip.cuh", "mprk_internal.h", "mprk_kernels.cu"),
-        "sha256": "eb96f71da41766e6a56fc6398d7a49b905e8575ace8b46cf96856cb259e008dd",
-        "bytes_per_step": 1171727872,
+        "sha256": "1cc93c59d4076bfba1a35f3537abd9cf162908f0f45fe50a6fd7e47b9f7c8894",
+        "bytes_per_step": 1170924544,
     },
     "stage_kernel_mixed": {
         "files": ("stage_tile_mixed.cuh", "mprk_internal.h", "mprk_kernels.cu"),

@@ -1,5 +1,6 @@
 // fp64_recip.cuh — the double-precision reciprocal and reciprocal square
-// root of the FP64 flux arithmetic.
+// root of the FP64 flux arithmetic, and the wave-speed maximum taken on the
+// integer pipes.
 //
 // Each takes the hardware's approximate value (rcp.approx.ftz.f64,
 // rsqrt.approx.ftz.f64: correct to about 2^-23 relative) and refines it with
@@ -53,5 +54,16 @@ __device__ __forceinline__ double sqrt_f64(double x) {
   const double e = __fma_rn(-t, y, 1.0);
   return __fma_rn(__dmul_rn(t, e), __fma_rn(0.375, e, 0.5), t);
 }
+
+// The larger of two wave speeds |u_n| + a, both >= 0. For doubles the IEEE
+// bit patterns of non-negative values order as signed integers, so the
+// comparison runs on the integer pipes and leaves the FP64 pipe (two
+// operations per clock per SM on this GPU) to the arithmetic; the result is
+// the same value.
+__device__ __forceinline__ double max_speed(double a, double b) {
+  const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double(x > y ? x : y);
+}
+__device__ __forceinline__ float max_speed(float a, float b) { return fmaxf(a, b); }
 
 }  // namespace mprk

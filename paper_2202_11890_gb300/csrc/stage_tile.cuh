@@ -106,7 +106,7 @@ __device__ __forceinline__ void lf_face(Real lr, Real lmn, Real lmt, Real lE, Re
   const Real ut = (sL * utL + sR * utR) * den;
   const Real H = (eL * rsL + eR * rsR) * den;
   const Real c = sqr(gm1 * (H - half * (un * un + ut * ut)));
-  const Real lam = fmax(fmax(fabs(unL) + cL, fabs(unR) + cR), fabs(un) + c);
+  const Real lam = max_speed(max_speed(fabs(unL) + cL, fabs(unR) + cR), fabs(un) + c);
   out[0] = hs * fma(lam, lr - rr, lmn + rmn) - sub[0];
   out[1] = fma(hs, fma(lam, lmn - rmn, (lmn * unL + pL) + (rmn * unR + pR)), -sub[1]);
   out[2] = fma(hs, fma(lam, lmt - rmt, lmt * unL + rmt * unR), -sub[2]);

@@ -82,7 +82,7 @@ __device__ __forceinline__ void lf_face5(const double l[5], const double r[5], d
   const double H = (eL * rsL + eR * rsR) * den;
   const double X = gm1 * (H - 0.5 * (un * un + t1 * t1 + t2 * t2));
   const double c = X * rsqrt_f64(X);
-  const double lam = fmax(fmax(fabs(unL) + cL, fabs(unR) + cR), fabs(un) + c);
+  const double lam = max_speed(max_speed(fabs(unL) + cL, fabs(unR) + cR), fabs(un) + c);
   const double hl = hs * lam;
   out[0] = hs * (l[1] + r[1]) + hl * (l[0] - r[0]);
   out[1] = hs * ((l[1] * unL + pL) + (r[1] * unR + pR)) + hl * (l[1] - r[1]);
