@@ -176,3 +176,42 @@ def test_tuned_launch_leaves_states_and_results_unchanged(precision, tmp_path):
         for i in a + b:
             i.close()
         M.mprk_tune_clear()
+
+
+@pytest.mark.parametrize("groups", [1, 2, 4])
+def test_per_stage_form_groups_match_each_instance_alone(groups, tmp_path):
+    """The per-stage form of FP32-flux batches with 1, 2 or 4 instance
+    groups (each group's launches on a stream of its own, forked from and
+    joined into the batch's stream), forced through a tuning entry: uneven
+    instances with m from 1 to 8 (so groups end their stages at different
+    launches, and some launches cover one instance) end within float
+    rounding of each instance stepped alone, and report no status."""
+    from paper_2202_11890_gb300 import mprk as M
+    cases = uneven(9, 40 + groups, 1)
+    steps = 3
+    alone = []
+    for cfg, P, q in cases:
+        with M.Instance(cfg, q) as inst:
+            inst.step(steps)
+            alone.append(inst.state())
+    mean = np.mean([c.nx * (c.nz_S + c.nz_B + c.nz_F) for c, P, q in cases])
+    bucket = int(np.floor(np.log2(mean)))
+    path = tmp_path / "t.json"
+    path.write_text('{"gpu": "%s", "entries": [{"precision": 1, "bucket": %d, "group": 0, '
+                    '"ctas_per_sm": %d, "ms": 1}]}' % (torch.cuda.get_device_name(0), bucket, groups))
+    M.mprk_tune_clear()
+    M.mprk_tune_load(str(path))
+    look = M.mprk_tune_lookup(1, mean)
+    assert look["tiles_per_item"] == 0 and look["ctas_per_sm"] == groups
+    insts = [M.Instance(cfg, q) for cfg, P, q in cases]
+    try:
+        M.mprk_step_batch([i.h for i in insts], steps)
+        for i, ref in zip(insts, alone):
+            err = rel_err(i.state(), ref)
+            assert np.all(err < 1e-6), err
+            assert i.status() == 0
+            assert i.diagnostics()[14] == steps
+    finally:
+        for i in insts:
+            i.close()
+        M.mprk_tune_clear()
