@@ -284,7 +284,8 @@ def _handles(hs):
 
 
 def mprk_step_batch(handles, n: int) -> None:
-    """One persistent launch per slow step over all the instances."""
+    """One graph launch per slow step over all the instances: the persistent
+    kernel, or for FP32 flux the per-stage launches (the tuned form)."""
     _check(lib().mprk_step_batch(_handles(handles), len(handles), int(n)))
 
 
